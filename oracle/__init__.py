@@ -1,0 +1,134 @@
+"""CPU oracle for RICI generation and CRSS search.
+
+TEST INFRASTRUCTURE ONLY: the tests, the smoke check and the benchmark's CPU-baseline leg
+may import this package; the product path (``paper_2007_02306_gb300``) never does.  It
+shares no code with the GPU library.
+
+The arithmetic lives in ``rici_oracle.c`` (FP64 brute force, int64 distances), compiled
+with contraction disabled; this module only builds it with gcc and marshals numpy arrays.
+``oracle.exact`` is an independent exact-rational restatement for tiny inputs.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "rici_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle_rici.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle (gcc, FP contraction off, OpenMP when available)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= os.path.getmtime(_SRC):
+        return _LIB_PATH
+    base = ["gcc", "-O2", "-ffp-contract=off", "-fno-fast-math", "-std=c11", "-shared", "-fPIC"]
+    tmp = _LIB_PATH + f".tmp{os.getpid()}"
+    try:
+        subprocess.run(base + ["-fopenmp", _SRC, "-o", tmp, "-lm"], check=True,
+                       capture_output=True)
+    except subprocess.CalledProcessError:
+        subprocess.run(base + [_SRC, "-o", tmp, "-lm"], check=True, capture_output=True)
+    os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            P = ctypes.c_void_p
+            i64, i32, f32 = ctypes.c_int64, ctypes.c_int32, ctypes.c_float
+            lib.oracle_rici_fp64.argtypes = [P, P, i64, P, i64, P, i64, f32, i32, P, i32, P]
+            lib.oracle_rici_fp64.restype = ctypes.c_int
+            lib.oracle_crss.argtypes = [P, P, i32]
+            lib.oracle_crss.restype = i64
+            lib.oracle_crss_search.argtypes = [P, i64, P, i64, i32, P, P, P, P, P, i32]
+            lib.oracle_crss_search.restype = ctypes.c_int
+            lib.oracle_max_threads.restype = ctypes.c_int
+            lib.oracle_project_fp64.argtypes = [P, i64, P, P, P]
+            lib.oracle_project_fp64.restype = None
+            _lib = lib
+    return _lib
+
+
+def _ptr(a):
+    return None if a is None else a.ctypes.data_as(ctypes.c_void_p)
+
+
+def max_threads() -> int:
+    return int(_load().oracle_max_threads())
+
+
+def rici_fp64(vertices, normals, triangles, origins, support_radius: float, resolution: int,
+              num_threads: int = 0, return_counters: bool = False):
+    """RICI images (uint16 [O, N, N]) by FP64 brute force over every triangle."""
+    lib = _load()
+    v = np.ascontiguousarray(vertices, dtype=np.float32).reshape(-1, 3)
+    n = np.ascontiguousarray(normals, dtype=np.float32).reshape(-1, 3)
+    t = np.ascontiguousarray(triangles, dtype=np.int32).reshape(-1, 3)
+    o = np.ascontiguousarray(origins, dtype=np.int32).reshape(-1)
+    if n.shape != v.shape:
+        raise ValueError("normals must match vertices")
+    N = int(resolution)
+    out = np.zeros((o.size, N, N), dtype=np.uint16)
+    cnt = np.zeros(2, dtype=np.int64)
+    rc = lib.oracle_rici_fp64(_ptr(v), _ptr(n), v.shape[0], _ptr(t), t.shape[0], _ptr(o), o.size,
+                              float(support_radius), N, _ptr(out), int(num_threads), _ptr(cnt))
+    if rc != 0:
+        raise ValueError(f"oracle_rici_fp64 failed with status {rc}")
+    if return_counters:
+        return out, {"pairs_crossing": int(cnt[0]), "layer_crossings": int(cnt[1])}
+    return out
+
+
+def project_fp64(points, spin_vertex, spin_normal):
+    """(Tx, Ty, Tz) float64 [n, 3] of FP32 points in the frame of one FP32 oriented point."""
+    lib = _load()
+    p = np.ascontiguousarray(points, dtype=np.float32).reshape(-1, 3)
+    s = np.ascontiguousarray(spin_vertex, dtype=np.float32).reshape(3)
+    n = np.ascontiguousarray(spin_normal, dtype=np.float32).reshape(3)
+    out = np.zeros((p.shape[0], 3), np.float64)
+    lib.oracle_project_fp64(_ptr(p), p.shape[0], _ptr(s), _ptr(n), _ptr(out))
+    return out
+
+
+def crss(needle, haystack) -> int:
+    """Clutter-resistant distance of one needle image against one haystack image."""
+    a = np.ascontiguousarray(needle, dtype=np.uint16)
+    b = np.ascontiguousarray(haystack, dtype=np.uint16)
+    if a.shape != b.shape or a.ndim != 2 or a.shape[0] != a.shape[1]:
+        raise ValueError("expected two N x N images")
+    return int(_load().oracle_crss(_ptr(a), _ptr(b), a.shape[0]))
+
+
+def crss_search(needles, haystack, true_match=None, return_distances: bool = False,
+                num_threads: int = 0):
+    """Per needle: rank of its true match, true distance, top-1 index (and optionally all distances)."""
+    lib = _load()
+    q = np.ascontiguousarray(needles, dtype=np.uint16)
+    h = np.ascontiguousarray(haystack, dtype=np.uint16)
+    N = int(q.shape[-1])
+    Q, H = int(q.shape[0]), int(h.shape[0])
+    m = None if true_match is None else np.ascontiguousarray(true_match, dtype=np.int64).reshape(-1)
+    rank = np.zeros(Q, np.int32)
+    dt = np.zeros(Q, np.int64)
+    top1 = np.zeros(Q, np.int32)
+    dist = np.zeros((Q, H), np.int64) if return_distances else None
+    rc = lib.oracle_crss_search(_ptr(q), Q, _ptr(h), H, N, _ptr(m), _ptr(rank), _ptr(dt),
+                                _ptr(top1), _ptr(dist), int(num_threads))
+    if rc != 0:
+        raise ValueError(f"oracle_crss_search failed with status {rc}")
+    out = {"rank": rank, "true_distance": dt, "top1": top1}
+    if dist is not None:
+        out["distances"] = dist
+    return out

@@ -1,0 +1,299 @@
+/*
+ * Plain CPU oracle for the Radial Intersection Count Image (RICI) method.
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the slow, obviously correct reference that the
+ * GPU library is checked against.  Only the tests, the smoke check and the benchmark's CPU
+ * baseline may load it; the product path never does.  It shares no code, header, table or
+ * constant with the GPU library.
+ *
+ * Build: gcc -O2 -ffp-contract=off -fopenmp -shared -fPIC.  Contraction must stay off so
+ * every product and sum below is rounded separately, exactly as written.
+ *
+ * What it computes (van Blokland & Theoharis, "Radial intersection count image: a clutter
+ * resistant 3D shape descriptor", 2020):
+ *
+ *  - oracle_rici_fp64: one N x N count image per oriented point, by brute force over every
+ *    triangle of the mesh (Section 3.1: "iterate over each triangle in the scene"), in FP64:
+ *      frame coefficients      Eq. rotationCoefficients (second pair read on the rotated x,
+ *                              see the readings below), identity rule of Section 3.1.1
+ *      projection              Eqs. relativeLocation, firstRotation, secondRotation,
+ *                              calculateAlphaBeta
+ *      slicing + counting      Section 3.1.2, steps 1-6 (intersection segment E0E1 of the
+ *                              triangle with the plane of a circle layer; single crossings for
+ *                              radii between |E0| and |E1|; double crossings between |C| and
+ *                              min(|E0|,|E1|) when the closest point C lies inside the segment)
+ *  - oracle_crss: the clutter-resistant distance of Listing 1 / Eq. distanceFunctionExpression,
+ *    in int64.
+ *  - oracle_crss_search: per needle, the distance to its true match, the rank of that match
+ *    (number of haystack images strictly closer, the tie rule of Section 4.2) and the top-1
+ *    haystack index (smallest index among the minimal distances).
+ *
+ * Readings where the paper is silent or garbled (each listed with its reason in the design
+ * notes):
+ *  (1) circle radii and layer heights sit at bin centres:
+ *        alpha_c = R*(2c+1)/(2N),  beta_r = R*(2r+1-N)/(2N),  r,c in [0,N)
+ *      (the support plane is R wide and R high with the spin vertex at mid-height, Sec. 2.1);
+ *  (2) row r of the image is layer beta_r (ascending), column c is radius alpha_c;
+ *  (3) the second normalisation acts on the rotated x component:
+ *        [Nbx, Nbz] = Normalize[Nax*Snx + Nay*Sny, Snz]
+ *      (Eq. secondRotation uses P''_x; the printed Normalize[Snx, Snz] only aligns the normal
+ *      when Sny = 0);
+ *  (4) identity rotations are (Nax,Nay) = (1,0) and (Nbx,Nbz) = (0,1);
+ *  (5) a vertex is on the upper side of layer r when Tz >= beta_r; a triangle whose three
+ *      vertices are on one side does not cross the layer (this also drops triangles lying
+ *      inside the layer plane, the unhandled "infinite" case of Section 3.1.2);
+ *  (6) intervals are half-open: single crossings for alpha^2 in (min e, max e], double
+ *      crossings for alpha^2 in (|C|^2, min e], with e = |E|^2;
+ *  (7) each crossed edge is evaluated from its lower-indexed vertex u to its higher-indexed
+ *      vertex v (global indices), and E0 is the crossed edge with the smaller (u,v) key, so
+ *      an edge shared by two triangles yields the same point in both;
+ *  (8) counts saturate at 65535 (uint16 images);
+ *  (9) Listing 1's loops run r in [0,N) and c in [1,N).
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define ORACLE_OK 0
+#define ORACLE_BAD_ARGUMENT 1
+#define ORACLE_BAD_INDEX 2
+#define ORACLE_NO_MEMORY 3
+
+/* Eq. rotationCoefficients with readings (3) and (4). */
+static void frame_coefficients(double nx, double ny, double nz,
+                               double *Nax, double *Nay, double *Nbx, double *Nbz) {
+    double h = sqrt(nx * nx + ny * ny);
+    if (h == 0.0) {
+        *Nax = 1.0;
+        *Nay = 0.0;
+    } else {
+        *Nax = nx / h;
+        *Nay = ny / h;
+    }
+    double n2x = (*Nax) * nx + (*Nay) * ny;
+    double g = sqrt(n2x * n2x + nz * nz);
+    if (g == 0.0) {
+        *Nbx = 0.0;
+        *Nbz = 1.0;
+    } else {
+        *Nbx = n2x / g;
+        *Nbz = nz / g;
+    }
+}
+
+/* Eqs. relativeLocation, firstRotation, secondRotation: T = (Tx, Ty, Tz), beta = Tz. */
+static void project_point(const float *P, const double S[3], double Nax, double Nay, double Nbx,
+                          double Nbz, double T[3]) {
+    double px = (double)P[0] - S[0];
+    double py = (double)P[1] - S[1];
+    double pz = (double)P[2] - S[2];
+    double qx = Nax * px + Nay * py;     /* P''_x */
+    double qy = (-Nay) * px + Nax * py;  /* P''_y */
+    T[0] = Nbz * qx - Nbx * pz;          /* T_x */
+    T[1] = qy;                           /* T_y */
+    T[2] = Nbx * qx + Nbz * pz;          /* T_z */
+}
+
+/* Section 3.1.2 step 1 for one crossed edge, evaluated from lower to higher vertex index. */
+static void slice_edge(const double Tu[3], const double Tv[3], double beta, double E[2]) {
+    double lambda = (beta - Tu[2]) / (Tv[2] - Tu[2]);
+    E[0] = Tu[0] + lambda * (Tv[0] - Tu[0]);
+    E[1] = Tu[1] + lambda * (Tv[1] - Tu[1]);
+}
+
+static int key_less(int32_t a0, int32_t a1, int32_t b0, int32_t b1) {
+    return a0 < b0 || (a0 == b0 && a1 < b1);
+}
+
+/* Counts of one triangle in one layer, added to the row (steps 2-6 of Section 3.1.2). */
+static void count_layer(const double T[3][3], const int32_t gid[3], double beta,
+                        const double *alpha2, int32_t N, int64_t *row, int64_t *crossings) {
+    int s0 = T[0][2] >= beta, s1 = T[1][2] >= beta, s2 = T[2][2] >= beta;
+    if (s0 == s1 && s1 == s2) return;
+    int lone = (s0 != s1 && s0 != s2) ? 0 : ((s1 != s0 && s1 != s2) ? 1 : 2);
+    int oa = (lone + 1) % 3, ob = (lone + 2) % 3;
+    /* the two crossed edges, each ordered by global vertex index */
+    int ua = gid[lone] < gid[oa] ? lone : oa, va = gid[lone] < gid[oa] ? oa : lone;
+    int ub = gid[lone] < gid[ob] ? lone : ob, vb = gid[lone] < gid[ob] ? ob : lone;
+    double Ea[2], Eb[2];
+    slice_edge(T[ua], T[va], beta, Ea);
+    slice_edge(T[ub], T[vb], beta, Eb);
+    const double *E0 = Ea, *E1 = Eb;
+    if (key_less(gid[ub], gid[vb], gid[ua], gid[va])) {
+        E0 = Eb;
+        E1 = Ea;
+    }
+    (*crossings)++;
+    double e0 = E0[0] * E0[0] + E0[1] * E0[1];
+    double e1 = E1[0] * E1[0] + E1[1] * E1[1];
+    double Dx = E1[0] - E0[0], Dy = E1[1] - E0[1];
+    double d0 = E0[0] * Dx + E0[1] * Dy; /* sign: is C beyond E0 along D? */
+    double d1 = E1[0] * Dx + E1[1] * Dy; /* sign: is C before E1 along D? */
+    double cr = E0[0] * Dy - E0[1] * Dx; /* |C| * |D| (signed) */
+    double dd = Dx * Dx + Dy * Dy;       /* |D|^2 */
+    for (int32_t c = 0; c < N; c++) {
+        int in0 = e0 >= alpha2[c];
+        int in1 = e1 >= alpha2[c];
+        if (in0 != in1) {
+            row[c] += 1;
+        } else if (in0 && in1 && d0 < 0.0 && d1 > 0.0 && alpha2[c] * dd > cr * cr) {
+            row[c] += 2;
+        }
+    }
+}
+
+int oracle_rici_fp64(const float *vertices, const float *normals, int64_t num_vertices,
+                     const int32_t *triangles, int64_t num_triangles, const int32_t *origins,
+                     int64_t num_origins, float support_radius, int32_t resolution,
+                     uint16_t *out_images, int32_t num_threads, int64_t *counters) {
+    const int32_t N = resolution;
+    if (N < 1 || N > 1024 || !(support_radius > 0.0f) || num_vertices < 0 || num_triangles < 0 ||
+        num_origins < 0)
+        return ORACLE_BAD_ARGUMENT;
+    for (int64_t t = 0; t < 3 * num_triangles; t++)
+        if (triangles[t] < 0 || triangles[t] >= num_vertices) return ORACLE_BAD_INDEX;
+    for (int64_t o = 0; o < num_origins; o++)
+        if (origins[o] < 0 || origins[o] >= num_vertices) return ORACLE_BAD_INDEX;
+
+    const double R = (double)support_radius;
+    double *alpha2 = (double *)malloc(sizeof(double) * (size_t)N);
+    double *beta = (double *)malloc(sizeof(double) * (size_t)N);
+    if (!alpha2 || !beta) {
+        free(alpha2);
+        free(beta);
+        return ORACLE_NO_MEMORY;
+    }
+    for (int32_t i = 0; i < N; i++) {
+        double a = (R * (double)(2 * i + 1)) / (double)(2 * N);
+        alpha2[i] = a * a;
+        beta[i] = (R * (double)(2 * i + 1 - N)) / (double)(2 * N);
+    }
+    int64_t total_crossings = 0, total_pairs = 0;
+    int status = ORACLE_OK;
+#ifdef _OPENMP
+    if (num_threads > 0) omp_set_num_threads(num_threads);
+#pragma omp parallel reduction(+ : total_crossings, total_pairs)
+#endif
+    {
+        int64_t *img = (int64_t *)malloc(sizeof(int64_t) * (size_t)N * (size_t)N);
+        if (!img) {
+#ifdef _OPENMP
+#pragma omp atomic write
+#endif
+            status = ORACLE_NO_MEMORY;
+        } else {
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 1)
+#endif
+            for (int64_t o = 0; o < num_origins; o++) {
+                memset(img, 0, sizeof(int64_t) * (size_t)N * (size_t)N);
+                const int32_t sv = origins[o];
+                const double S[3] = {vertices[3 * sv], vertices[3 * sv + 1], vertices[3 * sv + 2]};
+                double Nax, Nay, Nbx, Nbz;
+                frame_coefficients(normals[3 * sv], normals[3 * sv + 1], normals[3 * sv + 2], &Nax,
+                                   &Nay, &Nbx, &Nbz);
+                for (int64_t t = 0; t < num_triangles; t++) {
+                    double T[3][3];
+                    int32_t gid[3];
+                    for (int k = 0; k < 3; k++) {
+                        gid[k] = triangles[3 * t + k];
+                        project_point(vertices + 3 * (int64_t)gid[k], S, Nax, Nay, Nbx, Nbz, T[k]);
+                    }
+                    int64_t before = total_crossings;
+                    for (int32_t r = 0; r < N; r++)
+                        count_layer(T, gid, beta[r], alpha2, N, img + (int64_t)r * N,
+                                    &total_crossings);
+                    if (total_crossings != before) total_pairs++;
+                }
+                uint16_t *out = out_images + o * (int64_t)N * N;
+                for (int64_t b = 0; b < (int64_t)N * N; b++)
+                    out[b] = (uint16_t)(img[b] > 65535 ? 65535 : img[b]);
+            }
+            free(img);
+        }
+    }
+    free(alpha2);
+    free(beta);
+    if (counters) {
+        counters[0] = total_pairs;     /* (origin, triangle) pairs crossing at least one layer */
+        counters[1] = total_crossings; /* (origin, triangle, layer) crossings */
+    }
+    return status;
+}
+
+/* Listing 1 / Eq. distanceFunctionExpression. */
+int64_t oracle_crss(const uint16_t *needle, const uint16_t *haystack, int32_t N) {
+    int64_t score = 0;
+    for (int32_t r = 0; r < N; r++) {
+        for (int32_t c = 1; c < N; c++) {
+            int64_t nd = (int64_t)needle[r * N + c] - (int64_t)needle[r * N + c - 1];
+            int64_t hd = (int64_t)haystack[r * N + c] - (int64_t)haystack[r * N + c - 1];
+            if (nd != 0) score += (nd - hd) * (nd - hd);
+        }
+    }
+    return score;
+}
+
+/*
+ * For every needle i: d_true[i] = CRD(needle_i, haystack[match_i]);
+ * rank[i] = #{j : CRD(needle_i, haystack_j) < d_true[i]}  (Section 4.1 step 6c, ties -> best);
+ * top1[i] = smallest j with the minimal distance.  distances (optional) = full Q x H matrix.
+ */
+int oracle_crss_search(const uint16_t *needles, int64_t num_needles, const uint16_t *haystack,
+                       int64_t num_haystack, int32_t resolution, const int64_t *true_match,
+                       int32_t *out_rank, int64_t *out_true_distance, int32_t *out_top1,
+                       int64_t *out_distances, int32_t num_threads) {
+    const int32_t N = resolution;
+    if (N < 1 || num_needles < 0 || num_haystack < 0) return ORACLE_BAD_ARGUMENT;
+    if (num_needles > 0 && num_haystack == 0) return ORACLE_BAD_ARGUMENT;
+    for (int64_t i = 0; i < num_needles; i++) {
+        int64_t m = true_match ? true_match[i] : i;
+        if (m < 0 || m >= num_haystack) return ORACLE_BAD_INDEX;
+    }
+    const int64_t img = (int64_t)N * N;
+#ifdef _OPENMP
+    if (num_threads > 0) omp_set_num_threads(num_threads);
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+    for (int64_t i = 0; i < num_needles; i++) {
+        const uint16_t *n = needles + i * img;
+        int64_t m = true_match ? true_match[i] : i;
+        int64_t dt = oracle_crss(n, haystack + m * img, N);
+        int64_t rank = 0, best = INT64_MAX, best_j = -1;
+        for (int64_t j = 0; j < num_haystack; j++) {
+            int64_t d = oracle_crss(n, haystack + j * img, N);
+            if (out_distances) out_distances[i * num_haystack + j] = d;
+            if (d < dt) rank++;
+            if (d < best) {
+                best = d;
+                best_j = j;
+            }
+        }
+        if (out_rank) out_rank[i] = (int32_t)rank;
+        if (out_true_distance) out_true_distance[i] = dt;
+        if (out_top1) out_top1[i] = (int32_t)best_j;
+    }
+    return ORACLE_OK;
+}
+
+int oracle_max_threads(void) {
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/* Projection of n points into the (alpha, beta) frame of one oriented point (Section 3.1.1):
+ * out[3k..3k+2] = (Tx, Ty, Tz); alpha^2 = Tx^2 + Ty^2, beta = Tz. */
+void oracle_project_fp64(const float *points, int64_t n, const float *spin_vertex,
+                         const float *spin_normal, double *out) {
+    const double S[3] = {spin_vertex[0], spin_vertex[1], spin_vertex[2]};
+    double Nax, Nay, Nbx, Nbz;
+    frame_coefficients(spin_normal[0], spin_normal[1], spin_normal[2], &Nax, &Nay, &Nbx, &Nbz);
+    for (int64_t k = 0; k < n; k++) project_point(points + 3 * k, S, Nax, Nay, Nbx, Nbz, out + 3 * k);
+}
