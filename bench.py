@@ -1,0 +1,424 @@
+#!/usr/bin/env python
+"""Benchmark of the RICI hot path on one clutter scene (one JSON line on stdout).
+
+Workload: a displaced-icosphere target (20,480 triangles) plus 9 clutter meshes of
+5k-50k triangles in a box of side 2 (229,756 triangles, 114,892 vertices, seed 2).
+One step is the whole hot path over that scene:
+  1. RICI 64x64 images (R = 0.3) of the target's 10,242 vertices with the target alone
+     (the needles),
+  2. RICI images of all 114,892 scene vertices (the haystack),
+  3. CUDA-core clutter-resistant search of every needle against every haystack image
+     (1.18e9 comparisons): rank of its true match, true distance, top-1.
+value = (needle + haystack images) / step time, whole job.  Inputs are resident in HBM and
+L2 is flushed (512 MB write) before every timed step.  e2e repeats the step through the
+same public API starting from pinned host buffers, with the host<->device copies timed.
+
+--impl reference times the CPU oracle (FP64 brute force / int64 Listing 1) on bounded
+samples of the same workload and extrapolates to the full step.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "RICI images/s; CRSS comparisons/s (int8-TC vs CUDA-core), ranks exact vs oracle"
+N_RES = 64
+R_SUP = 0.3
+SEED = 2
+WORKLOAD = ("clutter scene: displaced icosphere target (subdivision 5, 20,480 triangles) + 9 "
+            "clutter meshes (5k-50k triangles, displaced icospheres/tori), box side 2; RICI 64x64 "
+            "uint16 at R=0.3 for the 10,242 target vertices (target alone) and all 114,892 scene "
+            "vertices; CUDA-core CRSS search of every needle against every haystack image, ranks")
+
+# FP32-pipe operations of the definition per unit of generation work:
+F_PROJ = 15   # per projected vertex of an (origin, triangle) pair that crosses a layer
+F_LAYER = 40  # per (origin, triangle, layer) crossing: slicing + segment quantities + boundaries
+# packed-integer operations per masked squared difference on this ALU (3 dp4a + 1 AND +
+# 1 combine per 4 positions)
+OPS_PER_TERM = 1.25
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--search-mode", type=int, default=1)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-origins", type=int, default=96)
+    ap.add_argument("--cpu-needle-origins", type=int, default=48)
+    ap.add_argument("--cpu-needles", type=int, default=12)
+    ap.add_argument("--cpu-haystack", type=int, default=24000)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return json.load(f), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for name, v in zip(names, parts[5:9]):
+                    if v.lower() == "active":
+                        reasons.add(name)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def build_workload():
+    import synth
+
+    return synth.clutter_scene(seed=SEED)
+
+
+def cpu_baseline(scene, args, steps: int = 1):
+    """Oracle on bounded samples of the step; returns per-step extrapolated seconds and info."""
+    import oracle
+    import synth
+
+    oracle.build()
+    rng = np.random.default_rng(123)
+    V, Vt = scene.num_vertices, scene.target_vertices
+    tgt = scene.target_only()
+    og = rng.choice(V, args.cpu_origins, replace=False)
+    on = rng.choice(Vt, args.cpu_needle_origins, replace=False)
+    ims_rng = np.random.default_rng(7)
+    nd = synth.images.rici_like_images(ims_rng, args.cpu_needles, N_RES)
+    hay = synth.images.rici_like_images(ims_rng, args.cpu_haystack, N_RES)
+    threads = oracle.max_threads()
+    est = []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        oracle.rici_fp64(scene.vertices, scene.normals, scene.triangles, og, R_SUP, N_RES)
+        t1 = time.perf_counter()
+        oracle.rici_fp64(tgt.vertices, tgt.normals, tgt.triangles, on, R_SUP, N_RES)
+        t2 = time.perf_counter()
+        oracle.crss_search(nd, hay, np.zeros(len(nd), np.int64))
+        t3 = time.perf_counter()
+        per_o = (t1 - t0) / len(og)
+        per_n = (t2 - t1) / len(on)
+        per_pair = (t3 - t2) / (len(nd) * len(hay))
+        est.append(per_o * V + per_n * Vt + per_pair * Vt * V)
+    sample = (f"{len(og)} scene-vertex images + {len(on)} target-alone images (FP64 brute force "
+              f"over all triangles) and {len(nd)} needles x {len(hay)} haystack images (int64 "
+              f"Listing 1) per step, extrapolated to {Vt + V} images and {Vt * V} comparisons")
+    return est, threads, sample
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    scene = build_workload()
+    cpu_baseline(scene, args, steps=max(0, args.warmup))
+    est, threads, sample = cpu_baseline(scene, args, steps=args.steps)
+    images = scene.num_vertices + scene.target_vertices
+    sec = statistics.mean(est)
+    value = images / sec
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "images/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64+i64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "resolution": N_RES, "support_radius": R_SUP,
+                   "seed": SEED},
+        "cpu_baseline": {"value": value, "unit": "images/s", "cores": threads, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "images/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import torch
+
+    rank, world, local = dist_env()
+    if world > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    import paper_2007_02306_gb300 as p
+    from paper_2007_02306_gb300 import build as libbuild
+
+    if rank == 0:
+        libbuild.build()
+    if world > 1:
+        torch.distributed.barrier()
+    p.load_library()
+
+    scene = build_workload()
+    V, T, Vt, Tt = scene.num_vertices, scene.num_triangles, scene.target_vertices, scene.target_triangles
+    h_vert = torch.from_numpy(scene.vertices).pin_memory()
+    h_norm = torch.from_numpy(scene.normals).pin_memory()
+    h_tri = torch.from_numpy(scene.triangles).pin_memory()
+    h_oh = torch.arange(V, dtype=torch.int32).pin_memory()
+    h_on = torch.arange(Vt, dtype=torch.int32).pin_memory()
+    h_match = torch.arange(Vt, dtype=torch.int64).pin_memory()
+
+    vert, norm, tri = h_vert.to(dev), h_norm.to(dev), h_tri.to(dev)
+    tri_t = tri[:Tt]
+    oh, on, match = h_oh.to(dev), h_on.to(dev), h_match.to(dev)
+    needles = torch.empty((Vt, N_RES, N_RES), dtype=torch.uint16, device=dev)
+    hay = torch.empty((V, N_RES, N_RES), dtype=torch.uint16, device=dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        p.rici_generate(vert, norm, tri_t, on, R_SUP, N_RES, out=needles)
+        p.rici_generate(vert, norm, tri, oh, R_SUP, N_RES, out=hay)
+        return p.crss_search(needles, hay, match, mode=args.search_mode)
+
+    for _ in range(args.warmup):
+        step()
+    st = p.sync_status()
+    if st != 0:
+        raise RuntimeError(f"device status {st} during warm-up")
+
+    # untimed: work counters for the roofline
+    gcnt = torch.zeros(4, dtype=torch.int64, device=dev)
+    scnt = torch.zeros(4, dtype=torch.int64, device=dev)
+    p.rici_generate(vert, norm, tri, oh, R_SUP, N_RES, out=hay, counters=gcnt)
+    p.crss_search(needles, hay, match, mode=args.search_mode, counters=scnt)
+    torch.cuda.synchronize()
+    gcnt, scnt = gcnt.cpu().tolist(), scnt.cpu().tolist()
+
+    clocks = ClockSampler(dev.index if world == 1 else local)
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
+    launches0 = p.binding.kernel_launches()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    for k in range(args.steps):
+        flush.zero_()
+        e = ev[k]
+        e[0].record(stream)
+        p.rici_generate(vert, norm, tri_t, on, R_SUP, N_RES, out=needles)
+        e[1].record(stream)
+        p.rici_generate(vert, norm, tri, oh, R_SUP, N_RES, out=hay)
+        e[2].record(stream)
+        res = p.crss_search(needles, hay, match, mode=args.search_mode)
+        e[3].record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    launches = p.binding.kernel_launches() - launches0
+    if world > 1:
+        torch.distributed.barrier()
+    st = p.sync_status()
+    if st != 0:
+        raise RuntimeError(f"device status {st} in the timed region")
+    t_nd = [ev[k][0].elapsed_time(ev[k][1]) for k in range(args.steps)]
+    t_hy = [ev[k][1].elapsed_time(ev[k][2]) for k in range(args.steps)]
+    t_se = [ev[k][2].elapsed_time(ev[k][3]) for k in range(args.steps)]
+    ms = [a + b + c for a, b, c in zip(t_nd, t_hy, t_se)]
+    ms_step = statistics.mean(ms)
+    if world > 1:
+        t = torch.tensor([ms_step], device=dev)
+        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+        ms_step = float(t.item())
+    images = V + Vt
+    pairs = V * Vt
+    value = world * images / (ms_step / 1e3)
+
+    # e2e: same step from pinned host buffers, host<->device copies inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        h_rank = torch.empty(Vt, dtype=torch.int32).pin_memory()
+        h_top1 = torch.empty(Vt, dtype=torch.int32).pin_memory()
+        h_dt = torch.empty(Vt, dtype=torch.int64).pin_memory()
+        e2e_ms = []
+        for k in range(args.steps + 1):
+            flush.zero_()
+            a0 = torch.cuda.Event(enable_timing=True)
+            a1 = torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            dv = h_vert.to(dev, non_blocking=True)
+            dn = h_norm.to(dev, non_blocking=True)
+            dtri = h_tri.to(dev, non_blocking=True)
+            doh = h_oh.to(dev, non_blocking=True)
+            don = h_on.to(dev, non_blocking=True)
+            dm = h_match.to(dev, non_blocking=True)
+            p.rici_generate(dv, dn, dtri[:Tt], don, R_SUP, N_RES, out=needles)
+            p.rici_generate(dv, dn, dtri, doh, R_SUP, N_RES, out=hay)
+            r = p.crss_search(needles, hay, dm, mode=args.search_mode)
+            h_rank.copy_(r["rank"], non_blocking=True)
+            h_top1.copy_(r["top1"], non_blocking=True)
+            h_dt.copy_(r["true_distance"], non_blocking=True)
+            a1.record(stream)
+            torch.cuda.synchronize()
+            if k > 0:  # first pass warms the copy path
+                e2e_ms.append(a0.elapsed_time(a1))
+        e_ms = statistics.mean(e2e_ms)
+        if world > 1:
+            t = torch.tensor([e_ms], device=dev)
+            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
+            e_ms = float(t.item())
+        h2d = sum(x.numel() * x.element_size() for x in (h_vert, h_norm, h_tri, h_oh, h_on, h_match))
+        d2h = Vt * (4 + 4 + 8)
+        e2e = {"value": world * images / (e_ms / 1e3), "unit": "images/s",
+               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e_ms}
+
+    pk, pk_kind = peaks()
+    clk_mhz = (clk or {}).get("sm_mhz") or pk.get("sm_max_mhz", 2070.0)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    alu_peak_gops = sms * 128 * clk_mhz * 1e6 / 1e9  # 32-bit lane operations per second
+
+    gen_ms = statistics.mean(t_hy)
+    se_ms = statistics.mean(t_se)
+    cpu = None
+    cpu_ops = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        est, threads, sample = cpu_baseline(scene, args)
+        cpu = {"value": images / est[0], "unit": "images/s", "cores": threads, "kind": "oracle",
+               "sample": sample}
+        import oracle
+
+        rng = np.random.default_rng(5)
+        og = rng.choice(V, 32, replace=False)
+        _, cc = oracle.rici_fp64(scene.vertices, scene.normals, scene.triangles, og, R_SUP, N_RES,
+                                 return_counters=True)
+        cpu_ops = cc
+    # roofline of the dominant kernel (the larger of haystack generation and search)
+    rooflines = {}
+    search_terms = scnt[0] * (N_RES - 1)
+    rooflines["search"] = {
+        "bound": "alu", "unit": "Gop/s",
+        "achieved": OPS_PER_TERM * search_terms / (se_ms / 1e3) / 1e9,
+        "peak": alu_peak_gops,
+        "work": f"{scnt[0]} (pair, row) evaluations x {N_RES - 1} masked squared differences x "
+                f"{OPS_PER_TERM} packed int ops",
+        "traffic": None,
+    }
+    if cpu_ops is not None:
+        per_o = (F_PROJ * 3 * cpu_ops["pairs_crossing"] + F_LAYER * cpu_ops["layer_crossings"]) / 32
+        rooflines["generation"] = {
+            "bound": "alu", "unit": "Gop/s",
+            "achieved": per_o * V / (gen_ms / 1e3) / 1e9, "peak": alu_peak_gops,
+            "work": f"{F_PROJ} ops x 3 vertices per crossing (origin, triangle) pair + {F_LAYER} "
+                    "ops per (origin, triangle, layer) crossing, counted by the oracle on 32 "
+                    "sampled origins and scaled to all haystack origins",
+            "traffic": None,
+        }
+    for r in rooflines.values():
+        r["frac"] = r["achieved"] / r["peak"]
+        r["peak_kind"] = f"derived: {sms} SMs x 128 lanes x {clk_mhz:.0f} MHz (median SM clock)"
+    dom = "search" if se_ms >= gen_ms or "generation" not in rooflines else "generation"
+    roof = dict(rooflines[dom])
+    roof["kernel"] = "k_dense (CUDA-core CRSS)" if dom == "search" else "k_generate"
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "images/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+i32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "resolution": N_RES, "support_radius": R_SUP,
+                   "triangles": T, "needles": Vt, "haystack": V, "comparisons": pairs, "seed": SEED,
+                   "search_mode": args.search_mode,
+                   "l2": "flushed by a 512 MB device write before every timed step",
+                   "parallelism": f"replicas x{world}"},
+        "breakdown": {
+            "needle_generation_ms": statistics.mean(t_nd),
+            "haystack_generation_ms": gen_ms,
+            "search_ms": se_ms,
+            "generation_images_per_s": images / ((statistics.mean(t_nd) + gen_ms) / 1e3),
+            "search_comparisons_per_s": pairs / (se_ms / 1e3),
+            "generation_counters": {"triangles_processed": gcnt[0], "layer_items": gcnt[1],
+                                    "fp64_band_items": gcnt[2], "cull_candidates": gcnt[3]},
+            "search_counters": {"pair_rows": scnt[0], "wide_pairs": scnt[1],
+                                "wide_terms": scnt[2]},
+        },
+        "roofline": roof,
+        "rooflines": rooflines,
+        "peaks": {"kind": pk_kind, "hbm_gbs": pk.get("hbm_gbs")},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "clocks": clk,
+        "gpu_launches": launches,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,157 @@
+/*
+ * rici.h — C ABI of the GB300 (sm_103a) RICI library.
+ *
+ * Radial Intersection Count Images (van Blokland & Theoharis, "Radial intersection count
+ * image: a clutter resistant 3D shape descriptor", 2020): generation of uint16 count images
+ * from a triangle mesh (Section 3.1) and search with the clutter-resistant distance
+ * (Section 3.2, Listing 1, Eq. distanceFunctionExpression), ranking the true match as in the
+ * clutterbox experiment (Section 4.1, tie rule of Section 4.2).
+ *
+ * Conventions for every call:
+ *  - Array arguments are DEVICE pointers owned by the caller (for example torch CUDA tensor
+ *    storage).  The library never frees or retains them after the call's work completes.
+ *  - `stream` is a cudaStream_t passed as void*; NULL means the legacy default stream.  All
+ *    work is enqueued asynchronously on that stream; outputs are valid once it completes.
+ *  - `workspace` is optional device scratch memory of at least the size returned by the
+ *    matching *_workspace_size query, 256-byte aligned.  When it is NULL the library uses a
+ *    per-device workspace of its own that grows on demand (cudaMalloc) and is released by
+ *    rici_release_workspace().  A caller-provided workspace must not be used by another call
+ *    that may run concurrently.
+ *  - Return value: RICI_OK, or an error code for problems detectable on the host (invalid
+ *    argument, CUDA launch error).  Errors found while the kernels run (an out-of-range
+ *    triangle or match index, a non-finite coordinate) are OR-ed into a per-device status
+ *    word that rici_sync_status() reads and clears.
+ *  - Zero origins / triangles / needles are valid no-ops (images of a mesh without
+ *    triangles are all zero).
+ */
+#ifndef RICI_H_
+#define RICI_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define RICI_API __attribute__((visibility("default")))
+#else
+#define RICI_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Return and status codes (status bits may be OR-ed together). */
+#define RICI_OK 0
+#define RICI_ERR_INVALID_ARGUMENT 1   /* null pointer, negative count, bad resolution/radius */
+#define RICI_ERR_INDEX_OUT_OF_RANGE 2 /* triangle, origin or true-match index out of range */
+#define RICI_ERR_NONFINITE_INPUT 4    /* NaN or infinite vertex / normal coordinate */
+#define RICI_ERR_OUT_TOO_LARGE 8      /* requested output exceeds the library's size cap */
+#define RICI_ERR_CUDA 16              /* a CUDA runtime call failed */
+#define RICI_ERR_WORKSPACE 32         /* caller workspace too small or misaligned */
+#define RICI_ERR_TIMEOUT 64           /* a bounded device-side wait gave up */
+
+/* Largest supported image resolution N (images are N x N). */
+#define RICI_MAX_RESOLUTION 128
+
+/* Generation modes (rici_generate_ex). */
+#define RICI_GEN_DEFAULT 0   /* FP32 arithmetic; predicates inside the error band redone in FP64 */
+#define RICI_GEN_FP64 1      /* every (triangle, layer) evaluated in FP64 (slow reference mode) */
+
+/* Search modes (crss_search). */
+#define RICI_SEARCH_DEFAULT 0   /* fastest exact form available */
+#define RICI_SEARCH_CUDA_CORE 1 /* Listing 1 per pair on CUDA cores, early exit */
+#define RICI_SEARCH_EXACT_SLOW 2 /* generic int64 per-pair kernel for every pair (test reference) */
+
+/*
+ * rici_generate — one RICI image per oriented point (Section 3.1).
+ *
+ *   vertices   [num_vertices][3] float32 positions.
+ *   normals    [num_vertices][3] float32 normals; any positive length (the frame coefficients
+ *              of Eq. rotationCoefficients normalise), zero selects the identity rotations.
+ *   triangles  [num_triangles][3] int32 vertex indices.
+ *   origins    [num_origins] int32 vertex indices: oriented point k is
+ *              (vertices[origins[k]], normals[origins[k]]).
+ *   support_radius  R > 0 and finite: circles have radii alpha_c = R(2c+1)/(2N) and sit in
+ *              layers beta_r = R(2r+1-N)/(2N) along the normal, c, r in [0, N).
+ *   resolution N in [1, RICI_MAX_RESOLUTION].
+ *   out_images [num_origins][N][N] uint16, row r = layer beta_r, column c = radius alpha_c;
+ *              bin (r, c) counts how many times circle (r, c) crosses the mesh surface,
+ *              saturated at 65535.  Bit-identical to the FP64 brute-force definition.
+ *
+ * Errors: RICI_ERR_INVALID_ARGUMENT on the host; RICI_ERR_INDEX_OUT_OF_RANGE and
+ * RICI_ERR_NONFINITE_INPUT in the status word (outputs are then unspecified).
+ */
+RICI_API int64_t rici_generate_workspace_size(int64_t num_vertices, int64_t num_triangles,
+                                     int64_t num_origins, int32_t resolution);
+RICI_API int rici_generate(const float *vertices, const float *normals, int64_t num_vertices,
+                  const int32_t *triangles, int64_t num_triangles, const int32_t *origins,
+                  int64_t num_origins, float support_radius, int32_t resolution,
+                  uint16_t *out_images, void *workspace, int64_t workspace_bytes, void *stream);
+/* As rici_generate with a mode (RICI_GEN_*) and optional device counters:
+ * counters (NULL or device int64[4]) receives, added to its contents:
+ *   [0] (origin, triangle) pairs fully processed after culling,
+ *   [1] (origin, triangle, layer) items processed,
+ *   [2] items re-evaluated in FP64 because a predicate fell inside the FP32 error band,
+ *   [3] candidate (origin, triangle) pairs tested by the spatial cull. */
+RICI_API int rici_generate_ex(const float *vertices, const float *normals, int64_t num_vertices,
+                     const int32_t *triangles, int64_t num_triangles, const int32_t *origins,
+                     int64_t num_origins, float support_radius, int32_t resolution,
+                     uint16_t *out_images, int32_t mode, int64_t *counters, void *workspace,
+                     int64_t workspace_bytes, void *stream);
+
+/*
+ * crss_search — clutter-resistant search (Listing 1, Eq. distanceFunctionExpression).
+ *
+ *   d(i, j) = sum over r in [0,N), c in [1,N) with a != 0 of (a - b)^2, where
+ *   a = needle_i[r][c] - needle_i[r][c-1] and b = haystack_j[r][c] - haystack_j[r][c-1].
+ *
+ *   needles    [num_needles][N][N] uint16;  haystack [num_haystack][N][N] uint16.
+ *   true_match [num_needles] int64 haystack index of needle i's true match, or NULL for i.
+ *   out_rank   [num_needles] int32: #{j : d(i,j) < d(i, match_i)} (ties keep the best rank).
+ *   out_true_distance [num_needles] int64 d(i, match_i), or NULL.
+ *   out_top1   [num_needles] int32 smallest j with minimal d(i, j), or NULL.
+ *   out_distances [num_needles][num_haystack] int64 full distance matrix, or NULL; rejected
+ *              with RICI_ERR_OUT_TOO_LARGE when num_needles*num_haystack > 2^28.
+ *   mode       RICI_SEARCH_*.
+ * All outputs are exact (integer arithmetic).  num_haystack must be > 0 when
+ * num_needles > 0.  An out-of-range true_match entry sets RICI_ERR_INDEX_OUT_OF_RANGE.
+ */
+RICI_API int64_t crss_search_workspace_size(int64_t num_needles, int64_t num_haystack,
+                                   int32_t resolution, int32_t mode);
+RICI_API int crss_search(const uint16_t *needles, int64_t num_needles, const uint16_t *haystack,
+                int64_t num_haystack, int32_t resolution, const int64_t *true_match,
+                int32_t *out_rank, int64_t *out_true_distance, int32_t *out_top1,
+                int64_t *out_distances, int32_t mode, void *workspace, int64_t workspace_bytes,
+                void *stream);
+
+/* As crss_search with optional device counters (NULL or int64[4]), added to:
+ *   [0] (pair, row) evaluations by the packed CUDA-core kernel (each row = N-1 positions;
+ *       rows after a pair's early exit are not evaluated),
+ *   [1] pairs evaluated by the int64 kernel (pairs with a delta outside int8),
+ *   [2] needle non-zero positions evaluated by the int64 kernel. */
+RICI_API int crss_search_ex(const uint16_t *needles, int64_t num_needles,
+                            const uint16_t *haystack, int64_t num_haystack, int32_t resolution,
+                            const int64_t *true_match, int32_t *out_rank,
+                            int64_t *out_true_distance, int32_t *out_top1,
+                            int64_t *out_distances, int32_t mode, int64_t *counters,
+                            void *workspace, int64_t workspace_bytes, void *stream);
+
+/* Synchronise `stream`, then read and clear the per-device status word (RICI_ERR_* bits). */
+RICI_API int rici_sync_status(void *stream, int32_t *device_status);
+
+/* Release the library-owned workspace of the current device. */
+RICI_API int rici_release_workspace(void);
+
+/* Text for the last host-side error on the calling thread ("" if none). */
+RICI_API const char *rici_last_error_string(void);
+
+/* Number of CUDA kernels this library has enqueued in the calling process so far. */
+RICI_API int64_t rici_kernel_launches(void);
+
+/* Library version string. */
+RICI_API const char *rici_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RICI_H_ */

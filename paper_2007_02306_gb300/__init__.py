@@ -1,0 +1,10 @@
+"""GB300-native (sm_103a) Radial Intersection Count Image generation and clutter-resistant search.
+
+The computation lives in the CUDA library ``_build/librici.so`` (sources in ``csrc/``, C ABI
+in ``include/rici.h``); ``binding`` marshals torch CUDA tensors into it.  Build the library
+with ``paper_2007_02306_gb300.build.build()``.
+"""
+from .binding import (  # noqa: F401
+    GEN_DEFAULT, GEN_FP64, SEARCH_CUDA_CORE, SEARCH_DEFAULT, SEARCH_EXACT_SLOW, RiciError,
+    crss_search, load_library, rici_generate, sync_status, version,
+)

@@ -1,0 +1,214 @@
+"""ctypes binding of librici (argument marshalling only).
+
+Every step of generation and search runs in the CUDA library; this module checks tensor
+dtypes/devices, allocates outputs and a cached workspace with PyTorch, and passes raw device
+pointers plus the current CUDA stream through the C ABI declared in include/rici.h.  There
+is no CPU fallback: if the library is missing or cannot be loaded the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+from . import build as _build
+
+GEN_DEFAULT = 0
+GEN_FP64 = 1
+SEARCH_DEFAULT = 0
+SEARCH_CUDA_CORE = 1
+SEARCH_EXACT_SLOW = 2
+
+ERR_INVALID_ARGUMENT = 1
+ERR_INDEX_OUT_OF_RANGE = 2
+ERR_NONFINITE_INPUT = 4
+ERR_OUT_TOO_LARGE = 8
+ERR_CUDA = 16
+ERR_WORKSPACE = 32
+ERR_TIMEOUT = 64
+
+MAX_RESOLUTION = 128
+
+_lock = threading.Lock()
+_lib = None
+_workspaces: dict = {}
+
+
+class RiciError(RuntimeError):
+    def __init__(self, code: int, message: str):
+        super().__init__(f"librici error {code}: {message}")
+        self.code = code
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load_library(path: str | None = None):
+    """Load librici.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        p = path or library_path()
+        if not os.path.exists(p):
+            raise RuntimeError(f"librici.so not found at {p}; build it with "
+                               "paper_2007_02306_gb300.build.build() (nvcc, sm_103a)")
+        lib = ctypes.CDLL(p)
+        P, i64, i32, f32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_float
+        lib.rici_generate_workspace_size.argtypes = [i64, i64, i64, i32]
+        lib.rici_generate_workspace_size.restype = i64
+        lib.rici_generate.argtypes = [P, P, i64, P, i64, P, i64, f32, i32, P, P, i64, P]
+        lib.rici_generate.restype = ctypes.c_int
+        lib.rici_generate_ex.argtypes = [P, P, i64, P, i64, P, i64, f32, i32, P, i32, P, P, i64, P]
+        lib.rici_generate_ex.restype = ctypes.c_int
+        lib.crss_search_workspace_size.argtypes = [i64, i64, i32, i32]
+        lib.crss_search_workspace_size.restype = i64
+        lib.crss_search.argtypes = [P, i64, P, i64, i32, P, P, P, P, P, i32, P, i64, P]
+        lib.crss_search.restype = ctypes.c_int
+        lib.crss_search_ex.argtypes = [P, i64, P, i64, i32, P, P, P, P, P, i32, P, P, i64, P]
+        lib.crss_search_ex.restype = ctypes.c_int
+        lib.rici_sync_status.argtypes = [P, ctypes.POINTER(i32)]
+        lib.rici_sync_status.restype = ctypes.c_int
+        lib.rici_release_workspace.argtypes = []
+        lib.rici_release_workspace.restype = ctypes.c_int
+        lib.rici_last_error_string.argtypes = []
+        lib.rici_last_error_string.restype = ctypes.c_char_p
+        lib.rici_kernel_launches.argtypes = []
+        lib.rici_kernel_launches.restype = i64
+        lib.rici_version.argtypes = []
+        lib.rici_version.restype = ctypes.c_char_p
+        _lib = lib
+        return lib
+
+
+def _check(rc: int):
+    if rc != 0:
+        msg = load_library().rici_last_error_string().decode(errors="replace")
+        raise RiciError(rc, msg)
+
+
+def _ptr(t):
+    return None if t is None else ctypes.c_void_p(t.data_ptr())
+
+
+def _stream_handle(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _need(t, dtype, name, shape_tail=None):
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor")
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must have dtype {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if shape_tail is not None and tuple(t.shape[1:]) != tuple(shape_tail):
+        raise ValueError(f"{name} must have shape [*, {', '.join(map(str, shape_tail))}]")
+    return t
+
+
+def workspace(device, nbytes: int) -> torch.Tensor:
+    """Cached per-device scratch buffer (uint8, 256-byte aligned), grown on demand."""
+    dev = torch.device(device)
+    key = dev.index if dev.index is not None else torch.cuda.current_device()
+    buf = _workspaces.get(key)
+    if buf is None or buf.numel() < nbytes:
+        _workspaces.pop(key, None)
+        buf = torch.empty(max(int(nbytes), 256) + 256, dtype=torch.uint8, device=dev)
+        _workspaces[key] = buf
+    off = (-buf.data_ptr()) % 256
+    return buf[off:]
+
+
+def rici_generate(vertices, normals, triangles, origins, support_radius: float, resolution: int,
+                  *, out=None, mode: int = GEN_DEFAULT, counters=None, stream=None):
+    """uint16 [O, N, N] RICI images of the oriented points (vertices[origins], normals[origins])."""
+    lib = load_library()
+    v = _need(vertices, torch.float32, "vertices", (3,))
+    n = _need(normals, torch.float32, "normals", (3,))
+    t = _need(triangles, torch.int32, "triangles", (3,))
+    o = _need(origins, torch.int32, "origins")
+    if n.shape != v.shape:
+        raise ValueError("normals must have the same shape as vertices")
+    N = int(resolution)
+    if out is None:
+        out = torch.empty((o.numel(), N, N), dtype=torch.uint16, device=v.device)
+    else:
+        _need(out, torch.uint16, "out", (N, N))
+        if out.shape[0] != o.numel():
+            raise ValueError("out must have one image per origin")
+    if counters is not None:
+        _need(counters, torch.int64, "counters")
+        if counters.numel() < 4:
+            raise ValueError("counters needs 4 int64 entries")
+    nb = lib.rici_generate_workspace_size(v.shape[0], t.shape[0], o.numel(), N)
+    if nb < 0:
+        raise ValueError("invalid sizes")
+    ws = workspace(v.device, nb)
+    with torch.cuda.device(v.device):
+        _check(lib.rici_generate_ex(_ptr(v), _ptr(n), v.shape[0], _ptr(t), t.shape[0], _ptr(o),
+                                    o.numel(), float(support_radius), N, _ptr(out), int(mode),
+                                    _ptr(counters), _ptr(ws), ws.numel(), _stream_handle(stream)))
+    return out
+
+
+def crss_search(needles, haystack, true_match=None, *, mode: int = SEARCH_DEFAULT,
+                return_distances: bool = False, counters=None, stream=None):
+    """Rank of each needle's true match, its true distance and the top-1 haystack index."""
+    lib = load_library()
+    q = _need(needles, torch.uint16, "needles")
+    h = _need(haystack, torch.uint16, "haystack")
+    if q.dim() != 3 or h.dim() != 3 or q.shape[1] != q.shape[2] or tuple(h.shape[1:]) != tuple(q.shape[1:]):
+        raise ValueError("needles and haystack must be [*, N, N] with the same N")
+    N = int(q.shape[-1])
+    Q, H = int(q.shape[0]), int(h.shape[0])
+    dev = q.device
+    m = None
+    if true_match is not None:
+        m = _need(true_match, torch.int64, "true_match")
+        if m.numel() != Q:
+            raise ValueError("true_match needs one entry per needle")
+    rank = torch.empty(Q, dtype=torch.int32, device=dev)
+    dt = torch.empty(Q, dtype=torch.int64, device=dev)
+    top1 = torch.empty(Q, dtype=torch.int32, device=dev)
+    dist = torch.empty((Q, H), dtype=torch.int64, device=dev) if return_distances else None
+    if counters is not None:
+        _need(counters, torch.int64, "counters")
+        if counters.numel() < 4:
+            raise ValueError("counters needs 4 int64 entries")
+    nb = lib.crss_search_workspace_size(Q, H, N, int(mode))
+    if nb < 0:
+        raise ValueError("invalid sizes")
+    ws = workspace(dev, nb)
+    with torch.cuda.device(dev):
+        _check(lib.crss_search_ex(_ptr(q), Q, _ptr(h), H, N, _ptr(m), _ptr(rank), _ptr(dt),
+                                  _ptr(top1), _ptr(dist), int(mode), _ptr(counters), _ptr(ws),
+                                  ws.numel(), _stream_handle(stream)))
+    out = {"rank": rank, "true_distance": dt, "top1": top1}
+    if dist is not None:
+        out["distances"] = dist
+    return out
+
+
+def sync_status(stream=None) -> int:
+    """Synchronise the stream and return (and clear) the device status word."""
+    lib = load_library()
+    v = ctypes.c_int32(0)
+    _check(lib.rici_sync_status(_stream_handle(stream), ctypes.byref(v)))
+    return int(v.value)
+
+
+def kernel_launches() -> int:
+    """Kernels the library has enqueued in this process so far."""
+    return int(load_library().rici_kernel_launches())
+
+
+def version() -> str:
+    return load_library().rici_version().decode()

@@ -1,0 +1,281 @@
+// extern "C" entry points of librici: argument validation, workspace management and the
+// per-device status word.  The compute stages live in generate.cu and search.cu.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdint.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <atomic>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+
+namespace rici {
+namespace {
+
+__device__ int g_status;  // OR of RICI_ERR_* bits raised by kernels on this device
+
+thread_local std::string t_last_error;
+std::atomic<int64_t> g_launches{0};
+
+int fail(int code, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  t_last_error = buf;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char *where) {
+  return fail(RICI_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+struct DeviceState {
+  void *ws = nullptr;
+  int64_t ws_bytes = 0;
+  int *status = nullptr;
+};
+
+std::mutex g_mu;
+std::vector<DeviceState> g_dev;
+
+// Per-device state (status word address, library workspace); call with the device current.
+int device_state(DeviceState **out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  std::lock_guard<std::mutex> lk(g_mu);
+  if ((int)g_dev.size() <= dev) g_dev.resize(dev + 1);
+  DeviceState &d = g_dev[dev];
+  if (!d.status) {
+    e = cudaGetSymbolAddress((void **)&d.status, g_status);
+    if (e != cudaSuccess) return cuda_fail(e, "cudaGetSymbolAddress(status)");
+  }
+  *out = &d;
+  return RICI_OK;
+}
+
+// Library-owned workspace of at least `bytes`, grown on demand.
+int library_workspace(DeviceState *d, int64_t bytes, void **ws) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (d->ws_bytes < bytes) {
+    if (d->ws) {
+      cudaError_t e = cudaFree(d->ws);
+      d->ws = nullptr;
+      d->ws_bytes = 0;
+      if (e != cudaSuccess) return cuda_fail(e, "cudaFree(workspace)");
+    }
+    cudaError_t e = cudaMalloc(&d->ws, (size_t)bytes);
+    if (e != cudaSuccess) {
+      d->ws = nullptr;
+      return cuda_fail(e, "cudaMalloc(workspace)");
+    }
+    d->ws_bytes = bytes;
+  }
+  *ws = d->ws;
+  return RICI_OK;
+}
+
+int resolve_workspace(DeviceState *d, void *user, int64_t user_bytes, int64_t need, void **ws) {
+  if (user) {
+    if (user_bytes < need)
+      return fail(RICI_ERR_WORKSPACE, "workspace too small: %lld < %lld bytes",
+                  (long long)user_bytes, (long long)need);
+    if (reinterpret_cast<uintptr_t>(user) & 255)
+      return fail(RICI_ERR_WORKSPACE, "workspace must be 256-byte aligned");
+    *ws = user;
+    return RICI_OK;
+  }
+  return library_workspace(d, need, ws);
+}
+
+int check_generate_args(const float *V, const float *Nrm, int64_t nv, const int32_t *T, int64_t nt,
+                        const int32_t *O, int64_t no, float R, int32_t N, const uint16_t *out) {
+  if (nv < 0 || nt < 0 || no < 0) return fail(RICI_ERR_INVALID_ARGUMENT, "negative count");
+  if (N < 1 || N > RICI_MAX_RESOLUTION)
+    return fail(RICI_ERR_INVALID_ARGUMENT, "resolution must be in [1, %d]", RICI_MAX_RESOLUTION);
+  if (!(R > 0.0f) || !isfinite(R))
+    return fail(RICI_ERR_INVALID_ARGUMENT, "support_radius must be positive and finite");
+  if (nt > 0 && (!T || !V)) return fail(RICI_ERR_INVALID_ARGUMENT, "null triangles/vertices");
+  if (no > 0 && (!O || !V || !Nrm || !out))
+    return fail(RICI_ERR_INVALID_ARGUMENT, "null origins/vertices/normals/output");
+  if (no > 0 && nv == 0) return fail(RICI_ERR_INVALID_ARGUMENT, "origins given without vertices");
+  if (nt > (int64_t(1) << 31) - 2 || nv > (int64_t(1) << 31) - 2)
+    return fail(RICI_ERR_OUT_TOO_LARGE, "more than 2^31-2 triangles or vertices");
+  return RICI_OK;
+}
+
+}  // namespace
+
+void count_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+
+}  // namespace rici
+
+using namespace rici;
+
+extern "C" {
+
+int64_t rici_generate_workspace_size(int64_t num_vertices, int64_t num_triangles,
+                                     int64_t num_origins, int32_t resolution) {
+  (void)num_vertices;
+  (void)num_origins;
+  (void)resolution;
+  if (num_triangles < 0) return -1;
+  return generate_workspace_bytes(num_triangles);
+}
+
+int rici_generate_ex(const float *vertices, const float *normals, int64_t num_vertices,
+                     const int32_t *triangles, int64_t num_triangles, const int32_t *origins,
+                     int64_t num_origins, float support_radius, int32_t resolution,
+                     uint16_t *out_images, int32_t mode, int64_t *counters, void *workspace,
+                     int64_t workspace_bytes, void *stream) {
+  t_last_error.clear();
+  int rc = check_generate_args(vertices, normals, num_vertices, triangles, num_triangles, origins,
+                               num_origins, support_radius, resolution, out_images);
+  if (rc) return rc;
+  if (mode != RICI_GEN_DEFAULT && mode != RICI_GEN_FP64)
+    return fail(RICI_ERR_INVALID_ARGUMENT, "unknown generation mode %d", mode);
+  if (num_origins == 0) return RICI_OK;
+  DeviceState *d;
+  if ((rc = device_state(&d))) return rc;
+  void *ws;
+  if ((rc = resolve_workspace(d, workspace, workspace_bytes,
+                              generate_workspace_bytes(num_triangles), &ws)))
+    return rc;
+  GenerateArgs a;
+  a.vertices = vertices;
+  a.normals = normals;
+  a.num_vertices = num_vertices;
+  a.triangles = triangles;
+  a.num_triangles = num_triangles;
+  a.origins = origins;
+  a.num_origins = num_origins;
+  a.support_radius = support_radius;
+  a.resolution = resolution;
+  a.out_images = out_images;
+  a.mode = mode;
+  a.counters = counters;
+  a.status = d->status;
+  cudaError_t e = launch_generate(a, ws, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "rici_generate launch");
+  return RICI_OK;
+}
+
+int rici_generate(const float *vertices, const float *normals, int64_t num_vertices,
+                  const int32_t *triangles, int64_t num_triangles, const int32_t *origins,
+                  int64_t num_origins, float support_radius, int32_t resolution,
+                  uint16_t *out_images, void *workspace, int64_t workspace_bytes, void *stream) {
+  return rici_generate_ex(vertices, normals, num_vertices, triangles, num_triangles, origins,
+                          num_origins, support_radius, resolution, out_images, RICI_GEN_DEFAULT,
+                          nullptr, workspace, workspace_bytes, stream);
+}
+
+int64_t crss_search_workspace_size(int64_t num_needles, int64_t num_haystack, int32_t resolution,
+                                   int32_t mode) {
+  if (num_needles < 0 || num_haystack < 0 || resolution < 1 ||
+      resolution > RICI_MAX_RESOLUTION)
+    return -1;
+  return search_workspace_bytes(num_needles, num_haystack, resolution, mode);
+}
+
+int crss_search_ex(const uint16_t *needles, int64_t num_needles, const uint16_t *haystack,
+                   int64_t num_haystack, int32_t resolution, const int64_t *true_match,
+                   int32_t *out_rank, int64_t *out_true_distance, int32_t *out_top1,
+                   int64_t *out_distances, int32_t mode, int64_t *counters, void *workspace,
+                   int64_t workspace_bytes, void *stream) {
+  t_last_error.clear();
+  if (num_needles < 0 || num_haystack < 0) return fail(RICI_ERR_INVALID_ARGUMENT, "negative count");
+  if (resolution < 2 || resolution > RICI_MAX_RESOLUTION)
+    return fail(RICI_ERR_INVALID_ARGUMENT, "resolution must be in [2, %d]", RICI_MAX_RESOLUTION);
+  if (mode != RICI_SEARCH_DEFAULT && mode != RICI_SEARCH_CUDA_CORE &&
+      mode != RICI_SEARCH_EXACT_SLOW)
+    return fail(RICI_ERR_INVALID_ARGUMENT, "unknown search mode %d", mode);
+  if (num_needles == 0) return RICI_OK;
+  if (num_haystack == 0)
+    return fail(RICI_ERR_INVALID_ARGUMENT, "needles given with an empty haystack");
+  if (!needles || !haystack || !out_rank)
+    return fail(RICI_ERR_INVALID_ARGUMENT, "null needles/haystack/out_rank");
+  if (num_haystack > (int64_t(1) << 31) - 1 || num_needles > (int64_t(1) << 31) - 1)
+    return fail(RICI_ERR_OUT_TOO_LARGE, "more than 2^31-1 needles or haystack images");
+  if (out_distances && (double)num_needles * (double)num_haystack > (double)(int64_t(1) << 28))
+    return fail(RICI_ERR_OUT_TOO_LARGE, "distance matrix larger than 2^28 entries");
+  DeviceState *d;
+  int rc;
+  if ((rc = device_state(&d))) return rc;
+  void *ws;
+  if ((rc = resolve_workspace(d, workspace, workspace_bytes,
+                              search_workspace_bytes(num_needles, num_haystack, resolution, mode),
+                              &ws)))
+    return rc;
+  SearchArgs a;
+  a.needles = needles;
+  a.num_needles = num_needles;
+  a.haystack = haystack;
+  a.num_haystack = num_haystack;
+  a.resolution = resolution;
+  a.true_match = true_match;
+  a.out_rank = out_rank;
+  a.out_true_distance = out_true_distance;
+  a.out_top1 = out_top1;
+  a.out_distances = out_distances;
+  a.mode = mode;
+  a.counters = counters;
+  a.status = d->status;
+  cudaError_t e = launch_search(a, ws, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "crss_search launch");
+  return RICI_OK;
+}
+
+int crss_search(const uint16_t *needles, int64_t num_needles, const uint16_t *haystack,
+                int64_t num_haystack, int32_t resolution, const int64_t *true_match,
+                int32_t *out_rank, int64_t *out_true_distance, int32_t *out_top1,
+                int64_t *out_distances, int32_t mode, void *workspace, int64_t workspace_bytes,
+                void *stream) {
+  return crss_search_ex(needles, num_needles, haystack, num_haystack, resolution, true_match,
+                        out_rank, out_true_distance, out_top1, out_distances, mode, nullptr,
+                        workspace, workspace_bytes, stream);
+}
+
+int rici_sync_status(void *stream, int32_t *device_status) {
+  DeviceState *d;
+  int rc;
+  if ((rc = device_state(&d))) return rc;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  cudaError_t e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamSynchronize");
+  int v = 0;
+  e = cudaMemcpy(&v, d->status, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(e, "read status");
+  e = cudaMemset(d->status, 0, sizeof(int));
+  if (e != cudaSuccess) return cuda_fail(e, "clear status");
+  if (device_status) *device_status = v;
+  return RICI_OK;
+}
+
+int rici_release_workspace(void) {
+  DeviceState *d;
+  int rc;
+  if ((rc = device_state(&d))) return rc;
+  std::lock_guard<std::mutex> lk(g_mu);
+  if (d->ws) {
+    cudaError_t e = cudaFree(d->ws);
+    d->ws = nullptr;
+    d->ws_bytes = 0;
+    if (e != cudaSuccess) return cuda_fail(e, "cudaFree(workspace)");
+  }
+  return RICI_OK;
+}
+
+const char *rici_last_error_string(void) { return t_last_error.c_str(); }
+
+int64_t rici_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+const char *rici_version(void) { return "rici-gb300 0.1 (sm_103a)"; }
+
+}  // extern "C"

@@ -1,0 +1,850 @@
+// RICI generation on sm_103a (Section 3.1 of the paper).
+//
+// Pipeline per rici_generate call (all on the caller's stream, no host synchronisation):
+//   1. k_tri_bin      bounding sphere of every triangle; bin it into a hashed uniform grid
+//                     (cell = 1.25 x the support sphere) or into a "big" list.
+//   2. scan           bucket counts -> bucket starts.
+//   3. k_tri_scatter  64-byte triangle records (sphere, FP32 vertices, global indices) in
+//                     bucket order, so candidates of one cell are contiguous.
+//   4. k_generate     one CTA per oriented point.  Its warps stream the triangles of the 27
+//                     neighbouring cells (plus the big list), cull them against the support
+//                     cylinder, project the survivors (Eqs. relativeLocation..secondRotation)
+//                     and split the (triangle, layer) work evenly over the 32 lanes.  Each
+//                     layer's single/double crossing radii (Section 3.1.2) become column
+//                     intervals added to a shared-memory difference image, which is prefix
+//                     summed, saturated and stored as uint16.
+//
+// Exactness: the FP32 path carries a forward error bound for every predicate (vertex side
+// of a layer, |E|^2 against alpha^2, the signs of E0.D and E1.D, alpha^2 |D|^2 against
+// (E0 x D)^2).  A (triangle, layer) whose predicate lies inside its bound is recomputed in
+// FP64 with the definition's operation order (explicit _rn intrinsics, no contraction), so
+// every count equals the FP64 definition bit for bit.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace rici {
+namespace {
+
+constexpr float kU = 5.9604644775390625e-08f;  // 2^-24: unit roundoff of FP32
+constexpr float kSafety = 2.0f;                // multiplies every derived error bound
+constexpr uint32_t kBig = 0xFFFFFFFFu;
+constexpr uint32_t kSkip = 0xFFFFFFFEu;
+constexpr float kCellClamp = 1048576.0f;  // |cell coordinate| limit (2^20)
+constexpr int kWarps = 4;
+constexpr int kSlot = 25;  // words per staged triangle (odd stride: conflict-free lookups)
+constexpr int kScanItems = 2048;
+
+__host__ __device__ inline uint32_t bucket_count(int64_t nt) {
+  uint32_t b = 1024;
+  while (b < (uint64_t)nt && b < (1u << 22)) b <<= 1;
+  return b;
+}
+
+__device__ __forceinline__ int cell_coord(float x, float inv_cell) {
+  float f = floorf(x * inv_cell);
+  f = fminf(fmaxf(f, -kCellClamp), kCellClamp);
+  return (int)f;
+}
+
+__device__ __forceinline__ uint32_t cell_hash(int ix, int iy, int iz, uint32_t mask) {
+  return (((uint32_t)ix * 73856093u) ^ ((uint32_t)iy * 19349663u) ^ ((uint32_t)iz * 83492791u)) &
+         mask;
+}
+
+struct TriSphere {
+  float cx, cy, cz, r;
+};
+
+// Bounding sphere of the triangle's AABB, inflated to cover rounding of centre and radius.
+__device__ __forceinline__ TriSphere tri_sphere(const float v[9]) {
+  float lx = fminf(fminf(v[0], v[3]), v[6]), hx = fmaxf(fmaxf(v[0], v[3]), v[6]);
+  float ly = fminf(fminf(v[1], v[4]), v[7]), hy = fmaxf(fmaxf(v[1], v[4]), v[7]);
+  float lz = fminf(fminf(v[2], v[5]), v[8]), hz = fmaxf(fmaxf(v[2], v[5]), v[8]);
+  TriSphere s;
+  s.cx = 0.5f * (lx + hx);
+  s.cy = 0.5f * (ly + hy);
+  s.cz = 0.5f * (lz + hz);
+  float ex = 0.5f * (hx - lx), ey = 0.5f * (hy - ly), ez = 0.5f * (hz - lz);
+  float cm = fmaxf(fabsf(s.cx), fmaxf(fabsf(s.cy), fabsf(s.cz)));
+  s.r = sqrtf(ex * ex + ey * ey + ez * ez) * (1.0f + 1e-5f) + 1e-6f * cm + 1e-30f;
+  return s;
+}
+
+struct GridParams {
+  float inv_cell;
+  float r_big;
+  uint32_t mask;
+};
+
+__global__ void k_tri_bin(const float *__restrict__ V, const int32_t *__restrict__ tri, int64_t nv,
+                          int64_t nt, GridParams g, int *__restrict__ counts,
+                          uint32_t *__restrict__ tb, int *__restrict__ ts, int *__restrict__ nbig,
+                          int *status) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nt;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    int id[3] = {tri[3 * t], tri[3 * t + 1], tri[3 * t + 2]};
+    if (id[0] < 0 || id[0] >= nv || id[1] < 0 || id[1] >= nv || id[2] < 0 || id[2] >= nv) {
+      set_status(status, RICI_ERR_INDEX_OUT_OF_RANGE);
+      tb[t] = kSkip;
+      continue;
+    }
+    float v[9];
+    bool fin = true;
+    for (int k = 0; k < 3; ++k)
+      for (int d = 0; d < 3; ++d) {
+        v[3 * k + d] = V[3 * (int64_t)id[k] + d];
+        fin = fin && isfinite(v[3 * k + d]);
+      }
+    if (!fin) {
+      set_status(status, RICI_ERR_NONFINITE_INPUT);
+      tb[t] = kSkip;
+      continue;
+    }
+    TriSphere s = tri_sphere(v);
+    const float lim = kCellClamp - 4.0f;
+    bool big = s.r > g.r_big || !(fabsf(s.cx * g.inv_cell) < lim) ||
+               !(fabsf(s.cy * g.inv_cell) < lim) || !(fabsf(s.cz * g.inv_cell) < lim);
+    if (big) {
+      tb[t] = kBig;
+      ts[t] = atomicAdd(nbig, 1);
+    } else {
+      uint32_t b = cell_hash(cell_coord(s.cx, g.inv_cell), cell_coord(s.cy, g.inv_cell),
+                             cell_coord(s.cz, g.inv_cell), g.mask);
+      tb[t] = b;
+      ts[t] = atomicAdd(&counts[b], 1);
+    }
+  }
+}
+
+__global__ void k_tri_scatter(const float *__restrict__ V, const int32_t *__restrict__ tri,
+                              int64_t nt, uint32_t nbuckets, const uint32_t *__restrict__ tb,
+                              const int *__restrict__ ts, const int *__restrict__ starts,
+                              float4 *__restrict__ rec) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nt;
+       t += (int64_t)gridDim.x * blockDim.x) {
+    uint32_t b = tb[t];
+    if (b == kSkip) continue;
+    int64_t pos = (b == kBig ? (int64_t)starts[nbuckets] : (int64_t)starts[b]) + ts[t];
+    int id[3] = {tri[3 * t], tri[3 * t + 1], tri[3 * t + 2]};
+    float v[9];
+    for (int k = 0; k < 3; ++k)
+      for (int d = 0; d < 3; ++d) v[3 * k + d] = V[3 * (int64_t)id[k] + d];
+    TriSphere s = tri_sphere(v);
+    rec[4 * pos + 0] = make_float4(s.cx, s.cy, s.cz, s.r);
+    rec[4 * pos + 1] = make_float4(v[0], v[1], v[2], v[3]);
+    rec[4 * pos + 2] = make_float4(v[4], v[5], v[6], v[7]);
+    rec[4 * pos + 3] = make_float4(v[8], __int_as_float(id[0]), __int_as_float(id[1]),
+                                   __int_as_float(id[2]));
+  }
+}
+
+// ------------------------------------------------------------------ exclusive scan (int32)
+
+__device__ __forceinline__ int block_exclusive_scan(int v, int *warp_sums, int *total) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  int x = v;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    int y = __shfl_up_sync(0xffffffffu, x, d);
+    if (lane >= d) x += y;
+  }
+  if (lane == 31) warp_sums[warp] = x;
+  __syncthreads();
+  if (warp == 0) {
+    int w = lane < nw ? warp_sums[lane] : 0;
+    int wi = w;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      int y = __shfl_up_sync(0xffffffffu, wi, d);
+      if (lane >= d) wi += y;
+    }
+    if (lane < nw) warp_sums[lane] = wi - w;
+    if (lane == 31) *total = wi;
+  }
+  __syncthreads();
+  int r = warp_sums[warp] + x - v;
+  __syncthreads();
+  return r;
+}
+
+__global__ void k_scan_partials(const int *__restrict__ in, int64_t n, int *__restrict__ partials) {
+  __shared__ int ws[32];
+  __shared__ int tot;
+  int64_t base = (int64_t)blockIdx.x * kScanItems;
+  int s = 0;
+  for (int i = threadIdx.x; i < kScanItems; i += blockDim.x)
+    if (base + i < n) s += in[base + i];
+  block_exclusive_scan(s, ws, &tot);
+  if (threadIdx.x == 0) partials[blockIdx.x] = tot;
+}
+
+__global__ void k_scan_top(int *partials, int nb) {
+  __shared__ int ws[32];
+  __shared__ int tot;
+  __shared__ int carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int base = 0; base < nb; base += blockDim.x) {
+    int i = base + threadIdx.x;
+    int v = i < nb ? partials[i] : 0;
+    int ex = block_exclusive_scan(v, ws, &tot);
+    if (i < nb) partials[i] = carry + ex;
+    __syncthreads();
+    if (threadIdx.x == 0) carry += tot;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) partials[nb] = carry;
+}
+
+__global__ void k_scan_final(const int *__restrict__ in, int64_t n, const int *__restrict__ partials,
+                             int *__restrict__ out) {
+  __shared__ int ws[32];
+  __shared__ int tot;
+  const int per = kScanItems / 256;  // blockDim.x == 256
+  int64_t base = (int64_t)blockIdx.x * kScanItems + threadIdx.x * per;
+  int v[per];
+  int s = 0;
+#pragma unroll
+  for (int k = 0; k < per; ++k) {
+    v[k] = (base + k < n) ? in[base + k] : 0;
+    s += v[k];
+  }
+  int run = partials[blockIdx.x] + block_exclusive_scan(s, ws, &tot);
+#pragma unroll
+  for (int k = 0; k < per; ++k) {
+    if (base + k < n) out[base + k] = run;
+    run += v[k];
+  }
+  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) out[n] = partials[gridDim.x];
+}
+
+// ------------------------------------------------------------------ generation kernel
+
+struct KArgs {
+  const float *V;
+  const float *Nrm;
+  int64_t nv;
+  const int32_t *origins;
+  const float4 *rec;
+  const int *starts;
+  const int *nbig;
+  uint32_t nbuckets;
+  float inv_cell;
+  float R;
+  int N;
+  float alpha_cull;  // pretest radius limit (alpha_{N-1} plus margin)
+  float beta_cull;   // pretest height limit (beta_{N-1} plus margin)
+  uint16_t *out;
+  int mode;
+  unsigned long long *counters;
+  int *status;
+};
+
+struct Shared {
+  int *diff;     // [N][N] difference image
+  double *a2d;   // alpha_c^2 (FP64 definition)
+  double *bd;    // beta_r (FP64 definition)
+  float *a2f;    // alpha_c^2 rounded to FP32
+  float *bf;     // beta_r rounded to FP32
+  double *fr;    // S (3 doubles), Nax, Nay, Nbx, Nbz
+  int *buckets;  // 27 neighbour buckets
+  int *wq;       // this warp's queue [64]
+  int *wst;      // this warp's item starts [32]
+  float *slots;  // this warp's staged triangles [32][kSlot]
+};
+
+// slot layout (words)
+enum {
+  SX = 0, SY = 3, SZ = 6, SGID = 9, SDE = 12, SW = 15, SRLO = 16, SBAND = 17, SFLAGS = 20,
+  SREC = 21
+};
+constexpr int kAll64 = 1;
+
+__device__ __forceinline__ int lower_count_f(float x, const float *a2f, int N, float scale) {
+  // number of columns c with a2f[c] <= x
+  float s = sqrtf(fmaxf(x, 0.0f)) * scale;
+  float fc = floorf((s + 1.0f) * 0.5f);
+  int c = (fc >= (float)N) ? N : ((fc > 0.0f) ? (int)fc : 0);
+  while (c < N && a2f[c] <= x) ++c;
+  while (c > 0 && a2f[c - 1] > x) --c;
+  return c;
+}
+
+__device__ __forceinline__ int lower_count_d(double x, const double *a2d, int N) {
+  // number of columns c with a2d[c] <= x (a2d strictly increasing)
+  int lo = 0, hi = N;
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    if (a2d[mid] <= x) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ void project64(float px, float py, float pz, const double *fr,
+                                          double T[3]) {
+  double dx = __dsub_rn((double)px, fr[0]);
+  double dy = __dsub_rn((double)py, fr[1]);
+  double dz = __dsub_rn((double)pz, fr[2]);
+  const double Nax = fr[3], Nay = fr[4], Nbx = fr[5], Nbz = fr[6];
+  double qx = __dadd_rn(__dmul_rn(Nax, dx), __dmul_rn(Nay, dy));
+  double qy = __dadd_rn(__dmul_rn(-Nay, dx), __dmul_rn(Nax, dy));
+  T[0] = __dsub_rn(__dmul_rn(Nbz, qx), __dmul_rn(Nbx, dz));
+  T[1] = qy;
+  T[2] = __dadd_rn(__dmul_rn(Nbx, qx), __dmul_rn(Nbz, dz));
+}
+
+// FP64 evaluation of one (triangle, layer) with the definition's operation order.
+// Returns false when the triangle does not cross the layer; otherwise the single-crossing
+// columns are [lo, hi) and the double-crossing columns [dlo, lo).
+__device__ bool layer_fp64(const KArgs &a, const Shared &s, const float *sl, int r, int &lo,
+                           int &hi, int &dlo) {
+  const int N = a.N;
+  const int rec = __float_as_int(sl[SREC]);
+  float4 r1 = a.rec[4 * (int64_t)rec + 1], r2 = a.rec[4 * (int64_t)rec + 2],
+         r3 = a.rec[4 * (int64_t)rec + 3];
+  double T[3][3];
+  project64(r1.x, r1.y, r1.z, s.fr, T[0]);
+  project64(r1.w, r2.x, r2.y, s.fr, T[1]);
+  project64(r2.z, r2.w, r3.x, s.fr, T[2]);
+  int gid[3] = {__float_as_int(sl[SGID]), __float_as_int(sl[SGID + 1]),
+                __float_as_int(sl[SGID + 2])};
+  const double beta = s.bd[r];
+  int s0 = T[0][2] >= beta, s1 = T[1][2] >= beta, s2 = T[2][2] >= beta;
+  if (s0 == s1 && s1 == s2) return false;
+  int lone = (s0 != s1 && s0 != s2) ? 0 : ((s1 != s0 && s1 != s2) ? 1 : 2);
+  int oa = lone == 0 ? 1 : 0;
+  int ob = lone == 2 ? 1 : 2;
+  // crossed edges evaluated from the lower to the higher global vertex index
+  int ua = gid[lone] < gid[oa] ? lone : oa, va = gid[lone] < gid[oa] ? oa : lone;
+  int ub = gid[lone] < gid[ob] ? lone : ob, vb = gid[lone] < gid[ob] ? ob : lone;
+  double la = __ddiv_rn(__dsub_rn(beta, T[ua][2]), __dsub_rn(T[va][2], T[ua][2]));
+  double lb = __ddiv_rn(__dsub_rn(beta, T[ub][2]), __dsub_rn(T[vb][2], T[ub][2]));
+  double Eax = __dadd_rn(T[ua][0], __dmul_rn(la, __dsub_rn(T[va][0], T[ua][0])));
+  double Eay = __dadd_rn(T[ua][1], __dmul_rn(la, __dsub_rn(T[va][1], T[ua][1])));
+  double Ebx = __dadd_rn(T[ub][0], __dmul_rn(lb, __dsub_rn(T[vb][0], T[ub][0])));
+  double Eby = __dadd_rn(T[ub][1], __dmul_rn(lb, __dsub_rn(T[vb][1], T[ub][1])));
+  bool swap = gid[ub] < gid[ua] || (gid[ub] == gid[ua] && gid[vb] < gid[va]);
+  double E0x = swap ? Ebx : Eax, E0y = swap ? Eby : Eay;
+  double E1x = swap ? Eax : Ebx, E1y = swap ? Eay : Eby;
+  double e0 = __dadd_rn(__dmul_rn(E0x, E0x), __dmul_rn(E0y, E0y));
+  double e1 = __dadd_rn(__dmul_rn(E1x, E1x), __dmul_rn(E1y, E1y));
+  int c0 = lower_count_d(e0, s.a2d, N), c1 = lower_count_d(e1, s.a2d, N);
+  lo = min(c0, c1);
+  hi = max(c0, c1);
+  dlo = lo;
+  if (lo > 0) {
+    double Dx = __dsub_rn(E1x, E0x), Dy = __dsub_rn(E1y, E0y);
+    double d0 = __dadd_rn(__dmul_rn(E0x, Dx), __dmul_rn(E0y, Dy));
+    double d1 = __dadd_rn(__dmul_rn(E1x, Dx), __dmul_rn(E1y, Dy));
+    if (d0 < 0.0 && d1 > 0.0) {
+      double cr = __dsub_rn(__dmul_rn(E0x, Dy), __dmul_rn(E0y, Dx));
+      double dd = __dadd_rn(__dmul_rn(Dx, Dx), __dmul_rn(Dy, Dy));
+      double cr2 = __dmul_rn(cr, cr);
+      // first column with alpha^2 * dd > cr^2 (monotone in the column)
+      int l = 0, h = lo;
+      while (l < h) {
+        int mid = (l + h) >> 1;
+        if (__dmul_rn(s.a2d[mid], dd) > cr2) h = mid; else l = mid + 1;
+      }
+      dlo = l;
+    }
+  }
+  return true;
+}
+
+// FP32 evaluation with error bounds.  Returns 0: no crossing, 1: intervals valid,
+// 2: a predicate is inside its error band (caller re-evaluates in FP64).
+__device__ __forceinline__ int layer_fp32(const KArgs &a, const Shared &s, const float *sl, int r,
+                                          float scale, int &lo, int &hi, int &dlo) {
+  const int N = a.N;
+  const float beta = s.bf[r];
+  float tz0 = sl[SZ], tz1 = sl[SZ + 1], tz2 = sl[SZ + 2];
+  int s0 = tz0 >= beta, s1 = tz1 >= beta, s2 = tz2 >= beta;
+  if (s0 == s1 && s1 == s2) return 0;
+  int lone = (s0 != s1 && s0 != s2) ? 0 : ((s1 != s0 && s1 != s2) ? 1 : 2);
+  int oa = lone == 0 ? 1 : 0;
+  int ob = lone == 2 ? 1 : 2;
+  int g_l = __float_as_int(sl[SGID + lone]), g_a = __float_as_int(sl[SGID + oa]),
+      g_b = __float_as_int(sl[SGID + ob]);
+  int ua = g_l < g_a ? lone : oa, va = g_l < g_a ? oa : lone;
+  int ub = g_l < g_b ? lone : ob, vb = g_l < g_b ? ob : lone;
+  float la = __fdiv_rn(__fsub_rn(beta, sl[SZ + ua]), __fsub_rn(sl[SZ + va], sl[SZ + ua]));
+  float lb = __fdiv_rn(__fsub_rn(beta, sl[SZ + ub]), __fsub_rn(sl[SZ + vb], sl[SZ + ub]));
+  float Eax = __fmaf_rn(la, __fsub_rn(sl[SX + va], sl[SX + ua]), sl[SX + ua]);
+  float Eay = __fmaf_rn(la, __fsub_rn(sl[SY + va], sl[SY + ua]), sl[SY + ua]);
+  float Ebx = __fmaf_rn(lb, __fsub_rn(sl[SX + vb], sl[SX + ub]), sl[SX + ub]);
+  float Eby = __fmaf_rn(lb, __fsub_rn(sl[SY + vb], sl[SY + ub]), sl[SY + ub]);
+  int gua = ua == lone ? g_l : g_a, gva = va == lone ? g_l : g_a;
+  int gub = ub == lone ? g_l : g_b, gvb = vb == lone ? g_l : g_b;
+  bool swap = gub < gua || (gub == gua && gvb < gva);
+  float E0x = swap ? Ebx : Eax, E0y = swap ? Eby : Eay;
+  float E1x = swap ? Eax : Ebx, E1y = swap ? Eay : Eby;
+  // edge opposite vertex k has index k; edge (lone, oa) is opposite ob and vice versa
+  const float dE = fmaxf(sl[SDE + ob], sl[SDE + oa]);
+  const float W = sl[SW];
+  const float W2 = W * W;
+  float e0 = __fmaf_rn(E0x, E0x, __fmul_rn(E0y, E0y));
+  float e1 = __fmaf_rn(E1x, E1x, __fmul_rn(E1y, E1y));
+  const float de = kSafety * (4.0f * W * dE + 6.0f * dE * dE + 3.01f * kU * W2);
+  const float ds = de + kU * s.a2f[N - 1] + 1e-37f;
+  int c0 = lower_count_f(e0, s.a2f, N, scale), c1 = lower_count_f(e1, s.a2f, N, scale);
+  if (!(de < 1e30f)) return 2;
+  if ((c0 > 0 && e0 - s.a2f[c0 - 1] <= ds) || (c0 < N && s.a2f[c0] - e0 <= ds) ||
+      (c1 > 0 && e1 - s.a2f[c1 - 1] <= ds) || (c1 < N && s.a2f[c1] - e1 <= ds))
+    return 2;
+  lo = min(c0, c1);
+  hi = max(c0, c1);
+  dlo = lo;
+  if (lo > 0) {
+    float Dx = __fsub_rn(E1x, E0x), Dy = __fsub_rn(E1y, E0y);
+    float d0 = __fmaf_rn(E0x, Dx, __fmul_rn(E0y, Dy));
+    float d1 = __fmaf_rn(E1x, Dx, __fmul_rn(E1y, Dy));
+    const float dD = 2.0f * dE + 2.1f * kU * W;
+    const float dd0 = kSafety * (2.0f * W * dD + 4.0f * W * dE + 2.0f * dD * dE + 6.0f * kU * W2) +
+                      1e-37f;
+    if (fabsf(d0) <= dd0 || fabsf(d1) <= dd0) return 2;
+    if (d0 < 0.0f && d1 > 0.0f) {
+      float cr = __fmaf_rn(E0x, Dy, -__fmul_rn(E0y, Dx));
+      float dd = __fmaf_rn(Dx, Dx, __fmul_rn(Dy, Dy));
+      const float ddd = kSafety * (8.0f * W * dD + 2.0f * dD * dD + 12.0f * kU * W2) + 1e-37f;
+      if (dd <= ddd) return 2;
+      float cr2 = __fmul_rn(cr, cr);
+      int cs = lower_count_f(__fdiv_rn(cr2, dd), s.a2f, N, scale);
+      while (cs > 0 && __fmul_rn(s.a2f[cs - 1], dd) > cr2) --cs;
+      while (cs < N && !(__fmul_rn(s.a2f[cs], dd) > cr2)) ++cs;
+      const float acr = fabsf(cr);
+      // certainty of alpha_c^2 * dd > cr^2 at the columns where it matters
+      int cchk[2] = {cs - 1, cs};
+      if (cs >= lo) {
+        cchk[0] = lo - 1;
+        cchk[1] = -1;
+      }
+#pragma unroll
+      for (int k = 0; k < 2; ++k) {
+        int c = cchk[k];
+        if (c < 0 || c >= lo) continue;
+        float a2 = s.a2f[c];
+        float dq = kSafety * (a2 * (ddd + 2.0f * kU * (dd + ddd)) + dd0 * (2.0f * acr + 3.0f * dd0) +
+                              2.0f * kU * cr2) + 1e-37f;
+        float p1 = __fmul_rn(a2, dd);
+        if (fabsf(p1 - cr2) <= dq) return 2;
+      }
+      dlo = min(cs, lo);
+    }
+  }
+  return 1;
+}
+
+template <int NW>
+__global__ void __launch_bounds__(NW * 32) k_generate(KArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int N = a.N;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t o = blockIdx.x;
+
+  Shared s;
+  {
+    unsigned char *p = smem;
+    s.diff = reinterpret_cast<int *>(p);
+    p += ((size_t)N * N * 4 + 15) & ~(size_t)15;
+    s.a2d = reinterpret_cast<double *>(p);
+    s.bd = s.a2d + N;
+    s.fr = s.bd + N;
+    s.a2f = reinterpret_cast<float *>(s.fr + 8);
+    s.bf = s.a2f + N;
+    s.buckets = reinterpret_cast<int *>(s.bf + N);
+    int *wbase = s.buckets + 28;
+    const int per_warp = 64 + 32 + 32 * kSlot;
+    s.wq = wbase + warp * per_warp;
+    s.wst = s.wq + 64;
+    s.slots = reinterpret_cast<float *>(s.wst + 32);
+  }
+
+  const int vid = a.origins[o];
+  if (vid < 0 || vid >= a.nv) {
+    if (tid == 0) set_status(a.status, RICI_ERR_INDEX_OUT_OF_RANGE);
+    return;
+  }
+  const float Sx = a.V[3 * (int64_t)vid], Sy = a.V[3 * (int64_t)vid + 1],
+              Sz = a.V[3 * (int64_t)vid + 2];
+  const float nxf = a.Nrm[3 * (int64_t)vid], nyf = a.Nrm[3 * (int64_t)vid + 1],
+              nzf = a.Nrm[3 * (int64_t)vid + 2];
+  if (!(isfinite(Sx) && isfinite(Sy) && isfinite(Sz) && isfinite(nxf) && isfinite(nyf) &&
+        isfinite(nzf))) {
+    if (tid == 0) set_status(a.status, RICI_ERR_NONFINITE_INPUT);
+    return;
+  }
+
+  for (int i = tid; i < N * N; i += NW * 32) s.diff[i] = 0;
+  const double Rd = (double)a.R;
+  for (int i = tid; i < N; i += NW * 32) {
+    double al = __ddiv_rn(__dmul_rn(Rd, (double)(2 * i + 1)), (double)(2 * N));
+    double a2 = __dmul_rn(al, al);
+    double b = __ddiv_rn(__dmul_rn(Rd, (double)(2 * i + 1 - N)), (double)(2 * N));
+    s.a2d[i] = a2;
+    s.bd[i] = b;
+    s.a2f[i] = __double2float_rn(a2);
+    s.bf[i] = __double2float_rn(b);
+  }
+  if (tid == 0) {
+    // Eq. rotationCoefficients (second pair on the rotated x) with the identity rule
+    double nx = nxf, ny = nyf, nz = nzf;
+    double h = __dsqrt_rn(__dadd_rn(__dmul_rn(nx, nx), __dmul_rn(ny, ny)));
+    double Nax = 1.0, Nay = 0.0;
+    if (h != 0.0) {
+      Nax = __ddiv_rn(nx, h);
+      Nay = __ddiv_rn(ny, h);
+    }
+    double n2x = __dadd_rn(__dmul_rn(Nax, nx), __dmul_rn(Nay, ny));
+    double g = __dsqrt_rn(__dadd_rn(__dmul_rn(n2x, n2x), __dmul_rn(nz, nz)));
+    double Nbx = 0.0, Nbz = 1.0;
+    if (g != 0.0) {
+      Nbx = __ddiv_rn(n2x, g);
+      Nbz = __ddiv_rn(nz, g);
+    }
+    s.fr[0] = Sx;
+    s.fr[1] = Sy;
+    s.fr[2] = Sz;
+    s.fr[3] = Nax;
+    s.fr[4] = Nay;
+    s.fr[5] = Nbx;
+    s.fr[6] = Nbz;
+  }
+  if (tid < 27) {
+    int ix = cell_coord(Sx, a.inv_cell) + tid % 3 - 1;
+    int iy = cell_coord(Sy, a.inv_cell) + (tid / 3) % 3 - 1;
+    int iz = cell_coord(Sz, a.inv_cell) + tid / 9 - 1;
+    s.buckets[tid] = (int)cell_hash(ix, iy, iz, a.nbuckets - 1);
+  }
+  __syncthreads();
+
+  const float fax = __double2float_rn(s.fr[3]), fay = __double2float_rn(s.fr[4]);
+  const float fbx = __double2float_rn(s.fr[5]), fbz = __double2float_rn(s.fr[6]);
+  const float wx = fbx * fax, wy = fbx * fay, wz = fbz;  // central axis in world coordinates
+  const float R = a.R;
+  const float scale = (float)(2 * N) / R;
+  const float spacing = R / (float)N;
+  const float acull_xy = sqrtf(s.a2f[N - 1]) * (1.0f + 1.0f / 4096.0f);
+  const bool fp64_only = a.mode == RICI_GEN_FP64;
+
+  unsigned long long n_tri = 0, n_items = 0, n_band = 0, n_cand = 0;
+  int qn = 0;  // warp-uniform queue length
+
+  auto process_batch = [&](int cnt) {
+    // ---- per-triangle setup: one survivor per lane
+    int nlay = 0;
+    float *sl = s.slots + lane * kSlot;
+    if (lane < cnt) {
+      const int rec = s.wq[lane];
+      float4 r1 = a.rec[4 * (int64_t)rec + 1], r2 = a.rec[4 * (int64_t)rec + 2],
+             r3 = a.rec[4 * (int64_t)rec + 3];
+      float P[9] = {r1.x, r1.y, r1.z, r1.w, r2.x, r2.y, r2.z, r2.w, r3.x};
+      float tx[3], ty[3], tz[3], M = 0.0f;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        // Eqs. relativeLocation, firstRotation, secondRotation in FP32 (explicit roundings)
+        float dx = __fsub_rn(P[3 * k], Sx), dy = __fsub_rn(P[3 * k + 1], Sy),
+              dz = __fsub_rn(P[3 * k + 2], Sz);
+        float qx = __fmaf_rn(fay, dy, __fmul_rn(fax, dx));
+        float qy = __fmaf_rn(fax, dy, -__fmul_rn(fay, dx));
+        tx[k] = __fmaf_rn(fbz, qx, -__fmul_rn(fbx, dz));
+        ty[k] = qy;
+        tz[k] = __fmaf_rn(fbx, qx, __fmul_rn(fbz, dz));
+        M = fmaxf(M, fabsf(dx) + fabsf(dy) + fabsf(dz));
+      }
+      // |T32 - T64| <= dT for every coordinate (first-order bound 7uM, 10uM with slack)
+      const float dT = 10.0f * kU * M + 1e-37f;
+      const float dside = kSafety * (dT + kU * R);
+      float zmin = fminf(fminf(tz[0], tz[1]), tz[2]), zmax = fmaxf(fmaxf(tz[0], tz[1]), tz[2]);
+      float xl = fminf(fminf(tx[0], tx[1]), tx[2]), xh = fmaxf(fmaxf(tx[0], tx[1]), tx[2]);
+      float yl = fminf(fminf(ty[0], ty[1]), ty[2]), yh = fmaxf(fmaxf(ty[0], ty[1]), ty[2]);
+      float gx = fmaxf(0.0f, fmaxf(xl, -xh)), gy = fmaxf(0.0f, fmaxf(yl, -yh));
+      float lim = acull_xy + 2.0f * dT;
+      bool keep = gx * gx + gy * gy <= lim * lim;
+      // layers whose side decision is not certainly identical for all three vertices
+      int r_lo = 0, r_hi = -1;
+      if (keep) {
+        float zl = zmin - dside, zh = zmax + dside;
+        float fl = ceilf((zl * scale + (float)(N - 1)) * 0.5f);
+        r_lo = fl <= 0.0f ? 0 : (fl >= (float)N ? N : (int)fl);
+        while (r_lo > 0 && s.bf[r_lo - 1] > zl) --r_lo;
+        while (r_lo < N && s.bf[r_lo] <= zl) ++r_lo;
+        float fh = floorf((zh * scale + (float)(N - 1)) * 0.5f);
+        r_hi = fh < 0.0f ? -1 : (fh >= (float)(N - 1) ? N - 1 : (int)fh);
+        while (r_hi < N - 1 && s.bf[r_hi + 1] <= zh) ++r_hi;
+        while (r_hi >= 0 && s.bf[r_hi] > zh) --r_hi;
+        nlay = max(0, r_hi - r_lo + 1);
+      }
+      if (nlay > 0) {
+        int flags = (fp64_only || dside >= 0.25f * spacing) ? kAll64 : 0;
+        float W = 0.0f;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          W = fmaxf(W, fmaxf(fabsf(tx[k]), fabsf(ty[k])));
+          sl[SX + k] = tx[k];
+          sl[SY + k] = ty[k];
+          sl[SZ + k] = tz[k];
+          // side band: the one layer a vertex could be ambiguous against
+          float fr_ = rintf((tz[k] * scale + (float)(N - 1)) * 0.5f);
+          int rk = fr_ <= 0.0f ? 0 : (fr_ >= (float)(N - 1) ? N - 1 : (int)fr_);
+          int band = -1;
+          for (int d = -1; d <= 1; ++d) {
+            int rr = rk + d;
+            if (rr >= 0 && rr < N && fabsf(tz[k] - s.bf[rr]) <= dside) band = rr;
+          }
+          sl[SBAND + k] = __int_as_float(band);
+        }
+        sl[SGID + 0] = r3.y;
+        sl[SGID + 1] = r3.z;
+        sl[SGID + 2] = r3.w;
+        // per-edge bound on |E32 - E64| (edge k is opposite vertex k)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          int i = k == 0 ? 1 : 0, j = k == 2 ? 1 : 2;
+          float den = fabsf(tz[j] - tz[i]);
+          float el = (kU * R + 3.0f * dT) / den + 4.0f * kU;
+          float de = 1.1f * (3.0f * dT + 3.0f * kU * W + 2.0f * W * el);
+          sl[SDE + k] = (den > 0.0f && de < 1e30f) ? de : __int_as_float(0x7f800000);
+        }
+        sl[SW] = W;
+        sl[SRLO] = __int_as_float(r_lo);
+        sl[SFLAGS] = __int_as_float(flags);
+        sl[SREC] = __int_as_float(rec);
+      }
+    }
+    // ---- distribute (triangle, layer) items over the lanes
+    int incl = nlay;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      int y = __shfl_up_sync(0xffffffffu, incl, d);
+      if (lane >= d) incl += y;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    s.wst[lane] = incl - nlay;
+    n_tri += nlay > 0;
+    __syncwarp();
+    for (int it = lane; it < total; it += 32) {
+      int lo_ = 0, hi_ = cnt - 1;
+      while (lo_ < hi_) {
+        int mid = (lo_ + hi_ + 1) >> 1;
+        if (s.wst[mid] <= it) lo_ = mid; else hi_ = mid - 1;
+      }
+      const float *ts = s.slots + lo_ * kSlot;
+      const int r = __float_as_int(ts[SRLO]) + (it - s.wst[lo_]);
+      const int flags = __float_as_int(ts[SFLAGS]);
+      int lo = 0, hi = 0, dlo = 0, res;
+      bool band = (flags & kAll64) || r == __float_as_int(ts[SBAND]) ||
+                  r == __float_as_int(ts[SBAND + 1]) || r == __float_as_int(ts[SBAND + 2]);
+      res = band ? 2 : layer_fp32(a, s, ts, r, scale, lo, hi, dlo);
+      if (res == 2) {
+        ++n_band;
+        res = layer_fp64(a, s, ts, r, lo, hi, dlo) ? 1 : 0;
+      }
+      ++n_items;
+      if (res == 1) {
+        int *row = s.diff + r * N;
+        if (lo < hi) {
+          atomicAdd(row + lo, 1);
+          if (hi < N) atomicAdd(row + hi, -1);
+        }
+        if (dlo < lo) {
+          atomicAdd(row + dlo, 2);
+          if (lo < N) atomicAdd(row + lo, -2);
+        }
+      }
+    }
+    __syncwarp();
+  };
+
+  // ---- stream candidates of the 27 neighbouring cells and the big list
+  const int64_t big_start = a.starts[a.nbuckets];
+  const int nbig = *a.nbig;
+  for (int nb = 0; nb < 28; ++nb) {
+    int64_t beg, end;
+    if (nb < 27) {
+      const int b = s.buckets[nb];
+      bool dup = false;
+      for (int k = 0; k < nb; ++k) dup = dup || (s.buckets[k] == b);
+      if (dup) continue;
+      beg = a.starts[b];
+      end = a.starts[b + 1];
+    } else {
+      beg = big_start;
+      end = big_start + nbig;
+    }
+    for (int64_t base = beg + warp * 32; base < end; base += NW * 32) {
+      const int64_t t = base + lane;
+      bool pass = false;
+      if (t < end) {
+        float4 c = a.rec[4 * t];
+        float dx = c.x - Sx, dy = c.y - Sy, dz = c.z - Sz;
+        float z = fmaf(wx, dx, fmaf(wy, dy, wz * dz));
+        float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        float m = 1e-3f * R + 1e-5f * (fabsf(dx) + fabsf(dy) + fabsf(dz));
+        float al = a.alpha_cull + c.w + m;
+        pass = fabsf(z) <= a.beta_cull + c.w + m && d2 - z * z <= al * al;
+        ++n_cand;
+      }
+      unsigned bal = __ballot_sync(0xffffffffu, pass);
+      if (pass) s.wq[qn + __popc(bal & ((1u << lane) - 1u))] = (int)t;
+      qn += __popc(bal);
+      __syncwarp();
+      if (qn >= 32) {
+        process_batch(32);
+        int rest = qn - 32;
+        int moved = lane < rest ? s.wq[32 + lane] : 0;
+        __syncwarp();
+        if (lane < rest) s.wq[lane] = moved;
+        qn = rest;
+        __syncwarp();
+      }
+    }
+  }
+  if (qn > 0) process_batch(qn);
+
+  if (a.counters) {
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+      n_tri += __shfl_down_sync(0xffffffffu, n_tri, d);
+      n_items += __shfl_down_sync(0xffffffffu, n_items, d);
+      n_band += __shfl_down_sync(0xffffffffu, n_band, d);
+      n_cand += __shfl_down_sync(0xffffffffu, n_cand, d);
+    }
+    if (lane == 0) {
+      atomicAdd(a.counters + 0, n_tri);
+      atomicAdd(a.counters + 1, n_items);
+      atomicAdd(a.counters + 2, n_band);
+      atomicAdd(a.counters + 3, n_cand);
+    }
+  }
+  __syncthreads();
+
+  // ---- prefix-sum each row of the difference image, saturate, store uint16
+  uint16_t *out = a.out + o * (int64_t)N * N;
+  const int cpl = (N + 31) / 32;
+  for (int r = warp; r < N; r += NW) {
+    const int *row = s.diff + r * N;
+    const int c0 = lane * cpl, c1 = min(N, c0 + cpl);
+    int sum = 0;
+    for (int c = c0; c < c1; ++c) sum += row[c];
+    int incl = sum;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      int y = __shfl_up_sync(0xffffffffu, incl, d);
+      if (lane >= d) incl += y;
+    }
+    int run = incl - sum;
+    for (int c = c0; c < c1; ++c) {
+      run += row[c];
+      out[r * N + c] = (uint16_t)min(max(run, 0), 65535);
+    }
+  }
+}
+
+size_t generate_smem_bytes(int N) {
+  size_t b = ((size_t)N * N * 4 + 15) & ~(size_t)15;
+  b += (size_t)(2 * N + 8) * sizeof(double);
+  b += (size_t)(2 * N) * sizeof(float);
+  b += 28 * sizeof(int);
+  b += (size_t)kWarps * (64 + 32 + 32 * kSlot) * 4;
+  return b;
+}
+
+}  // namespace
+
+int64_t generate_workspace_bytes(int64_t num_triangles) {
+  const uint32_t B = bucket_count(num_triangles);
+  Carver c(nullptr);
+  c.take<int>(B);                  // counts
+  c.take<int>((int64_t)B + 1);     // starts
+  c.take<int>(kScanItems + 1);     // scan partials
+  c.take<uint32_t>(num_triangles); // bucket of each triangle
+  c.take<int>(num_triangles);      // slot within its bucket
+  c.take<float4>(4 * num_triangles);
+  c.take<int>(4);                  // big-list length
+  return c.off + 256;
+}
+
+cudaError_t launch_generate(const GenerateArgs &g, void *ws, cudaStream_t st) {
+  const int64_t nt = g.num_triangles;
+  const int N = g.resolution;
+  if (g.num_origins == 0) return cudaSuccess;
+  const uint32_t B = bucket_count(nt);
+  Carver c(ws);
+  int *counts = c.take<int>(B);
+  int *starts = c.take<int>((int64_t)B + 1);
+  int *partials = c.take<int>(kScanItems + 1);
+  uint32_t *tb = c.take<uint32_t>(nt);
+  int *ts = c.take<int>(nt);
+  float4 *rec = c.take<float4>(4 * nt);
+  int *nbig = c.take<int>(4);
+
+  // support cylinder: alpha <= alpha_{N-1}, |beta| <= beta_{N-1}; enclosing sphere radius
+  const double R = g.support_radius;
+  const double amax = R * (2.0 * N - 1.0) / (2.0 * N);
+  const double bmax = R * (N - 1.0) / (2.0 * N);
+  const double rho = sqrt(amax * amax + bmax * bmax) * (1.0 + 1.0 / 1024.0) + 1e-3 * R;
+  GridParams gp;
+  gp.r_big = (float)(0.25 * rho);
+  const double cell = 1.25 * rho * 1.01;
+  gp.inv_cell = (float)(1.0 / cell);
+  gp.mask = B - 1;
+
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(counts, 0, sizeof(int) * B, st)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(nbig, 0, sizeof(int) * 4, st)) != cudaSuccess) return e;
+  const int tpb = 256;
+  const int64_t want = (nt + tpb - 1) / tpb;
+  const int grid = (int)(want < 152 * 32 ? (want > 0 ? want : 1) : 152 * 32);
+  if (nt > 0) {
+    k_tri_bin<<<grid, tpb, 0, st>>>(g.vertices, g.triangles, g.num_vertices, nt, gp, counts, tb,
+                                     ts, nbig, g.status);
+    count_launches(1);
+  }
+  const int nb = (int)((B + kScanItems - 1) / kScanItems);
+  k_scan_partials<<<nb, 256, 0, st>>>(counts, B, partials);
+  k_scan_top<<<1, 1024, 0, st>>>(partials, nb);
+  k_scan_final<<<nb, 256, 0, st>>>(counts, B, partials, starts);
+  count_launches(3);
+  if (nt > 0) {
+    k_tri_scatter<<<grid, tpb, 0, st>>>(g.vertices, g.triangles, nt, B, tb, ts, starts, rec);
+    count_launches(1);
+  }
+
+  KArgs k;
+  k.V = g.vertices;
+  k.Nrm = g.normals;
+  k.nv = g.num_vertices;
+  k.origins = g.origins;
+  k.rec = rec;
+  k.starts = starts;
+  k.nbig = nbig;
+  k.nbuckets = B;
+  k.inv_cell = gp.inv_cell;
+  k.R = g.support_radius;
+  k.N = N;
+  k.alpha_cull = (float)(amax * (1.0 + 1.0 / 1024.0) + 1e-3 * R);
+  k.beta_cull = (float)(bmax * (1.0 + 1.0 / 1024.0) + 1e-3 * R);
+  k.out = g.out_images;
+  k.mode = g.mode;
+  k.counters = reinterpret_cast<unsigned long long *>(g.counters);
+  k.status = g.status;
+  const size_t smem = generate_smem_bytes(N);
+  if ((e = cudaFuncSetAttribute(k_generate<kWarps>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem)) != cudaSuccess)
+    return e;
+  for (int64_t o0 = 0; o0 < g.num_origins; o0 += 0x7fffffff) {
+    const int64_t cnt = g.num_origins - o0 < 0x7fffffff ? g.num_origins - o0 : 0x7fffffff;
+    KArgs kk = k;
+    kk.origins = g.origins + o0;
+    kk.out = g.out_images + o0 * (int64_t)N * N;
+    k_generate<kWarps><<<(unsigned)cnt, kWarps * 32, smem, st>>>(kk);
+    count_launches(1);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace rici

@@ -1,0 +1,504 @@
+// Clutter-resistant search on sm_103a (Section 3.2: Listing 1, Eq. distanceFunctionExpression;
+// ranking of Section 4.1 with the tie rule of Section 4.2).
+//
+// d(i, j) = sum over r in [0,N), c in [1,N) with a != 0 of (a - b)^2, a and b the needle's and
+// haystack's column deltas.  rank_i = #{j : d(i,j) < d(i,match_i)}, top1_i = smallest j with
+// minimal d(i,j).  Everything is integer arithmetic, so results are exact.
+//
+// Stages:
+//   k_encode        per image: int8 column deltas (delta of column 0 := 0) and, for needles,
+//                   a byte mask of the non-zero deltas; images with any |delta| > 127 are
+//                   "wide" and listed separately.
+//   k_true_distance d(i, match_i) in int64 straight from the uint16 images.
+//   k_dense         narrow x narrow pairs on CUDA cores.  Per 4 packed deltas the masked sum
+//                   of squares m(a-b)^2 = a^2 - 2ab + (mb)^2 runs as three dp4a; each per-word
+//                   sum is >= 0, so partial sums are monotone and a pair stops once it exceeds
+//                   d(i, match_i) (the early exit of Section 4.4, which never changes a rank).
+//   k_wide          pairs with a wide side: Listing 1 over the needle's non-zero deltas in
+//                   int64, reading the uint16 images.
+//   k_finalize / k_top1_exact   combine counts and top-1 candidates.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace rici {
+namespace {
+
+constexpr int kDenseThreads = 256;     // haystack images per dense tile
+constexpr int kWideThreads = 256;
+constexpr unsigned long long kNoBest = ~0ull;
+
+__device__ __forceinline__ int delta_at(const uint16_t *img, int N, int r, int c) {
+  return c == 0 ? 0 : (int)img[r * N + c] - (int)img[r * N + c - 1];
+}
+
+// One warp per image.
+__global__ void k_encode(const uint16_t *__restrict__ imgs, int64_t n, int N,
+                         int8_t *__restrict__ delta, int8_t *__restrict__ mask,
+                         int *__restrict__ wide_flag, int *__restrict__ wide_list,
+                         int *__restrict__ wide_count) {
+  const int lane = threadIdx.x & 31;
+  const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int K = N * N;
+  for (int64_t i = w; i < n; i += nw) {
+    const uint16_t *img = imgs + i * K;
+    int wide = 0;
+    for (int k = lane; k < K; k += 32) {
+      int r = k / N, c = k - r * N;
+      int d = delta_at(img, N, r, c);
+      wide |= (d > 127 || d < -127);
+      int dc = d > 127 ? 127 : (d < -127 ? -127 : d);
+      delta[i * K + k] = (int8_t)dc;
+      if (mask) mask[i * K + k] = (int8_t)(d != 0 ? -1 : 0);
+    }
+    wide = __any_sync(0xffffffffu, wide);
+    if (lane == 0) {
+      wide_flag[i] = wide;
+      if (wide) wide_list[atomicAdd(wide_count, 1)] = (int)i;
+    }
+  }
+}
+
+// Exact int64 distance of one pair, one warp.
+__device__ int64_t warp_crss(const uint16_t *n, const uint16_t *h, int N) {
+  const int lane = threadIdx.x & 31;
+  long long s = 0;
+  for (int k = lane; k < N * N; k += 32) {
+    int r = k / N, c = k - r * N;
+    if (c == 0) continue;
+    int a = delta_at(n, N, r, c);
+    if (a != 0) {
+      long long d = (long long)a - (long long)delta_at(h, N, r, c);
+      s += d * d;
+    }
+  }
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) s += __shfl_down_sync(0xffffffffu, s, d);
+  return __shfl_sync(0xffffffffu, s, 0);
+}
+
+__global__ void k_true_distance(const uint16_t *__restrict__ nd, int64_t Q,
+                                const uint16_t *__restrict__ hs, int64_t H, int N,
+                                const int64_t *__restrict__ match, int64_t *__restrict__ dtrue,
+                                int *__restrict__ rank, unsigned long long *__restrict__ best,
+                                int *__restrict__ flags, int *status) {
+  const int lane = threadIdx.x & 31;
+  const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t K = (int64_t)N * N;
+  for (int64_t i = w; i < Q; i += nw) {
+    const int64_t m = match ? match[i] : i;
+    if (m < 0 || m >= H) {
+      if (lane == 0) {
+        set_status(status, RICI_ERR_INDEX_OUT_OF_RANGE);
+        dtrue[i] = -1;
+        rank[i] = -1;
+        best[i] = kNoBest;
+        flags[i] = 2;  // invalid: no search for this needle
+      }
+      continue;
+    }
+    int64_t d = warp_crss(nd + i * K, hs + m * K, N);
+    if (lane == 0) {
+      dtrue[i] = d;
+      rank[i] = 0;
+      best[i] = kNoBest;
+      flags[i] = 0;
+    }
+  }
+}
+
+__device__ __forceinline__ unsigned long long pack_best(int64_t d, int64_t j) {
+  unsigned long long dd = d >= 0xffffffffll ? 0xffffffffull : (unsigned long long)d;
+  return (dd << 32) | (unsigned long long)(uint32_t)j;
+}
+
+__device__ __forceinline__ unsigned long long warp_min_u64(unsigned long long v) {
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) {
+    unsigned long long o = __shfl_down_sync(0xffffffffu, v, d);
+    v = o < v ? o : v;
+  }
+  return v;
+}
+
+// Narrow x narrow pairs.  Block: kTQ needles (deltas + masks in shared memory) x
+// kDenseThreads haystack images (one per thread).
+template <int N, int kTQ>
+__global__ void __launch_bounds__(kDenseThreads) k_dense(
+    const int8_t *__restrict__ ndelta, const int8_t *__restrict__ nmask,
+    const int *__restrict__ nwide, int64_t Q, const int8_t *__restrict__ hdelta,
+    const int *__restrict__ hwide, int64_t H, const int64_t *__restrict__ dtrue,
+    const int *__restrict__ nflags, int *__restrict__ rank, unsigned long long *__restrict__ best,
+    unsigned long long *__restrict__ counters) {
+  constexpr int WPR = N / 4;  // 32-bit words per row
+  constexpr int K = N * N;
+  extern __shared__ int2 am_raw[];  // [kTQ][K/4] (needle delta word, mask word)
+  auto am = reinterpret_cast<int2(*)[K / 4]>(am_raw);
+  __shared__ int thr_s[kTQ];
+  __shared__ int act_s[kTQ];
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int64_t q0 = (int64_t)blockIdx.y * kTQ;
+  const int64_t j = (int64_t)blockIdx.x * kDenseThreads + tid;
+
+  for (int x = tid; x < kTQ * (K / 4); x += kDenseThreads) {
+    int q = x / (K / 4), wd = x - q * (K / 4);
+    int a = 0, m = 0;
+    if (q0 + q < Q) {
+      a = reinterpret_cast<const int *>(ndelta + (q0 + q) * K)[wd];
+      m = reinterpret_cast<const int *>(nmask + (q0 + q) * K)[wd];
+    }
+    am[q][wd] = make_int2(a, m);
+  }
+  if (tid < kTQ) {
+    const int64_t q = q0 + tid;
+    bool act = q < Q && nflags[q] == 0 && !nwide[q];
+    int64_t t = act ? dtrue[q] : -1;
+    thr_s[tid] = t > 0x7fffffffll ? 0x7fffffff : (int)t;
+    act_s[tid] = act;
+  }
+  __syncthreads();
+
+  const bool valid = j < H && !hwide[j];
+  int acc[kTQ];
+  unsigned alive = 0;
+#pragma unroll
+  for (int q = 0; q < kTQ; ++q) {
+    acc[q] = 0;
+    if (valid && act_s[q]) alive |= 1u << q;
+  }
+  const int4 *hrow = reinterpret_cast<const int4 *>(hdelta + (valid ? j : 0) * K);
+  unsigned long long pair_rows = 0;
+  for (int r = 0; r < N; ++r) {
+    if (__ballot_sync(0xffffffffu, alive != 0) == 0) break;
+    if (counters) pair_rows += __popc(alive);
+    int hw[WPR];
+    if (alive) {
+#pragma unroll
+      for (int v = 0; v < WPR / 4; ++v) {
+        int4 x = hrow[r * (WPR / 4) + v];
+        hw[4 * v] = x.x;
+        hw[4 * v + 1] = x.y;
+        hw[4 * v + 2] = x.z;
+        hw[4 * v + 3] = x.w;
+      }
+#pragma unroll
+      for (int v = (WPR / 4) * 4; v < WPR; ++v)
+        hw[v] = reinterpret_cast<const int *>(hrow)[r * WPR + v];
+    }
+#pragma unroll
+    for (int q = 0; q < kTQ; ++q) {
+      if (__ballot_sync(0xffffffffu, (alive >> q) & 1u) == 0) continue;
+      int s = 0;
+#pragma unroll
+      for (int v = 0; v < WPR; ++v) {
+        int2 x = am[q][r * WPR + v];
+        int b = hw[v];
+        int bm = b & x.y;
+        s = __dp4a(x.x, x.x, s);
+        s = __dp4a(bm, bm, s);
+        s -= 2 * __dp4a(x.x, b, 0);
+      }
+      acc[q] += s;
+      if (acc[q] > thr_s[q]) alive &= ~(1u << q);
+    }
+  }
+  // count and top-1 candidates (pairs that never exceeded the threshold hold exact values)
+#pragma unroll
+  for (int q = 0; q < kTQ; ++q) {
+    if (!act_s[q]) continue;
+    const bool fin = (alive >> q) & 1u;
+    int c = fin && acc[q] < thr_s[q];
+    unsigned long long b = fin ? pack_best(acc[q], j) : kNoBest;
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) c += __shfl_down_sync(0xffffffffu, c, d);
+    b = warp_min_u64(b);
+    if (lane == 0) {
+      if (c) atomicAdd(&rank[q0 + q], c);
+      if (b != kNoBest) atomicMin(&best[q0 + q], b);
+    }
+  }
+  if (counters) {
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) pair_rows += __shfl_down_sync(0xffffffffu, pair_rows, d);
+    if (lane == 0 && pair_rows) atomicAdd(counters, pair_rows);
+  }
+}
+
+// Pairs with a wide side, exact int64.  List mode:
+//   pass 0: needles = wide needle list, haystack = all.
+//   pass 1: needles = all needles that are not wide, haystack = wide haystack list.
+//   pass 2: needles = all needles, haystack = all (reference path).
+__global__ void __launch_bounds__(kWideThreads) k_wide(
+    const uint16_t *__restrict__ nimg, int64_t Q, const uint16_t *__restrict__ himg, int64_t H,
+    int N, int pass, const int *__restrict__ nwide, const int *__restrict__ wide_n_list,
+    const int *__restrict__ wide_n_count, const int *__restrict__ wide_h_list,
+    const int *__restrict__ wide_h_count, const int64_t *__restrict__ dtrue,
+    const int *__restrict__ nflags, int *__restrict__ rank, unsigned long long *__restrict__ best,
+    int *__restrict__ top1_flag, unsigned long long *__restrict__ counters) {
+  extern __shared__ int2 nz[];  // (flat position, needle delta) of non-zero needle deltas
+  __shared__ int nnz_s;
+  const int tid = threadIdx.x, lane = tid & 31;
+  const int64_t K = (int64_t)N * N;
+  const int64_t nq = pass == 0 ? *wide_n_count : Q;
+  const int64_t nh = pass == 1 ? *wide_h_count : H;
+  const int64_t chunks = (nh + kWideThreads - 1) / kWideThreads;
+  const int64_t items = nq * chunks;
+  for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
+    const int64_t qi = it / chunks, ch = it - qi * chunks;
+    const int64_t i = pass == 0 ? wide_n_list[qi] : qi;
+    if (nflags[i] != 0 || (pass == 1 && nwide[i])) continue;  // uniform over the block
+    const uint16_t *n = nimg + i * K;
+    // compact the needle's non-zero deltas (row-major order)
+    __syncthreads();
+    if (tid == 0) nnz_s = 0;
+    __syncthreads();
+    for (int64_t base = 0; base < K; base += kWideThreads) {
+      int k = (int)(base + tid);
+      int a = 0;
+      if (k < K) {
+        int r = k / N, c = k - r * N;
+        a = delta_at(n, N, r, c);
+      }
+      unsigned bal = __ballot_sync(0xffffffffu, a != 0);
+      int wbase = 0;
+      if (lane == 0) wbase = atomicAdd(&nnz_s, __popc(bal));
+      wbase = __shfl_sync(0xffffffffu, wbase, 0);
+      if (a != 0) nz[wbase + __popc(bal & ((1u << lane) - 1u))] = make_int2(k, a);
+    }
+    __syncthreads();
+    const int nnz = nnz_s;
+    const int64_t thr = dtrue[i];
+    const int64_t hj = ch * kWideThreads + tid;
+    int64_t j = -1;
+    if (hj < nh) j = pass == 1 ? wide_h_list[hj] : hj;
+    int cnt = 0;
+    unsigned long long b = kNoBest;
+    unsigned long long npairs = 0, nterms = 0;
+    if (j >= 0) {
+      const uint16_t *h = himg + j * K;
+      long long acc = 0;
+      int e = 0;
+      for (; e < nnz && acc <= thr; ++e) {
+        int2 p = nz[e];
+        long long d = (long long)p.y - ((long long)h[p.x] - (long long)h[p.x - 1]);
+        acc += d * d;
+      }
+      npairs = 1;
+      nterms = e;
+      if (acc <= thr) {
+        cnt = acc < thr;
+        b = pack_best(acc, j);
+        if (acc >= 0xffffffffll) atomicOr(&top1_flag[i], 1);
+      }
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) cnt += __shfl_down_sync(0xffffffffu, cnt, d);
+    b = warp_min_u64(b);
+    if (counters) {
+#pragma unroll
+      for (int d = 16; d > 0; d >>= 1) {
+        npairs += __shfl_down_sync(0xffffffffu, npairs, d);
+        nterms += __shfl_down_sync(0xffffffffu, nterms, d);
+      }
+    }
+    if (lane == 0) {
+      if (cnt) atomicAdd(&rank[i], cnt);
+      if (b != kNoBest) atomicMin(&best[i], b);
+      if (counters && npairs) {
+        atomicAdd(counters + 1, npairs);
+        atomicAdd(counters + 2, nterms);
+      }
+    }
+  }
+}
+
+__global__ void k_finalize(int64_t Q, const unsigned long long *__restrict__ best,
+                           const int *__restrict__ nflags, int32_t *__restrict__ top1) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < Q;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    top1[i] = (nflags[i] != 0 || best[i] == kNoBest) ? -1 : (int32_t)(uint32_t)(best[i] & 0xffffffffull);
+  }
+}
+
+// Needles whose best distance reached 2^32-1: exact (distance, index) minimum over all j.
+__global__ void __launch_bounds__(256) k_top1_exact(const uint16_t *__restrict__ nimg, int64_t Q,
+                                                   const uint16_t *__restrict__ himg, int64_t H,
+                                                   int N, const int *__restrict__ top1_flag,
+                                                   const int *__restrict__ nflags,
+                                                   int32_t *__restrict__ top1) {
+  __shared__ long long bd[8];
+  __shared__ long long bj[8];
+  const int64_t K = (int64_t)N * N;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int64_t i = blockIdx.x; i < Q; i += gridDim.x) {
+    if (!top1_flag[i] || nflags[i]) continue;
+    long long md = 0x7fffffffffffffffll, mj = -1;
+    for (int64_t j = warp; j < H; j += 8) {
+      long long d = warp_crss(nimg + i * K, himg + j * K, N);
+      if (d < md) {
+        md = d;
+        mj = j;
+      }
+    }
+    if (lane == 0) {
+      bd[warp] = md;
+      bj[warp] = mj;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      long long d0 = bd[0], j0 = bj[0];
+      for (int w = 1; w < 8; ++w)
+        if (bd[w] < d0 || (bd[w] == d0 && bj[w] < j0)) {
+          d0 = bd[w];
+          j0 = bj[w];
+        }
+      top1[i] = (int32_t)j0;
+    }
+    __syncthreads();
+  }
+}
+
+// Full distance matrix (exact int64), one warp per pair.
+__global__ void k_distances(const uint16_t *__restrict__ nimg, int64_t Q,
+                            const uint16_t *__restrict__ himg, int64_t H, int N,
+                            int64_t *__restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int64_t K = (int64_t)N * N;
+  for (int64_t p = w; p < Q * H; p += nw) {
+    const int64_t i = p / H, j = p - i * H;
+    int64_t d = warp_crss(nimg + i * K, himg + j * K, N);
+    if (lane == 0) out[p] = d;
+  }
+}
+
+bool dense_supported(int N) { return N == 8 || N == 16 || N == 32 || N == 64 || N == 128; }
+
+template <int N>
+cudaError_t launch_dense(const int8_t *nd, const int8_t *nm, const int *nw, int64_t Q,
+                         const int8_t *hd, const int *hw, int64_t H, const int64_t *dt,
+                         const int *nf, int *rank, unsigned long long *best,
+                         unsigned long long *counters, cudaStream_t st) {
+  constexpr int kTQ = N <= 64 ? 8 : 4;
+  const size_t smem = sizeof(int2) * kTQ * (N * N / 4);
+  cudaError_t e = cudaFuncSetAttribute(k_dense<N, kTQ>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int64_t gx = (H + kDenseThreads - 1) / kDenseThreads;
+  const int64_t gy = (Q + kTQ - 1) / kTQ;
+  for (int64_t y0 = 0; y0 < gy; y0 += 65535) {
+    const int64_t ny = gy - y0 < 65535 ? gy - y0 : 65535;
+    dim3 grid((unsigned)gx, (unsigned)ny);
+    k_dense<N, kTQ><<<grid, kDenseThreads, smem, st>>>(
+        nd + y0 * kTQ * N * N, nm + y0 * kTQ * N * N, nw + y0 * kTQ, Q - y0 * kTQ, hd, hw, H,
+        dt + y0 * kTQ, nf + y0 * kTQ, rank + y0 * kTQ, best + y0 * kTQ, counters);
+    count_launches(1);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+int64_t search_workspace_bytes(int64_t Q, int64_t H, int32_t N, int32_t mode) {
+  const int64_t K = (int64_t)N * N;
+  Carver c(nullptr);
+  c.take<int8_t>(Q * K);  // needle deltas
+  c.take<int8_t>(Q * K);  // needle masks
+  c.take<int8_t>(H * K);  // haystack deltas
+  c.take<int>(Q);         // needle wide flags
+  c.take<int>(H);         // haystack wide flags
+  c.take<int>(Q);         // wide needle list
+  c.take<int>(H);         // wide haystack list
+  c.take<int>(4);         // list lengths
+  c.take<int>(Q);         // per-needle state flags
+  c.take<int>(Q);         // top-1 exact fallback flags
+  c.take<unsigned long long>(Q);  // packed best (distance, index)
+  c.take<int64_t>(Q);     // true distance when the caller passes none
+  c.take<int32_t>(Q);     // top-1 when the caller passes none
+  (void)mode;
+  return c.off + 256;
+}
+
+cudaError_t launch_search(const SearchArgs &s, void *ws, cudaStream_t st) {
+  const int64_t Q = s.num_needles, H = s.num_haystack;
+  const int N = s.resolution;
+  const int64_t K = (int64_t)N * N;
+  if (Q == 0) return cudaSuccess;
+  Carver c(ws);
+  int8_t *nd = c.take<int8_t>(Q * K);
+  int8_t *nm = c.take<int8_t>(Q * K);
+  int8_t *hd = c.take<int8_t>(H * K);
+  int *nwide = c.take<int>(Q);
+  int *hwide = c.take<int>(H);
+  int *wn_list = c.take<int>(Q);
+  int *wh_list = c.take<int>(H);
+  int *counts = c.take<int>(4);
+  int *nflags = c.take<int>(Q);
+  int *t1flag = c.take<int>(Q);
+  unsigned long long *best = c.take<unsigned long long>(Q);
+  int64_t *dt_ws = c.take<int64_t>(Q);
+  int32_t *top1_ws = c.take<int32_t>(Q);
+  int64_t *dt = s.out_true_distance ? s.out_true_distance : dt_ws;
+  int32_t *top1 = s.out_top1 ? s.out_top1 : top1_ws;
+
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(counts, 0, sizeof(int) * 4, st)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(t1flag, 0, sizeof(int) * Q, st)) != cudaSuccess) return e;
+  const int wpb = 8;
+  auto blocks_for = [&](int64_t items) {
+    int64_t b = (items + wpb - 1) / wpb;
+    return (int)(b < 152 * 64 ? (b > 0 ? b : 1) : 152 * 64);
+  };
+  k_true_distance<<<blocks_for(Q), 32 * wpb, 0, st>>>(s.needles, Q, s.haystack, H, N,
+                                                       s.true_match, dt, s.out_rank, best, nflags,
+                                                       s.status);
+  count_launches(1);
+  const bool dense = s.mode != RICI_SEARCH_EXACT_SLOW && dense_supported(N);
+  unsigned long long *cnt = reinterpret_cast<unsigned long long *>(s.counters);
+  const size_t wide_smem = sizeof(int2) * (size_t)K;
+  if ((e = cudaFuncSetAttribute(k_wide, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)wide_smem)) != cudaSuccess)
+    return e;
+  if (dense) {
+    k_encode<<<blocks_for(Q), 32 * wpb, 0, st>>>(s.needles, Q, N, nd, nm, nwide, wn_list,
+                                                 counts + 0);
+    k_encode<<<blocks_for(H), 32 * wpb, 0, st>>>(s.haystack, H, N, hd, nullptr, hwide, wh_list,
+                                                 counts + 1);
+    count_launches(2);
+    switch (N) {
+      case 8: e = launch_dense<8>(nd, nm, nwide, Q, hd, hwide, H, dt, nflags, s.out_rank, best, cnt, st); break;
+      case 16: e = launch_dense<16>(nd, nm, nwide, Q, hd, hwide, H, dt, nflags, s.out_rank, best, cnt, st); break;
+      case 32: e = launch_dense<32>(nd, nm, nwide, Q, hd, hwide, H, dt, nflags, s.out_rank, best, cnt, st); break;
+      case 64: e = launch_dense<64>(nd, nm, nwide, Q, hd, hwide, H, dt, nflags, s.out_rank, best, cnt, st); break;
+      default: e = launch_dense<128>(nd, nm, nwide, Q, hd, hwide, H, dt, nflags, s.out_rank, best, cnt, st); break;
+    }
+    if (e != cudaSuccess) return e;
+    for (int pass = 0; pass < 2; ++pass)
+      k_wide<<<152 * 8, kWideThreads, wide_smem, st>>>(s.needles, Q, s.haystack, H, N, pass, nwide,
+                                                     wn_list, counts + 0, wh_list, counts + 1, dt,
+                                                     nflags, s.out_rank, best, t1flag, cnt);
+    count_launches(2);
+  } else {
+    if ((e = cudaMemsetAsync(nwide, 0, sizeof(int) * Q, st)) != cudaSuccess) return e;
+    k_wide<<<152 * 8, kWideThreads, wide_smem, st>>>(s.needles, Q, s.haystack, H, N, 2, nwide,
+                                                   wn_list, counts + 0, wh_list, counts + 1, dt,
+                                                   nflags, s.out_rank, best, t1flag, cnt);
+    count_launches(1);
+  }
+  k_finalize<<<blocks_for(Q * wpb), 256, 0, st>>>(Q, best, nflags, top1);
+  k_top1_exact<<<(int)(Q < 152 * 8 ? Q : 152 * 8), 256, 0, st>>>(s.needles, Q, s.haystack, H, N,
+                                                                 t1flag, nflags, top1);
+  count_launches(2);
+  if (s.out_distances) {
+    k_distances<<<blocks_for(Q * H), 32 * wpb, 0, st>>>(s.needles, Q, s.haystack, H, N,
+                                                         s.out_distances);
+    count_launches(1);
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace rici

@@ -1,0 +1,105 @@
+"""The C-ABI library builds, loads and exports every symbol include/*.h declares (CPU only).
+
+No compute call is made here: argument checks that fail on the host return before any CUDA
+call, so they run without a GPU.
+"""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2007_02306_gb300 import build, binding
+
+    build.build()
+    return binding.load_library()
+
+
+def declared_functions():
+    names = []
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        src = open(h).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        names += re.findall(r"RICI_API\s+[\w\s\*]+?\b(\w+)\s*\(", src)
+    return sorted(set(names))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for required in ("rici_generate", "crss_search", "rici_sync_status", "rici_last_error_string"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for name in declared_functions():
+        assert hasattr(lib, name), name
+
+
+def test_library_exports_nothing_undeclared(lib):
+    import subprocess
+
+    from paper_2007_02306_gb300 import binding
+
+    out = subprocess.run(["nm", "-D", "--defined-only", binding.library_path()],
+                         capture_output=True, text=True).stdout
+    exported = {l.split()[-1] for l in out.splitlines() if " T " in l}
+    assert exported == set(declared_functions())
+
+
+def test_version_and_workspace_queries(lib):
+    assert b"sm_103a" in lib.rici_version()
+    assert lib.rici_generate_workspace_size(10, 100, 5, 64) > 100 * 64
+    assert lib.rici_generate_workspace_size(10, -1, 5, 64) == -1
+    assert lib.crss_search_workspace_size(10, 100, 64, 0) >= 110 * 64 * 64
+    assert lib.crss_search_workspace_size(10, 100, 0, 0) == -1
+
+
+@pytest.mark.parametrize("N,R", [(0, 0.3), (129, 0.3), (64, 0.0), (64, -1.0), (64, float("nan")),
+                                 (64, float("inf"))])
+def test_generate_rejects_bad_arguments_on_host(lib, N, R):
+    dummy = ctypes.c_void_p(16)
+    rc = lib.rici_generate(dummy, dummy, 3, dummy, 1, dummy, 1, R, N, dummy, None, 0, None)
+    assert rc == 1
+    assert lib.rici_last_error_string()
+
+
+def test_generate_rejects_null_and_negative(lib):
+    dummy = ctypes.c_void_p(16)
+    assert lib.rici_generate(dummy, dummy, -1, dummy, 1, dummy, 1, 0.3, 64, dummy, None, 0, None) == 1
+    assert lib.rici_generate(None, dummy, 3, dummy, 1, dummy, 1, 0.3, 64, dummy, None, 0, None) == 1
+    assert lib.rici_generate_ex(dummy, dummy, 3, dummy, 1, dummy, 1, 0.3, 64, dummy, 7, None, None,
+                                0, None) == 1
+
+
+def test_search_rejects_bad_arguments_on_host(lib):
+    dummy = ctypes.c_void_p(16)
+    # empty haystack with needles, bad resolution, bad mode, oversized distance matrix
+    assert lib.crss_search(dummy, 1, dummy, 0, 64, None, dummy, None, None, None, 0, None, 0, None) == 1
+    assert lib.crss_search(dummy, 1, dummy, 1, 1, None, dummy, None, None, None, 0, None, 0, None) == 1
+    assert lib.crss_search(dummy, 1, dummy, 1, 64, None, dummy, None, None, None, 9, None, 0, None) == 1
+    assert lib.crss_search(dummy, 1 << 15, dummy, 1 << 14, 64, None, dummy, None, None, dummy, 0,
+                           None, 0, None) == 8
+
+
+def test_zero_work_calls_are_no_ops(lib):
+    dummy = ctypes.c_void_p(16)
+    assert lib.rici_generate(dummy, dummy, 3, dummy, 1, dummy, 0, 0.3, 64, dummy, None, 0, None) == 0
+    assert lib.crss_search(dummy, 0, dummy, 5, 64, None, dummy, None, None, None, 0, None, 0, None) == 0
+
+
+def test_binding_fails_loudly_without_library(tmp_path):
+    from paper_2007_02306_gb300 import binding
+
+    saved = binding._lib
+    binding._lib = None
+    try:
+        with pytest.raises(RuntimeError):
+            binding.load_library(str(tmp_path / "missing.so"))
+    finally:
+        binding._lib = saved

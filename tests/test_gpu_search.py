@@ -1,0 +1,147 @@
+"""GPU parity of CRSS search against the int64 CPU oracle: exact ranks, distances, top-1.
+
+Covers RICI-like synthetic image sets (narrow deltas, heavy tails, 16-bit extremes), planted
+ties, every resolution class (the packed-int8 CUDA-core kernel for N in {8,16,32,64,128}
+and the generic int64 path otherwise), both search modes, images generated by the GPU from
+the tiny scene, invalid true-match indices, and the benchmark's full-size search
+(10,242 needles x 114,892 haystack images) on sampled needles.
+"""
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def rici():
+    import torch
+
+    import paper_2007_02306_gb300 as p
+    from paper_2007_02306_gb300 import build
+
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    build.build()
+    p.load_library()
+    return p
+
+
+def dev(a):
+    import torch
+
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def run(rici, needles, hay, match=None, mode=0, dist=False):
+    r = rici.crss_search(dev(needles), dev(hay), None if match is None else dev(match.astype(np.int64)),
+                         mode=mode, return_distances=dist)
+    assert rici.sync_status() == 0
+    return {k: v.cpu().numpy() for k, v in r.items()}
+
+
+def check(got, ref, dist=False):
+    assert np.array_equal(got["true_distance"], ref["true_distance"])
+    assert np.array_equal(got["rank"], ref["rank"])
+    assert np.array_equal(got["top1"], ref["top1"])
+    if dist:
+        assert np.array_equal(got["distances"], ref["distances"])
+
+
+def dataset(seed, Q, H, N, **kw):
+    rng = np.random.default_rng(seed)
+    return synth.images.needle_haystack_set(rng, Q, H, N, **kw)
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2])
+def test_small_set_all_outputs(rici, oracle_mod, mode):
+    nd, hay, m = dataset(1, 64, 700, 64)
+    ref = oracle_mod.crss_search(nd, hay, m, return_distances=True)
+    got = run(rici, nd, hay, m, mode=mode, dist=True)
+    check(got, ref, dist=True)
+
+
+@pytest.mark.parametrize("N", [8, 16, 32, 128, 12, 2])
+def test_resolutions(rici, oracle_mod, N):
+    nd, hay, m = dataset(2, 40, 300, N)
+    ref = oracle_mod.crss_search(nd, hay, m)
+    check(run(rici, nd, hay, m), ref)
+
+
+def test_heavy_tails_and_extremes(rici, oracle_mod):
+    rng = np.random.default_rng(3)
+    nd, hay, m = synth.images.needle_haystack_set(rng, 60, 900, 64, tail_image_fraction=0.3,
+                                                  tail_row_fraction=0.2)
+    # 16-bit extremes in a few needles and haystack images (wide on both sides)
+    nd[5, 10, 20:] = 65535
+    nd[6, :, ::2] = 0
+    nd[6, :, 1::2] = 65535
+    hay[m[7], 3, :31] = 65535
+    hay[17, :, 1::2] = 65535
+    hay[18] = 0
+    ref = oracle_mod.crss_search(nd, hay, m, return_distances=True)
+    got = run(rici, nd, hay, m, dist=True)
+    check(got, ref, dist=True)
+
+
+def test_ties_keep_best_rank(rici, oracle_mod):
+    nd, hay, m = dataset(4, 50, 500, 32)
+    for k in range(0, 50, 3):  # duplicates of true matches elsewhere in the haystack
+        hay[(m[k] + 17) % 500] = hay[m[k]]
+    ref = oracle_mod.crss_search(nd, hay, m)
+    check(run(rici, nd, hay, m), ref)
+
+
+def test_identity_match_default(rici, oracle_mod):
+    rng = np.random.default_rng(5)
+    ims = synth.images.rici_like_images(rng, 120, 64)
+    ref = oracle_mod.crss_search(ims, ims)
+    got = run(rici, ims, ims)
+    check(got, ref)
+    assert (got["rank"] == 0).all()
+
+
+def test_gpu_generated_tiny_scene_self_search(rici, oracle_mod):
+    import torch
+
+    s = synth.tiny_scene()
+    o = np.arange(s.num_vertices, dtype=np.int32)
+    ims = rici.rici_generate(dev(s.vertices), dev(s.normals), dev(s.triangles), dev(o), 0.3, 32)
+    r = rici.crss_search(ims, ims)
+    assert rici.sync_status() == 0
+    assert (r["rank"].cpu().numpy() == 0).all()
+    ref_imgs = oracle_mod.rici_fp64(s.vertices, s.normals, s.triangles, o, 0.3, 32)
+    ref = oracle_mod.crss_search(ref_imgs, ref_imgs)
+    check({k: v.cpu().numpy() for k, v in r.items()}, ref)
+    del torch
+
+
+def test_invalid_true_match_sets_status(rici):
+    import torch
+
+    nd, hay, m = dataset(6, 10, 50, 16)
+    m[3] = 50
+    r = rici.crss_search(dev(nd), dev(hay), dev(m.astype(np.int64)))
+    assert rici.sync_status() & rici.binding.ERR_INDEX_OUT_OF_RANGE
+    assert r["rank"][3].item() == -1
+    del torch
+
+
+def test_single_haystack_and_single_needle(rici, oracle_mod):
+    nd, hay, m = dataset(7, 1, 1, 64)
+    check(run(rici, nd, hay, m), oracle_mod.crss_search(nd, hay, m))
+    nd, hay, m = dataset(8, 1, 257, 64)  # ragged haystack tile
+    check(run(rici, nd, hay, m), oracle_mod.crss_search(nd, hay, m))
+
+
+def test_clutter_scale_search_sampled_needles(rici, oracle_mod):
+    """Full benchmark size: 10,242 needles x 114,892 haystack images, N = 64."""
+    Q, H = 10242, 114892
+    nd, hay, m = dataset(9, Q, H, 64, clutter_fraction=0.3)
+    got = run(rici, nd, hay, m)
+    rng = np.random.default_rng(1)
+    s = np.unique(np.concatenate([[0, Q - 1], rng.integers(0, Q, 30)]))
+    ref = oracle_mod.crss_search(nd[s], hay, m[s])
+    assert np.array_equal(got["true_distance"][s], ref["true_distance"])
+    assert np.array_equal(got["rank"][s], ref["rank"])
+    assert np.array_equal(got["top1"][s], ref["top1"])
