@@ -36,6 +36,7 @@ constexpr float kCellClamp = 1048576.0f;  // |cell coordinate| limit (2^20)
 constexpr int kWarps = 4;
 constexpr int kSlot = 25;  // words per staged triangle (odd stride: conflict-free lookups)
 constexpr int kScanItems = 2048;
+constexpr int kPerWarp = 64 + 32 + 64 + 64 + 32 * kSlot;  // shared words per warp
 
 __host__ __device__ inline uint32_t bucket_count(int64_t nt) {
   uint32_t b = 1024;
@@ -251,15 +252,16 @@ struct Shared {
   float *bf;     // beta_r rounded to FP32
   double *fr;    // S (3 doubles), Nax, Nay, Nbx, Nbz
   int *buckets;  // 27 neighbour buckets
-  int *wq;       // this warp's queue [64]
+  int *wq;       // this warp's candidate queue [64]
   int *wst;      // this warp's item starts [32]
+  int *bq_rec;   // this warp's FP64 queue: triangle record [64]
+  int *bq_r;     // this warp's FP64 queue: layer [64]
   float *slots;  // this warp's staged triangles [32][kSlot]
 };
 
 // slot layout (words)
 enum {
-  SX = 0, SY = 3, SZ = 6, SGID = 9, SDE = 12, SW = 15, SRLO = 16, SBAND = 17, SFLAGS = 20,
-  SREC = 21
+  SX = 0, SY = 3, SZ = 6, SGID = 9, SDE = 12, SRLO = 16, SBAND = 17, SFLAGS = 20, SREC = 21
 };
 constexpr int kAll64 = 1;
 
@@ -299,18 +301,16 @@ __device__ __forceinline__ void project64(float px, float py, float pz, const do
 // FP64 evaluation of one (triangle, layer) with the definition's operation order.
 // Returns false when the triangle does not cross the layer; otherwise the single-crossing
 // columns are [lo, hi) and the double-crossing columns [dlo, lo).
-__device__ bool layer_fp64(const KArgs &a, const Shared &s, const float *sl, int r, int &lo,
-                           int &hi, int &dlo) {
+__device__ bool layer_fp64(const KArgs &a, const Shared &s, int rec, int r, int &lo, int &hi,
+                           int &dlo) {
   const int N = a.N;
-  const int rec = __float_as_int(sl[SREC]);
   float4 r1 = a.rec[4 * (int64_t)rec + 1], r2 = a.rec[4 * (int64_t)rec + 2],
          r3 = a.rec[4 * (int64_t)rec + 3];
   double T[3][3];
   project64(r1.x, r1.y, r1.z, s.fr, T[0]);
   project64(r1.w, r2.x, r2.y, s.fr, T[1]);
   project64(r2.z, r2.w, r3.x, s.fr, T[2]);
-  int gid[3] = {__float_as_int(sl[SGID]), __float_as_int(sl[SGID + 1]),
-                __float_as_int(sl[SGID + 2])};
+  const int gid[3] = {__float_as_int(r3.y), __float_as_int(r3.z), __float_as_int(r3.w)};
   const double beta = s.bd[r];
   int s0 = T[0][2] >= beta, s1 = T[1][2] >= beta, s2 = T[2][2] >= beta;
   if (s0 == s1 && s1 == s2) return false;
@@ -355,8 +355,9 @@ __device__ bool layer_fp64(const KArgs &a, const Shared &s, const float *sl, int
   return true;
 }
 
-// FP32 evaluation with error bounds.  Returns 0: no crossing, 1: intervals valid,
-// 2: a predicate is inside its error band (caller re-evaluates in FP64).
+// FP32 evaluation with forward error bounds against the FP64 definition.
+// Returns 0: no crossing, 1: intervals valid, 2: a predicate lies inside its error band
+// (the caller re-evaluates the item in FP64).
 __device__ __forceinline__ int layer_fp32(const KArgs &a, const Shared &s, const float *sl, int r,
                                           float scale, int &lo, int &hi, int &dlo) {
   const int N = a.N;
@@ -382,60 +383,72 @@ __device__ __forceinline__ int layer_fp32(const KArgs &a, const Shared &s, const
   bool swap = gub < gua || (gub == gua && gvb < gva);
   float E0x = swap ? Ebx : Eax, E0y = swap ? Eby : Eay;
   float E1x = swap ? Eax : Ebx, E1y = swap ? Eay : Eby;
-  // edge opposite vertex k has index k; edge (lone, oa) is opposite ob and vice versa
+  // |E32 - E64| per component; edge (lone, oa) is opposite ob and vice versa
   const float dE = fmaxf(sl[SDE + ob], sl[SDE + oa]);
-  const float W = sl[SW];
-  const float W2 = W * W;
+  if (!(dE < 1e30f)) return 2;
   float e0 = __fmaf_rn(E0x, E0x, __fmul_rn(E0y, E0y));
   float e1 = __fmaf_rn(E1x, E1x, __fmul_rn(E1y, E1y));
-  const float de = kSafety * (4.0f * W * dE + 6.0f * dE * dE + 3.01f * kU * W2);
-  const float ds = de + kU * s.a2f[N - 1] + 1e-37f;
+  const float A0 = fabsf(E0x) + fabsf(E0y) + 2.0f * dE;  // bounds |E0x*| + |E0y*|
+  const float A1 = fabsf(E1x) + fabsf(E1y) + 2.0f * dE;
+  const float de0 = kSafety * (2.0f * A0 * dE + 3.01f * kU * e0) + 1e-37f;
+  const float de1 = kSafety * (2.0f * A1 * dE + 3.01f * kU * e1) + 1e-37f;
   int c0 = lower_count_f(e0, s.a2f, N, scale), c1 = lower_count_f(e1, s.a2f, N, scale);
-  if (!(de < 1e30f)) return 2;
-  if ((c0 > 0 && e0 - s.a2f[c0 - 1] <= ds) || (c0 < N && s.a2f[c0] - e0 <= ds) ||
-      (c1 > 0 && e1 - s.a2f[c1 - 1] <= ds) || (c1 < N && s.a2f[c1] - e1 <= ds))
-    return 2;
+  // the two columns around each transition must be decided with certainty
+  if (c0 > 0 && e0 - s.a2f[c0 - 1] <= de0 + kU * s.a2f[c0 - 1]) return 2;
+  if (c0 < N && s.a2f[c0] - e0 <= de0 + kU * s.a2f[c0]) return 2;
+  if (c1 > 0 && e1 - s.a2f[c1 - 1] <= de1 + kU * s.a2f[c1 - 1]) return 2;
+  if (c1 < N && s.a2f[c1] - e1 <= de1 + kU * s.a2f[c1]) return 2;
   lo = min(c0, c1);
   hi = max(c0, c1);
   dlo = lo;
   if (lo > 0) {
     float Dx = __fsub_rn(E1x, E0x), Dy = __fsub_rn(E1y, E0y);
-    float d0 = __fmaf_rn(E0x, Dx, __fmul_rn(E0y, Dy));
-    float d1 = __fmaf_rn(E1x, Dx, __fmul_rn(E1y, Dy));
-    const float dD = 2.0f * dE + 2.1f * kU * W;
-    const float dd0 = kSafety * (2.0f * W * dD + 4.0f * W * dE + 2.0f * dD * dE + 6.0f * kU * W2) +
-                      1e-37f;
-    if (fabsf(d0) <= dd0 || fabsf(d1) <= dd0) return 2;
-    if (d0 < 0.0f && d1 > 0.0f) {
-      float cr = __fmaf_rn(E0x, Dy, -__fmul_rn(E0y, Dx));
-      float dd = __fmaf_rn(Dx, Dx, __fmul_rn(Dy, Dy));
-      const float ddd = kSafety * (8.0f * W * dD + 2.0f * dD * dD + 12.0f * kU * W2) + 1e-37f;
-      if (dd <= ddd) return 2;
-      float cr2 = __fmul_rn(cr, cr);
-      int cs = lower_count_f(__fdiv_rn(cr2, dd), s.a2f, N, scale);
-      while (cs > 0 && __fmul_rn(s.a2f[cs - 1], dd) > cr2) --cs;
-      while (cs < N && !(__fmul_rn(s.a2f[cs], dd) > cr2)) ++cs;
-      const float acr = fabsf(cr);
-      // certainty of alpha_c^2 * dd > cr^2 at the columns where it matters
-      int cchk[2] = {cs - 1, cs};
-      if (cs >= lo) {
-        cchk[0] = lo - 1;
-        cchk[1] = -1;
-      }
-#pragma unroll
-      for (int k = 0; k < 2; ++k) {
-        int c = cchk[k];
-        if (c < 0 || c >= lo) continue;
-        float a2 = s.a2f[c];
-        float dq = kSafety * (a2 * (ddd + 2.0f * kU * (dd + ddd)) + dd0 * (2.0f * acr + 3.0f * dd0) +
-                              2.0f * kU * cr2) + 1e-37f;
-        float p1 = __fmul_rn(a2, dd);
-        if (fabsf(p1 - cr2) <= dq) return 2;
-      }
-      dlo = min(cs, lo);
+    const float dD = 2.0f * dE + kU * (fabsf(Dx) + fabsf(Dy));
+    const float B = fabsf(Dx) + fabsf(Dy) + 2.0f * dD;      // bounds |Dx*| + |Dy*|
+    float cr = __fmaf_rn(E0x, Dy, -__fmul_rn(E0y, Dx));
+    float dd = __fmaf_rn(Dx, Dx, __fmul_rn(Dy, Dy));
+    const float dcr = kSafety * (A0 * dD + B * dE + 2.0f * kU * A0 * B) + 1e-37f;
+    const float ddd = kSafety * (2.0f * B * dD + 2.0f * kU * B * B) + 1e-37f;
+    float cr2 = __fmul_rn(cr, cr);
+    const float acr = fabsf(cr);
+    auto q_band = [&](int c) {  // is the sign of alpha_c^2 dd - cr^2 uncertain?
+      float a2 = s.a2f[c];
+      float dq = kSafety * (a2 * (ddd + 2.0f * kU * (dd + ddd)) + dcr * (2.0f * acr + 2.0f * dcr) +
+                            2.0f * kU * cr2) + 1e-37f;
+      return fabsf(__fmul_rn(a2, dd) - cr2) <= dq;
+    };
+    int cs = lower_count_f(__fdiv_rn(cr2, dd), s.a2f, N, scale);
+    while (cs > 0 && __fmul_rn(s.a2f[cs - 1], dd) > cr2) --cs;
+    while (cs < N && !(__fmul_rn(s.a2f[cs], dd) > cr2)) ++cs;
+    if (cs >= lo) {
+      // no column below lo has alpha^2 > |C|^2: no double crossings whatever E0.D, E1.D are
+      if (q_band(lo - 1)) return 2;
+    } else {
+      // certainty at cs-1 and cs extends to every column when dd exceeds the alpha^2
+      // coefficient of the q bound (q - dq is then increasing in the column)
+      if (dd <= kSafety * (ddd + 2.0f * kU * (dd + ddd))) return 2;
+      if (cs > 0 && q_band(cs - 1)) return 2;
+      if (q_band(cs)) return 2;
+      float d0 = __fmaf_rn(E0x, Dx, __fmul_rn(E0y, Dy));
+      float d1 = __fmaf_rn(E1x, Dx, __fmul_rn(E1y, Dy));
+      const float dd0 = kSafety * (A0 * dD + B * dE + 2.0f * kU * A0 * B) + 1e-37f;
+      const float dd1 = kSafety * (A1 * dD + B * dE + 2.0f * kU * A1 * B) + 1e-37f;
+      if (fabsf(d0) <= dd0 || fabsf(d1) <= dd1) return 2;
+      if (d0 < 0.0f && d1 > 0.0f) dlo = cs;
     }
   }
   return 1;
+}
+
+__device__ __forceinline__ void add_intervals(int *row, int N, int lo, int hi, int dlo) {
+  if (lo < hi) {
+    atomicAdd(row + lo, 1);
+    if (hi < N) atomicAdd(row + hi, -1);
+  }
+  if (dlo < lo) {
+    atomicAdd(row + dlo, 2);
+    if (lo < N) atomicAdd(row + lo, -2);
+  }
 }
 
 template <int NW>
@@ -457,10 +470,11 @@ __global__ void __launch_bounds__(NW * 32) k_generate(KArgs a) {
     s.bf = s.a2f + N;
     s.buckets = reinterpret_cast<int *>(s.bf + N);
     int *wbase = s.buckets + 28;
-    const int per_warp = 64 + 32 + 32 * kSlot;
-    s.wq = wbase + warp * per_warp;
+    s.wq = wbase + warp * kPerWarp;
     s.wst = s.wq + 64;
-    s.slots = reinterpret_cast<float *>(s.wst + 32);
+    s.bq_rec = s.wst + 32;
+    s.bq_r = s.bq_rec + 64;
+    s.slots = reinterpret_cast<float *>(s.bq_r + 64);
   }
 
   const int vid = a.origins[o];
@@ -531,7 +545,31 @@ __global__ void __launch_bounds__(NW * 32) k_generate(KArgs a) {
   const bool fp64_only = a.mode == RICI_GEN_FP64;
 
   unsigned long long n_tri = 0, n_items = 0, n_band = 0, n_cand = 0;
-  int qn = 0;  // warp-uniform queue length
+  int qn = 0;  // warp-uniform candidate queue length
+  int bn = 0;  // warp-uniform FP64 queue length
+
+  // FP64 re-evaluation of queued band items, one per lane
+  auto flush_band = [&](int cnt) {
+    if (lane < cnt) {
+      int lo = 0, hi = 0, dlo = 0;
+      const int r = s.bq_r[lane];
+      if (layer_fp64(a, s, s.bq_rec[lane], r, lo, hi, dlo)) add_intervals(s.diff + r * N, N, lo, hi, dlo);
+    }
+    __syncwarp();
+    const int rest = bn - cnt;
+    int mr = 0, mq = 0;
+    if (lane < rest) {
+      mr = s.bq_rec[cnt + lane];
+      mq = s.bq_r[cnt + lane];
+    }
+    __syncwarp();
+    if (lane < rest) {
+      s.bq_rec[lane] = mr;
+      s.bq_r[lane] = mq;
+    }
+    bn = rest;
+    __syncwarp();
+  };
 
   auto process_batch = [&](int cnt) {
     // ---- per-triangle setup: one survivor per lane
@@ -580,10 +618,8 @@ __global__ void __launch_bounds__(NW * 32) k_generate(KArgs a) {
       }
       if (nlay > 0) {
         int flags = (fp64_only || dside >= 0.25f * spacing) ? kAll64 : 0;
-        float W = 0.0f;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-          W = fmaxf(W, fmaxf(fabsf(tx[k]), fabsf(ty[k])));
           sl[SX + k] = tx[k];
           sl[SY + k] = ty[k];
           sl[SZ + k] = tz[k];
@@ -600,16 +636,19 @@ __global__ void __launch_bounds__(NW * 32) k_generate(KArgs a) {
         sl[SGID + 0] = r3.y;
         sl[SGID + 1] = r3.z;
         sl[SGID + 2] = r3.w;
-        // per-edge bound on |E32 - E64| (edge k is opposite vertex k)
+        // per-edge bound on |E32 - E64| per component (edge k is opposite vertex k):
+        // E = T_u + lambda (T_v - T_u); lambda = (beta - z_u) / (z_v - z_u)
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-          int i = k == 0 ? 1 : 0, j = k == 2 ? 1 : 2;
-          float den = fabsf(tz[j] - tz[i]);
-          float el = (kU * R + 3.0f * dT) / den + 4.0f * kU;
-          float de = 1.1f * (3.0f * dT + 3.0f * kU * W + 2.0f * W * el);
-          sl[SDE + k] = (den > 0.0f && de < 1e30f) ? de : __int_as_float(0x7f800000);
+          const int i = k == 0 ? 1 : 0, j = k == 2 ? 1 : 2;
+          const float den = fabsf(tz[j] - tz[i]);
+          const float eden = 2.0f * dT + kU * den;
+          const float el = (kU * R + dT + kU * den + eden) / (den - eden) + 2.0f * kU;
+          const float ext = fmaxf(fabsf(tx[j] - tx[i]), fabsf(ty[j] - ty[i]));
+          const float mag = fmaxf(fmaxf(fabsf(tx[i]), fabsf(tx[j])), fmaxf(fabsf(ty[i]), fabsf(ty[j])));
+          const float de = 1.1f * (3.0f * dT + kU * (ext + mag) + (ext + 2.0f * dT) * el);
+          sl[SDE + k] = (den > eden && de < 1e30f) ? de : __int_as_float(0x7f800000);
         }
-        sl[SW] = W;
         sl[SRLO] = __int_as_float(r_lo);
         sl[SFLAGS] = __int_as_float(flags);
         sl[SREC] = __int_as_float(rec);
@@ -626,35 +665,37 @@ __global__ void __launch_bounds__(NW * 32) k_generate(KArgs a) {
     s.wst[lane] = incl - nlay;
     n_tri += nlay > 0;
     __syncwarp();
-    for (int it = lane; it < total; it += 32) {
-      int lo_ = 0, hi_ = cnt - 1;
-      while (lo_ < hi_) {
-        int mid = (lo_ + hi_ + 1) >> 1;
-        if (s.wst[mid] <= it) lo_ = mid; else hi_ = mid - 1;
+    for (int base = 0; base < total; base += 32) {
+      const int it = base + lane;
+      const bool act = it < total;
+      int res = 0, r = 0, rec = 0, lo = 0, hi = 0, dlo = 0;
+      if (act) {
+        int lo_ = 0, hi_ = cnt - 1;
+        while (lo_ < hi_) {
+          int mid = (lo_ + hi_ + 1) >> 1;
+          if (s.wst[mid] <= it) lo_ = mid; else hi_ = mid - 1;
+        }
+        const float *ts = s.slots + lo_ * kSlot;
+        r = __float_as_int(ts[SRLO]) + (it - s.wst[lo_]);
+        rec = __float_as_int(ts[SREC]);
+        const int flags = __float_as_int(ts[SFLAGS]);
+        bool band = (flags & kAll64) || r == __float_as_int(ts[SBAND]) ||
+                    r == __float_as_int(ts[SBAND + 1]) || r == __float_as_int(ts[SBAND + 2]);
+        res = band ? 2 : layer_fp32(a, s, ts, r, scale, lo, hi, dlo);
+        ++n_items;
       }
-      const float *ts = s.slots + lo_ * kSlot;
-      const int r = __float_as_int(ts[SRLO]) + (it - s.wst[lo_]);
-      const int flags = __float_as_int(ts[SFLAGS]);
-      int lo = 0, hi = 0, dlo = 0, res;
-      bool band = (flags & kAll64) || r == __float_as_int(ts[SBAND]) ||
-                  r == __float_as_int(ts[SBAND + 1]) || r == __float_as_int(ts[SBAND + 2]);
-      res = band ? 2 : layer_fp32(a, s, ts, r, scale, lo, hi, dlo);
+      // items inside the error band wait in the FP64 queue (evaluated 32 at a time)
+      const unsigned bal = __ballot_sync(0xffffffffu, res == 2);
       if (res == 2) {
+        const int pos = bn + __popc(bal & ((1u << lane) - 1u));
+        s.bq_rec[pos] = rec;
+        s.bq_r[pos] = r;
         ++n_band;
-        res = layer_fp64(a, s, ts, r, lo, hi, dlo) ? 1 : 0;
       }
-      ++n_items;
-      if (res == 1) {
-        int *row = s.diff + r * N;
-        if (lo < hi) {
-          atomicAdd(row + lo, 1);
-          if (hi < N) atomicAdd(row + hi, -1);
-        }
-        if (dlo < lo) {
-          atomicAdd(row + dlo, 2);
-          if (lo < N) atomicAdd(row + lo, -2);
-        }
-      }
+      bn += __popc(bal);
+      if (res == 1) add_intervals(s.diff + r * N, N, lo, hi, dlo);
+      __syncwarp();
+      if (bn >= 32) flush_band(32);
     }
     __syncwarp();
   };
@@ -704,6 +745,7 @@ __global__ void __launch_bounds__(NW * 32) k_generate(KArgs a) {
     }
   }
   if (qn > 0) process_batch(qn);
+  if (bn > 0) flush_band(bn);
 
   if (a.counters) {
 #pragma unroll
@@ -749,7 +791,7 @@ size_t generate_smem_bytes(int N) {
   b += (size_t)(2 * N + 8) * sizeof(double);
   b += (size_t)(2 * N) * sizeof(float);
   b += 28 * sizeof(int);
-  b += (size_t)kWarps * (64 + 32 + 32 * kSlot) * 4;
+  b += (size_t)kWarps * kPerWarp * 4;
   return b;
 }
 

@@ -139,6 +139,10 @@ __global__ void __launch_bounds__(kDenseThreads) k_dense(
   auto am = reinterpret_cast<int2(*)[K / 4]>(am_raw);
   __shared__ int thr_s[kTQ];
   __shared__ int act_s[kTQ];
+  __shared__ int wrow[kTQ][N];     // sum of squared needle deltas per (needle, row)
+  __shared__ int ord[N];           // rows by decreasing tile weight
+  __shared__ unsigned rmask[N];    // needles of the tile with a non-zero delta in the row
+  __shared__ int nrows_s;
   const int tid = threadIdx.x, lane = tid & 31;
   const int64_t q0 = (int64_t)blockIdx.y * kTQ;
   const int64_t j = (int64_t)blockIdx.x * kDenseThreads + tid;
@@ -160,6 +164,45 @@ __global__ void __launch_bounds__(kDenseThreads) k_dense(
     act_s[tid] = act;
   }
   __syncthreads();
+  // Rows are visited heaviest first so that distances pass the early-exit threshold sooner;
+  // the sum is order independent, so the result is unchanged.  Rows where no needle of the
+  // tile has a non-zero delta contribute nothing and are skipped.
+  for (int x = tid; x < kTQ * N; x += kDenseThreads) {
+    int q = x / N, r = x - q * N;
+    int w = 0;
+#pragma unroll
+    for (int v = 0; v < WPR; ++v) {
+      int av = am[q][r * WPR + v].x;
+      w = __dp4a(av, av, w);
+    }
+    wrow[q][r] = act_s[q] ? w : 0;
+  }
+  __syncthreads();
+  if (tid < N) {
+    int W = 0;
+    unsigned msk = 0;
+#pragma unroll
+    for (int q = 0; q < kTQ; ++q) {
+      W += wrow[q][tid];
+      if (wrow[q][tid] > 0) msk |= 1u << q;
+    }
+    rmask[tid] = msk;
+    wrow[0][tid] = W;  // reuse row 0 of the table for the tile weight (read below after sync)
+  }
+  __syncthreads();
+  if (tid < N) {
+    const int W = wrow[0][tid];
+    int rk = 0, nz = 0;
+    for (int r2 = 0; r2 < N; ++r2) {
+      const int W2 = wrow[0][r2];
+      rk += (W2 > W) || (W2 == W && r2 < tid);
+      nz += W2 > 0;
+    }
+    ord[rk] = tid;
+    if (tid == 0) nrows_s = nz;
+  }
+  __syncthreads();
+  const int nrows = nrows_s;
 
   const bool valid = j < H && !hwide[j];
   int acc[kTQ];
@@ -171,11 +214,13 @@ __global__ void __launch_bounds__(kDenseThreads) k_dense(
   }
   const int4 *hrow = reinterpret_cast<const int4 *>(hdelta + (valid ? j : 0) * K);
   unsigned long long pair_rows = 0;
-  for (int r = 0; r < N; ++r) {
+  for (int i = 0; i < nrows; ++i) {
     if (__ballot_sync(0xffffffffu, alive != 0) == 0) break;
-    if (counters) pair_rows += __popc(alive);
+    const int r = ord[i];
+    const unsigned use = alive & rmask[r];
+    if (counters) pair_rows += __popc(use);
     int hw[WPR];
-    if (alive) {
+    if (use) {
 #pragma unroll
       for (int v = 0; v < WPR / 4; ++v) {
         int4 x = hrow[r * (WPR / 4) + v];
@@ -190,7 +235,7 @@ __global__ void __launch_bounds__(kDenseThreads) k_dense(
     }
 #pragma unroll
     for (int q = 0; q < kTQ; ++q) {
-      if (__ballot_sync(0xffffffffu, (alive >> q) & 1u) == 0) continue;
+      if (__ballot_sync(0xffffffffu, (use >> q) & 1u) == 0) continue;
       int s = 0;
 #pragma unroll
       for (int v = 0; v < WPR; ++v) {
@@ -201,8 +246,10 @@ __global__ void __launch_bounds__(kDenseThreads) k_dense(
         s = __dp4a(bm, bm, s);
         s -= 2 * __dp4a(x.x, b, 0);
       }
-      acc[q] += s;
-      if (acc[q] > thr_s[q]) alive &= ~(1u << q);
+      if ((use >> q) & 1u) {
+        acc[q] += s;
+        if (acc[q] > thr_s[q]) alive &= ~(1u << q);
+      }
     }
   }
   // count and top-1 candidates (pairs that never exceeded the threshold hold exact values)

@@ -172,7 +172,8 @@ def test_clutter_scene_full_size_sampled_origins(rici, oracle_mod):
     sample = np.unique(np.concatenate([[0, s.num_vertices - 1, s.target_vertices - 1,
                                         s.target_vertices], rng.integers(0, s.num_vertices, 200)]))
     ref = oracle_mod.rici_fp64(s.vertices, s.normals, s.triangles, sample, 0.3, 64)
-    got = out[torch.from_numpy(sample).cuda()].cpu().numpy()
+    pick = lambda imgs, idx: imgs.view(torch.int16)[torch.from_numpy(idx).cuda()].view(torch.uint16)  # noqa: E731
+    got = pick(out, sample).cpu().numpy()
     assert np.array_equal(got, ref)
     # needles: the target alone, same vertex indices
     tgt = s.target_only()
@@ -181,6 +182,6 @@ def test_clutter_scene_full_size_sampled_origins(rici, oracle_mod):
     assert rici.sync_status() == 0
     ts = sample[sample < s.target_vertices]
     ref_t = oracle_mod.rici_fp64(tgt.vertices, tgt.normals, tgt.triangles, ts, 0.3, 64)
-    assert np.array_equal(nd[torch.from_numpy(ts).cuda()].cpu().numpy(), ref_t)
+    assert np.array_equal(pick(nd, ts).cpu().numpy(), ref_t)
     c = cnt.cpu().numpy()
-    assert c[1] > 0 and c[2] < c[1] * 0.05
+    assert c[1] > 0 and c[2] < c[1] * 0.02, f"FP64 band fraction too high: {c}"
