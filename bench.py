@@ -63,6 +63,10 @@ def parse():
     ap.add_argument("--cpu-needle-origins", type=int, default=48)
     ap.add_argument("--cpu-needles", type=int, default=12)
     ap.add_argument("--cpu-haystack", type=int, default=24000)
+    ap.add_argument("--haystack-limit", type=int, default=0,
+                    help="image only the first H scene vertices (small profiling case)")
+    ap.add_argument("--needle-limit", type=int, default=0,
+                    help="use only the first Q target vertices as needles (small profiling case)")
     return ap.parse_args()
 
 
@@ -227,6 +231,10 @@ def main():
 
     scene = build_workload()
     V, T, Vt, Tt = scene.num_vertices, scene.num_triangles, scene.target_vertices, scene.target_triangles
+    if args.needle_limit:
+        Vt = min(Vt, args.needle_limit)
+    if args.haystack_limit:
+        V = max(Vt, min(V, args.haystack_limit))
     h_vert = torch.from_numpy(scene.vertices).pin_memory()
     h_norm = torch.from_numpy(scene.normals).pin_memory()
     h_tri = torch.from_numpy(scene.triangles).pin_memory()
@@ -235,6 +243,8 @@ def main():
     h_match = torch.arange(Vt, dtype=torch.int64).pin_memory()
 
     vert, norm, tri = h_vert.to(dev), h_norm.to(dev), h_tri.to(dev)
+    if args.needle_limit or args.haystack_limit:
+        args.no_cpu_baseline = True
     tri_t = tri[:Tt]
     oh, on, match = h_oh.to(dev), h_on.to(dev), h_match.to(dev)
     needles = torch.empty((Vt, N_RES, N_RES), dtype=torch.uint16, device=dev)

@@ -404,37 +404,35 @@ __device__ __forceinline__ int layer_fp32(const KArgs &a, const Shared &s, const
   if (lo > 0) {
     float Dx = __fsub_rn(E1x, E0x), Dy = __fsub_rn(E1y, E0y);
     const float dD = 2.0f * dE + kU * (fabsf(Dx) + fabsf(Dy));
-    const float B = fabsf(Dx) + fabsf(Dy) + 2.0f * dD;      // bounds |Dx*| + |Dy*|
-    float cr = __fmaf_rn(E0x, Dy, -__fmul_rn(E0y, Dx));
-    float dd = __fmaf_rn(Dx, Dx, __fmul_rn(Dy, Dy));
-    const float dcr = kSafety * (A0 * dD + B * dE + 2.0f * kU * A0 * B) + 1e-37f;
-    const float ddd = kSafety * (2.0f * B * dD + 2.0f * kU * B * B) + 1e-37f;
-    float cr2 = __fmul_rn(cr, cr);
-    const float acr = fabsf(cr);
-    auto q_band = [&](int c) {  // is the sign of alpha_c^2 dd - cr^2 uncertain?
-      float a2 = s.a2f[c];
-      float dq = kSafety * (a2 * (ddd + 2.0f * kU * (dd + ddd)) + dcr * (2.0f * acr + 2.0f * dcr) +
-                            2.0f * kU * cr2) + 1e-37f;
-      return fabsf(__fmul_rn(a2, dd) - cr2) <= dq;
-    };
-    int cs = lower_count_f(__fdiv_rn(cr2, dd), s.a2f, N, scale);
-    while (cs > 0 && __fmul_rn(s.a2f[cs - 1], dd) > cr2) --cs;
-    while (cs < N && !(__fmul_rn(s.a2f[cs], dd) > cr2)) ++cs;
-    if (cs >= lo) {
-      // no column below lo has alpha^2 > |C|^2: no double crossings whatever E0.D, E1.D are
-      if (q_band(lo - 1)) return 2;
-    } else {
-      // certainty at cs-1 and cs extends to every column when dd exceeds the alpha^2
-      // coefficient of the q bound (q - dq is then increasing in the column)
-      if (dd <= kSafety * (ddd + 2.0f * kU * (dd + ddd))) return 2;
-      if (cs > 0 && q_band(cs - 1)) return 2;
-      if (q_band(cs)) return 2;
-      float d0 = __fmaf_rn(E0x, Dx, __fmul_rn(E0y, Dy));
-      float d1 = __fmaf_rn(E1x, Dx, __fmul_rn(E1y, Dy));
-      const float dd0 = kSafety * (A0 * dD + B * dE + 2.0f * kU * A0 * B) + 1e-37f;
-      const float dd1 = kSafety * (A1 * dD + B * dE + 2.0f * kU * A1 * B) + 1e-37f;
-      if (fabsf(d0) <= dd0 || fabsf(d1) <= dd1) return 2;
-      if (d0 < 0.0f && d1 > 0.0f) dlo = cs;
+    const float B = fabsf(Dx) + fabsf(Dy) + 2.0f * dD;  // bounds |Dx*| + |Dy*|
+    // is the line's closest point C strictly inside the segment (E0.D < 0 < E1.D)?
+    float d0 = __fmaf_rn(E0x, Dx, __fmul_rn(E0y, Dy));
+    float d1 = __fmaf_rn(E1x, Dx, __fmul_rn(E1y, Dy));
+    const float dd0 = kSafety * (A0 * dD + B * dE + 2.0f * kU * A0 * B) + 1e-37f;
+    const float dd1 = kSafety * (A1 * dD + B * dE + 2.0f * kU * A1 * B) + 1e-37f;
+    if (fabsf(d0) <= dd0 || fabsf(d1) <= dd1) return 2;
+    if (d0 < 0.0f && d1 > 0.0f) {
+      // alpha_c^2 |D|^2 > (E0 x D)^2  <=>  alpha_c^2 > h^2, h = |C| the segment's distance to
+      // the axis.  C is inside the segment for the FP32 and the FP64 endpoints, and moving
+      // each endpoint by at most dE per component moves h by at most sqrt(2) dE, so h^2 is
+      // known to 2 h dh + dh^2 plus the rounding of the cross product, |D|^2 and the quotient.
+      float cr = __fmaf_rn(E0x, Dy, -__fmul_rn(E0y, Dx));
+      float dd = __fmaf_rn(Dx, Dx, __fmul_rn(Dy, Dy));
+      float h2 = __fdiv_rn(__fmul_rn(cr, cr), dd);
+      const float h = sqrtf(h2);
+      const float dh = 1.5f * (dE + kU * B);
+      const float rb = B * rsqrtf(dd);  // (|Dx| + |Dy| + 2 dD) / |D|
+      const float dq = kSafety * (2.0f * h * dh + 2.0f * dh * dh + 4.0f * kU * h * A0 * rb +
+                                  2.0f * kU * h2 * (1.0f + rb * rb)) + 1e-37f;
+      if (!(dq < 1e30f)) return 2;
+      const int cs = lower_count_f(h2, s.a2f, N, scale);  // first column with alpha^2 > h^2
+      if (cs >= lo) {
+        if (h2 - s.a2f[lo - 1] <= dq + kU * s.a2f[lo - 1]) return 2;
+      } else {
+        if (cs > 0 && h2 - s.a2f[cs - 1] <= dq + kU * s.a2f[cs - 1]) return 2;
+        if (s.a2f[cs] - h2 <= dq + kU * s.a2f[cs]) return 2;
+        dlo = cs;
+      }
     }
   }
   return 1;
