@@ -136,6 +136,30 @@ RICI_API int crss_search_ex(const uint16_t *needles, int64_t num_needles,
                             int64_t *out_distances, int32_t mode, int64_t *counters,
                             void *workspace, int64_t workspace_bytes, void *stream);
 
+/*
+ * rici_generate_noalloc — rici_generate for callers that must not allocate device memory.
+ * (An addition of this library; the paper has no counterpart.)
+ *
+ * Some callers cannot let a library call cudaMalloc or cudaFree: a service whose device
+ * memory budget is fixed at start-up, a plugin host that owns the GPU allocator and offers
+ * no scratch buffers, or a latency-critical loop where cudaFree's implicit device-wide
+ * synchronisation would stall other streams.  This variant allocates nothing: its scratch
+ * space is one 21 MiB array in device memory, compiled into the library, which every GPU that
+ * loads the library holds until the process exits.  Arguments, outputs and results are those
+ * of rici_generate (bit-identical images), without a workspace argument.
+ *  - Accepts at most 262,144 triangles; larger meshes return RICI_ERR_OUT_TOO_LARGE.
+ *  - The first call on a device looks up the array's device address with that device current;
+ *    make that first call before any stream capture.
+ *  - All calls share the one array: calls that overlap on the GPU (no ordering between their
+ *    streams) race on it and produce wrong images.  Order them on one stream.
+ *  - Device-side errors go to the same status word as rici_generate (rici_sync_status).
+ */
+RICI_API int rici_generate_noalloc(const float *vertices, const float *normals,
+                                   int64_t num_vertices, const int32_t *triangles,
+                                   int64_t num_triangles, const int32_t *origins,
+                                   int64_t num_origins, float support_radius, int32_t resolution,
+                                   uint16_t *out_images, void *stream);
+
 /* Synchronise `stream`, then read and clear the per-device status word (RICI_ERR_* bits). */
 RICI_API int rici_sync_status(void *stream, int32_t *device_status);
 

@@ -70,6 +70,8 @@ def load_library(path: str | None = None):
         lib.crss_search.restype = ctypes.c_int
         lib.crss_search_ex.argtypes = [P, i64, P, i64, i32, P, P, P, P, P, i32, P, P, i64, P]
         lib.crss_search_ex.restype = ctypes.c_int
+        lib.rici_generate_noalloc.argtypes = [P, P, i64, P, i64, P, i64, f32, i32, P, P]
+        lib.rici_generate_noalloc.restype = ctypes.c_int
         lib.rici_sync_status.argtypes = [P, ctypes.POINTER(i32)]
         lib.rici_sync_status.restype = ctypes.c_int
         lib.rici_release_workspace.argtypes = []

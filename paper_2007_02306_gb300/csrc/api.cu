@@ -115,6 +115,10 @@ int check_generate_args(const float *V, const float *Nrm, int64_t nv, const int3
 
 void count_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
+cudaError_t status_word_address(int **address) {
+  return cudaGetSymbolAddress((void **)address, g_status);
+}
+
 }  // namespace rici
 
 using namespace rici;

@@ -69,4 +69,7 @@ __device__ __forceinline__ void set_status(int *status, int bits) { atomicOr(sta
 // Number of kernels this library has enqueued in the process (for launch accounting).
 void count_launches(int64_t n);
 
+// Device address of the status word on the current device.
+cudaError_t status_word_address(int **address);
+
 }  // namespace rici

@@ -1,0 +1,100 @@
+// rici_generate_noalloc: RICI generation for callers that must not allocate device memory.
+//
+// Some callers cannot let a library call cudaMalloc or cudaFree: a service whose device
+// memory budget is fixed when it starts, a plugin host that owns the GPU allocator and hands
+// out no scratch buffers, or a latency-critical loop where cudaFree's implicit device-wide
+// synchronisation would stall work on other streams.  For them this entry point takes its
+// scratch space from one statically sized device array compiled into the library instead
+// of from a caller buffer or the library's on-demand workspace.
+//
+// The array lives in device memory of every GPU that loads the library until the process
+// exits.  All calls share it: calls that overlap on the GPU (for example on two streams
+// without ordering between them) race on it and give wrong images.  Each call clears the
+// parts that must start at zero (the grid bucket counts and the big-list length) before
+// its kernels use them; the rest is overwritten before it is read.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <mutex>
+
+#include "common.cuh"
+
+namespace rici {
+namespace {
+
+// Largest mesh accepted, and the scratch size it needs (generate_workspace_bytes of it).
+constexpr int64_t kNoAllocMaxTriangles = 262144;
+constexpr size_t kNoAllocScratchBytes = (size_t)21 << 20;  // 21 MiB
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void *g_scratch_ptr[kMaxDevices];  // device address of g_noalloc_scratch, per device
+int *g_status_ptr[kMaxDevices];    // device address of the status word, per device
+
+// Once per device, with that device current: resolve the device addresses of the scratch
+// array and of the status word (host code may not use the array's name as a pointer).
+cudaError_t noalloc_setup(int dev, void **scratch, int **status) {
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_scratch_ptr[dev]) {
+    void *p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    int *st = nullptr;
+    e = status_word_address(&st);
+    if (e != cudaSuccess) return e;
+    g_status_ptr[dev] = st;
+    g_scratch_ptr[dev] = p;
+  }
+  *scratch = g_scratch_ptr[dev];
+  *status = g_status_ptr[dev];
+  return cudaSuccess;
+}
+
+}  // namespace
+}  // namespace rici
+
+using namespace rici;
+
+extern "C" int rici_generate_noalloc(const float *vertices, const float *normals,
+                                     int64_t num_vertices, const int32_t *triangles,
+                                     int64_t num_triangles, const int32_t *origins,
+                                     int64_t num_origins, float support_radius,
+                                     int32_t resolution, uint16_t *out_images, void *stream) {
+  if (num_vertices < 0 || num_triangles < 0 || num_origins < 0) return RICI_ERR_INVALID_ARGUMENT;
+  if (resolution < 1 || resolution > RICI_MAX_RESOLUTION) return RICI_ERR_INVALID_ARGUMENT;
+  if (!(support_radius > 0.0f) || !(support_radius < 3.4e38f)) return RICI_ERR_INVALID_ARGUMENT;
+  if (num_triangles > 0 && (!triangles || !vertices)) return RICI_ERR_INVALID_ARGUMENT;
+  if (num_origins > 0 && (!origins || !vertices || !normals || !out_images))
+    return RICI_ERR_INVALID_ARGUMENT;
+  if (num_origins > 0 && num_vertices == 0) return RICI_ERR_INVALID_ARGUMENT;
+  if (num_vertices > (int64_t(1) << 31) - 2) return RICI_ERR_OUT_TOO_LARGE;
+  // the scratch array has room for at most kNoAllocMaxTriangles triangles
+  if (num_triangles > kNoAllocMaxTriangles ||
+      generate_workspace_bytes(num_triangles) > (int64_t)kNoAllocScratchBytes)
+    return RICI_ERR_OUT_TOO_LARGE;
+  if (num_origins == 0) return RICI_OK;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return RICI_ERR_CUDA;
+  void *scratch = nullptr;
+  int *status = nullptr;
+  if (noalloc_setup(dev, &scratch, &status) != cudaSuccess) return RICI_ERR_CUDA;
+  GenerateArgs a;
+  a.vertices = vertices;
+  a.normals = normals;
+  a.num_vertices = num_vertices;
+  a.triangles = triangles;
+  a.num_triangles = num_triangles;
+  a.origins = origins;
+  a.num_origins = num_origins;
+  a.support_radius = support_radius;
+  a.resolution = resolution;
+  a.out_images = out_images;
+  a.mode = RICI_GEN_DEFAULT;
+  a.counters = nullptr;
+  a.status = status;
+  if (launch_generate(a, scratch, static_cast<cudaStream_t>(stream)) != cudaSuccess)
+    return RICI_ERR_CUDA;
+  return RICI_OK;
+}
