@@ -63,6 +63,8 @@ def parse():
     ap.add_argument("--cpu-needle-origins", type=int, default=48)
     ap.add_argument("--cpu-needles", type=int, default=12)
     ap.add_argument("--cpu-haystack", type=int, default=24000)
+    ap.add_argument("--tc-compare", type=int, default=1,
+                    help="also time the tensor-core search on the same images (breakdown)")
     ap.add_argument("--haystack-limit", type=int, default=0,
                     help="image only the first H scene vertices (small profiling case)")
     ap.add_argument("--needle-limit", type=int, default=0,
@@ -309,6 +311,27 @@ def main():
     pairs = V * Vt
     value = world * images / (ms_step / 1e3)
 
+    # tensor-core form of the same search (exact fp16 tcgen05 GEMM), timed separately
+    tc = None
+    if args.tc_compare:
+        for _ in range(2):
+            p.crss_search(needles, hay, match, mode=p.SEARCH_TENSOR)
+        torch.cuda.synchronize()
+        tc_ms = []
+        for k in range(args.steps):
+            flush.zero_()
+            b0 = torch.cuda.Event(enable_timing=True)
+            b1 = torch.cuda.Event(enable_timing=True)
+            b0.record(stream)
+            rt = p.crss_search(needles, hay, match, mode=p.SEARCH_TENSOR)
+            b1.record(stream)
+            torch.cuda.synchronize()
+            tc_ms.append(b0.elapsed_time(b1))
+        same = all(bool(torch.equal(rt[k2], res[k2])) for k2 in ("rank", "true_distance", "top1"))
+        st = p.sync_status()
+        tc = {"ms": statistics.mean(tc_ms), "comparisons_per_s": pairs / (statistics.mean(tc_ms) / 1e3),
+              "same_ranks_as_cuda_core": same, "status": st}
+
     # e2e: same step from pinned host buffers, host<->device copies inside the timed region
     e2e = None
     if not args.no_e2e:
@@ -391,6 +414,17 @@ def main():
     for r in rooflines.values():
         r["frac"] = r["achieved"] / r["peak"]
         r["peak_kind"] = f"derived: {sms} SMs x 128 lanes x {clk_mhz:.0f} MHz (median SM clock)"
+    if tc is not None:
+        kt = 2 * N_RES * N_RES
+        rooflines["search_tensor_core"] = {
+            "bound": "tensor", "unit": "TFLOP/s",
+            "achieved": 2.0 * kt * pairs / (tc["ms"] / 1e3) / 1e12,
+            "peak": pk.get("bf16_tflops", 1900.0),
+            "work": f"{pairs} pairs x 2 x {kt} fp16 multiply-adds (dense, K = 2 N^2)",
+            "traffic": None, "peak_kind": f"{pk_kind} bf16 dense burst (fp16 runs at the bf16 rate)",
+        }
+        rooflines["search_tensor_core"]["frac"] = (rooflines["search_tensor_core"]["achieved"] /
+                                                   rooflines["search_tensor_core"]["peak"])
     dom = "search" if se_ms >= gen_ms or "generation" not in rooflines else "generation"
     roof = dict(rooflines[dom])
     roof["kernel"] = "k_dense (CUDA-core CRSS)" if dom == "search" else "k_generate"
@@ -415,6 +449,7 @@ def main():
                                     "fp64_band_items": gcnt[2], "cull_candidates": gcnt[3]},
             "search_counters": {"pair_rows": scnt[0], "wide_pairs": scnt[1],
                                 "wide_terms": scnt[2]},
+            "search_tensor_core": tc,
         },
         "roofline": roof,
         "rooflines": rooflines,

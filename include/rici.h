@@ -61,6 +61,9 @@ extern "C" {
 #define RICI_SEARCH_DEFAULT 0   /* fastest exact form available */
 #define RICI_SEARCH_CUDA_CORE 1 /* Listing 1 per pair on CUDA cores, early exit */
 #define RICI_SEARCH_EXACT_SLOW 2 /* generic int64 per-pair kernel for every pair (test reference) */
+#define RICI_SEARCH_TENSOR 3    /* exact fp16 tcgen05 GEMM of the expanded distance (N in 8..128,
+                                   powers of two); pairs with |delta| > 32 on either side run in
+                                   exact int64 on CUDA cores */
 
 /*
  * rici_generate — one RICI image per oriented point (Section 3.1).

@@ -5,6 +5,6 @@ in ``include/rici.h``); ``binding`` marshals torch CUDA tensors into it.  Build 
 with ``paper_2007_02306_gb300.build.build()``.
 """
 from .binding import (  # noqa: F401
-    GEN_DEFAULT, GEN_FP64, SEARCH_CUDA_CORE, SEARCH_DEFAULT, SEARCH_EXACT_SLOW, RiciError,
+    GEN_DEFAULT, GEN_FP64, SEARCH_CUDA_CORE, SEARCH_DEFAULT, SEARCH_EXACT_SLOW, SEARCH_TENSOR, RiciError,
     crss_search, load_library, rici_generate, sync_status, version,
 )

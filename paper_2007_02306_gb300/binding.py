@@ -20,6 +20,7 @@ GEN_FP64 = 1
 SEARCH_DEFAULT = 0
 SEARCH_CUDA_CORE = 1
 SEARCH_EXACT_SLOW = 2
+SEARCH_TENSOR = 3
 
 ERR_INVALID_ARGUMENT = 1
 ERR_INDEX_OUT_OF_RANGE = 2

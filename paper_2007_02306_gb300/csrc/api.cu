@@ -198,7 +198,7 @@ int crss_search_ex(const uint16_t *needles, int64_t num_needles, const uint16_t 
   if (resolution < 2 || resolution > RICI_MAX_RESOLUTION)
     return fail(RICI_ERR_INVALID_ARGUMENT, "resolution must be in [2, %d]", RICI_MAX_RESOLUTION);
   if (mode != RICI_SEARCH_DEFAULT && mode != RICI_SEARCH_CUDA_CORE &&
-      mode != RICI_SEARCH_EXACT_SLOW)
+      mode != RICI_SEARCH_EXACT_SLOW && mode != RICI_SEARCH_TENSOR)
     return fail(RICI_ERR_INVALID_ARGUMENT, "unknown search mode %d", mode);
   if (num_needles == 0) return RICI_OK;
   if (num_haystack == 0)

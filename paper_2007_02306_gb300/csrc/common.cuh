@@ -50,6 +50,16 @@ int64_t search_workspace_bytes(int64_t num_needles, int64_t num_haystack, int32_
                                int32_t mode);
 cudaError_t launch_search(const SearchArgs &a, void *ws, cudaStream_t stream);
 
+// Tensor-core search (tc_search.cu): operand encoding + persistent tcgen05 GEMM with the rank /
+// top-1 epilogue for narrow x narrow pairs.  Fills nwide/hwide and the wide lists/counts.
+bool tc_supported(int N);
+int64_t tc_workspace_bytes(int64_t Q, int64_t H, int N);
+cudaError_t launch_tc_encode_and_rank(const uint16_t *needles, int64_t Q, const uint16_t *haystack,
+                                      int64_t H, int N, void *ws, int *nwide, int *hwide,
+                                      int *wn_list, int *wh_list, int *counts,
+                                      const int *nflags, const int64_t *dtrue, int *rank,
+                                      unsigned long long *best, int *status, cudaStream_t st);
+
 // Carve 256-byte aligned sub-buffers out of one workspace allocation.
 struct Carver {
   char *base;

@@ -466,7 +466,7 @@ int64_t search_workspace_bytes(int64_t Q, int64_t H, int32_t N, int32_t mode) {
   c.take<unsigned long long>(Q);  // packed best (distance, index)
   c.take<int64_t>(Q);     // true distance when the caller passes none
   c.take<int32_t>(Q);     // top-1 when the caller passes none
-  (void)mode;
+  if (mode == RICI_SEARCH_TENSOR && tc_supported(N)) c.take<char>(tc_workspace_bytes(Q, H, N));
   return c.off + 256;
 }
 
@@ -489,6 +489,8 @@ cudaError_t launch_search(const SearchArgs &s, void *ws, cudaStream_t st) {
   unsigned long long *best = c.take<unsigned long long>(Q);
   int64_t *dt_ws = c.take<int64_t>(Q);
   int32_t *top1_ws = c.take<int32_t>(Q);
+  const bool tensor = s.mode == RICI_SEARCH_TENSOR && tc_supported(N);
+  char *tc_ws = tensor ? c.take<char>(tc_workspace_bytes(Q, H, N)) : nullptr;
   int64_t *dt = s.out_true_distance ? s.out_true_distance : dt_ws;
   int32_t *top1 = s.out_top1 ? s.out_top1 : top1_ws;
 
@@ -504,13 +506,23 @@ cudaError_t launch_search(const SearchArgs &s, void *ws, cudaStream_t st) {
                                                        s.true_match, dt, s.out_rank, best, nflags,
                                                        s.status);
   count_launches(1);
-  const bool dense = s.mode != RICI_SEARCH_EXACT_SLOW && dense_supported(N);
+  const bool dense = !tensor && s.mode != RICI_SEARCH_EXACT_SLOW && dense_supported(N);
   unsigned long long *cnt = reinterpret_cast<unsigned long long *>(s.counters);
   const size_t wide_smem = sizeof(int2) * (size_t)K;
   if ((e = cudaFuncSetAttribute(k_wide, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)wide_smem)) != cudaSuccess)
     return e;
-  if (dense) {
+  if (tensor) {
+    if ((e = launch_tc_encode_and_rank(s.needles, Q, s.haystack, H, N, tc_ws, nwide, hwide,
+                                       wn_list, wh_list, counts, nflags, dt, s.out_rank, best,
+                                       s.status, st)) != cudaSuccess)
+      return e;
+    for (int pass = 0; pass < 2; ++pass)
+      k_wide<<<152 * 8, kWideThreads, wide_smem, st>>>(s.needles, Q, s.haystack, H, N, pass, nwide,
+                                                     wn_list, counts + 0, wh_list, counts + 1, dt,
+                                                     nflags, s.out_rank, best, t1flag, cnt);
+    count_launches(2);
+  } else if (dense) {
     k_encode<<<blocks_for(Q), 32 * wpb, 0, st>>>(s.needles, Q, N, nd, nm, nwide, wn_list,
                                                  counts + 0);
     k_encode<<<blocks_for(H), 32 * wpb, 0, st>>>(s.haystack, H, N, hd, nullptr, hwide, wh_list,

@@ -53,7 +53,7 @@ def dataset(seed, Q, H, N, **kw):
     return synth.images.needle_haystack_set(rng, Q, H, N, **kw)
 
 
-@pytest.mark.parametrize("mode", [0, 1, 2])
+@pytest.mark.parametrize("mode", [0, 1, 2, 3])
 def test_small_set_all_outputs(rici, oracle_mod, mode):
     nd, hay, m = dataset(1, 64, 700, 64)
     ref = oracle_mod.crss_search(nd, hay, m, return_distances=True)
@@ -62,13 +62,15 @@ def test_small_set_all_outputs(rici, oracle_mod, mode):
 
 
 @pytest.mark.parametrize("N", [8, 16, 32, 128, 12, 2])
-def test_resolutions(rici, oracle_mod, N):
+@pytest.mark.parametrize("mode", [1, 3])
+def test_resolutions(rici, oracle_mod, N, mode):
     nd, hay, m = dataset(2, 40, 300, N)
     ref = oracle_mod.crss_search(nd, hay, m)
-    check(run(rici, nd, hay, m), ref)
+    check(run(rici, nd, hay, m, mode=mode), ref)
 
 
-def test_heavy_tails_and_extremes(rici, oracle_mod):
+@pytest.mark.parametrize("mode", [1, 3])
+def test_heavy_tails_and_extremes(rici, oracle_mod, mode):
     rng = np.random.default_rng(3)
     nd, hay, m = synth.images.needle_haystack_set(rng, 60, 900, 64, tail_image_fraction=0.3,
                                                   tail_row_fraction=0.2)
@@ -80,8 +82,33 @@ def test_heavy_tails_and_extremes(rici, oracle_mod):
     hay[17, :, 1::2] = 65535
     hay[18] = 0
     ref = oracle_mod.crss_search(nd, hay, m, return_distances=True)
-    got = run(rici, nd, hay, m, dist=True)
+    got = run(rici, nd, hay, m, mode=mode, dist=True)
     check(got, ref, dist=True)
+
+
+def test_tensor_accumulator_exact_at_the_narrow_limit(rici, oracle_mod):
+    """Largest sums the fp16 operands allow: every delta +-32 (|S| up to 4032 * 3072)."""
+    N = 64
+    col = np.arange(N)
+    up = np.tile((32 * col).astype(np.uint16), (N, 1))          # deltas +32 everywhere
+    down = np.tile((32 * (N - 1 - col)).astype(np.uint16), (N, 1))  # deltas -32 everywhere
+    zig = np.tile(np.where(col % 2 == 0, 0, 32).astype(np.uint16), (N, 1))  # +32/-32 alternating
+    rng = np.random.default_rng(12)
+    rnd = np.cumsum(rng.choice([-32, 32], size=(6, N, N)), axis=2)
+    rnd = (rnd - rnd.min(axis=2, keepdims=True)).astype(np.uint16)
+    ims = np.concatenate([np.stack([up, down, zig, np.zeros((N, N), np.uint16)]), rnd])
+    nd = ims.copy()
+    hay = np.concatenate([ims[::-1], ims])
+    m = np.arange(len(nd)) + len(ims)
+    ref = oracle_mod.crss_search(nd, hay, m, return_distances=True)
+    assert ref["distances"].max() == 64 * 63 * 64 ** 2  # +32 against -32 at every position
+    check(run(rici, nd, hay, m, mode=3, dist=True), ref, dist=True)
+
+
+@pytest.mark.parametrize("Q,H", [(1, 1), (129, 257), (300, 1000)])
+def test_tensor_ragged_tiles(rici, oracle_mod, Q, H):
+    nd, hay, m = dataset(11, Q, H, 64)
+    check(run(rici, nd, hay, m, mode=3), oracle_mod.crss_search(nd, hay, m))
 
 
 def test_ties_keep_best_rank(rici, oracle_mod):
@@ -134,11 +161,12 @@ def test_single_haystack_and_single_needle(rici, oracle_mod):
     check(run(rici, nd, hay, m), oracle_mod.crss_search(nd, hay, m))
 
 
-def test_clutter_scale_search_sampled_needles(rici, oracle_mod):
+@pytest.mark.parametrize("mode", [1, 3])
+def test_clutter_scale_search_sampled_needles(rici, oracle_mod, mode):
     """Full benchmark size: 10,242 needles x 114,892 haystack images, N = 64."""
     Q, H = 10242, 114892
     nd, hay, m = dataset(9, Q, H, 64, clutter_fraction=0.3)
-    got = run(rici, nd, hay, m)
+    got = run(rici, nd, hay, m, mode=mode)
     rng = np.random.default_rng(1)
     s = np.unique(np.concatenate([[0, Q - 1], rng.integers(0, Q, 30)]))
     ref = oracle_mod.crss_search(nd[s], hay, m[s])
