@@ -261,13 +261,14 @@ struct Shared {
 
 // slot layout (words)
 enum {
-  SX = 0, SY = 3, SZ = 6, SGID = 9, SDE = 12, SRLO = 16, SBAND = 17, SFLAGS = 20, SREC = 21
+  SX = 0, SY = 3, SZ = 6, SGID = 9, SDE = 12, SRLO = 15, SBAND = 16, SFLAGS = 19, SREC = 20,
+  SINV = 21  // 1 / (z_j - z_i) of edge k (opposite vertex k, i < j local indices)
 };
 constexpr int kAll64 = 1;
 
 __device__ __forceinline__ int lower_count_f(float x, const float *a2f, int N, float scale) {
   // number of columns c with a2f[c] <= x
-  float s = sqrtf(fmaxf(x, 0.0f)) * scale;
+  float s = x > 0.0f ? x * rsqrtf(x) * scale : 0.0f;  // estimate only, corrected below
   float fc = floorf((s + 1.0f) * 0.5f);
   int c = (fc >= (float)N) ? N : ((fc > 0.0f) ? (int)fc : 0);
   while (c < N && a2f[c] <= x) ++c;
@@ -368,18 +369,22 @@ __device__ __forceinline__ int layer_fp32(const KArgs &a, const Shared &s, const
   int lone = (s0 != s1 && s0 != s2) ? 0 : ((s1 != s0 && s1 != s2) ? 1 : 2);
   int oa = lone == 0 ? 1 : 0;
   int ob = lone == 2 ? 1 : 2;
-  int g_l = __float_as_int(sl[SGID + lone]), g_a = __float_as_int(sl[SGID + oa]),
-      g_b = __float_as_int(sl[SGID + ob]);
-  int ua = g_l < g_a ? lone : oa, va = g_l < g_a ? oa : lone;
-  int ub = g_l < g_b ? lone : ob, vb = g_l < g_b ? ob : lone;
-  float la = __fdiv_rn(__fsub_rn(beta, sl[SZ + ua]), __fsub_rn(sl[SZ + va], sl[SZ + ua]));
-  float lb = __fdiv_rn(__fsub_rn(beta, sl[SZ + ub]), __fsub_rn(sl[SZ + vb], sl[SZ + ub]));
-  float Eax = __fmaf_rn(la, __fsub_rn(sl[SX + va], sl[SX + ua]), sl[SX + ua]);
-  float Eay = __fmaf_rn(la, __fsub_rn(sl[SY + va], sl[SY + ua]), sl[SY + ua]);
-  float Ebx = __fmaf_rn(lb, __fsub_rn(sl[SX + vb], sl[SX + ub]), sl[SX + ub]);
-  float Eby = __fmaf_rn(lb, __fsub_rn(sl[SY + vb], sl[SY + ub]), sl[SY + ub]);
-  int gua = ua == lone ? g_l : g_a, gva = va == lone ? g_l : g_a;
-  int gub = ub == lone ? g_l : g_b, gvb = vb == lone ? g_l : g_b;
+  // slice the two crossed edges (lone, oa) and (lone, ob) in local vertex order: E lies within
+  // the per-edge bound of the FP64 point whatever the orientation, so the FP32 path only has to
+  // keep the roles of E0 and E1 (chosen by global vertex indices as in the definition)
+  const int g_l = __float_as_int(sl[SGID + lone]), g_a = __float_as_int(sl[SGID + oa]),
+            g_b = __float_as_int(sl[SGID + ob]);
+  const int ia = min(lone, oa), ja = max(lone, oa);  // edge opposite ob
+  const int ib = min(lone, ob), jb = max(lone, ob);  // edge opposite oa
+  const float la = __fmul_rn(__fsub_rn(beta, sl[SZ + ia]), sl[SINV + ob]);
+  const float lb = __fmul_rn(__fsub_rn(beta, sl[SZ + ib]), sl[SINV + oa]);
+  float Eax = __fmaf_rn(la, __fsub_rn(sl[SX + ja], sl[SX + ia]), sl[SX + ia]);
+  float Eay = __fmaf_rn(la, __fsub_rn(sl[SY + ja], sl[SY + ia]), sl[SY + ia]);
+  float Ebx = __fmaf_rn(lb, __fsub_rn(sl[SX + jb], sl[SX + ib]), sl[SX + ib]);
+  float Eby = __fmaf_rn(lb, __fsub_rn(sl[SY + jb], sl[SY + ib]), sl[SY + ib]);
+  // E0 is the crossed edge with the smaller (lower, higher) global index key
+  const int gua = min(g_l, g_a), gva = max(g_l, g_a);
+  const int gub = min(g_l, g_b), gvb = max(g_l, g_b);
   bool swap = gub < gua || (gub == gua && gvb < gva);
   float E0x = swap ? Ebx : Eax, E0y = swap ? Eby : Eay;
   float E1x = swap ? Eax : Ebx, E1y = swap ? Eay : Eby;
@@ -641,11 +646,13 @@ __global__ void __launch_bounds__(NW * 32) k_generate(KArgs a) {
           const int i = k == 0 ? 1 : 0, j = k == 2 ? 1 : 2;
           const float den = fabsf(tz[j] - tz[i]);
           const float eden = 2.0f * dT + kU * den;
-          const float el = (kU * R + dT + kU * den + eden) / (den - eden) + 2.0f * kU;
+          // lambda = (beta - z_i) * (1 / (z_j - z_i)): reciprocal and product each round once
+          const float el = (kU * R + dT + kU * den + eden) / (den - eden) + 3.0f * kU;
           const float ext = fmaxf(fabsf(tx[j] - tx[i]), fabsf(ty[j] - ty[i]));
           const float mag = fmaxf(fmaxf(fabsf(tx[i]), fabsf(tx[j])), fmaxf(fabsf(ty[i]), fabsf(ty[j])));
           const float de = 1.1f * (3.0f * dT + kU * (ext + mag) + (ext + 2.0f * dT) * el);
           sl[SDE + k] = (den > eden && de < 1e30f) ? de : __int_as_float(0x7f800000);
+          sl[SINV + k] = __frcp_rn(tz[j] - tz[i]);
         }
         sl[SRLO] = __int_as_float(r_lo);
         sl[SFLAGS] = __int_as_float(flags);

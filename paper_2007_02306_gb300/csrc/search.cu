@@ -178,6 +178,7 @@ __global__ void __launch_bounds__(kDenseThreads) k_dense(
     wrow[q][r] = act_s[q] ? w : 0;
   }
   __syncthreads();
+  __shared__ int tile_w[N];
   if (tid < N) {
     int W = 0;
     unsigned msk = 0;
@@ -187,14 +188,14 @@ __global__ void __launch_bounds__(kDenseThreads) k_dense(
       if (wrow[q][tid] > 0) msk |= 1u << q;
     }
     rmask[tid] = msk;
-    wrow[0][tid] = W;  // reuse row 0 of the table for the tile weight (read below after sync)
+    tile_w[tid] = W;
   }
   __syncthreads();
   if (tid < N) {
-    const int W = wrow[0][tid];
+    const int W = tile_w[tid];
     int rk = 0, nz = 0;
     for (int r2 = 0; r2 < N; ++r2) {
-      const int W2 = wrow[0][r2];
+      const int W2 = tile_w[r2];
       rk += (W2 > W) || (W2 == W && r2 < tid);
       nz += W2 > 0;
     }
@@ -236,18 +237,22 @@ __global__ void __launch_bounds__(kDenseThreads) k_dense(
 #pragma unroll
     for (int q = 0; q < kTQ; ++q) {
       if (__ballot_sync(0xffffffffu, (use >> q) & 1u) == 0) continue;
-      int s = 0;
+      // row sum of m (a - b)^2 = sum a^2 + sum (m b)^2 - 2 sum a b, with sum a^2 precomputed;
+      // two independent accumulator chains per term
+      int sbb0 = 0, sbb1 = 0, sab0 = 0, sab1 = 0;
+      const int4 *amq = reinterpret_cast<const int4 *>(&am[q][r * WPR]);
 #pragma unroll
-      for (int v = 0; v < WPR; ++v) {
-        int2 x = am[q][r * WPR + v];
-        int b = hw[v];
-        int bm = b & x.y;
-        s = __dp4a(x.x, x.x, s);
-        s = __dp4a(bm, bm, s);
-        s -= 2 * __dp4a(x.x, b, 0);
+      for (int v = 0; v < WPR; v += 2) {
+        const int4 x = amq[v >> 1];  // (a_v, m_v, a_v+1, m_v+1)
+        const int b0 = hw[v], b1 = hw[v + 1];
+        const int bm0 = b0 & x.y, bm1 = b1 & x.w;
+        sbb0 = __dp4a(bm0, bm0, sbb0);
+        sab0 = __dp4a(x.x, b0, sab0);
+        sbb1 = __dp4a(bm1, bm1, sbb1);
+        sab1 = __dp4a(x.z, b1, sab1);
       }
       if ((use >> q) & 1u) {
-        acc[q] += s;
+        acc[q] += wrow[q][r] + (sbb0 + sbb1) - 2 * (sab0 + sab1);
         if (acc[q] > thr_s[q]) alive &= ~(1u << q);
       }
     }
