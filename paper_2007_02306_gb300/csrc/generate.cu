@@ -302,17 +302,18 @@ __device__ __forceinline__ void project64(float px, float py, float pz, const do
 // FP64 evaluation of one (triangle, layer) with the definition's operation order.
 // Returns false when the triangle does not cross the layer; otherwise the single-crossing
 // columns are [lo, hi) and the double-crossing columns [dlo, lo).
-__device__ bool layer_fp64(const KArgs &a, const Shared &s, int rec, int r, int &lo, int &hi,
-                           int &dlo) {
-  const int N = a.N;
-  float4 r1 = a.rec[4 * (int64_t)rec + 1], r2 = a.rec[4 * (int64_t)rec + 2],
-         r3 = a.rec[4 * (int64_t)rec + 3];
+// (Plain pointer arguments: no structure has to live in local memory.)
+__device__ __forceinline__ bool layer_fp64(const float4 *__restrict__ recs, const double *fr,
+                                        const double *bd, const double *a2d, int N, int rec, int r,
+                                        int &lo, int &hi, int &dlo) {
+  float4 r1 = recs[4 * (int64_t)rec + 1], r2 = recs[4 * (int64_t)rec + 2],
+         r3 = recs[4 * (int64_t)rec + 3];
   double T[3][3];
-  project64(r1.x, r1.y, r1.z, s.fr, T[0]);
-  project64(r1.w, r2.x, r2.y, s.fr, T[1]);
-  project64(r2.z, r2.w, r3.x, s.fr, T[2]);
+  project64(r1.x, r1.y, r1.z, fr, T[0]);
+  project64(r1.w, r2.x, r2.y, fr, T[1]);
+  project64(r2.z, r2.w, r3.x, fr, T[2]);
   const int gid[3] = {__float_as_int(r3.y), __float_as_int(r3.z), __float_as_int(r3.w)};
-  const double beta = s.bd[r];
+  const double beta = bd[r];
   int s0 = T[0][2] >= beta, s1 = T[1][2] >= beta, s2 = T[2][2] >= beta;
   if (s0 == s1 && s1 == s2) return false;
   int lone = (s0 != s1 && s0 != s2) ? 0 : ((s1 != s0 && s1 != s2) ? 1 : 2);
@@ -332,7 +333,7 @@ __device__ bool layer_fp64(const KArgs &a, const Shared &s, int rec, int r, int 
   double E1x = swap ? Eax : Ebx, E1y = swap ? Eay : Eby;
   double e0 = __dadd_rn(__dmul_rn(E0x, E0x), __dmul_rn(E0y, E0y));
   double e1 = __dadd_rn(__dmul_rn(E1x, E1x), __dmul_rn(E1y, E1y));
-  int c0 = lower_count_d(e0, s.a2d, N), c1 = lower_count_d(e1, s.a2d, N);
+  int c0 = lower_count_d(e0, a2d, N), c1 = lower_count_d(e1, a2d, N);
   lo = min(c0, c1);
   hi = max(c0, c1);
   dlo = lo;
@@ -348,7 +349,7 @@ __device__ bool layer_fp64(const KArgs &a, const Shared &s, int rec, int r, int 
       int l = 0, h = lo;
       while (l < h) {
         int mid = (l + h) >> 1;
-        if (__dmul_rn(s.a2d[mid], dd) > cr2) h = mid; else l = mid + 1;
+        if (__dmul_rn(a2d[mid], dd) > cr2) h = mid; else l = mid + 1;
       }
       dlo = l;
     }
@@ -359,10 +360,10 @@ __device__ bool layer_fp64(const KArgs &a, const Shared &s, int rec, int r, int 
 // FP32 evaluation with forward error bounds against the FP64 definition.
 // Returns 0: no crossing, 1: intervals valid, 2: a predicate lies inside its error band
 // (the caller re-evaluates the item in FP64).
-__device__ __forceinline__ int layer_fp32(const KArgs &a, const Shared &s, const float *sl, int r,
-                                          float scale, int &lo, int &hi, int &dlo) {
-  const int N = a.N;
-  const float beta = s.bf[r];
+__device__ __forceinline__ int layer_fp32(const float *__restrict__ bf, const float *__restrict__ a2f,
+                                          int N, const float *sl, int r, float scale, int &lo,
+                                          int &hi, int &dlo) {
+  const float beta = bf[r];
   float tz0 = sl[SZ], tz1 = sl[SZ + 1], tz2 = sl[SZ + 2];
   int s0 = tz0 >= beta, s1 = tz1 >= beta, s2 = tz2 >= beta;
   if (s0 == s1 && s1 == s2) return 0;
@@ -397,12 +398,12 @@ __device__ __forceinline__ int layer_fp32(const KArgs &a, const Shared &s, const
   const float A1 = fabsf(E1x) + fabsf(E1y) + 2.0f * dE;
   const float de0 = kSafety * (2.0f * A0 * dE + 3.01f * kU * e0) + 1e-37f;
   const float de1 = kSafety * (2.0f * A1 * dE + 3.01f * kU * e1) + 1e-37f;
-  int c0 = lower_count_f(e0, s.a2f, N, scale), c1 = lower_count_f(e1, s.a2f, N, scale);
+  int c0 = lower_count_f(e0, a2f, N, scale), c1 = lower_count_f(e1, a2f, N, scale);
   // the two columns around each transition must be decided with certainty
-  if (c0 > 0 && e0 - s.a2f[c0 - 1] <= de0 + kU * s.a2f[c0 - 1]) return 2;
-  if (c0 < N && s.a2f[c0] - e0 <= de0 + kU * s.a2f[c0]) return 2;
-  if (c1 > 0 && e1 - s.a2f[c1 - 1] <= de1 + kU * s.a2f[c1 - 1]) return 2;
-  if (c1 < N && s.a2f[c1] - e1 <= de1 + kU * s.a2f[c1]) return 2;
+  if (c0 > 0 && e0 - a2f[c0 - 1] <= de0 + kU * a2f[c0 - 1]) return 2;
+  if (c0 < N && a2f[c0] - e0 <= de0 + kU * a2f[c0]) return 2;
+  if (c1 > 0 && e1 - a2f[c1 - 1] <= de1 + kU * a2f[c1 - 1]) return 2;
+  if (c1 < N && a2f[c1] - e1 <= de1 + kU * a2f[c1]) return 2;
   lo = min(c0, c1);
   hi = max(c0, c1);
   dlo = lo;
@@ -430,12 +431,12 @@ __device__ __forceinline__ int layer_fp32(const KArgs &a, const Shared &s, const
       const float dq = kSafety * (2.0f * h * dh + 2.0f * dh * dh + 4.0f * kU * h * A0 * rb +
                                   2.0f * kU * h2 * (1.0f + rb * rb)) + 1e-37f;
       if (!(dq < 1e30f)) return 2;
-      const int cs = lower_count_f(h2, s.a2f, N, scale);  // first column with alpha^2 > h^2
+      const int cs = lower_count_f(h2, a2f, N, scale);  // first column with alpha^2 > h^2
       if (cs >= lo) {
-        if (h2 - s.a2f[lo - 1] <= dq + kU * s.a2f[lo - 1]) return 2;
+        if (h2 - a2f[lo - 1] <= dq + kU * a2f[lo - 1]) return 2;
       } else {
-        if (cs > 0 && h2 - s.a2f[cs - 1] <= dq + kU * s.a2f[cs - 1]) return 2;
-        if (s.a2f[cs] - h2 <= dq + kU * s.a2f[cs]) return 2;
+        if (cs > 0 && h2 - a2f[cs - 1] <= dq + kU * a2f[cs - 1]) return 2;
+        if (a2f[cs] - h2 <= dq + kU * a2f[cs]) return 2;
         dlo = cs;
       }
     }
@@ -556,7 +557,8 @@ __global__ void __launch_bounds__(NW * 32) k_generate(KArgs a) {
     if (lane < cnt) {
       int lo = 0, hi = 0, dlo = 0;
       const int r = s.bq_r[lane];
-      if (layer_fp64(a, s, s.bq_rec[lane], r, lo, hi, dlo)) add_intervals(s.diff + r * N, N, lo, hi, dlo);
+      if (layer_fp64(a.rec, s.fr, s.bd, s.a2d, N, s.bq_rec[lane], r, lo, hi, dlo))
+        add_intervals(s.diff + r * N, N, lo, hi, dlo);
     }
     __syncwarp();
     const int rest = bn - cnt;
@@ -686,7 +688,7 @@ __global__ void __launch_bounds__(NW * 32) k_generate(KArgs a) {
         const int flags = __float_as_int(ts[SFLAGS]);
         bool band = (flags & kAll64) || r == __float_as_int(ts[SBAND]) ||
                     r == __float_as_int(ts[SBAND + 1]) || r == __float_as_int(ts[SBAND + 2]);
-        res = band ? 2 : layer_fp32(a, s, ts, r, scale, lo, hi, dlo);
+        res = band ? 2 : layer_fp32(s.bf, s.a2f, N, ts, r, scale, lo, hi, dlo);
         ++n_items;
       }
       // items inside the error band wait in the FP64 queue (evaluated 32 at a time)

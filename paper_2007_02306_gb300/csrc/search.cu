@@ -458,9 +458,10 @@ cudaError_t launch_dense(const int8_t *nd, const int8_t *nm, const int *nw, int6
 int64_t search_workspace_bytes(int64_t Q, int64_t H, int32_t N, int32_t mode) {
   const int64_t K = (int64_t)N * N;
   Carver c(nullptr);
-  c.take<int8_t>(Q * K);  // needle deltas
-  c.take<int8_t>(Q * K);  // needle masks
-  c.take<int8_t>(H * K);  // haystack deltas
+  const bool packed = !(mode == RICI_SEARCH_TENSOR && tc_supported(N));
+  c.take<int8_t>(packed ? Q * K : 0);  // needle deltas (packed CUDA-core form only)
+  c.take<int8_t>(packed ? Q * K : 0);  // needle masks
+  c.take<int8_t>(packed ? H * K : 0);  // haystack deltas
   c.take<int>(Q);         // needle wide flags
   c.take<int>(H);         // haystack wide flags
   c.take<int>(Q);         // wide needle list
@@ -481,9 +482,10 @@ cudaError_t launch_search(const SearchArgs &s, void *ws, cudaStream_t st) {
   const int64_t K = (int64_t)N * N;
   if (Q == 0) return cudaSuccess;
   Carver c(ws);
-  int8_t *nd = c.take<int8_t>(Q * K);
-  int8_t *nm = c.take<int8_t>(Q * K);
-  int8_t *hd = c.take<int8_t>(H * K);
+  const bool tensor = s.mode == RICI_SEARCH_TENSOR && tc_supported(N);
+  int8_t *nd = c.take<int8_t>(tensor ? 0 : Q * K);
+  int8_t *nm = c.take<int8_t>(tensor ? 0 : Q * K);
+  int8_t *hd = c.take<int8_t>(tensor ? 0 : H * K);
   int *nwide = c.take<int>(Q);
   int *hwide = c.take<int>(H);
   int *wn_list = c.take<int>(Q);
@@ -494,7 +496,6 @@ cudaError_t launch_search(const SearchArgs &s, void *ws, cudaStream_t st) {
   unsigned long long *best = c.take<unsigned long long>(Q);
   int64_t *dt_ws = c.take<int64_t>(Q);
   int32_t *top1_ws = c.take<int32_t>(Q);
-  const bool tensor = s.mode == RICI_SEARCH_TENSOR && tc_supported(N);
   char *tc_ws = tensor ? c.take<char>(tc_workspace_bytes(Q, H, N)) : nullptr;
   int64_t *dt = s.out_true_distance ? s.out_true_distance : dt_ws;
   int32_t *top1 = s.out_top1 ? s.out_top1 : top1_ws;

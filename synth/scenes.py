@@ -12,8 +12,8 @@ collection itself is replaced by displaced icospheres and tori):
 * ``tiny_scene``    one displaced icosphere, 2 subdivisions (162 vertices, 320 triangles).
 * ``clutter_scene`` a subdivision-5 target (20,480 triangles) plus 9 clutter meshes of
   5k-50k triangles (log-uniform), centres uniform in [-1,1]^3 (box side 2).
-* ``large_scene``   about 40 meshes totalling ~5M triangles, box side 4 with every
-  bounding sphere inside the box (centres in [-1,1]^3).
+* ``large_scene``   a subdivision-7 target plus meshes up to ~5M triangles in total (about 40
+  meshes), box side 4 with every bounding sphere inside the box (centres in [-1,1]^3).
 """
 from __future__ import annotations
 
@@ -102,17 +102,20 @@ def clutter_scene(seed: int = 2, target_subdivisions: int = 5, n_clutter: int = 
 
 def large_scene(seed: int = 5, total_triangles: int = 5_000_000, n_meshes: int = 40,
                 half_box: float = 1.0) -> Scene:
-    """~total_triangles over n_meshes displaced icospheres/tori (subdivision 6-7 sized)."""
+    """~total_triangles over about n_meshes meshes: a subdivision-7 target (163,842 vertices),
+    then displaced icospheres (subdivision 6) and tori of the remaining average size."""
     rng = np.random.Generator(np.random.PCG64(seed))
-    per = total_triangles / n_meshes
-    placed = []
-    for i in range(n_meshes):
-        if i == 0 or rng.random() < 0.5:
-            k = 6 if per < 2 * 81920 else 7
-            m = M.displaced_icosphere(rng, k)
+    placed = [_place(rng, M.displaced_icosphere(rng, 7), half_box)]
+    total = placed[0].num_triangles
+    while total < total_triangles:
+        left = max(1, n_meshes - len(placed))
+        per = max(20_000, (total_triangles - total) // left)
+        if rng.random() < 0.5 and per < 2 * 81920:
+            m = M.displaced_icosphere(rng, 6)
         else:
             m = M.displaced_torus(rng, int(per))
         placed.append(_place(rng, m, half_box))
+        total += m.num_triangles
     return assemble(placed)
 
 
