@@ -140,6 +140,56 @@ RICI_API int crss_search_ex(const uint16_t *needles, int64_t num_needles,
                             void *workspace, int64_t workspace_bytes, void *stream);
 
 /*
+ * Multi-scene calls (batched run).  Every scene of a batch is processed by the same kernel
+ * launches: one triangle binning pass, one generation grid over all scenes' oriented points,
+ * one persistent tensor-core search over all scenes' tiles.  A batch call enqueues a fixed
+ * sequence of kernels and copies, performs no host synchronisation and, with a caller
+ * workspace, no allocation, so the sequence can be recorded into a CUDA graph and replayed.
+ * The scene arrays are read on the host during the call only.
+ */
+typedef struct RiciGenerateScene {
+  const float *vertices;   /* [num_vertices][3] */
+  const float *normals;    /* [num_vertices][3] */
+  int64_t num_vertices;
+  const int32_t *triangles; /* [num_triangles][3] */
+  int64_t num_triangles;
+  const int32_t *origins;  /* [num_origins] vertex indices */
+  int64_t num_origins;
+  uint16_t *out_images;    /* [num_origins][N][N] */
+} RiciGenerateScene;
+
+/* Workspace for rici_generate_batch (-1 on invalid sizes). */
+RICI_API int64_t rici_generate_batch_workspace_size(const RiciGenerateScene *scenes,
+                                                    int32_t num_scenes, int32_t resolution);
+/* rici_generate for every scene of the batch (same R and N; results identical to one
+ * rici_generate call per scene). */
+RICI_API int rici_generate_batch(const RiciGenerateScene *scenes, int32_t num_scenes,
+                                 float support_radius, int32_t resolution, void *workspace,
+                                 int64_t workspace_bytes, void *stream);
+
+typedef struct RiciSearchScene {
+  const uint16_t *needles;   /* [num_needles][N][N] */
+  int64_t num_needles;
+  const uint16_t *haystack;  /* [num_haystack][N][N] */
+  int64_t num_haystack;
+  const int64_t *true_match; /* [num_needles] scene-local haystack indices, or NULL for i */
+  int32_t *out_rank;         /* [num_needles] */
+  int64_t *out_true_distance; /* [num_needles] or NULL */
+  int32_t *out_top1;         /* [num_needles] scene-local index, or NULL */
+} RiciSearchScene;
+
+/* Workspace for crss_search_batch (-1 on invalid sizes). */
+RICI_API int64_t crss_search_batch_workspace_size(const RiciSearchScene *scenes,
+                                                  int32_t num_scenes, int32_t resolution,
+                                                  int32_t mode);
+/* crss_search for every scene of the batch: each needle is ranked against its own scene's
+ * haystack only.  mode RICI_SEARCH_TENSOR (or DEFAULT) runs one persistent tensor-core launch
+ * over all scenes; other modes use the exact int64 kernel for multi-scene batches. */
+RICI_API int crss_search_batch(const RiciSearchScene *scenes, int32_t num_scenes,
+                               int32_t resolution, int32_t mode, void *workspace,
+                               int64_t workspace_bytes, void *stream);
+
+/*
  * rici_generate_noalloc — rici_generate for callers that must not allocate device memory.
  * (An addition of this library; the paper has no counterpart.)
  *

@@ -6,5 +6,6 @@ with ``paper_2007_02306_gb300.build.build()``.
 """
 from .binding import (  # noqa: F401
     GEN_DEFAULT, GEN_FP64, SEARCH_CUDA_CORE, SEARCH_DEFAULT, SEARCH_EXACT_SLOW, SEARCH_TENSOR, RiciError,
-    crss_search, load_library, rici_generate, sync_status, version,
+    crss_search, crss_search_batch, load_library, rici_generate, rici_generate_batch, sync_status,
+    version,
 )

@@ -37,6 +37,20 @@ _lib = None
 _workspaces: dict = {}
 
 
+class _GenScene(ctypes.Structure):
+    _fields_ = [("vertices", ctypes.c_void_p), ("normals", ctypes.c_void_p),
+                ("num_vertices", ctypes.c_int64), ("triangles", ctypes.c_void_p),
+                ("num_triangles", ctypes.c_int64), ("origins", ctypes.c_void_p),
+                ("num_origins", ctypes.c_int64), ("out_images", ctypes.c_void_p)]
+
+
+class _SearchScene(ctypes.Structure):
+    _fields_ = [("needles", ctypes.c_void_p), ("num_needles", ctypes.c_int64),
+                ("haystack", ctypes.c_void_p), ("num_haystack", ctypes.c_int64),
+                ("true_match", ctypes.c_void_p), ("out_rank", ctypes.c_void_p),
+                ("out_true_distance", ctypes.c_void_p), ("out_top1", ctypes.c_void_p)]
+
+
 class RiciError(RuntimeError):
     def __init__(self, code: int, message: str):
         super().__init__(f"librici error {code}: {message}")
@@ -73,6 +87,14 @@ def load_library(path: str | None = None):
         lib.crss_search_ex.restype = ctypes.c_int
         lib.rici_generate_noalloc.argtypes = [P, P, i64, P, i64, P, i64, f32, i32, P, P]
         lib.rici_generate_noalloc.restype = ctypes.c_int
+        lib.rici_generate_batch_workspace_size.argtypes = [P, i32, i32]
+        lib.rici_generate_batch_workspace_size.restype = i64
+        lib.rici_generate_batch.argtypes = [P, i32, f32, i32, P, i64, P]
+        lib.rici_generate_batch.restype = ctypes.c_int
+        lib.crss_search_batch_workspace_size.argtypes = [P, i32, i32, i32]
+        lib.crss_search_batch_workspace_size.restype = i64
+        lib.crss_search_batch.argtypes = [P, i32, i32, i32, P, i64, P]
+        lib.crss_search_batch.restype = ctypes.c_int
         lib.rici_sync_status.argtypes = [P, ctypes.POINTER(i32)]
         lib.rici_sync_status.restype = ctypes.c_int
         lib.rici_release_workspace.argtypes = []
@@ -198,6 +220,108 @@ def crss_search(needles, haystack, true_match=None, *, mode: int = SEARCH_DEFAUL
     if dist is not None:
         out["distances"] = dist
     return out
+
+
+def _ptr0(t):
+    return None if t is None else t.data_ptr()
+
+
+def rici_generate_batch(scenes, support_radius: float, resolution: int, *, workspace_tensor=None,
+                        stream=None):
+    """Generation for several scenes in one set of launches.
+
+    scenes: list of dicts with CUDA tensors "vertices" [V,3] f32, "normals" [V,3] f32,
+    "triangles" [T,3] i32, "origins" [O] i32 and optionally "out" uint16 [O,N,N].
+    Returns the list of output tensors.  workspace_tensor: optional uint8 CUDA tensor (kept by
+    the caller, e.g. for CUDA-graph replay); otherwise the cached per-device workspace is used.
+    """
+    lib = load_library()
+    N = int(resolution)
+    arr = (_GenScene * max(1, len(scenes)))()
+    outs = []
+    for k, sc in enumerate(scenes):
+        v = _need(sc["vertices"], torch.float32, "vertices", (3,))
+        n = _need(sc["normals"], torch.float32, "normals", (3,))
+        t = _need(sc["triangles"], torch.int32, "triangles", (3,))
+        o = _need(sc["origins"], torch.int32, "origins")
+        out = sc.get("out")
+        if out is None:
+            out = torch.empty((o.numel(), N, N), dtype=torch.uint16, device=v.device)
+        _need(out, torch.uint16, "out", (N, N))
+        outs.append(out)
+        arr[k] = _GenScene(_ptr0(v), _ptr0(n), v.shape[0], _ptr0(t), t.shape[0], _ptr0(o), o.numel(),
+                           _ptr0(out))
+    nb = lib.rici_generate_batch_workspace_size(arr, len(scenes), N)
+    if nb < 0:
+        _check(1)
+    dev = outs[0].device if outs else torch.device("cuda")
+    ws = workspace_tensor if workspace_tensor is not None else workspace(dev, nb)
+    if ws.numel() < nb:
+        raise ValueError(f"workspace_tensor needs {nb} bytes")
+    with torch.cuda.device(dev):
+        _check(lib.rici_generate_batch(arr, len(scenes), float(support_radius), N, _ptr(ws),
+                                       ws.numel(), _stream_handle(stream)))
+    return outs
+
+
+def generate_batch_workspace_bytes(scenes, resolution: int) -> int:
+    lib = load_library()
+    arr = (_GenScene * max(1, len(scenes)))()
+    for k, sc in enumerate(scenes):
+        arr[k] = _GenScene(_ptr0(sc["vertices"]), _ptr0(sc["normals"]), sc["vertices"].shape[0],
+                           _ptr0(sc["triangles"]), sc["triangles"].shape[0], _ptr0(sc["origins"]),
+                           sc["origins"].numel(), 1)
+    return int(lib.rici_generate_batch_workspace_size(arr, len(scenes), int(resolution)))
+
+
+def crss_search_batch(scenes, resolution: int, *, mode: int = SEARCH_TENSOR, workspace_tensor=None,
+                      outputs=None, stream=None):
+    """Search several scenes in one set of launches; each needle only against its scene.
+
+    scenes: list of dicts with "needles" uint16 [Q,N,N], "haystack" uint16 [H,N,N] and optional
+    "true_match" int64 [Q] (scene-local).  outputs: optional list of dicts of preallocated
+    "rank" / "true_distance" / "top1" tensors (needed to replay a captured graph).
+    """
+    lib = load_library()
+    N = int(resolution)
+    arr = (_SearchScene * max(1, len(scenes)))()
+    res = []
+    for k, sc in enumerate(scenes):
+        q = _need(sc["needles"], torch.uint16, "needles")
+        h = _need(sc["haystack"], torch.uint16, "haystack")
+        m = sc.get("true_match")
+        if m is not None:
+            _need(m, torch.int64, "true_match")
+        if outputs is not None:
+            r = outputs[k]
+        else:
+            Q = q.shape[0]
+            r = {"rank": torch.empty(Q, dtype=torch.int32, device=q.device),
+                 "true_distance": torch.empty(Q, dtype=torch.int64, device=q.device),
+                 "top1": torch.empty(Q, dtype=torch.int32, device=q.device)}
+        res.append(r)
+        arr[k] = _SearchScene(_ptr0(q), q.shape[0], _ptr0(h), h.shape[0], _ptr0(m),
+                              _ptr0(r["rank"]), _ptr0(r["true_distance"]), _ptr0(r["top1"]))
+    nb = lib.crss_search_batch_workspace_size(arr, len(scenes), N, int(mode))
+    if nb < 0:
+        _check(1)
+    dev = scenes[0]["needles"].device if scenes else torch.device("cuda")
+    ws = workspace_tensor if workspace_tensor is not None else workspace(dev, nb)
+    if ws.numel() < nb:
+        raise ValueError(f"workspace_tensor needs {nb} bytes")
+    with torch.cuda.device(dev):
+        _check(lib.crss_search_batch(arr, len(scenes), N, int(mode), _ptr(ws), ws.numel(),
+                                     _stream_handle(stream)))
+    return res
+
+
+def search_batch_workspace_bytes(scenes, resolution: int, mode: int = SEARCH_TENSOR) -> int:
+    lib = load_library()
+    arr = (_SearchScene * max(1, len(scenes)))()
+    for k, sc in enumerate(scenes):
+        arr[k] = _SearchScene(_ptr0(sc["needles"]), sc["needles"].shape[0], _ptr0(sc["haystack"]),
+                              sc["haystack"].shape[0], None, 1, None, None)
+    return int(lib.crss_search_batch_workspace_size(arr, len(scenes), int(resolution), int(mode)))
 
 
 def sync_status(stream=None) -> int:

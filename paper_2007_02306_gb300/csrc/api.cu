@@ -246,6 +246,165 @@ int crss_search(const uint16_t *needles, int64_t num_needles, const uint16_t *ha
                         workspace, workspace_bytes, stream);
 }
 
+// ---------------------------------------------------------------- batched calls
+
+static int build_gen_batch(const RiciGenerateScene *scenes, int32_t ns, int32_t N,
+                           std::vector<GenScene> *out, GenerateBatch *b) {
+  if (ns < 0 || (ns > 0 && !scenes)) return fail(RICI_ERR_INVALID_ARGUMENT, "bad scene array");
+  if (N < 1 || N > RICI_MAX_RESOLUTION)
+    return fail(RICI_ERR_INVALID_ARGUMENT, "resolution must be in [1, %d]", RICI_MAX_RESOLUTION);
+  out->resize(ns);
+  int64_t tri = 0, ori = 0, bkt = 0;
+  for (int32_t i = 0; i < ns; ++i) {
+    const RiciGenerateScene &g = scenes[i];
+    int rc = check_generate_args(g.vertices, g.normals, g.num_vertices, g.triangles,
+                                 g.num_triangles, g.origins, g.num_origins, 1.0f, N, g.out_images);
+    if (rc) return fail(rc, "scene %d: %s", (int)i, t_last_error.c_str());
+    GenScene &e = (*out)[i];
+    e = GenScene{};
+    e.V = g.vertices;
+    e.Nrm = g.normals;
+    e.tris = g.triangles;
+    e.origins = g.origins;
+    e.out = g.out_images;
+    e.nv = g.num_vertices;
+    e.nt = g.num_triangles;
+    e.no = g.num_origins;
+    e.tri_off = tri;
+    e.origin_off = ori;
+    e.bucket_off = bkt;
+    e.nbuckets = generate_bucket_count(g.num_triangles);
+    tri += g.num_triangles;
+    ori += g.num_origins;
+    bkt += (int64_t)e.nbuckets + 1;
+  }
+  if (tri > (int64_t(1) << 31) - 2 || bkt > (int64_t(1) << 31) - 2)
+    return fail(RICI_ERR_OUT_TOO_LARGE, "batch too large: %lld triangles", (long long)tri);
+  b->num_scenes = ns;
+  b->total_tris = tri;
+  b->total_origins = ori;
+  b->total_buckets = bkt;
+  b->N = N;
+  return RICI_OK;
+}
+
+int64_t rici_generate_batch_workspace_size(const RiciGenerateScene *scenes, int32_t num_scenes,
+                                           int32_t resolution) {
+  std::vector<GenScene> tab;
+  GenerateBatch b;
+  if (build_gen_batch(scenes, num_scenes, resolution, &tab, &b)) return -1;
+  return generate_batch_workspace_bytes(num_scenes > 0 ? num_scenes : 1, b.total_tris,
+                                        b.total_buckets);
+}
+
+int rici_generate_batch(const RiciGenerateScene *scenes, int32_t num_scenes, float support_radius,
+                        int32_t resolution, void *workspace, int64_t workspace_bytes,
+                        void *stream) {
+  t_last_error.clear();
+  if (!(support_radius > 0.0f) || !isfinite(support_radius))
+    return fail(RICI_ERR_INVALID_ARGUMENT, "support_radius must be positive and finite");
+  std::vector<GenScene> tab;
+  GenerateBatch b;
+  int rc = build_gen_batch(scenes, num_scenes, resolution, &tab, &b);
+  if (rc) return rc;
+  if (b.total_origins == 0) return RICI_OK;
+  DeviceState *d;
+  if ((rc = device_state(&d))) return rc;
+  void *ws;
+  if ((rc = resolve_workspace(d, workspace, workspace_bytes,
+                              generate_batch_workspace_bytes(num_scenes, b.total_tris,
+                                                             b.total_buckets),
+                              &ws)))
+    return rc;
+  b.R = support_radius;
+  b.mode = RICI_GEN_DEFAULT;
+  b.counters = nullptr;
+  b.status = d->status;
+  cudaError_t e = launch_generate_batch(tab.data(), b, ws, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "rici_generate_batch launch");
+  return RICI_OK;
+}
+
+static int build_search_batch(const RiciSearchScene *scenes, int32_t ns, int32_t N, int32_t mode,
+                              std::vector<SearchScene> *out, SearchBatch *b) {
+  if (ns < 0 || (ns > 0 && !scenes)) return fail(RICI_ERR_INVALID_ARGUMENT, "bad scene array");
+  if (N < 2 || N > RICI_MAX_RESOLUTION)
+    return fail(RICI_ERR_INVALID_ARGUMENT, "resolution must be in [2, %d]", RICI_MAX_RESOLUTION);
+  if (mode != RICI_SEARCH_DEFAULT && mode != RICI_SEARCH_CUDA_CORE &&
+      mode != RICI_SEARCH_EXACT_SLOW && mode != RICI_SEARCH_TENSOR)
+    return fail(RICI_ERR_INVALID_ARGUMENT, "unknown search mode %d", mode);
+  out->resize(ns);
+  int64_t q = 0, h = 0, hmax = 0, tiles = 0;
+  for (int32_t i = 0; i < ns; ++i) {
+    const RiciSearchScene &g = scenes[i];
+    if (g.num_needles < 0 || g.num_haystack < 0)
+      return fail(RICI_ERR_INVALID_ARGUMENT, "scene %d: negative count", (int)i);
+    if (g.num_needles > 0 && (g.num_haystack == 0 || !g.needles || !g.haystack || !g.out_rank))
+      return fail(RICI_ERR_INVALID_ARGUMENT, "scene %d: null buffer or empty haystack", (int)i);
+    SearchScene &e = (*out)[i];
+    e = SearchScene{};
+    e.needles = g.needles;
+    e.haystack = g.haystack;
+    e.match = g.true_match;
+    e.rank = g.out_rank;
+    e.dtrue = g.out_true_distance;
+    e.top1 = g.out_top1;
+    e.Q = g.num_needles;
+    e.H = g.num_needles > 0 ? g.num_haystack : 0;
+    e.qoff = q;
+    e.hoff = h;
+    e.tile_off = tiles;
+    search_tiles(e.Q, e.H, &e.tiles_m, &e.tiles_n);
+    if (e.Q == 0) e.tiles_m = e.tiles_n = 0;
+    q += e.Q;
+    h += e.H;
+    hmax = e.H > hmax ? e.H : hmax;
+    tiles += (int64_t)e.tiles_m * e.tiles_n;
+  }
+  if (q > (int64_t(1) << 31) - 1 || h > (int64_t(1) << 31) - 1)
+    return fail(RICI_ERR_OUT_TOO_LARGE, "more than 2^31-1 needles or haystack images in a batch");
+  b->num_scenes = ns;
+  b->Qtot = q;
+  b->Htot = h;
+  b->Hmax = hmax;
+  b->tiles_total = tiles;
+  b->N = N;
+  b->mode = mode == RICI_SEARCH_DEFAULT ? RICI_SEARCH_TENSOR : mode;
+  return RICI_OK;
+}
+
+int64_t crss_search_batch_workspace_size(const RiciSearchScene *scenes, int32_t num_scenes,
+                                         int32_t resolution, int32_t mode) {
+  std::vector<SearchScene> tab;
+  SearchBatch b;
+  if (build_search_batch(scenes, num_scenes, resolution, mode, &tab, &b)) return -1;
+  return search_batch_workspace_bytes(num_scenes > 0 ? num_scenes : 1, b.Qtot, b.Htot, resolution,
+                                      b.mode);
+}
+
+int crss_search_batch(const RiciSearchScene *scenes, int32_t num_scenes, int32_t resolution,
+                      int32_t mode, void *workspace, int64_t workspace_bytes, void *stream) {
+  t_last_error.clear();
+  std::vector<SearchScene> tab;
+  SearchBatch b;
+  int rc = build_search_batch(scenes, num_scenes, resolution, mode, &tab, &b);
+  if (rc) return rc;
+  if (b.Qtot == 0) return RICI_OK;
+  DeviceState *d;
+  if ((rc = device_state(&d))) return rc;
+  void *ws;
+  if ((rc = resolve_workspace(d, workspace, workspace_bytes,
+                              search_batch_workspace_bytes(num_scenes, b.Qtot, b.Htot, resolution,
+                                                           b.mode),
+                              &ws)))
+    return rc;
+  b.counters = nullptr;
+  b.status = d->status;
+  cudaError_t e = launch_search_batch(tab.data(), b, ws, static_cast<cudaStream_t>(stream), nullptr);
+  if (e != cudaSuccess) return cuda_fail(e, "crss_search_batch launch");
+  return RICI_OK;
+}
+
 int rici_sync_status(void *stream, int32_t *device_status) {
   DeviceState *d;
   int rc;

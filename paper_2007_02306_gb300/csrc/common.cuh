@@ -30,6 +30,37 @@ int64_t generate_workspace_bytes(int64_t num_triangles);
 // Enqueue generation on `stream` using `ws` (>= generate_workspace_bytes, 256-aligned).
 cudaError_t launch_generate(const GenerateArgs &a, void *ws, cudaStream_t stream);
 
+// One scene of a multi-scene generation launch (entry of the device scene table).
+struct GenScene {
+  const float *V;
+  const float *Nrm;
+  const int32_t *tris;
+  const int32_t *origins;
+  uint16_t *out;
+  int64_t nv, nt, no;
+  int64_t tri_off, origin_off, bucket_off;  // starts in the launch-wide index spaces
+  uint32_t nbuckets;  // hashed buckets (power of two); bucket_off + nbuckets is the big list
+  uint32_t pad_;
+};
+
+struct GenerateBatch {
+  int num_scenes;
+  int64_t total_tris, total_origins, total_buckets;
+  float R;
+  int N;
+  int mode;
+  int64_t *counters;
+  int *status;
+};
+
+// Hashed buckets used for a scene of nt triangles (a power of two).
+uint32_t generate_bucket_count(int64_t nt);
+int64_t generate_batch_workspace_bytes(int num_scenes, int64_t total_tris, int64_t total_buckets);
+// scenes: host array with every offset filled; the table is written to the workspace by kernels
+// (no host memory is referenced after the call returns).
+cudaError_t launch_generate_batch(const GenScene *scenes, const GenerateBatch &b, void *ws,
+                                  cudaStream_t stream);
+
 struct SearchArgs {
   const uint16_t *needles;
   int64_t num_needles;
@@ -50,12 +81,44 @@ int64_t search_workspace_bytes(int64_t num_needles, int64_t num_haystack, int32_
                                int32_t mode);
 cudaError_t launch_search(const SearchArgs &a, void *ws, cudaStream_t stream);
 
+// One scene of a multi-scene search (entry of the device scene table).  Needle i of the scene is
+// launch-wide needle qoff + i; haystack image j is launch-wide image hoff + j; top-1 indices and
+// true matches are scene-local.
+struct SearchScene {
+  const uint16_t *needles;
+  const uint16_t *haystack;
+  const int64_t *match;  // null: identity
+  int32_t *rank;
+  int64_t *dtrue;        // may be null
+  int32_t *top1;         // may be null
+  int64_t Q, H, qoff, hoff, tile_off;
+  int32_t tiles_m, tiles_n;
+};
+
+struct SearchBatch {
+  int num_scenes;
+  int64_t Qtot, Htot, Hmax, tiles_total;
+  int N;
+  int mode;
+  int64_t *counters;
+  int *status;
+};
+
+// Tensor-core tiles of a scene (128 needles x 256 haystack images).
+void search_tiles(int64_t Q, int64_t H, int32_t *tiles_m, int32_t *tiles_n);
+int64_t search_batch_workspace_bytes(int num_scenes, int64_t Qtot, int64_t Htot, int N, int mode);
+// scenes: host array with every offset filled (copied into the workspace by kernels).
+cudaError_t launch_search_batch(const SearchScene *scenes, const SearchBatch &b, void *ws,
+                                cudaStream_t stream, int64_t *out_distances);
+
 // Tensor-core search (tc_search.cu): operand encoding + persistent tcgen05 GEMM with the rank /
-// top-1 epilogue for narrow x narrow pairs.  Fills nwide/hwide and the wide lists/counts.
+// top-1 epilogue for narrow x narrow pairs of every scene.  Fills nwide/hwide and the wide
+// lists/counts (launch-wide indices).
 bool tc_supported(int N);
 int64_t tc_workspace_bytes(int64_t Q, int64_t H, int N);
-cudaError_t launch_tc_encode_and_rank(const uint16_t *needles, int64_t Q, const uint16_t *haystack,
-                                      int64_t H, int N, void *ws, int *nwide, int *hwide,
+cudaError_t launch_tc_encode_and_rank(const SearchScene *tab, int num_scenes, const int *qscene,
+                                      const int *hscene, int64_t Qtot, int64_t Htot,
+                                      int64_t tiles_total, int N, void *ws, int *nwide, int *hwide,
                                       int *wn_list, int *wh_list, int *counts,
                                       const int *nflags, const int64_t *dtrue, int *rank,
                                       unsigned long long *best, int *status, cudaStream_t st);

@@ -30,7 +30,6 @@ namespace {
 
 constexpr float kU = 5.9604644775390625e-08f;  // 2^-24: unit roundoff of FP32
 constexpr float kSafety = 2.0f;                // multiplies every derived error bound
-constexpr uint32_t kBig = 0xFFFFFFFFu;
 constexpr uint32_t kSkip = 0xFFFFFFFEu;
 constexpr float kCellClamp = 1048576.0f;  // |cell coordinate| limit (2^20)
 constexpr int kWarps = 4;
@@ -80,13 +79,35 @@ struct GridParams {
   uint32_t mask;
 };
 
-__global__ void k_tri_bin(const float *__restrict__ V, const int32_t *__restrict__ tri, int64_t nv,
-                          int64_t nt, GridParams g, int *__restrict__ counts,
-                          uint32_t *__restrict__ tb, int *__restrict__ ts, int *__restrict__ nbig,
-                          int *status) {
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nt;
+// Scene of a launch-wide index: the last table entry whose offset is <= idx (entries with no
+// items share their offset with the next one, so the match always owns idx).
+__device__ __forceinline__ int scene_of_tri(const GenScene *tab, int ns, int64_t idx) {
+  int lo = 0, hi = ns - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (tab[mid].tri_off <= idx) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__device__ __forceinline__ int scene_of_origin(const GenScene *tab, int ns, int64_t idx) {
+  int lo = 0, hi = ns - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (tab[mid].origin_off <= idx) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__global__ void k_tri_bin(const GenScene *__restrict__ tab, int ns, int64_t nt_total, GridParams g,
+                          int *__restrict__ counts, uint32_t *__restrict__ tb,
+                          int *__restrict__ ts, int *status) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nt_total;
        t += (int64_t)gridDim.x * blockDim.x) {
-    int id[3] = {tri[3 * t], tri[3 * t + 1], tri[3 * t + 2]};
+    const GenScene &sc = tab[scene_of_tri(tab, ns, t)];
+    const int64_t tl = t - sc.tri_off;
+    const int64_t nv = sc.nv;
+    int id[3] = {sc.tris[3 * tl], sc.tris[3 * tl + 1], sc.tris[3 * tl + 2]};
     if (id[0] < 0 || id[0] >= nv || id[1] < 0 || id[1] >= nv || id[2] < 0 || id[2] >= nv) {
       set_status(status, RICI_ERR_INDEX_OUT_OF_RANGE);
       tb[t] = kSkip;
@@ -96,7 +117,7 @@ __global__ void k_tri_bin(const float *__restrict__ V, const int32_t *__restrict
     bool fin = true;
     for (int k = 0; k < 3; ++k)
       for (int d = 0; d < 3; ++d) {
-        v[3 * k + d] = V[3 * (int64_t)id[k] + d];
+        v[3 * k + d] = sc.V[3 * (int64_t)id[k] + d];
         fin = fin && isfinite(v[3 * k + d]);
       }
     if (!fin) {
@@ -108,31 +129,30 @@ __global__ void k_tri_bin(const float *__restrict__ V, const int32_t *__restrict
     const float lim = kCellClamp - 4.0f;
     bool big = s.r > g.r_big || !(fabsf(s.cx * g.inv_cell) < lim) ||
                !(fabsf(s.cy * g.inv_cell) < lim) || !(fabsf(s.cz * g.inv_cell) < lim);
-    if (big) {
-      tb[t] = kBig;
-      ts[t] = atomicAdd(nbig, 1);
-    } else {
-      uint32_t b = cell_hash(cell_coord(s.cx, g.inv_cell), cell_coord(s.cy, g.inv_cell),
-                             cell_coord(s.cz, g.inv_cell), g.mask);
-      tb[t] = b;
-      ts[t] = atomicAdd(&counts[b], 1);
-    }
+    uint32_t b = sc.nbuckets;  // the scene's big list
+    if (!big)
+      b = cell_hash(cell_coord(s.cx, g.inv_cell), cell_coord(s.cy, g.inv_cell),
+                    cell_coord(s.cz, g.inv_cell), sc.nbuckets - 1);
+    const uint32_t gb = (uint32_t)(sc.bucket_off + b);
+    tb[t] = gb;
+    ts[t] = atomicAdd(&counts[gb], 1);
   }
 }
 
-__global__ void k_tri_scatter(const float *__restrict__ V, const int32_t *__restrict__ tri,
-                              int64_t nt, uint32_t nbuckets, const uint32_t *__restrict__ tb,
-                              const int *__restrict__ ts, const int *__restrict__ starts,
-                              float4 *__restrict__ rec) {
-  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nt;
+__global__ void k_tri_scatter(const GenScene *__restrict__ tab, int ns, int64_t nt_total,
+                              const uint32_t *__restrict__ tb, const int *__restrict__ ts,
+                              const int *__restrict__ starts, float4 *__restrict__ rec) {
+  for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nt_total;
        t += (int64_t)gridDim.x * blockDim.x) {
     uint32_t b = tb[t];
     if (b == kSkip) continue;
-    int64_t pos = (b == kBig ? (int64_t)starts[nbuckets] : (int64_t)starts[b]) + ts[t];
-    int id[3] = {tri[3 * t], tri[3 * t + 1], tri[3 * t + 2]};
+    const GenScene &sc = tab[scene_of_tri(tab, ns, t)];
+    const int64_t tl = t - sc.tri_off;
+    const int64_t pos = (int64_t)starts[b] + ts[t];
+    int id[3] = {sc.tris[3 * tl], sc.tris[3 * tl + 1], sc.tris[3 * tl + 2]};
     float v[9];
     for (int k = 0; k < 3; ++k)
-      for (int d = 0; d < 3; ++d) v[3 * k + d] = V[3 * (int64_t)id[k] + d];
+      for (int d = 0; d < 3; ++d) v[3 * k + d] = sc.V[3 * (int64_t)id[k] + d];
     TriSphere s = tri_sphere(v);
     rec[4 * pos + 0] = make_float4(s.cx, s.cy, s.cz, s.r);
     rec[4 * pos + 1] = make_float4(v[0], v[1], v[2], v[3]);
@@ -140,6 +160,16 @@ __global__ void k_tri_scatter(const float *__restrict__ V, const int32_t *__rest
     rec[4 * pos + 3] = make_float4(v[8], __int_as_float(id[0]), __int_as_float(id[1]),
                                    __int_as_float(id[2]));
   }
+}
+
+// Writes up to kFillChunk scene-table entries passed by value (no host memory is read later).
+constexpr int kFillChunk = 200;
+struct GenFill {
+  GenScene e[kFillChunk];
+  int n;
+};
+__global__ void k_fill_gen_table(GenScene *dst, GenFill f) {
+  for (int i = threadIdx.x; i < f.n; i += blockDim.x) dst[i] = f.e[i];
 }
 
 // ------------------------------------------------------------------ exclusive scan (int32)
@@ -225,20 +255,16 @@ __global__ void k_scan_final(const int *__restrict__ in, int64_t n, const int *_
 // ------------------------------------------------------------------ generation kernel
 
 struct KArgs {
-  const float *V;
-  const float *Nrm;
-  int64_t nv;
-  const int32_t *origins;
+  const GenScene *tab;
+  int num_scenes;
+  int64_t origin_base;  // first launch-wide origin index of this grid
   const float4 *rec;
   const int *starts;
-  const int *nbig;
-  uint32_t nbuckets;
   float inv_cell;
   float R;
   int N;
   float alpha_cull;  // pretest radius limit (alpha_{N-1} plus margin)
   float beta_cull;   // pretest height limit (beta_{N-1} plus margin)
-  uint16_t *out;
   int mode;
   unsigned long long *counters;
   int *status;
@@ -481,15 +507,21 @@ __global__ void __launch_bounds__(NW * 32) k_generate(KArgs a) {
     s.slots = reinterpret_cast<float *>(s.bq_r + 64);
   }
 
-  const int vid = a.origins[o];
-  if (vid < 0 || vid >= a.nv) {
+  const int64_t og = a.origin_base + o;  // launch-wide origin index
+  const GenScene &sc = a.tab[scene_of_origin(a.tab, a.num_scenes, og)];
+  const int64_t ol = og - sc.origin_off;  // origin index within its scene
+  const int vid = sc.origins[ol];
+  if (vid < 0 || vid >= sc.nv) {
     if (tid == 0) set_status(a.status, RICI_ERR_INDEX_OUT_OF_RANGE);
     return;
   }
-  const float Sx = a.V[3 * (int64_t)vid], Sy = a.V[3 * (int64_t)vid + 1],
-              Sz = a.V[3 * (int64_t)vid + 2];
-  const float nxf = a.Nrm[3 * (int64_t)vid], nyf = a.Nrm[3 * (int64_t)vid + 1],
-              nzf = a.Nrm[3 * (int64_t)vid + 2];
+  const float Sx = sc.V[3 * (int64_t)vid], Sy = sc.V[3 * (int64_t)vid + 1],
+              Sz = sc.V[3 * (int64_t)vid + 2];
+  const float nxf = sc.Nrm[3 * (int64_t)vid], nyf = sc.Nrm[3 * (int64_t)vid + 1],
+              nzf = sc.Nrm[3 * (int64_t)vid + 2];
+  const int64_t bucket_off = sc.bucket_off;
+  const uint32_t nbuckets = sc.nbuckets;
+  uint16_t *const out_img = sc.out + ol * (int64_t)N * N;
   if (!(isfinite(Sx) && isfinite(Sy) && isfinite(Sz) && isfinite(nxf) && isfinite(nyf) &&
         isfinite(nzf))) {
     if (tid == 0) set_status(a.status, RICI_ERR_NONFINITE_INPUT);
@@ -535,7 +567,7 @@ __global__ void __launch_bounds__(NW * 32) k_generate(KArgs a) {
     int ix = cell_coord(Sx, a.inv_cell) + tid % 3 - 1;
     int iy = cell_coord(Sy, a.inv_cell) + (tid / 3) % 3 - 1;
     int iz = cell_coord(Sz, a.inv_cell) + tid / 9 - 1;
-    s.buckets[tid] = (int)cell_hash(ix, iy, iz, a.nbuckets - 1);
+    s.buckets[tid] = (int)(bucket_off + cell_hash(ix, iy, iz, nbuckets - 1));
   }
   __syncthreads();
 
@@ -707,22 +739,18 @@ __global__ void __launch_bounds__(NW * 32) k_generate(KArgs a) {
     __syncwarp();
   };
 
-  // ---- stream candidates of the 27 neighbouring cells and the big list
-  const int64_t big_start = a.starts[a.nbuckets];
-  const int nbig = *a.nbig;
+  // ---- stream candidates of the 27 neighbouring cells and the scene's big list
   for (int nb = 0; nb < 28; ++nb) {
-    int64_t beg, end;
+    int64_t b;
     if (nb < 27) {
-      const int b = s.buckets[nb];
+      b = s.buckets[nb];
       bool dup = false;
       for (int k = 0; k < nb; ++k) dup = dup || (s.buckets[k] == b);
       if (dup) continue;
-      beg = a.starts[b];
-      end = a.starts[b + 1];
     } else {
-      beg = big_start;
-      end = big_start + nbig;
+      b = bucket_off + nbuckets;
     }
+    const int64_t beg = a.starts[b], end = a.starts[b + 1];
     for (int64_t base = beg + warp * 32; base < end; base += NW * 32) {
       const int64_t t = base + lane;
       bool pass = false;
@@ -772,7 +800,7 @@ __global__ void __launch_bounds__(NW * 32) k_generate(KArgs a) {
   __syncthreads();
 
   // ---- prefix-sum each row of the difference image, saturate, store uint16
-  uint16_t *out = a.out + o * (int64_t)N * N;
+  uint16_t *out = out_img;
   const int cpl = (N + 31) / 32;
   for (int r = warp; r < N; r += NW) {
     const int *row = s.diff + r * N;
@@ -804,35 +832,49 @@ size_t generate_smem_bytes(int N) {
 
 }  // namespace
 
-int64_t generate_workspace_bytes(int64_t num_triangles) {
-  const uint32_t B = bucket_count(num_triangles);
+uint32_t generate_bucket_count(int64_t nt) { return bucket_count(nt); }
+
+int64_t generate_batch_workspace_bytes(int num_scenes, int64_t total_tris, int64_t total_buckets) {
   Carver c(nullptr);
-  c.take<int>(B);                  // counts
-  c.take<int>((int64_t)B + 1);     // starts
-  c.take<int>(kScanItems + 1);     // scan partials
-  c.take<uint32_t>(num_triangles); // bucket of each triangle
-  c.take<int>(num_triangles);      // slot within its bucket
-  c.take<float4>(4 * num_triangles);
-  c.take<int>(4);                  // big-list length
+  c.take<GenScene>(num_scenes);
+  c.take<int>(total_buckets);          // counts
+  c.take<int>(total_buckets + 1);      // starts
+  c.take<int>(total_buckets / kScanItems + 2);  // scan partials
+  c.take<uint32_t>(total_tris);        // bucket of each triangle
+  c.take<int>(total_tris);             // slot within its bucket
+  c.take<float4>(4 * total_tris);      // records
   return c.off + 256;
 }
 
-cudaError_t launch_generate(const GenerateArgs &g, void *ws, cudaStream_t st) {
-  const int64_t nt = g.num_triangles;
-  const int N = g.resolution;
-  if (g.num_origins == 0) return cudaSuccess;
-  const uint32_t B = bucket_count(nt);
+int64_t generate_workspace_bytes(int64_t num_triangles) {
+  return generate_batch_workspace_bytes(1, num_triangles, (int64_t)bucket_count(num_triangles) + 1);
+}
+
+cudaError_t launch_generate_batch(const GenScene *scenes, const GenerateBatch &g, void *ws,
+                                  cudaStream_t st) {
+  const int N = g.N;
+  const int64_t nt = g.total_tris, TB = g.total_buckets;
+  if (g.total_origins == 0) return cudaSuccess;
   Carver c(ws);
-  int *counts = c.take<int>(B);
-  int *starts = c.take<int>((int64_t)B + 1);
-  int *partials = c.take<int>(kScanItems + 1);
+  GenScene *tab = c.take<GenScene>(g.num_scenes);
+  int *counts = c.take<int>(TB);
+  int *starts = c.take<int>(TB + 1);
+  int *partials = c.take<int>(TB / kScanItems + 2);
   uint32_t *tb = c.take<uint32_t>(nt);
   int *ts = c.take<int>(nt);
   float4 *rec = c.take<float4>(4 * nt);
-  int *nbig = c.take<int>(4);
+
+  cudaError_t e;
+  for (int s0 = 0; s0 < g.num_scenes; s0 += kFillChunk) {
+    GenFill f;
+    f.n = g.num_scenes - s0 < kFillChunk ? g.num_scenes - s0 : kFillChunk;
+    for (int i = 0; i < f.n; ++i) f.e[i] = scenes[s0 + i];
+    k_fill_gen_table<<<1, 256, 0, st>>>(tab + s0, f);
+    count_launches(1);
+  }
 
   // support cylinder: alpha <= alpha_{N-1}, |beta| <= beta_{N-1}; enclosing sphere radius
-  const double R = g.support_radius;
+  const double R = g.R;
   const double amax = R * (2.0 * N - 1.0) / (2.0 * N);
   const double bmax = R * (N - 1.0) / (2.0 * N);
   const double rho = sqrt(amax * amax + bmax * bmax) * (1.0 + 1.0 / 1024.0) + 1e-3 * R;
@@ -840,44 +882,36 @@ cudaError_t launch_generate(const GenerateArgs &g, void *ws, cudaStream_t st) {
   gp.r_big = (float)(0.25 * rho);
   const double cell = 1.25 * rho * 1.01;
   gp.inv_cell = (float)(1.0 / cell);
-  gp.mask = B - 1;
+  gp.mask = 0;
 
-  cudaError_t e;
-  if ((e = cudaMemsetAsync(counts, 0, sizeof(int) * B, st)) != cudaSuccess) return e;
-  if ((e = cudaMemsetAsync(nbig, 0, sizeof(int) * 4, st)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(counts, 0, sizeof(int) * TB, st)) != cudaSuccess) return e;
   const int tpb = 256;
   const int64_t want = (nt + tpb - 1) / tpb;
   const int grid = (int)(want < 152 * 32 ? (want > 0 ? want : 1) : 152 * 32);
   if (nt > 0) {
-    k_tri_bin<<<grid, tpb, 0, st>>>(g.vertices, g.triangles, g.num_vertices, nt, gp, counts, tb,
-                                     ts, nbig, g.status);
+    k_tri_bin<<<grid, tpb, 0, st>>>(tab, g.num_scenes, nt, gp, counts, tb, ts, g.status);
     count_launches(1);
   }
-  const int nb = (int)((B + kScanItems - 1) / kScanItems);
-  k_scan_partials<<<nb, 256, 0, st>>>(counts, B, partials);
+  const int nb = (int)((TB + kScanItems - 1) / kScanItems);
+  k_scan_partials<<<nb, 256, 0, st>>>(counts, TB, partials);
   k_scan_top<<<1, 1024, 0, st>>>(partials, nb);
-  k_scan_final<<<nb, 256, 0, st>>>(counts, B, partials, starts);
+  k_scan_final<<<nb, 256, 0, st>>>(counts, TB, partials, starts);
   count_launches(3);
   if (nt > 0) {
-    k_tri_scatter<<<grid, tpb, 0, st>>>(g.vertices, g.triangles, nt, B, tb, ts, starts, rec);
+    k_tri_scatter<<<grid, tpb, 0, st>>>(tab, g.num_scenes, nt, tb, ts, starts, rec);
     count_launches(1);
   }
 
   KArgs k;
-  k.V = g.vertices;
-  k.Nrm = g.normals;
-  k.nv = g.num_vertices;
-  k.origins = g.origins;
+  k.tab = tab;
+  k.num_scenes = g.num_scenes;
   k.rec = rec;
   k.starts = starts;
-  k.nbig = nbig;
-  k.nbuckets = B;
   k.inv_cell = gp.inv_cell;
-  k.R = g.support_radius;
+  k.R = g.R;
   k.N = N;
   k.alpha_cull = (float)(amax * (1.0 + 1.0 / 1024.0) + 1e-3 * R);
   k.beta_cull = (float)(bmax * (1.0 + 1.0 / 1024.0) + 1e-3 * R);
-  k.out = g.out_images;
   k.mode = g.mode;
   k.counters = reinterpret_cast<unsigned long long *>(g.counters);
   k.status = g.status;
@@ -885,15 +919,38 @@ cudaError_t launch_generate(const GenerateArgs &g, void *ws, cudaStream_t st) {
   if ((e = cudaFuncSetAttribute(k_generate<kWarps>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)smem)) != cudaSuccess)
     return e;
-  for (int64_t o0 = 0; o0 < g.num_origins; o0 += 0x7fffffff) {
-    const int64_t cnt = g.num_origins - o0 < 0x7fffffff ? g.num_origins - o0 : 0x7fffffff;
+  for (int64_t o0 = 0; o0 < g.total_origins; o0 += 0x7fffffff) {
+    const int64_t cnt = g.total_origins - o0 < 0x7fffffff ? g.total_origins - o0 : 0x7fffffff;
     KArgs kk = k;
-    kk.origins = g.origins + o0;
-    kk.out = g.out_images + o0 * (int64_t)N * N;
+    kk.origin_base = o0;
     k_generate<kWarps><<<(unsigned)cnt, kWarps * 32, smem, st>>>(kk);
     count_launches(1);
   }
   return cudaGetLastError();
+}
+
+cudaError_t launch_generate(const GenerateArgs &a, void *ws, cudaStream_t st) {
+  GenScene sc = {};
+  sc.V = a.vertices;
+  sc.Nrm = a.normals;
+  sc.tris = a.triangles;
+  sc.origins = a.origins;
+  sc.out = a.out_images;
+  sc.nv = a.num_vertices;
+  sc.nt = a.num_triangles;
+  sc.no = a.num_origins;
+  sc.nbuckets = bucket_count(a.num_triangles);
+  GenerateBatch b;
+  b.num_scenes = 1;
+  b.total_tris = a.num_triangles;
+  b.total_origins = a.num_origins;
+  b.total_buckets = (int64_t)sc.nbuckets + 1;
+  b.R = a.support_radius;
+  b.N = a.resolution;
+  b.mode = a.mode;
+  b.counters = a.counters;
+  b.status = a.status;
+  return launch_generate_batch(&sc, b, ws, st);
 }
 
 }  // namespace rici

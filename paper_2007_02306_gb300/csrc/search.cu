@@ -79,18 +79,19 @@ __device__ int64_t warp_crss(const uint16_t *n, const uint16_t *h, int N) {
   return __shfl_sync(0xffffffffu, s, 0);
 }
 
-__global__ void k_true_distance(const uint16_t *__restrict__ nd, int64_t Q,
-                                const uint16_t *__restrict__ hs, int64_t H, int N,
-                                const int64_t *__restrict__ match, int64_t *__restrict__ dtrue,
+__global__ void k_true_distance(const SearchScene *__restrict__ tab, const int *__restrict__ qscene,
+                                int64_t Qtot, int N, int64_t *__restrict__ dtrue,
                                 int *__restrict__ rank, unsigned long long *__restrict__ best,
                                 int *__restrict__ flags, int *status) {
   const int lane = threadIdx.x & 31;
   const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int64_t K = (int64_t)N * N;
-  for (int64_t i = w; i < Q; i += nw) {
-    const int64_t m = match ? match[i] : i;
-    if (m < 0 || m >= H) {
+  for (int64_t i = w; i < Qtot; i += nw) {
+    const SearchScene &sc = tab[qscene[i]];
+    const int64_t il = i - sc.qoff;
+    const int64_t m = sc.match ? sc.match[il] : il;
+    if (m < 0 || m >= sc.H) {
       if (lane == 0) {
         set_status(status, RICI_ERR_INDEX_OUT_OF_RANGE);
         dtrue[i] = -1;
@@ -100,7 +101,7 @@ __global__ void k_true_distance(const uint16_t *__restrict__ nd, int64_t Q,
       }
       continue;
     }
-    int64_t d = warp_crss(nd + i * K, hs + m * K, N);
+    int64_t d = warp_crss(sc.needles + il * K, sc.haystack + m * K, N);
     if (lane == 0) {
       dtrue[i] = d;
       rank[i] = 0;
@@ -108,6 +109,40 @@ __global__ void k_true_distance(const uint16_t *__restrict__ nd, int64_t Q,
       flags[i] = 0;
     }
   }
+}
+
+// Scene of every launch-wide needle and haystack image.
+__global__ void k_scene_index(const SearchScene *__restrict__ tab, int ns, int64_t Qtot,
+                              int64_t Htot, int *__restrict__ qscene, int *__restrict__ hscene) {
+  const int64_t n = Qtot > Htot ? Qtot : Htot;
+  for (int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; x < n;
+       x += (int64_t)gridDim.x * blockDim.x) {
+    if (x < Qtot) {
+      int lo = 0, hi = ns - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (tab[mid].qoff <= x) lo = mid; else hi = mid - 1;
+      }
+      qscene[x] = lo;
+    }
+    if (x < Htot) {
+      int lo = 0, hi = ns - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (tab[mid].hoff <= x) lo = mid; else hi = mid - 1;
+      }
+      hscene[x] = lo;
+    }
+  }
+}
+
+constexpr int kFillChunk = 150;
+struct SearchFill {
+  SearchScene e[kFillChunk];
+  int n;
+};
+__global__ void k_fill_search_table(SearchScene *dst, SearchFill f) {
+  for (int i = threadIdx.x; i < f.n; i += blockDim.x) dst[i] = f.e[i];
 }
 
 __device__ __forceinline__ unsigned long long pack_best(int64_t d, int64_t j) {
@@ -279,13 +314,15 @@ __global__ void __launch_bounds__(kDenseThreads) k_dense(
   }
 }
 
-// Pairs with a wide side, exact int64.  List mode:
-//   pass 0: needles = wide needle list, haystack = all.
-//   pass 1: needles = all needles that are not wide, haystack = wide haystack list.
-//   pass 2: needles = all needles, haystack = all (reference path).
+// Pairs with a wide side, exact int64 (launch-wide indices; haystack restricted to the needle's
+// scene).  List mode:
+//   pass 0: needles = wide needle list, haystack = the needle's whole scene.
+//   pass 1: needles = all needles that are not wide, haystack = wide images of the same scene.
+//   pass 2: needles = all needles, haystack = the whole scene (reference path).
 __global__ void __launch_bounds__(kWideThreads) k_wide(
-    const uint16_t *__restrict__ nimg, int64_t Q, const uint16_t *__restrict__ himg, int64_t H,
-    int N, int pass, const int *__restrict__ nwide, const int *__restrict__ wide_n_list,
+    const SearchScene *__restrict__ tab, const int *__restrict__ qscene,
+    const int *__restrict__ hscene, int64_t Qtot, int64_t Hmax, int N, int pass,
+    const int *__restrict__ nwide, const int *__restrict__ wide_n_list,
     const int *__restrict__ wide_n_count, const int *__restrict__ wide_h_list,
     const int *__restrict__ wide_h_count, const int64_t *__restrict__ dtrue,
     const int *__restrict__ nflags, int *__restrict__ rank, unsigned long long *__restrict__ best,
@@ -294,15 +331,19 @@ __global__ void __launch_bounds__(kWideThreads) k_wide(
   __shared__ int nnz_s;
   const int tid = threadIdx.x, lane = tid & 31;
   const int64_t K = (int64_t)N * N;
-  const int64_t nq = pass == 0 ? *wide_n_count : Q;
-  const int64_t nh = pass == 1 ? *wide_h_count : H;
+  const int64_t nq = pass == 0 ? *wide_n_count : Qtot;
+  const int64_t nh = pass == 1 ? *wide_h_count : Hmax;
   const int64_t chunks = (nh + kWideThreads - 1) / kWideThreads;
   const int64_t items = nq * chunks;
   for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
     const int64_t qi = it / chunks, ch = it - qi * chunks;
     const int64_t i = pass == 0 ? wide_n_list[qi] : qi;
     if (nflags[i] != 0 || (pass == 1 && nwide[i])) continue;  // uniform over the block
-    const uint16_t *n = nimg + i * K;
+    const int si = qscene[i];
+    const SearchScene &sc = tab[si];
+    if (pass != 1 && ch * kWideThreads >= sc.H) continue;     // uniform over the block
+    const int64_t il = i - sc.qoff;
+    const uint16_t *n = sc.needles + il * K;
     // compact the needle's non-zero deltas (row-major order)
     __syncthreads();
     if (tid == 0) nnz_s = 0;
@@ -324,13 +365,20 @@ __global__ void __launch_bounds__(kWideThreads) k_wide(
     const int nnz = nnz_s;
     const int64_t thr = dtrue[i];
     const int64_t hj = ch * kWideThreads + tid;
-    int64_t j = -1;
-    if (hj < nh) j = pass == 1 ? wide_h_list[hj] : hj;
+    int64_t jl = -1;  // scene-local haystack index
+    if (pass == 1) {
+      if (hj < nh) {
+        const int64_t jg = wide_h_list[hj];
+        if (hscene[jg] == si) jl = jg - sc.hoff;
+      }
+    } else if (hj < sc.H) {
+      jl = hj;
+    }
     int cnt = 0;
     unsigned long long b = kNoBest;
     unsigned long long npairs = 0, nterms = 0;
-    if (j >= 0) {
-      const uint16_t *h = himg + j * K;
+    if (jl >= 0) {
+      const uint16_t *h = sc.haystack + jl * K;
       long long acc = 0;
       int e = 0;
       for (; e < nnz && acc <= thr; ++e) {
@@ -342,7 +390,7 @@ __global__ void __launch_bounds__(kWideThreads) k_wide(
       nterms = e;
       if (acc <= thr) {
         cnt = acc < thr;
-        b = pack_best(acc, j);
+        b = pack_best(acc, jl);
         if (acc >= 0xffffffffll) atomicOr(&top1_flag[i], 1);
       }
     }
@@ -367,29 +415,39 @@ __global__ void __launch_bounds__(kWideThreads) k_wide(
   }
 }
 
-__global__ void k_finalize(int64_t Q, const unsigned long long *__restrict__ best,
-                           const int *__restrict__ nflags, int32_t *__restrict__ top1) {
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < Q;
+// Scene-local outputs: rank, true distance and top-1 (smallest index among minimal distances).
+__global__ void k_finalize(const SearchScene *__restrict__ tab, const int *__restrict__ qscene,
+                           int64_t Qtot, const int *__restrict__ rank,
+                           const int64_t *__restrict__ dtrue, const unsigned long long *__restrict__ best,
+                           const int *__restrict__ nflags) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < Qtot;
        i += (int64_t)gridDim.x * blockDim.x) {
-    top1[i] = (nflags[i] != 0 || best[i] == kNoBest) ? -1 : (int32_t)(uint32_t)(best[i] & 0xffffffffull);
+    const SearchScene &sc = tab[qscene[i]];
+    const int64_t il = i - sc.qoff;
+    sc.rank[il] = rank[i];
+    if (sc.dtrue) sc.dtrue[il] = dtrue[i];
+    if (sc.top1)
+      sc.top1[il] = (nflags[i] != 0 || best[i] == kNoBest)
+                        ? -1 : (int32_t)(uint32_t)(best[i] & 0xffffffffull);
   }
 }
 
-// Needles whose best distance reached 2^32-1: exact (distance, index) minimum over all j.
-__global__ void __launch_bounds__(256) k_top1_exact(const uint16_t *__restrict__ nimg, int64_t Q,
-                                                   const uint16_t *__restrict__ himg, int64_t H,
+// Needles whose best distance reached 2^32-1: exact (distance, index) minimum over the scene.
+__global__ void __launch_bounds__(256) k_top1_exact(const SearchScene *__restrict__ tab,
+                                                   const int *__restrict__ qscene, int64_t Qtot,
                                                    int N, const int *__restrict__ top1_flag,
-                                                   const int *__restrict__ nflags,
-                                                   int32_t *__restrict__ top1) {
+                                                   const int *__restrict__ nflags) {
   __shared__ long long bd[8];
   __shared__ long long bj[8];
   const int64_t K = (int64_t)N * N;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int64_t i = blockIdx.x; i < Q; i += gridDim.x) {
+  for (int64_t i = blockIdx.x; i < Qtot; i += gridDim.x) {
     if (!top1_flag[i] || nflags[i]) continue;
+    const SearchScene &sc = tab[qscene[i]];
+    const int64_t il = i - sc.qoff;
     long long md = 0x7fffffffffffffffll, mj = -1;
-    for (int64_t j = warp; j < H; j += 8) {
-      long long d = warp_crss(nimg + i * K, himg + j * K, N);
+    for (int64_t j = warp; j < sc.H; j += 8) {
+      long long d = warp_crss(sc.needles + il * K, sc.haystack + j * K, N);
       if (d < md) {
         md = d;
         mj = j;
@@ -407,7 +465,7 @@ __global__ void __launch_bounds__(256) k_top1_exact(const uint16_t *__restrict__
           d0 = bd[w];
           j0 = bj[w];
         }
-      top1[i] = (int32_t)j0;
+      if (sc.top1) sc.top1[il] = (int32_t)j0;
     }
     __syncthreads();
   }
@@ -455,37 +513,56 @@ cudaError_t launch_dense(const int8_t *nd, const int8_t *nm, const int *nw, int6
 
 }  // namespace
 
-int64_t search_workspace_bytes(int64_t Q, int64_t H, int32_t N, int32_t mode) {
+void search_tiles(int64_t Q, int64_t H, int32_t *tiles_m, int32_t *tiles_n) {
+  *tiles_m = (int32_t)((Q + 127) / 128);
+  *tiles_n = (int32_t)((H + 255) / 256);
+}
+
+int64_t search_batch_workspace_bytes(int num_scenes, int64_t Q, int64_t H, int N, int mode) {
   const int64_t K = (int64_t)N * N;
+  const bool tensor = mode == RICI_SEARCH_TENSOR && tc_supported(N);
+  const bool packed = !tensor && mode != RICI_SEARCH_EXACT_SLOW && dense_supported(N);
   Carver c(nullptr);
-  const bool packed = !(mode == RICI_SEARCH_TENSOR && tc_supported(N));
-  c.take<int8_t>(packed ? Q * K : 0);  // needle deltas (packed CUDA-core form only)
-  c.take<int8_t>(packed ? Q * K : 0);  // needle masks
-  c.take<int8_t>(packed ? H * K : 0);  // haystack deltas
-  c.take<int>(Q);         // needle wide flags
-  c.take<int>(H);         // haystack wide flags
-  c.take<int>(Q);         // wide needle list
-  c.take<int>(H);         // wide haystack list
-  c.take<int>(4);         // list lengths
-  c.take<int>(Q);         // per-needle state flags
-  c.take<int>(Q);         // top-1 exact fallback flags
-  c.take<unsigned long long>(Q);  // packed best (distance, index)
-  c.take<int64_t>(Q);     // true distance when the caller passes none
-  c.take<int32_t>(Q);     // top-1 when the caller passes none
-  if (mode == RICI_SEARCH_TENSOR && tc_supported(N)) c.take<char>(tc_workspace_bytes(Q, H, N));
+  c.take<SearchScene>(num_scenes);
+  c.take<int>(Q);                        // scene of each needle
+  c.take<int>(H);                        // scene of each haystack image
+  c.take<int8_t>(packed ? Q * K : 0);    // needle deltas (packed CUDA-core form only)
+  c.take<int8_t>(packed ? Q * K : 0);    // needle masks
+  c.take<int8_t>(packed ? H * K : 0);    // haystack deltas
+  c.take<int>(Q);                        // needle wide flags
+  c.take<int>(H);                        // haystack wide flags
+  c.take<int>(Q);                        // wide needle list
+  c.take<int>(H);                        // wide haystack list
+  c.take<int>(4);                        // list lengths
+  c.take<int>(Q);                        // per-needle state flags
+  c.take<int>(Q);                        // top-1 exact fallback flags
+  c.take<unsigned long long>(Q);         // packed best (distance, index)
+  c.take<int64_t>(Q);                    // true distances
+  c.take<int>(Q);                        // ranks
+  c.take<char>(tensor ? tc_workspace_bytes(Q, H, N) : 0);
   return c.off + 256;
 }
 
-cudaError_t launch_search(const SearchArgs &s, void *ws, cudaStream_t st) {
-  const int64_t Q = s.num_needles, H = s.num_haystack;
-  const int N = s.resolution;
+int64_t search_workspace_bytes(int64_t Q, int64_t H, int32_t N, int32_t mode) {
+  return search_batch_workspace_bytes(1, Q, H, N, mode);
+}
+
+cudaError_t launch_search_batch(const SearchScene *scenes, const SearchBatch &b, void *ws,
+                                cudaStream_t st, int64_t *out_distances) {
+  const int64_t Q = b.Qtot, H = b.Htot;
+  const int N = b.N;
   const int64_t K = (int64_t)N * N;
   if (Q == 0) return cudaSuccess;
+  const bool tensor = b.mode == RICI_SEARCH_TENSOR && tc_supported(N);
+  const bool dense = !tensor && b.mode != RICI_SEARCH_EXACT_SLOW && dense_supported(N) &&
+                     b.num_scenes == 1;
   Carver c(ws);
-  const bool tensor = s.mode == RICI_SEARCH_TENSOR && tc_supported(N);
-  int8_t *nd = c.take<int8_t>(tensor ? 0 : Q * K);
-  int8_t *nm = c.take<int8_t>(tensor ? 0 : Q * K);
-  int8_t *hd = c.take<int8_t>(tensor ? 0 : H * K);
+  SearchScene *tab = c.take<SearchScene>(b.num_scenes);
+  int *qscene = c.take<int>(Q);
+  int *hscene = c.take<int>(H);
+  int8_t *nd = c.take<int8_t>(dense ? Q * K : 0);
+  int8_t *nm = c.take<int8_t>(dense ? Q * K : 0);
+  int8_t *hd = c.take<int8_t>(dense ? H * K : 0);
   int *nwide = c.take<int>(Q);
   int *hwide = c.take<int>(H);
   int *wn_list = c.take<int>(Q);
@@ -494,76 +571,104 @@ cudaError_t launch_search(const SearchArgs &s, void *ws, cudaStream_t st) {
   int *nflags = c.take<int>(Q);
   int *t1flag = c.take<int>(Q);
   unsigned long long *best = c.take<unsigned long long>(Q);
-  int64_t *dt_ws = c.take<int64_t>(Q);
-  int32_t *top1_ws = c.take<int32_t>(Q);
+  int64_t *dt = c.take<int64_t>(Q);
+  int *rank = c.take<int>(Q);
   char *tc_ws = tensor ? c.take<char>(tc_workspace_bytes(Q, H, N)) : nullptr;
-  int64_t *dt = s.out_true_distance ? s.out_true_distance : dt_ws;
-  int32_t *top1 = s.out_top1 ? s.out_top1 : top1_ws;
 
   cudaError_t e;
+  for (int s0 = 0; s0 < b.num_scenes; s0 += kFillChunk) {
+    SearchFill f;
+    f.n = b.num_scenes - s0 < kFillChunk ? b.num_scenes - s0 : kFillChunk;
+    for (int i = 0; i < f.n; ++i) f.e[i] = scenes[s0 + i];
+    k_fill_search_table<<<1, 256, 0, st>>>(tab + s0, f);
+    count_launches(1);
+  }
   if ((e = cudaMemsetAsync(counts, 0, sizeof(int) * 4, st)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(t1flag, 0, sizeof(int) * Q, st)) != cudaSuccess) return e;
   const int wpb = 8;
   auto blocks_for = [&](int64_t items) {
-    int64_t b = (items + wpb - 1) / wpb;
-    return (int)(b < 152 * 64 ? (b > 0 ? b : 1) : 152 * 64);
+    int64_t nb = (items + wpb - 1) / wpb;
+    return (int)(nb < 152 * 64 ? (nb > 0 ? nb : 1) : 152 * 64);
   };
-  k_true_distance<<<blocks_for(Q), 32 * wpb, 0, st>>>(s.needles, Q, s.haystack, H, N,
-                                                       s.true_match, dt, s.out_rank, best, nflags,
-                                                       s.status);
-  count_launches(1);
-  const bool dense = !tensor && s.mode != RICI_SEARCH_EXACT_SLOW && dense_supported(N);
-  unsigned long long *cnt = reinterpret_cast<unsigned long long *>(s.counters);
+  k_scene_index<<<blocks_for((Q > H ? Q : H) / 32 + 1), 256, 0, st>>>(tab, b.num_scenes, Q, H,
+                                                                      qscene, hscene);
+  k_true_distance<<<blocks_for(Q), 32 * wpb, 0, st>>>(tab, qscene, Q, N, dt, rank, best, nflags,
+                                                       b.status);
+  count_launches(2);
+  unsigned long long *cnt = reinterpret_cast<unsigned long long *>(b.counters);
   const size_t wide_smem = sizeof(int2) * (size_t)K;
   if ((e = cudaFuncSetAttribute(k_wide, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)wide_smem)) != cudaSuccess)
     return e;
+  auto wide = [&](int pass) {
+    k_wide<<<152 * 8, kWideThreads, wide_smem, st>>>(tab, qscene, hscene, Q, b.Hmax, N, pass,
+                                                   nwide, wn_list, counts + 0, wh_list,
+                                                   counts + 1, dt, nflags, rank, best, t1flag, cnt);
+    count_launches(1);
+  };
   if (tensor) {
-    if ((e = launch_tc_encode_and_rank(s.needles, Q, s.haystack, H, N, tc_ws, nwide, hwide,
-                                       wn_list, wh_list, counts, nflags, dt, s.out_rank, best,
-                                       s.status, st)) != cudaSuccess)
+    if ((e = launch_tc_encode_and_rank(tab, b.num_scenes, qscene, hscene, Q, H, b.tiles_total, N,
+                                       tc_ws, nwide, hwide, wn_list, wh_list, counts, nflags, dt,
+                                       rank, best, b.status, st)) != cudaSuccess)
       return e;
-    for (int pass = 0; pass < 2; ++pass)
-      k_wide<<<152 * 8, kWideThreads, wide_smem, st>>>(s.needles, Q, s.haystack, H, N, pass, nwide,
-                                                     wn_list, counts + 0, wh_list, counts + 1, dt,
-                                                     nflags, s.out_rank, best, t1flag, cnt);
-    count_launches(2);
+    wide(0);
+    wide(1);
   } else if (dense) {
-    k_encode<<<blocks_for(Q), 32 * wpb, 0, st>>>(s.needles, Q, N, nd, nm, nwide, wn_list,
+    // single scene: launch-wide indices are the scene's own
+    const SearchScene &s0 = scenes[0];
+    k_encode<<<blocks_for(Q), 32 * wpb, 0, st>>>(s0.needles, Q, N, nd, nm, nwide, wn_list,
                                                  counts + 0);
-    k_encode<<<blocks_for(H), 32 * wpb, 0, st>>>(s.haystack, H, N, hd, nullptr, hwide, wh_list,
+    k_encode<<<blocks_for(H), 32 * wpb, 0, st>>>(s0.haystack, H, N, hd, nullptr, hwide, wh_list,
                                                  counts + 1);
     count_launches(2);
     switch (N) {
-      case 8: e = launch_dense<8>(nd, nm, nwide, Q, hd, hwide, H, dt, nflags, s.out_rank, best, cnt, st); break;
-      case 16: e = launch_dense<16>(nd, nm, nwide, Q, hd, hwide, H, dt, nflags, s.out_rank, best, cnt, st); break;
-      case 32: e = launch_dense<32>(nd, nm, nwide, Q, hd, hwide, H, dt, nflags, s.out_rank, best, cnt, st); break;
-      case 64: e = launch_dense<64>(nd, nm, nwide, Q, hd, hwide, H, dt, nflags, s.out_rank, best, cnt, st); break;
-      default: e = launch_dense<128>(nd, nm, nwide, Q, hd, hwide, H, dt, nflags, s.out_rank, best, cnt, st); break;
+      case 8: e = launch_dense<8>(nd, nm, nwide, Q, hd, hwide, H, dt, nflags, rank, best, cnt, st); break;
+      case 16: e = launch_dense<16>(nd, nm, nwide, Q, hd, hwide, H, dt, nflags, rank, best, cnt, st); break;
+      case 32: e = launch_dense<32>(nd, nm, nwide, Q, hd, hwide, H, dt, nflags, rank, best, cnt, st); break;
+      case 64: e = launch_dense<64>(nd, nm, nwide, Q, hd, hwide, H, dt, nflags, rank, best, cnt, st); break;
+      default: e = launch_dense<128>(nd, nm, nwide, Q, hd, hwide, H, dt, nflags, rank, best, cnt, st); break;
     }
     if (e != cudaSuccess) return e;
-    for (int pass = 0; pass < 2; ++pass)
-      k_wide<<<152 * 8, kWideThreads, wide_smem, st>>>(s.needles, Q, s.haystack, H, N, pass, nwide,
-                                                     wn_list, counts + 0, wh_list, counts + 1, dt,
-                                                     nflags, s.out_rank, best, t1flag, cnt);
-    count_launches(2);
+    wide(0);
+    wide(1);
   } else {
     if ((e = cudaMemsetAsync(nwide, 0, sizeof(int) * Q, st)) != cudaSuccess) return e;
-    k_wide<<<152 * 8, kWideThreads, wide_smem, st>>>(s.needles, Q, s.haystack, H, N, 2, nwide,
-                                                   wn_list, counts + 0, wh_list, counts + 1, dt,
-                                                   nflags, s.out_rank, best, t1flag, cnt);
-    count_launches(1);
+    wide(2);
   }
-  k_finalize<<<blocks_for(Q * wpb), 256, 0, st>>>(Q, best, nflags, top1);
-  k_top1_exact<<<(int)(Q < 152 * 8 ? Q : 152 * 8), 256, 0, st>>>(s.needles, Q, s.haystack, H, N,
-                                                                 t1flag, nflags, top1);
+  k_finalize<<<blocks_for(Q * wpb), 256, 0, st>>>(tab, qscene, Q, rank, dt, best, nflags);
+  k_top1_exact<<<(int)(Q < 152 * 8 ? Q : 152 * 8), 256, 0, st>>>(tab, qscene, Q, N, t1flag,
+                                                                 nflags);
   count_launches(2);
-  if (s.out_distances) {
-    k_distances<<<blocks_for(Q * H), 32 * wpb, 0, st>>>(s.needles, Q, s.haystack, H, N,
-                                                         s.out_distances);
+  if (out_distances && b.num_scenes == 1) {
+    k_distances<<<blocks_for(Q * H), 32 * wpb, 0, st>>>(scenes[0].needles, Q, scenes[0].haystack,
+                                                         H, N, out_distances);
     count_launches(1);
   }
   return cudaGetLastError();
+}
+
+cudaError_t launch_search(const SearchArgs &a, void *ws, cudaStream_t st) {
+  SearchScene sc = {};
+  sc.needles = a.needles;
+  sc.haystack = a.haystack;
+  sc.match = a.true_match;
+  sc.rank = a.out_rank;
+  sc.dtrue = a.out_true_distance;
+  sc.top1 = a.out_top1;
+  sc.Q = a.num_needles;
+  sc.H = a.num_haystack;
+  search_tiles(sc.Q, sc.H, &sc.tiles_m, &sc.tiles_n);
+  SearchBatch b;
+  b.num_scenes = 1;
+  b.Qtot = sc.Q;
+  b.Htot = sc.H;
+  b.Hmax = sc.H;
+  b.tiles_total = (int64_t)sc.tiles_m * sc.tiles_n;
+  b.N = a.resolution;
+  b.mode = a.mode;
+  b.counters = a.counters;
+  b.status = a.status;
+  return launch_search_batch(&sc, b, ws, st, a.out_distances);
 }
 
 }  // namespace rici

@@ -157,18 +157,22 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
 
 // ---------------------------------------------------------------- operand encoding (S2)
 
-// One warp per image.  Needle rows: [m | a]; haystack rows: [b^2 | -2b] (fp16, K = 2 N^2).
-// Also: narrow flag (all |delta| <= kNarrow), list of wide images, and for needles A_i.
-__global__ void k_tc_encode(const uint16_t *__restrict__ imgs, int64_t n, int N, int needle_side,
-                            __half *__restrict__ op, int *__restrict__ wide_flag,
-                            int *__restrict__ wide_list, int *__restrict__ wide_count,
-                            int *__restrict__ asum, uint32_t *__restrict__ valid_mask) {
+// One warp per image (launch-wide index).  Needle rows: [m | a]; haystack rows: [b^2 | -2b]
+// (fp16, K = 2 N^2).  Also: narrow flag (all |delta| <= kNarrow), list of wide images, and for
+// needles A_i.
+__global__ void k_tc_encode(const SearchScene *__restrict__ tab, const int *__restrict__ scene_of,
+                            int64_t n, int N, int needle_side, __half *__restrict__ op,
+                            int *__restrict__ wide_flag, int *__restrict__ wide_list,
+                            int *__restrict__ wide_count, int *__restrict__ asum,
+                            uint32_t *__restrict__ valid_mask) {
   const int lane = threadIdx.x & 31;
   const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int K0 = N * N;
   for (int64_t i = w; i < n; i += nw) {
-    const uint16_t *img = imgs + i * K0;
+    const SearchScene &sc = tab[scene_of[i]];
+    const uint16_t *img = needle_side ? sc.needles + (i - sc.qoff) * K0
+                                      : sc.haystack + (i - sc.hoff) * K0;
     __half *row = op + i * (int64_t)(2 * K0);
     int wide = 0, a2 = 0;
     for (int k0 = lane * 8; k0 < K0; k0 += 32 * 8) {
@@ -208,7 +212,9 @@ __global__ void k_tc_encode(const uint16_t *__restrict__ imgs, int64_t n, int N,
 // ---------------------------------------------------------------- GEMM + rank epilogue (S3, S5)
 
 struct TcArgs {
-  int64_t Q, H;
+  const SearchScene *tab;
+  int num_scenes;
+  int64_t tiles;                  // all scenes' tiles
   int KT;                         // 2 N^2
   const int *nwide;               // needle wide flags (TC class)
   const int *nflags;              // per-needle state (0 = searchable)
@@ -220,18 +226,34 @@ struct TcArgs {
   int *status;
 };
 
+// A tile of one scene: needle rows [qbeg + 128 m, ...), haystack columns [hbeg + 256 n, ...),
+// valid for scene-local rows < Q and columns < H.
 struct TcTile {
-  int m, n;
+  int64_t m, n;          // tile coordinates within the scene
+  int64_t qbeg, hbeg;    // scene offsets in the launch-wide needle / haystack arrays
+  int64_t Q, H;
 };
 
-__device__ __forceinline__ TcTile tile_of(int64_t t, int tiles_m, int tiles_n) {
+__device__ __forceinline__ TcTile tile_of(const SearchScene *tab, int ns, int64_t t) {
+  int lo = 0, hi = ns - 1;
+  while (lo < hi) {  // last scene whose first tile is <= t (empty scenes own no tile)
+    const int mid = (lo + hi + 1) >> 1;
+    if (tab[mid].tile_off <= t) lo = mid; else hi = mid - 1;
+  }
+  const SearchScene &sc = tab[lo];
+  const int64_t tl = t - sc.tile_off;
+  const int tiles_m = sc.tiles_m, tiles_n = sc.tiles_n;
   const int64_t per_group = (int64_t)kGroupM * tiles_n;
-  const int g = (int)(t / per_group);
-  const int r = (int)(t - (int64_t)g * per_group);
-  const int gm = min(kGroupM, tiles_m - g * kGroupM);
+  const int64_t g = tl / per_group;
+  const int64_t r = tl - g * per_group;
+  const int64_t gm = min((int64_t)kGroupM, (int64_t)tiles_m - g * kGroupM);
   TcTile tt;
   tt.n = r / gm;
   tt.m = g * kGroupM + r % gm;
+  tt.qbeg = sc.qoff;
+  tt.hbeg = sc.hoff;
+  tt.Q = sc.Q;
+  tt.H = sc.H;
   return tt;
 }
 
@@ -252,9 +274,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   int *abort_flag = reinterpret_cast<int *>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int tiles_m = (int)((a.Q + kBM - 1) / kBM);
-  const int tiles_n = (int)((a.H + kBN - 1) / kBN);
-  const int64_t tiles = (int64_t)tiles_m * tiles_n;
+  const int64_t tiles = a.tiles;
   const int kblocks = a.KT / kBK;
 
   if (threadIdx.x == 0) {
@@ -286,7 +306,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       uint32_t it = 0;
       bool ok = true;
       for (int64_t t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
-        const TcTile tt = tile_of(t, tiles_m, tiles_n);
+        const TcTile tt = tile_of(a.tab, a.num_scenes, t);
+        const int ya = (int)(tt.qbeg + tt.m * kBM), yb = (int)(tt.hbeg + tt.n * kBN);
         for (int kb = 0; kb < kblocks; ++kb, ++it) {
           const uint32_t s = it % kStages, round = it / kStages;
           if (!mbar_wait(&empty[s], (round & 1) ^ 1, a.status, abort_flag)) {
@@ -294,8 +315,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             break;
           }
           mbar_arrive_expect_tx(&full[s], kStageA + kStageB);
-          tma_load_2d(sA + s * kStageA, &map_a, &full[s], kb * kBK, tt.m * kBM);
-          tma_load_2d(sB + s * kStageB, &map_b, &full[s], kb * kBK, tt.n * kBN);
+          tma_load_2d(sA + s * kStageA, &map_a, &full[s], kb * kBK, ya);
+          tma_load_2d(sB + s * kStageB, &map_b, &full[s], kb * kBK, yb);
         }
       }
     }
@@ -333,14 +354,15 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const int row = quarter * 32 + lane;
     uint32_t lt = 0;
     for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x, ++lt) {
-      const TcTile tt = tile_of(t, tiles_m, tiles_n);
+      const TcTile tt = tile_of(a.tab, a.num_scenes, t);
       const uint32_t buf = lt & 1, use = lt >> 1;
       // warp-uniform outcome before the .sync.aligned TMEM loads
       const bool ready = __all_sync(0xffffffffu, mbar_wait(&tfull[buf], use & 1, a.status, abort_flag));
       if (!ready) break;
       tc_fence_after();
-      const int64_t i = (int64_t)tt.m * kBM + row;
-      const bool row_ok = i < a.Q && a.nflags[i] == 0 && !a.nwide[i];
+      const int64_t il = tt.m * kBM + row;  // scene-local needle
+      const int64_t i = tt.qbeg + il;         // launch-wide needle
+      const bool row_ok = il < tt.Q && a.nflags[i] == 0 && !a.nwide[i];
       float thr = 0.0f;
       int64_t asum = 0, thr_i = 0;
       if (row_ok) {
@@ -356,11 +378,14 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       for (int c0 = 0; c0 < kBN; c0 += 32) {
         uint32_t v[32];
         tmem_ld32(taddr + c0, v);
-        const int64_t j0 = (int64_t)tt.n * kBN + c0;
-        uint32_t vm = 0;  // bit e: column j0 + e is a narrow haystack image
-        if (row_ok && j0 < a.H) {
-          vm = a.hvalid[j0 >> 5];  // j0 is a multiple of 32
-          const int64_t rem = a.H - j0;
+        const int64_t j0 = tt.n * kBN + c0;  // scene-local haystack column
+        uint32_t vm = 0;  // bit e: column j0 + e is a narrow haystack image of this scene
+        if (row_ok && j0 < tt.H) {
+          const int64_t g0 = tt.hbeg + j0;   // launch-wide index (any alignment)
+          const uint32_t lo = a.hvalid[g0 >> 5], hi = a.hvalid[(g0 >> 5) + 1];
+          const int sh = (int)(g0 & 31);
+          vm = sh ? (lo >> sh) | (hi << (32 - sh)) : lo;
+          const int64_t rem = tt.H - j0;
           if (rem < 32) vm &= (1u << rem) - 1u;
         }
 #pragma unroll
@@ -428,12 +453,13 @@ int64_t tc_workspace_bytes(int64_t Q, int64_t H, int N) {
   c.take<__half>(Q * KT);
   c.take<__half>(H * KT);
   c.take<int>(Q);                 // A_i
-  c.take<uint32_t>((H + 31) / 32 + 1);
+  c.take<uint32_t>((H + 31) / 32 + 2);
   return c.off + 256;
 }
 
-cudaError_t launch_tc_encode_and_rank(const uint16_t *needles, int64_t Q, const uint16_t *haystack,
-                                      int64_t H, int N, void *ws, int *nwide, int *hwide,
+cudaError_t launch_tc_encode_and_rank(const SearchScene *tab, int num_scenes, const int *qscene,
+                                      const int *hscene, int64_t Q, int64_t H,
+                                      int64_t tiles_total, int N, void *ws, int *nwide, int *hwide,
                                       int *wn_list, int *wh_list, int *counts,
                                       const int *nflags, const int64_t *dtrue, int *rank,
                                       unsigned long long *best, int *status, cudaStream_t st) {
@@ -442,25 +468,27 @@ cudaError_t launch_tc_encode_and_rank(const uint16_t *needles, int64_t Q, const 
   __half *opa = c.take<__half>(Q * KT);
   __half *opb = c.take<__half>(H * KT);
   int *asum = c.take<int>(Q);
-  uint32_t *hvalid = c.take<uint32_t>((H + 31) / 32 + 1);
+  uint32_t *hvalid = c.take<uint32_t>((H + 31) / 32 + 2);
   cudaError_t e;
-  if ((e = cudaMemsetAsync(hvalid, 0, sizeof(uint32_t) * ((H + 31) / 32 + 1), st)) != cudaSuccess)
+  if ((e = cudaMemsetAsync(hvalid, 0, sizeof(uint32_t) * ((H + 31) / 32 + 2), st)) != cudaSuccess)
     return e;
   auto blocks_for = [](int64_t warps) {
     int64_t b = (warps + 7) / 8;
     return (int)(b < 152 * 64 ? (b > 0 ? b : 1) : 152 * 64);
   };
-  k_tc_encode<<<blocks_for(Q), 256, 0, st>>>(needles, Q, N, 1, opa, nwide, wn_list, counts + 0,
+  k_tc_encode<<<blocks_for(Q), 256, 0, st>>>(tab, qscene, Q, N, 1, opa, nwide, wn_list, counts + 0,
                                              asum, nullptr);
-  k_tc_encode<<<blocks_for(H), 256, 0, st>>>(haystack, H, N, 0, opb, hwide, wh_list, counts + 1,
+  k_tc_encode<<<blocks_for(H), 256, 0, st>>>(tab, hscene, H, N, 0, opb, hwide, wh_list, counts + 1,
                                              nullptr, hvalid);
   count_launches(2);
+  if (tiles_total == 0) return cudaGetLastError();
   CUtensorMap ma, mb;
   if ((e = encode_map(&ma, opa, Q, (int)KT, kBM)) != cudaSuccess) return e;
   if ((e = encode_map(&mb, opb, H, (int)KT, kBN)) != cudaSuccess) return e;
   TcArgs a;
-  a.Q = Q;
-  a.H = H;
+  a.tab = tab;
+  a.num_scenes = num_scenes;
+  a.tiles = tiles_total;
   a.KT = (int)KT;
   a.nwide = nwide;
   a.nflags = nflags;
@@ -477,8 +505,7 @@ cudaError_t launch_tc_encode_and_rank(const uint16_t *needles, int64_t Q, const 
   int dev = 0, sms = 152;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int64_t tiles = ((Q + kBM - 1) / kBM) * ((H + kBN - 1) / kBN);
-  const int grid = (int)(tiles < sms ? tiles : sms);
+  const int grid = (int)(tiles_total < sms ? tiles_total : sms);
   k_tc_rank<<<grid, kTcThreads, smem, st>>>(ma, mb, a);
   count_launches(1);
   return cudaGetLastError();
