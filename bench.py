@@ -65,6 +65,8 @@ def parse():
     ap.add_argument("--cpu-haystack", type=int, default=24000)
     ap.add_argument("--tc-compare", type=int, default=1,
                     help="also time the tensor-core search on the same images (breakdown)")
+    ap.add_argument("--batched-compare", type=int, default=1,
+                    help="also time the batched multi-scene run (CUDA graph) against per-scene calls")
     ap.add_argument("--haystack-limit", type=int, default=0,
                     help="image only the first H scene vertices (small profiling case)")
     ap.add_argument("--needle-limit", type=int, default=0,
@@ -178,6 +180,88 @@ def cpu_baseline(scene, args, steps: int = 1):
               f"over all triangles) and {len(nd)} needles x {len(hay)} haystack images (int64 "
               f"Listing 1) per step, extrapolated to {Vt + V} images and {Vt * V} comparisons")
     return est, threads, sample
+
+
+def batched_comparison(p, torch, dev, stream, args, n_scenes=24, needles=256):
+    """Batched run of many uneven scenes (one set of launches, replayed from a CUDA graph)
+    against one plain generate/generate/search call sequence per scene."""
+    import synth
+
+    scenes = synth.scene_batch(seed=41, n_scenes=n_scenes, tri_hi=60_000, total_hi=300_000)
+    rng = np.random.default_rng(2)
+    d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)  # noqa: E731
+    xs = []
+    for s in scenes:
+        q = min(needles, s.target_vertices)
+        on = np.sort(rng.choice(s.target_vertices, q, replace=False)).astype(np.int32)
+        xs.append({"V": d(s.vertices), "Nrm": d(s.normals), "T": d(s.triangles),
+                   "Tt": d(s.triangles[: s.target_triangles]), "on": d(on),
+                   "oh": d(np.arange(s.num_vertices, dtype=np.int32)), "m": d(on.astype(np.int64))})
+    gen = []
+    for x in xs:
+        gen.append({"vertices": x["V"], "normals": x["Nrm"], "triangles": x["Tt"], "origins": x["on"]})
+        gen.append({"vertices": x["V"], "normals": x["Nrm"], "triangles": x["T"], "origins": x["oh"]})
+    outs = [torch.empty((g["origins"].numel(), N_RES, N_RES), dtype=torch.uint16, device=dev)
+            for g in gen]
+    for g, o in zip(gen, outs):
+        g["out"] = o
+    srch = [{"needles": outs[2 * i], "haystack": outs[2 * i + 1], "true_match": x["m"]}
+            for i, x in enumerate(xs)]
+    res = [{"rank": torch.empty(x["on"].numel(), dtype=torch.int32, device=dev),
+            "true_distance": torch.empty(x["on"].numel(), dtype=torch.int64, device=dev),
+            "top1": torch.empty(x["on"].numel(), dtype=torch.int32, device=dev)} for x in xs]
+    wg = torch.empty(p.binding.generate_batch_workspace_bytes(gen, N_RES) + 512, dtype=torch.uint8,
+                     device=dev)
+    wsr = torch.empty(p.binding.search_batch_workspace_bytes(srch, N_RES) + 512, dtype=torch.uint8,
+                      device=dev)
+    wg = wg[(-wg.data_ptr()) % 256:]
+    wsr = wsr[(-wsr.data_ptr()) % 256:]
+
+    def run_batched():
+        p.rici_generate_batch(gen, R_SUP, N_RES, workspace_tensor=wg)
+        p.crss_search_batch(srch, N_RES, workspace_tensor=wsr, outputs=res)
+
+    def run_plain():
+        for x, g0, g1 in zip(xs, gen[0::2], gen[1::2]):
+            p.rici_generate(x["V"], x["Nrm"], x["Tt"], x["on"], R_SUP, N_RES, out=g0["out"])
+            p.rici_generate(x["V"], x["Nrm"], x["T"], x["oh"], R_SUP, N_RES, out=g1["out"])
+            p.crss_search(g0["out"], g1["out"], x["m"], mode=p.SEARCH_TENSOR)
+
+    cs = torch.cuda.Stream(device=dev)
+    cs.wait_stream(stream)
+    with torch.cuda.stream(cs):
+        run_batched()
+    stream.wait_stream(cs)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph):
+        run_batched()
+    for _ in range(2):
+        graph.replay()
+        run_plain()
+    torch.cuda.synchronize()
+    reps = max(3, args.steps)
+    t_b, t_p = [], []
+    for _ in range(reps):
+        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0.record(stream)
+        graph.replay()
+        e1.record(stream)
+        run_plain()
+        e2.record(stream)
+        torch.cuda.synchronize()
+        t_b.append(e0.elapsed_time(e1))
+        t_p.append(e1.elapsed_time(e2))
+    st = p.sync_status()
+    images = sum(g["origins"].numel() for g in gen)
+    pairs = sum(x["on"].numel() * x["oh"].numel() for x in xs)
+    return {"scenes": n_scenes, "triangles": int(sum(s.num_triangles for s in scenes)),
+            "images": int(images), "comparisons": int(pairs),
+            "batched_graph_ms": statistics.mean(t_b), "per_scene_calls_ms": statistics.mean(t_p),
+            "speedup": statistics.mean(t_p) / statistics.mean(t_b),
+            "batched_images_per_s": images / (statistics.mean(t_b) / 1e3), "status": st,
+            "recipe": "synth.scene_batch(seed=41, 24 scenes, 10k-300k triangles each), 256 needles "
+                      "per scene (target alone) vs all scene vertices, tensor-core search"}
 
 
 def run_reference(args):
@@ -332,6 +416,10 @@ def main():
         tc = {"ms": statistics.mean(tc_ms), "comparisons_per_s": pairs / (statistics.mean(tc_ms) / 1e3),
               "same_ranks_as_cuda_core": same, "status": st}
 
+    batched = None
+    if args.batched_compare and rank == 0:
+        batched = batched_comparison(p, torch, dev, stream, args)
+
     # e2e: same step from pinned host buffers, host<->device copies inside the timed region
     e2e = None
     if not args.no_e2e:
@@ -450,6 +538,7 @@ def main():
             "search_counters": {"pair_rows": scnt[0], "wide_pairs": scnt[1],
                                 "wide_terms": scnt[2]},
             "search_tensor_core": tc,
+            "batched_run": batched,
         },
         "roofline": roof,
         "rooflines": rooflines,
