@@ -536,7 +536,8 @@ def main():
             "generation_counters": {"triangles_processed": gcnt[0], "layer_items": gcnt[1],
                                     "fp64_band_items": gcnt[2], "cull_candidates": gcnt[3]},
             "search_counters": {"pair_rows": scnt[0], "wide_pairs": scnt[1],
-                                "wide_terms": scnt[2]},
+                                "wide_terms": scnt[2], "lane_slots": scnt[3],
+                                "lane_utilisation": scnt[0] / scnt[3] if scnt[3] else None},
             "search_tensor_core": tc,
             "batched_run": batched,
         },

@@ -131,7 +131,9 @@ RICI_API int crss_search(const uint16_t *needles, int64_t num_needles, const uin
  *   [0] (pair, row) evaluations by the packed CUDA-core kernel (each row = N-1 positions;
  *       rows after a pair's early exit are not evaluated),
  *   [1] pairs evaluated by the int64 kernel (pairs with a delta outside int8),
- *   [2] needle non-zero positions evaluated by the int64 kernel. */
+ *   [2] needle non-zero positions evaluated by the int64 kernel,
+ *   [3] lane slots the packed kernel spent on (pair, row) evaluations (32 per warp-wide
+ *       needle-row iteration; [0] / [3] is its lane utilisation). */
 RICI_API int crss_search_ex(const uint16_t *needles, int64_t num_needles,
                             const uint16_t *haystack, int64_t num_haystack, int32_t resolution,
                             const int64_t *true_match, int32_t *out_rank,

@@ -249,7 +249,7 @@ __global__ void __launch_bounds__(kDenseThreads) k_dense(
     if (valid && act_s[q]) alive |= 1u << q;
   }
   const int4 *hrow = reinterpret_cast<const int4 *>(hdelta + (valid ? j : 0) * K);
-  unsigned long long pair_rows = 0;
+  unsigned long long pair_rows = 0, lane_slots = 0;
   for (int i = 0; i < nrows; ++i) {
     if (__ballot_sync(0xffffffffu, alive != 0) == 0) break;
     const int r = ord[i];
@@ -272,6 +272,7 @@ __global__ void __launch_bounds__(kDenseThreads) k_dense(
 #pragma unroll
     for (int q = 0; q < kTQ; ++q) {
       if (__ballot_sync(0xffffffffu, (use >> q) & 1u) == 0) continue;
+      if (counters) lane_slots += 1;  // one warp-wide needle-row iteration (32 lane slots)
       // row sum of m (a - b)^2 = sum a^2 + sum (m b)^2 - 2 sum a b, with sum a^2 precomputed;
       // two independent accumulator chains per term
       int sbb0 = 0, sbb1 = 0, sab0 = 0, sab1 = 0;
@@ -311,6 +312,7 @@ __global__ void __launch_bounds__(kDenseThreads) k_dense(
 #pragma unroll
     for (int d = 16; d > 0; d >>= 1) pair_rows += __shfl_down_sync(0xffffffffu, pair_rows, d);
     if (lane == 0 && pair_rows) atomicAdd(counters, pair_rows);
+    if (lane == 0 && lane_slots) atomicAdd(counters + 3, 32ull * lane_slots);
   }
 }
 
