@@ -261,8 +261,6 @@ struct KArgs {
   const float4 *rec;
   const int *starts;
   float inv_cell;
-  float cell;       // grid cell edge (1 / inv_cell)
-  float reach;      // support-sphere radius + largest small-triangle radius (+ margin)
   float R;
   int N;
   float alpha_cull;  // pretest radius limit (alpha_{N-1} plus margin)
@@ -569,14 +567,7 @@ __global__ void __launch_bounds__(NW * 32) k_generate(KArgs a) {
     int ix = cell_coord(Sx, a.inv_cell) + tid % 3 - 1;
     int iy = cell_coord(Sy, a.inv_cell) + (tid / 3) % 3 - 1;
     int iz = cell_coord(Sz, a.inv_cell) + tid / 9 - 1;
-    // a triangle binned in this cell can reach the support volume only if the cell's box
-    // lies within `reach` of the spin vertex (triangle centre in the cell, radius <= r_big)
-    const float c = a.cell;
-    const float gx = fmaxf(fmaxf((float)ix * c - Sx, Sx - (float)(ix + 1) * c), 0.0f);
-    const float gy = fmaxf(fmaxf((float)iy * c - Sy, Sy - (float)(iy + 1) * c), 0.0f);
-    const float gz = fmaxf(fmaxf((float)iz * c - Sz, Sz - (float)(iz + 1) * c), 0.0f);
-    const bool near = gx * gx + gy * gy + gz * gz <= a.reach * a.reach;
-    s.buckets[tid] = near ? (int)(bucket_off + cell_hash(ix, iy, iz, nbuckets - 1)) : -1;
+    s.buckets[tid] = (int)(bucket_off + cell_hash(ix, iy, iz, nbuckets - 1));
   }
   __syncthreads();
 
@@ -753,7 +744,6 @@ __global__ void __launch_bounds__(NW * 32) k_generate(KArgs a) {
     int64_t b;
     if (nb < 27) {
       b = s.buckets[nb];
-      if (b < 0) continue;  // cell out of reach
       bool dup = false;
       for (int k = 0; k < nb; ++k) dup = dup || (s.buckets[k] == b);
       if (dup) continue;
@@ -918,9 +908,6 @@ cudaError_t launch_generate_batch(const GenScene *scenes, const GenerateBatch &g
   k.rec = rec;
   k.starts = starts;
   k.inv_cell = gp.inv_cell;
-  k.cell = (float)cell;
-  // cell boxes are compared with rounding slack (cell coordinates come from floor(x / cell))
-  k.reach = (float)((rho + gp.r_big) * 1.001 + 1e-3 * cell);
   k.R = g.R;
   k.N = N;
   k.alpha_cull = (float)(amax * (1.0 + 1.0 / 1024.0) + 1e-3 * R);

@@ -250,29 +250,25 @@ __global__ void __launch_bounds__(kDenseThreads) k_dense(
   }
   const int4 *hrow = reinterpret_cast<const int4 *>(hdelta + (valid ? j : 0) * K);
   unsigned long long pair_rows = 0, lane_slots = 0;
-  // haystack rows are double-buffered in registers: row i+1 is requested before row i is used
-  int hw[WPR], hn[WPR];
-  auto load_row = [&](int r, int (&dst)[WPR]) {
-#pragma unroll
-    for (int v = 0; v < WPR / 4; ++v) {
-      int4 x = hrow[r * (WPR / 4) + v];
-      dst[4 * v] = x.x;
-      dst[4 * v + 1] = x.y;
-      dst[4 * v + 2] = x.z;
-      dst[4 * v + 3] = x.w;
-    }
-#pragma unroll
-    for (int v = (WPR / 4) * 4; v < WPR; ++v) dst[v] = reinterpret_cast<const int *>(hrow)[r * WPR + v];
-  };
-  if (nrows > 0 && (alive & rmask[ord[0]])) load_row(ord[0], hn);
   for (int i = 0; i < nrows; ++i) {
     if (__ballot_sync(0xffffffffu, alive != 0) == 0) break;
     const int r = ord[i];
     const unsigned use = alive & rmask[r];
-#pragma unroll
-    for (int v = 0; v < WPR; ++v) hw[v] = hn[v];
-    if (i + 1 < nrows && (alive & rmask[ord[i + 1]])) load_row(ord[i + 1], hn);
     if (counters) pair_rows += __popc(use);
+    int hw[WPR];
+    if (use) {
+#pragma unroll
+      for (int v = 0; v < WPR / 4; ++v) {
+        int4 x = hrow[r * (WPR / 4) + v];
+        hw[4 * v] = x.x;
+        hw[4 * v + 1] = x.y;
+        hw[4 * v + 2] = x.z;
+        hw[4 * v + 3] = x.w;
+      }
+#pragma unroll
+      for (int v = (WPR / 4) * 4; v < WPR; ++v)
+        hw[v] = reinterpret_cast<const int *>(hrow)[r * WPR + v];
+    }
 #pragma unroll
     for (int q = 0; q < kTQ; ++q) {
       if (__ballot_sync(0xffffffffu, (use >> q) & 1u) == 0) continue;
