@@ -35,6 +35,7 @@ constexpr float kCellClamp = 1048576.0f;  // |cell coordinate| limit (2^20)
 constexpr int kWarps = 4;
 constexpr int kSlot = 25;  // words per staged triangle (odd stride: conflict-free lookups)
 constexpr int kScanItems = 2048;
+constexpr int kNeigh = 125;  // 5 x 5 x 5 neighbouring cells
 constexpr int kPerWarp = 64 + 32 + 64 + 64 + 32 * kSlot;  // shared words per warp
 
 __host__ __device__ inline uint32_t bucket_count(int64_t nt) {
@@ -261,6 +262,8 @@ struct KArgs {
   const float4 *rec;
   const int *starts;
   float inv_cell;
+  float cell;       // grid cell edge (1 / inv_cell)
+  float reach;      // support-sphere radius + largest small-triangle radius (+ margin)
   float R;
   int N;
   float alpha_cull;  // pretest radius limit (alpha_{N-1} plus margin)
@@ -277,7 +280,8 @@ struct Shared {
   float *a2f;    // alpha_c^2 rounded to FP32
   float *bf;     // beta_r rounded to FP32
   double *fr;    // S (3 doubles), Nax, Nay, Nbx, Nbz
-  int *buckets;  // 27 neighbour buckets
+  int *buckets;  // neighbour buckets (kNeigh cells + the big list)
+  int *bdup;     // 1: skip this entry (out of reach or repeated bucket)
   int *wq;       // this warp's candidate queue [64]
   int *wst;      // this warp's item starts [32]
   int *bq_rec;   // this warp's FP64 queue: triangle record [64]
@@ -499,7 +503,8 @@ __global__ void __launch_bounds__(NW * 32) k_generate(KArgs a) {
     s.a2f = reinterpret_cast<float *>(s.fr + 8);
     s.bf = s.a2f + N;
     s.buckets = reinterpret_cast<int *>(s.bf + N);
-    int *wbase = s.buckets + 28;
+    s.bdup = s.buckets + kNeigh + 1;
+    int *wbase = s.bdup + kNeigh + 1;
     s.wq = wbase + warp * kPerWarp;
     s.wst = s.wq + 64;
     s.bq_rec = s.wst + 32;
@@ -563,12 +568,30 @@ __global__ void __launch_bounds__(NW * 32) k_generate(KArgs a) {
     s.fr[5] = Nbx;
     s.fr[6] = Nbz;
   }
-  if (tid < 27) {
-    int ix = cell_coord(Sx, a.inv_cell) + tid % 3 - 1;
-    int iy = cell_coord(Sy, a.inv_cell) + (tid / 3) % 3 - 1;
-    int iz = cell_coord(Sz, a.inv_cell) + tid / 9 - 1;
-    s.buckets[tid] = (int)(bucket_off + cell_hash(ix, iy, iz, nbuckets - 1));
+  // neighbourhood: the 5 x 5 x 5 cells around the spin vertex's cell (cell edge > reach / 2).
+  // A triangle binned in a cell (by its bounding-sphere centre) can reach the support volume only
+  // if the cell's box lies within `reach` of the spin vertex; farther cells are skipped, and cells
+  // that hash to an already listed bucket are listed once.
+  if (tid < kNeigh) {
+    const int ix = cell_coord(Sx, a.inv_cell) + tid % 5 - 2;
+    const int iy = cell_coord(Sy, a.inv_cell) + (tid / 5) % 5 - 2;
+    const int iz = cell_coord(Sz, a.inv_cell) + tid / 25 - 2;
+    const float c = a.cell;
+    const float gx = fmaxf(fmaxf((float)ix * c - Sx, Sx - (float)(ix + 1) * c), 0.0f);
+    const float gy = fmaxf(fmaxf((float)iy * c - Sy, Sy - (float)(iy + 1) * c), 0.0f);
+    const float gz = fmaxf(fmaxf((float)iz * c - Sz, Sz - (float)(iz + 1) * c), 0.0f);
+    const bool near = gx * gx + gy * gy + gz * gz <= a.reach * a.reach;
+    s.buckets[tid] = near ? (int)(bucket_off + cell_hash(ix, iy, iz, nbuckets - 1)) : -1;
   }
+  if (tid == 0) s.buckets[kNeigh] = (int)(bucket_off + nbuckets);  // the scene's big list
+  __syncthreads();
+  if (tid < kNeigh) {
+    const int b = s.buckets[tid];
+    bool dup = false;
+    for (int k = 0; k < tid && !dup; ++k) dup = s.buckets[k] == b;
+    s.bdup[tid] = (b < 0 || dup) ? 1 : 0;
+  }
+  if (tid == 0) s.bdup[kNeigh] = 0;
   __syncthreads();
 
   const float fax = __double2float_rn(s.fr[3]), fay = __double2float_rn(s.fr[4]);
@@ -739,17 +762,10 @@ __global__ void __launch_bounds__(NW * 32) k_generate(KArgs a) {
     __syncwarp();
   };
 
-  // ---- stream candidates of the 27 neighbouring cells and the scene's big list
-  for (int nb = 0; nb < 28; ++nb) {
-    int64_t b;
-    if (nb < 27) {
-      b = s.buckets[nb];
-      bool dup = false;
-      for (int k = 0; k < nb; ++k) dup = dup || (s.buckets[k] == b);
-      if (dup) continue;
-    } else {
-      b = bucket_off + nbuckets;
-    }
+  // ---- stream candidates of the listed neighbouring cells and the scene's big list
+  for (int nb = 0; nb <= kNeigh; ++nb) {
+    if (s.bdup[nb]) continue;
+    const int64_t b = s.buckets[nb];
     const int64_t beg = a.starts[b], end = a.starts[b + 1];
     for (int64_t base = beg + warp * 32; base < end; base += NW * 32) {
       const int64_t t = base + lane;
@@ -825,7 +841,7 @@ size_t generate_smem_bytes(int N) {
   size_t b = ((size_t)N * N * 4 + 15) & ~(size_t)15;
   b += (size_t)(2 * N + 8) * sizeof(double);
   b += (size_t)(2 * N) * sizeof(float);
-  b += 28 * sizeof(int);
+  b += 2 * (kNeigh + 1) * sizeof(int);
   b += (size_t)kWarps * kPerWarp * 4;
   return b;
 }
@@ -880,7 +896,10 @@ cudaError_t launch_generate_batch(const GenScene *scenes, const GenerateBatch &g
   const double rho = sqrt(amax * amax + bmax * bmax) * (1.0 + 1.0 / 1024.0) + 1e-3 * R;
   GridParams gp;
   gp.r_big = (float)(0.25 * rho);
-  const double cell = 1.25 * rho * 1.01;
+  // a triangle (centre c, radius <= r_big) reaching the support volume has |c - S| <= reach;
+  // with cell > reach / 2 its cell lies within +-2 cells of the spin vertex's cell
+  const double reach = (rho + gp.r_big) * 1.001;
+  const double cell = 0.5 * reach * 1.01;
   gp.inv_cell = (float)(1.0 / cell);
   gp.mask = 0;
 
@@ -908,6 +927,8 @@ cudaError_t launch_generate_batch(const GenScene *scenes, const GenerateBatch &g
   k.rec = rec;
   k.starts = starts;
   k.inv_cell = gp.inv_cell;
+  k.cell = (float)cell;
+  k.reach = (float)(reach + 1e-3 * cell);  // slack for the rounding of cell coordinates
   k.R = g.R;
   k.N = N;
   k.alpha_cull = (float)(amax * (1.0 + 1.0 / 1024.0) + 1e-3 * R);
