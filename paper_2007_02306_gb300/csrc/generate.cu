@@ -36,8 +36,7 @@ constexpr int kWarps = 4;
 constexpr int kSlot = 25;  // words per staged triangle (odd stride: conflict-free lookups)
 constexpr int kScanItems = 2048;
 constexpr int kNeigh = 125;  // 5 x 5 x 5 neighbouring cells
-constexpr int kQueue = 256;  // candidate ring queue per warp (power of two)
-constexpr int kPerWarp = 256 + 32 + 64 + 64 + 32 * kSlot;  // shared words per warp
+constexpr int kPerWarp = 64 + 32 + 64 + 64 + 32 * kSlot;  // shared words per warp
 
 __host__ __device__ inline uint32_t bucket_count(int64_t nt) {
   uint32_t b = 1024;
@@ -283,7 +282,7 @@ struct Shared {
   double *fr;    // S (3 doubles), Nax, Nay, Nbx, Nbz
   int *buckets;  // neighbour buckets (kNeigh cells + the big list)
   int *bdup;     // 1: skip this entry (out of reach or repeated bucket)
-  int *wq;       // this warp's candidate ring queue [kQueue]
+  int *wq;       // this warp's candidate queue [64]
   int *wst;      // this warp's item starts [32]
   int *bq_rec;   // this warp's FP64 queue: triangle record [64]
   int *bq_r;     // this warp's FP64 queue: layer [64]
@@ -487,7 +486,7 @@ __device__ __forceinline__ void add_intervals(int *row, int N, int lo, int hi, i
 }
 
 template <int NW>
-__global__ void __launch_bounds__(NW * 32, 5) k_generate(KArgs a) {
+__global__ void __launch_bounds__(NW * 32) k_generate(KArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int N = a.N;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -507,7 +506,7 @@ __global__ void __launch_bounds__(NW * 32, 5) k_generate(KArgs a) {
     s.bdup = s.buckets + kNeigh + 1;
     int *wbase = s.bdup + kNeigh + 1;
     s.wq = wbase + warp * kPerWarp;
-    s.wst = s.wq + kQueue;
+    s.wst = s.wq + 64;
     s.bq_rec = s.wst + 32;
     s.bq_r = s.bq_rec + 64;
     s.slots = reinterpret_cast<float *>(s.bq_r + 64);
@@ -605,7 +604,7 @@ __global__ void __launch_bounds__(NW * 32, 5) k_generate(KArgs a) {
   const bool fp64_only = a.mode == RICI_GEN_FP64;
 
   unsigned long long n_tri = 0, n_items = 0, n_band = 0, n_cand = 0;
-  int qhead = 0, qtail = 0;  // warp-uniform ring-queue positions (entries qhead..qtail-1)
+  int qn = 0;  // warp-uniform candidate queue length
   int bn = 0;  // warp-uniform FP64 queue length
 
   // FP64 re-evaluation of queued band items, one per lane
@@ -637,7 +636,7 @@ __global__ void __launch_bounds__(NW * 32, 5) k_generate(KArgs a) {
     int nlay = 0;
     float *sl = s.slots + lane * kSlot;
     if (lane < cnt) {
-      const int rec = s.wq[(qhead + lane) & (kQueue - 1)];
+      const int rec = s.wq[lane];
       float4 r1 = a.rec[4 * (int64_t)rec + 1], r2 = a.rec[4 * (int64_t)rec + 2],
              r3 = a.rec[4 * (int64_t)rec + 3];
       float P[9] = {r1.x, r1.y, r1.z, r1.w, r2.x, r2.y, r2.z, r2.w, r3.x};
@@ -768,41 +767,35 @@ __global__ void __launch_bounds__(NW * 32, 5) k_generate(KArgs a) {
     if (s.bdup[nb]) continue;
     const int64_t b = s.buckets[nb];
     const int64_t beg = a.starts[b], end = a.starts[b + 1];
-    // four chunks of 32 candidates per iteration: their record loads are issued together,
-    // survivors go to the ring queue, full batches of 32 are processed afterwards
-    for (int64_t base = beg + warp * 32; base < end; base += 4 * NW * 32) {
-      float4 cr[4];
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int64_t t = base + u * NW * 32 + lane;
-        cr[u] = t < end ? a.rec[4 * t] : make_float4(0.0f, 0.0f, 0.0f, -1.0f);
+    for (int64_t base = beg + warp * 32; base < end; base += NW * 32) {
+      const int64_t t = base + lane;
+      bool pass = false;
+      if (t < end) {
+        float4 c = a.rec[4 * t];
+        float dx = c.x - Sx, dy = c.y - Sy, dz = c.z - Sz;
+        float z = fmaf(wx, dx, fmaf(wy, dy, wz * dz));
+        float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        float m = 1e-3f * R + 1e-5f * (fabsf(dx) + fabsf(dy) + fabsf(dz));
+        float al = a.alpha_cull + c.w + m;
+        pass = fabsf(z) <= a.beta_cull + c.w + m && d2 - z * z <= al * al;
+        ++n_cand;
       }
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int64_t t = base + u * NW * 32 + lane;
-        bool pass = false;
-        if (t < end) {
-          const float4 c = cr[u];
-          float dx = c.x - Sx, dy = c.y - Sy, dz = c.z - Sz;
-          float z = fmaf(wx, dx, fmaf(wy, dy, wz * dz));
-          float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-          float m = 1e-3f * R + 1e-5f * (fabsf(dx) + fabsf(dy) + fabsf(dz));
-          float al = a.alpha_cull + c.w + m;
-          pass = fabsf(z) <= a.beta_cull + c.w + m && d2 - z * z <= al * al;
-          ++n_cand;
-        }
-        const unsigned bal = __ballot_sync(0xffffffffu, pass);
-        if (pass) s.wq[(qtail + __popc(bal & ((1u << lane) - 1u))) & (kQueue - 1)] = (int)t;
-        qtail += __popc(bal);
-      }
+      unsigned bal = __ballot_sync(0xffffffffu, pass);
+      if (pass) s.wq[qn + __popc(bal & ((1u << lane) - 1u))] = (int)t;
+      qn += __popc(bal);
       __syncwarp();
-      while (qtail - qhead >= 32) {
+      if (qn >= 32) {
         process_batch(32);
-        qhead += 32;
+        int rest = qn - 32;
+        int moved = lane < rest ? s.wq[32 + lane] : 0;
+        __syncwarp();
+        if (lane < rest) s.wq[lane] = moved;
+        qn = rest;
+        __syncwarp();
       }
     }
   }
-  if (qtail > qhead) process_batch(qtail - qhead);
+  if (qn > 0) process_batch(qn);
   if (bn > 0) flush_band(bn);
 
   if (a.counters) {
