@@ -162,7 +162,7 @@ __device__ __forceinline__ unsigned long long warp_min_u64(unsigned long long v)
 // Narrow x narrow pairs.  Block: kTQ needles (deltas + masks in shared memory) x
 // kDenseThreads haystack images (one per thread).
 template <int N, int kTQ>
-__global__ void __launch_bounds__(kDenseThreads, 4) k_dense(
+__global__ void __launch_bounds__(kDenseThreads) k_dense(
     const int8_t *__restrict__ ndelta, const int8_t *__restrict__ nmask,
     const int *__restrict__ nwide, int64_t Q, const int8_t *__restrict__ hdelta,
     const int *__restrict__ hwide, int64_t H, const int64_t *__restrict__ dtrue,
@@ -495,7 +495,7 @@ cudaError_t launch_dense(const int8_t *nd, const int8_t *nm, const int *nw, int6
                          const int8_t *hd, const int *hw, int64_t H, const int64_t *dt,
                          const int *nf, int *rank, unsigned long long *best,
                          unsigned long long *counters, cudaStream_t st) {
-  constexpr int kTQ = N <= 32 ? 8 : 4;
+  constexpr int kTQ = N <= 64 ? 8 : 4;
   const size_t smem = sizeof(int2) * kTQ * (N * N / 4);
   cudaError_t e = cudaFuncSetAttribute(k_dense<N, kTQ>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
