@@ -64,6 +64,10 @@ extern "C" {
 #define RICI_SEARCH_TENSOR 3    /* exact fp16 tcgen05 GEMM of the expanded distance (N in 8..128,
                                    powers of two); pairs with |delta| > 32 on either side run in
                                    exact int64 on CUDA cores */
+/* Test hook, OR-ed into RICI_SEARCH_TENSOR: one CTA of the tensor-core kernel withholds its
+ * first tile load, so its bounded waits run out (about 2 s), RICI_ERR_TIMEOUT is raised in the
+ * status word and the kernel returns; outputs of that call are unspecified. */
+#define RICI_SEARCH_TEST_WITHHOLD_LOAD 0x100
 
 /*
  * rici_generate — one RICI image per oriented point (Section 3.1).

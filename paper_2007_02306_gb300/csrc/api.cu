@@ -197,8 +197,11 @@ int crss_search_ex(const uint16_t *needles, int64_t num_needles, const uint16_t 
   if (num_needles < 0 || num_haystack < 0) return fail(RICI_ERR_INVALID_ARGUMENT, "negative count");
   if (resolution < 2 || resolution > RICI_MAX_RESOLUTION)
     return fail(RICI_ERR_INVALID_ARGUMENT, "resolution must be in [2, %d]", RICI_MAX_RESOLUTION);
-  if (mode != RICI_SEARCH_DEFAULT && mode != RICI_SEARCH_CUDA_CORE &&
-      mode != RICI_SEARCH_EXACT_SLOW && mode != RICI_SEARCH_TENSOR)
+  const int base_mode = mode & 0xff;
+  if ((base_mode != RICI_SEARCH_DEFAULT && base_mode != RICI_SEARCH_CUDA_CORE &&
+       base_mode != RICI_SEARCH_EXACT_SLOW && base_mode != RICI_SEARCH_TENSOR) ||
+      (mode & ~(0xff | RICI_SEARCH_TEST_WITHHOLD_LOAD)) ||
+      ((mode & RICI_SEARCH_TEST_WITHHOLD_LOAD) && base_mode != RICI_SEARCH_TENSOR))
     return fail(RICI_ERR_INVALID_ARGUMENT, "unknown search mode %d", mode);
   if (num_needles == 0) return RICI_OK;
   if (num_haystack == 0)

@@ -121,7 +121,8 @@ cudaError_t launch_tc_encode_and_rank(const SearchScene *tab, int num_scenes, co
                                       int64_t tiles_total, int N, void *ws, int *nwide, int *hwide,
                                       int *wn_list, int *wh_list, int *counts,
                                       const int *nflags, const int64_t *dtrue, int *rank,
-                                      unsigned long long *best, int *status, cudaStream_t st);
+                                      unsigned long long *best, int *status, int test_withhold,
+                                      cudaStream_t st);
 
 // Carve 256-byte aligned sub-buffers out of one workspace allocation.
 struct Carver {

@@ -522,6 +522,7 @@ void search_tiles(int64_t Q, int64_t H, int32_t *tiles_m, int32_t *tiles_n) {
 
 int64_t search_batch_workspace_bytes(int num_scenes, int64_t Q, int64_t H, int N, int mode) {
   const int64_t K = (int64_t)N * N;
+  mode &= 0xff;
   const bool tensor = mode == RICI_SEARCH_TENSOR && tc_supported(N);
   const bool packed = !tensor && mode != RICI_SEARCH_EXACT_SLOW && dense_supported(N);
   Carver c(nullptr);
@@ -555,8 +556,10 @@ cudaError_t launch_search_batch(const SearchScene *scenes, const SearchBatch &b,
   const int N = b.N;
   const int64_t K = (int64_t)N * N;
   if (Q == 0) return cudaSuccess;
-  const bool tensor = b.mode == RICI_SEARCH_TENSOR && tc_supported(N);
-  const bool dense = !tensor && b.mode != RICI_SEARCH_EXACT_SLOW && dense_supported(N) &&
+  const int withhold = (b.mode & RICI_SEARCH_TEST_WITHHOLD_LOAD) ? 1 : 0;
+  const int mode = b.mode & 0xff;
+  const bool tensor = mode == RICI_SEARCH_TENSOR && tc_supported(N);
+  const bool dense = !tensor && mode != RICI_SEARCH_EXACT_SLOW && dense_supported(N) &&
                      b.num_scenes == 1;
   Carver c(ws);
   SearchScene *tab = c.take<SearchScene>(b.num_scenes);
@@ -611,7 +614,7 @@ cudaError_t launch_search_batch(const SearchScene *scenes, const SearchBatch &b,
   if (tensor) {
     if ((e = launch_tc_encode_and_rank(tab, b.num_scenes, qscene, hscene, Q, H, b.tiles_total, N,
                                        tc_ws, nwide, hwide, wn_list, wh_list, counts, nflags, dt,
-                                       rank, best, b.status, st)) != cudaSuccess)
+                                       rank, best, b.status, withhold, st)) != cudaSuccess)
       return e;
     wide(0);
     wide(1);

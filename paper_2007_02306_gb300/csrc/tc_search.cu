@@ -40,6 +40,7 @@ constexpr uint32_t kStageB = kBN * kBK * 2;  // 32 KB
 constexpr int kNarrow = 32;       // |delta| limit of the exact fp16 operands
 constexpr unsigned long long kNoBestTc = ~0ull;
 constexpr unsigned long long kWaitBudgetNs = 2000000000ull;
+constexpr unsigned long long kDrainBudgetNs = 200000000ull;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -88,6 +89,19 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int *s
       set_status(status, RICI_ERR_TIMEOUT);
       *(volatile int *)abort_flag = 1;
       return false;
+    }
+    __nanosleep(32);
+  }
+}
+
+// Bounded wait used while tearing down: no abort flag, a short budget (copies and MMAs that are
+// still in flight after an abort finish within microseconds unless the GPU itself is stuck).
+__device__ __forceinline__ void mbar_drain(uint64_t *bar, uint32_t parity, int *status) {
+  const unsigned long long t0 = globaltimer();
+  while (!mbar_try_wait(bar, parity)) {
+    if (globaltimer() - t0 > kDrainBudgetNs) {
+      set_status(status, RICI_ERR_TIMEOUT);
+      return;
     }
     __nanosleep(32);
   }
@@ -224,6 +238,7 @@ struct TcArgs {
   int *rank;
   unsigned long long *best;
   int *status;
+  int withhold_first_load;  // test hook: CTA 0 never issues its first stage (its waits time out)
 };
 
 // A tile of one scene: needle rows [qbeg + 128 m, ...), haystack columns [hbeg + 256 n, ...),
@@ -270,7 +285,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   uint64_t *empty = full + kStages;
   uint64_t *tfull = empty + kStages;
   uint64_t *tempty = tfull + 2;
-  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(tempty + 2);
+  uint64_t *drain = tempty + 2;
+  uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drain + 1);
   int *abort_flag = reinterpret_cast<int *>(tmem_slot + 1);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -286,6 +302,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       mbar_init(&tfull[b], 1);
       mbar_init(&tempty[b], 4);
     }
+    mbar_init(drain, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -314,10 +331,18 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             ok = false;
             break;
           }
+          if (a.withhold_first_load && blockIdx.x == 0 && it == 0) continue;
           mbar_arrive_expect_tx(&full[s], kStageA + kStageB);
           tma_load_2d(sA + s * kStageA, &map_a, &full[s], kb * kBK, ya);
           tma_load_2d(sB + s * kStageB, &map_b, &full[s], kb * kBK, yb);
         }
+      }
+      // Loads issued in the last kStages iterations may be unconsumed after an abort: wait for
+      // them before the CTA exits (already-complete phases return at once).
+      for (uint32_t j = 1; j <= (uint32_t)kStages && j <= it; ++j) {
+        const uint32_t i = it - j;
+        if (a.withhold_first_load && blockIdx.x == 0 && i == 0) continue;
+        mbar_drain(&full[i % kStages], (i / kStages) & 1, a.status);
       }
     }
   } else if (warp == 1) {
@@ -345,8 +370,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
           }
           tc_commit(&empty[s]);  // frees the stage once these MMAs have read it
         }
+        if (!ok) break;
         tc_commit(&tfull[buf]);  // accumulator ready for the epilogue
       }
+      // every MMA this thread issued has finished before TMEM is released
+      tc_commit(drain);
+      mbar_drain(drain, 0, a.status);
     }
   } else {
     // ---------------- epilogue: warps 2..5, TMEM lane quarter = warp % 4
@@ -462,7 +491,8 @@ cudaError_t launch_tc_encode_and_rank(const SearchScene *tab, int num_scenes, co
                                       int64_t tiles_total, int N, void *ws, int *nwide, int *hwide,
                                       int *wn_list, int *wh_list, int *counts,
                                       const int *nflags, const int64_t *dtrue, int *rank,
-                                      unsigned long long *best, int *status, cudaStream_t st) {
+                                      unsigned long long *best, int *status, int test_withhold,
+                                      cudaStream_t st) {
   const int64_t KT = 2ll * N * N;
   Carver c(ws);
   __half *opa = c.take<__half>(Q * KT);
@@ -498,6 +528,7 @@ cudaError_t launch_tc_encode_and_rank(const SearchScene *tab, int num_scenes, co
   a.rank = rank;
   a.best = best;
   a.status = status;
+  a.withhold_first_load = test_withhold;
   const size_t smem = 1024 + kStages * (kStageA + kStageB) + 256;
   if ((e = cudaFuncSetAttribute(k_tc_rank, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)smem)) != cudaSuccess)

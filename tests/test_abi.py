@@ -83,6 +83,11 @@ def test_search_rejects_bad_arguments_on_host(lib):
     assert lib.crss_search(dummy, 1, dummy, 0, 64, None, dummy, None, None, None, 0, None, 0, None) == 1
     assert lib.crss_search(dummy, 1, dummy, 1, 1, None, dummy, None, None, None, 0, None, 0, None) == 1
     assert lib.crss_search(dummy, 1, dummy, 1, 64, None, dummy, None, None, None, 9, None, 0, None) == 1
+    # the withheld-load test bit is only accepted with the tensor-core form; other high bits never
+    assert lib.crss_search(dummy, 1, dummy, 1, 64, None, dummy, None, None, None, 0x101, None, 0,
+                           None) == 1
+    assert lib.crss_search(dummy, 1, dummy, 1, 64, None, dummy, None, None, None, 0x203, None, 0,
+                           None) == 1
     assert lib.crss_search(dummy, 1 << 15, dummy, 1 << 14, 64, None, dummy, None, None, dummy, 0,
                            None, 0, None) == 8
 
