@@ -26,6 +26,7 @@ namespace rici {
 namespace {
 
 constexpr int kDenseThreads = 256;     // haystack images per dense tile
+constexpr int64_t kBandH = 8;          // haystack tiles per band of the dense tile order
 constexpr int kWideThreads = 256;
 constexpr unsigned long long kNoBest = ~0ull;
 
@@ -33,11 +34,24 @@ __device__ __forceinline__ int delta_at(const uint16_t *img, int N, int r, int c
   return c == 0 ? 0 : (int)img[r * N + c] - (int)img[r * N + c - 1];
 }
 
-// One warp per image.
+// Byte offset of the delta at flat position k of image i in the warp-interleaved layout read by
+// k_dense: 32 consecutive images form a group, and within a group each row is stored as chunks
+// of CW 32-bit words per image, chunk-major, so the 32 lanes of a warp (32 consecutive images)
+// read the same chunk of the same row with one contiguous 32 x 4CW-byte access.
+__device__ __forceinline__ int64_t interleaved_offset(int64_t i, int N, int k) {
+  const int WPR = N / 4, CW = WPR < 4 ? WPR : 4;
+  const int r = k / N, c = k - r * N;
+  const int w = c >> 2, v = w / CW, ww = w - v * CW;
+  const int64_t g = i >> 5, l = i & 31;
+  return ((((g * N + r) * (WPR / CW) + v) * 32 + l) * CW + ww) * 4 + (c & 3);
+}
+
+// One warp per image.  interleave: write the deltas in the layout of interleaved_offset (the
+// haystack of the dense kernel) instead of image-major.
 __global__ void k_encode(const uint16_t *__restrict__ imgs, int64_t n, int N,
                          int8_t *__restrict__ delta, int8_t *__restrict__ mask,
                          int *__restrict__ wide_flag, int *__restrict__ wide_list,
-                         int *__restrict__ wide_count) {
+                         int *__restrict__ wide_count, int interleave) {
   const int lane = threadIdx.x & 31;
   const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -50,7 +64,7 @@ __global__ void k_encode(const uint16_t *__restrict__ imgs, int64_t n, int N,
       int d = delta_at(img, N, r, c);
       wide |= (d > 127 || d < -127);
       int dc = d > 127 ? 127 : (d < -127 ? -127 : d);
-      delta[i * K + k] = (int8_t)dc;
+      delta[interleave ? interleaved_offset(i, N, k) : i * K + k] = (int8_t)dc;
       if (mask) mask[i * K + k] = (int8_t)(d != 0 ? -1 : 0);
     }
     wide = __any_sync(0xffffffffu, wide);
@@ -167,7 +181,7 @@ __global__ void __launch_bounds__(kDenseThreads) k_dense(
     const int *__restrict__ nwide, int64_t Q, const int8_t *__restrict__ hdelta,
     const int *__restrict__ hwide, int64_t H, const int64_t *__restrict__ dtrue,
     const int *__restrict__ nflags, int *__restrict__ rank, unsigned long long *__restrict__ best,
-    unsigned long long *__restrict__ counters) {
+    unsigned long long *__restrict__ counters, int64_t tile0, int64_t tiles_q, int64_t tiles_h) {
   constexpr int WPR = N / 4;  // 32-bit words per row
   constexpr int K = N * N;
   extern __shared__ int2 am_raw[];  // [kTQ][K/4] (needle delta word, mask word)
@@ -179,8 +193,20 @@ __global__ void __launch_bounds__(kDenseThreads) k_dense(
   __shared__ unsigned rmask[N];    // needles of the tile with a non-zero delta in the row
   __shared__ int nrows_s;
   const int tid = threadIdx.x, lane = tid & 31;
-  const int64_t q0 = (int64_t)blockIdx.y * kTQ;
-  const int64_t j = (int64_t)blockIdx.x * kDenseThreads + tid;
+  // Tile order: bands of kBandH haystack tiles; within a band the haystack tile varies fastest,
+  // then the needle tile, so a band's haystack images are read from DRAM once and reused from L2
+  // by every needle tile.
+  int64_t qt, ht;
+  {
+    const int64_t L = tile0 + blockIdx.x;
+    const int64_t band = L / (kBandH * tiles_q), rem = L - band * (kBandH * tiles_q);
+    const int64_t h0 = band * kBandH;
+    const int64_t bh = tiles_h - h0 < kBandH ? tiles_h - h0 : kBandH;
+    qt = rem / bh;
+    ht = h0 + (rem - qt * bh);
+  }
+  const int64_t q0 = qt * kTQ;
+  const int64_t j = ht * kDenseThreads + tid;
 
   for (int x = tid; x < kTQ * (K / 4); x += kDenseThreads) {
     int q = x / (K / 4), wd = x - q * (K / 4);
@@ -248,7 +274,10 @@ __global__ void __launch_bounds__(kDenseThreads) k_dense(
     acc[q] = 0;
     if (valid && act_s[q]) alive |= 1u << q;
   }
-  const int4 *hrow = reinterpret_cast<const int4 *>(hdelta + (valid ? j : 0) * K);
+  // this thread's image in the warp-interleaved layout (group of 32 images, chunks of CW words)
+  constexpr int CW = WPR < 4 ? WPR : 4;
+  const int *hgrp = reinterpret_cast<const int *>(hdelta) + (j >> 5) * (int64_t)(N * WPR * 32) +
+                    lane * CW;
   unsigned long long pair_rows = 0, lane_slots = 0;
   for (int i = 0; i < nrows; ++i) {
     if (__ballot_sync(0xffffffffu, alive != 0) == 0) break;
@@ -257,17 +286,21 @@ __global__ void __launch_bounds__(kDenseThreads) k_dense(
     if (counters) pair_rows += __popc(use);
     int hw[WPR];
     if (use) {
+      const int *src = hgrp + r * (WPR * 32);
 #pragma unroll
-      for (int v = 0; v < WPR / 4; ++v) {
-        int4 x = hrow[r * (WPR / 4) + v];
-        hw[4 * v] = x.x;
-        hw[4 * v + 1] = x.y;
-        hw[4 * v + 2] = x.z;
-        hw[4 * v + 3] = x.w;
+      for (int v = 0; v < WPR / CW; ++v) {
+        if constexpr (CW == 4) {
+          const int4 x = *reinterpret_cast<const int4 *>(src + v * 32 * CW);
+          hw[4 * v] = x.x;
+          hw[4 * v + 1] = x.y;
+          hw[4 * v + 2] = x.z;
+          hw[4 * v + 3] = x.w;
+        } else {
+          const int2 x = *reinterpret_cast<const int2 *>(src + v * 32 * CW);
+          hw[2 * v] = x.x;
+          hw[2 * v + 1] = x.y;
+        }
       }
-#pragma unroll
-      for (int v = (WPR / 4) * 4; v < WPR; ++v)
-        hw[v] = reinterpret_cast<const int *>(hrow)[r * WPR + v];
     }
 #pragma unroll
     for (int q = 0; q < kTQ; ++q) {
@@ -500,14 +533,14 @@ cudaError_t launch_dense(const int8_t *nd, const int8_t *nm, const int *nw, int6
   cudaError_t e = cudaFuncSetAttribute(k_dense<N, kTQ>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  const int64_t gx = (H + kDenseThreads - 1) / kDenseThreads;
-  const int64_t gy = (Q + kTQ - 1) / kTQ;
-  for (int64_t y0 = 0; y0 < gy; y0 += 65535) {
-    const int64_t ny = gy - y0 < 65535 ? gy - y0 : 65535;
-    dim3 grid((unsigned)gx, (unsigned)ny);
-    k_dense<N, kTQ><<<grid, kDenseThreads, smem, st>>>(
-        nd + y0 * kTQ * N * N, nm + y0 * kTQ * N * N, nw + y0 * kTQ, Q - y0 * kTQ, hd, hw, H,
-        dt + y0 * kTQ, nf + y0 * kTQ, rank + y0 * kTQ, best + y0 * kTQ, counters);
+  const int64_t th = (H + kDenseThreads - 1) / kDenseThreads;
+  const int64_t tq = (Q + kTQ - 1) / kTQ;
+  const int64_t total = th * tq;
+  constexpr int64_t kMaxGrid = 0x7fffffffll;
+  for (int64_t t0 = 0; t0 < total; t0 += kMaxGrid) {
+    const int64_t n = total - t0 < kMaxGrid ? total - t0 : kMaxGrid;
+    k_dense<N, kTQ><<<(unsigned)n, kDenseThreads, smem, st>>>(nd, nm, nw, Q, hd, hw, H, dt, nf,
+                                                             rank, best, counters, t0, tq, th);
     count_launches(1);
   }
   return cudaGetLastError();
@@ -531,7 +564,7 @@ int64_t search_batch_workspace_bytes(int num_scenes, int64_t Q, int64_t H, int N
   c.take<int>(H);                        // scene of each haystack image
   c.take<int8_t>(packed ? Q * K : 0);    // needle deltas (packed CUDA-core form only)
   c.take<int8_t>(packed ? Q * K : 0);    // needle masks
-  c.take<int8_t>(packed ? H * K : 0);    // haystack deltas
+  c.take<int8_t>(packed ? (H + 31) / 32 * 32 * K : 0);  // haystack deltas (groups of 32)
   c.take<int>(Q);                        // needle wide flags
   c.take<int>(H);                        // haystack wide flags
   c.take<int>(Q);                        // wide needle list
@@ -567,7 +600,7 @@ cudaError_t launch_search_batch(const SearchScene *scenes, const SearchBatch &b,
   int *hscene = c.take<int>(H);
   int8_t *nd = c.take<int8_t>(dense ? Q * K : 0);
   int8_t *nm = c.take<int8_t>(dense ? Q * K : 0);
-  int8_t *hd = c.take<int8_t>(dense ? H * K : 0);
+  int8_t *hd = c.take<int8_t>(dense ? (H + 31) / 32 * 32 * K : 0);
   int *nwide = c.take<int>(Q);
   int *hwide = c.take<int>(H);
   int *wn_list = c.take<int>(Q);
@@ -622,9 +655,9 @@ cudaError_t launch_search_batch(const SearchScene *scenes, const SearchBatch &b,
     // single scene: launch-wide indices are the scene's own
     const SearchScene &s0 = scenes[0];
     k_encode<<<blocks_for(Q), 32 * wpb, 0, st>>>(s0.needles, Q, N, nd, nm, nwide, wn_list,
-                                                 counts + 0);
+                                                 counts + 0, 0);
     k_encode<<<blocks_for(H), 32 * wpb, 0, st>>>(s0.haystack, H, N, hd, nullptr, hwide, wh_list,
-                                                 counts + 1);
+                                                 counts + 1, 1);
     count_launches(2);
     switch (N) {
       case 8: e = launch_dense<8>(nd, nm, nwide, Q, hd, hwide, H, dt, nflags, rank, best, cnt, st); break;
