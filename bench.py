@@ -45,9 +45,13 @@ WORKLOAD = ("clutter scene: displaced icosphere target (subdivision 5, 20,480 tr
 # FP32-pipe operations of the definition per unit of generation work:
 F_PROJ = 15   # per projected vertex of an (origin, triangle) pair that crosses a layer
 F_LAYER = 40  # per (origin, triangle, layer) crossing: slicing + segment quantities + boundaries
-# packed-integer operations per masked squared difference on this ALU (3 dp4a + 1 AND +
-# 1 combine per 4 positions)
-OPS_PER_TERM = 1.25
+# int8 multiply-adds per masked squared difference in the expanded form m(a-b)^2 =
+# a^2 - 2ab + (mb)^2 with sum a^2 per row precomputed: one for a*b and one for (mb)*(mb); dp4a
+# performs four of them per instruction.
+MACS_PER_TERM = 2
+# dp4a instructions per SM per clock: half the 128 FP32 lanes (a microbenchmark of independent
+# dp4a chains measured 61.3 per SM per clock at 2070 MHz; FFMA measured 117.3)
+DP4A_PER_SM_CLK = 64
 
 
 def parse():
@@ -462,6 +466,8 @@ def main():
     clk_mhz = (clk or {}).get("sm_mhz") or pk.get("sm_max_mhz", 2070.0)
     sms = torch.cuda.get_device_properties(dev).multi_processor_count
     alu_peak_gops = sms * 128 * clk_mhz * 1e6 / 1e9  # 32-bit lane operations per second
+    mac_peak_gops = sms * DP4A_PER_SM_CLK * 4 * clk_mhz * 1e6 / 1e9  # int8 MACs via dp4a
+    dp4a_rate = p.binding.measure_dp4a_rate()  # after the timed regions
 
     gen_ms = statistics.mean(t_hy)
     se_ms = statistics.mean(t_se)
@@ -482,12 +488,15 @@ def main():
     rooflines = {}
     search_terms = scnt[0] * (N_RES - 1)
     rooflines["search"] = {
-        "bound": "alu", "unit": "Gop/s",
-        "achieved": OPS_PER_TERM * search_terms / (se_ms / 1e3) / 1e9,
-        "peak": alu_peak_gops,
+        "bound": "alu", "unit": "G int8-MAC/s",
+        "achieved": MACS_PER_TERM * search_terms / (se_ms / 1e3) / 1e9,
+        "peak": mac_peak_gops,
         "work": f"{scnt[0]} (pair, row) evaluations x {N_RES - 1} masked squared differences x "
-                f"{OPS_PER_TERM} packed int ops",
+                f"{MACS_PER_TERM} int8 multiply-adds",
         "traffic": None,
+        "peak_kind": f"derived: {sms} SMs x {DP4A_PER_SM_CLK} dp4a per clock x 4 MACs x "
+                     f"{clk_mhz:.0f} MHz (median SM clock)",
+        "measured_dp4a_per_sm_per_clk": dp4a_rate / sms / (clk_mhz * 1e6),
     }
     if cpu_ops is not None:
         per_o = (F_PROJ * 3 * cpu_ops["pairs_crossing"] + F_LAYER * cpu_ops["layer_crossings"]) / 32
@@ -501,7 +510,8 @@ def main():
         }
     for r in rooflines.values():
         r["frac"] = r["achieved"] / r["peak"]
-        r["peak_kind"] = f"derived: {sms} SMs x 128 lanes x {clk_mhz:.0f} MHz (median SM clock)"
+        r.setdefault("peak_kind", f"derived: {sms} SMs x 128 lanes x {clk_mhz:.0f} MHz "
+                                  "(median SM clock)")
     if tc is not None:
         kt = 2 * N_RES * N_RES
         rooflines["search_tensor_core"] = {

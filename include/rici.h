@@ -231,6 +231,14 @@ RICI_API const char *rici_last_error_string(void);
 /* Number of CUDA kernels this library has enqueued in the calling process so far. */
 RICI_API int64_t rici_kernel_launches(void);
 
+/* Measures, on the current device and the given stream, how many dp4a instructions (four int8
+ * multiply-adds into an int32 each; the arithmetic of the CUDA-core search) the whole GPU issues
+ * per second, running independent accumulator chains on every SM; the result goes to
+ * *dp4a_per_second.  Synchronises the stream; allocates and frees a small device buffer.
+ * A measurement helper for roofline peaks: the paper has no counterpart.  Returns RICI_OK, or
+ * RICI_ERR_INVALID_ARGUMENT for a null pointer, or RICI_ERR_CUDA. */
+RICI_API int rici_measure_dp4a_rate(void *stream, double *dp4a_per_second);
+
 /* Library version string. */
 RICI_API const char *rici_version(void);
 

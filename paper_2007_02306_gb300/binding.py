@@ -104,6 +104,8 @@ def load_library(path: str | None = None):
         lib.rici_last_error_string.restype = ctypes.c_char_p
         lib.rici_kernel_launches.argtypes = []
         lib.rici_kernel_launches.restype = i64
+        lib.rici_measure_dp4a_rate.argtypes = [P, ctypes.POINTER(ctypes.c_double)]
+        lib.rici_measure_dp4a_rate.restype = ctypes.c_int
         lib.rici_version.argtypes = []
         lib.rici_version.restype = ctypes.c_char_p
         _lib = lib
@@ -340,3 +342,11 @@ def kernel_launches() -> int:
 
 def version() -> str:
     return load_library().rici_version().decode()
+
+
+def measure_dp4a_rate(stream=None) -> float:
+    """Whole-device dp4a instructions per second (the search kernel's multiply pipe)."""
+    lib = load_library()
+    out = ctypes.c_double(0.0)
+    _check(lib.rici_measure_dp4a_rate(_stream_handle(stream), ctypes.byref(out)))
+    return float(out.value)

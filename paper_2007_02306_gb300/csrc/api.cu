@@ -442,6 +442,13 @@ const char *rici_last_error_string(void) { return t_last_error.c_str(); }
 
 int64_t rici_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 
+int rici_measure_dp4a_rate(void *stream, double *dp4a_per_second) {
+  if (!dp4a_per_second) return fail(RICI_ERR_INVALID_ARGUMENT, "null output pointer");
+  cudaError_t e = measure_dp4a_rate(static_cast<cudaStream_t>(stream), dp4a_per_second);
+  if (e != cudaSuccess) return cuda_fail(e, "dp4a rate");
+  return RICI_OK;
+}
+
 const char *rici_version(void) { return "rici-gb300 0.1 (sm_103a)"; }
 
 }  // extern "C"

@@ -146,4 +146,7 @@ void count_launches(int64_t n);
 // Device address of the status word on the current device.
 cudaError_t status_word_address(int **address);
 
+// Measured whole-device dp4a issue rate (instructions per second), for roofline peaks.
+cudaError_t measure_dp4a_rate(cudaStream_t st, double *per_second);
+
 }  // namespace rici
