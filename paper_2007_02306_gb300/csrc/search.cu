@@ -47,11 +47,12 @@ __device__ __forceinline__ int64_t interleaved_offset(int64_t i, int N, int k) {
 }
 
 // One warp per image.  interleave: write the deltas in the layout of interleaved_offset (the
-// haystack of the dense kernel) instead of image-major.
+// haystack of the dense kernel) instead of image-major.  row_sq (optional): per row, the sum of
+// the squared (clamped) deltas, [n][N].
 __global__ void k_encode(const uint16_t *__restrict__ imgs, int64_t n, int N,
                          int8_t *__restrict__ delta, int8_t *__restrict__ mask,
                          int *__restrict__ wide_flag, int *__restrict__ wide_list,
-                         int *__restrict__ wide_count, int interleave) {
+                         int *__restrict__ wide_count, int interleave, int *__restrict__ row_sq) {
   const int lane = threadIdx.x & 31;
   const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
@@ -66,6 +67,17 @@ __global__ void k_encode(const uint16_t *__restrict__ imgs, int64_t n, int N,
       int dc = d > 127 ? 127 : (d < -127 ? -127 : d);
       delta[interleave ? interleaved_offset(i, N, k) : i * K + k] = (int8_t)dc;
       if (mask) mask[i * K + k] = (int8_t)(d != 0 ? -1 : 0);
+    }
+    if (row_sq) {
+      for (int r = lane; r < N; r += 32) {
+        int sq = 0;
+        for (int c = 1; c < N; ++c) {
+          int d = delta_at(img, N, r, c);
+          d = d > 127 ? 127 : (d < -127 ? -127 : d);
+          sq += d * d;
+        }
+        row_sq[i * N + r] = sq;
+      }
     }
     wide = __any_sync(0xffffffffu, wide);
     if (lane == 0) {
@@ -178,7 +190,8 @@ __device__ __forceinline__ unsigned long long warp_min_u64(unsigned long long v)
 template <int N, int kTQ>
 __global__ void __launch_bounds__(kDenseThreads) k_dense(
     const int8_t *__restrict__ ndelta, const int8_t *__restrict__ nmask,
-    const int *__restrict__ nwide, int64_t Q, const int8_t *__restrict__ hdelta,
+    const int *__restrict__ nrowsq, const int *__restrict__ nwide, int64_t Q,
+    const int8_t *__restrict__ hdelta,
     const int *__restrict__ hwide, int64_t H, const int64_t *__restrict__ dtrue,
     const int *__restrict__ nflags, int *__restrict__ rank, unsigned long long *__restrict__ best,
     unsigned long long *__restrict__ counters, int64_t tile0, int64_t tiles_q, int64_t tiles_h) {
@@ -230,13 +243,7 @@ __global__ void __launch_bounds__(kDenseThreads) k_dense(
   // tile has a non-zero delta contribute nothing and are skipped.
   for (int x = tid; x < kTQ * N; x += kDenseThreads) {
     int q = x / N, r = x - q * N;
-    int w = 0;
-#pragma unroll
-    for (int v = 0; v < WPR; ++v) {
-      int av = am[q][r * WPR + v].x;
-      w = __dp4a(av, av, w);
-    }
-    wrow[q][r] = act_s[q] ? w : 0;
+    wrow[q][r] = act_s[q] ? nrowsq[(q0 + q) * N + r] : 0;
   }
   __syncthreads();
   __shared__ int tile_w[N];
@@ -307,21 +314,31 @@ __global__ void __launch_bounds__(kDenseThreads) k_dense(
       if (__ballot_sync(0xffffffffu, (use >> q) & 1u) == 0) continue;
       if (counters) lane_slots += 1;  // one warp-wide needle-row iteration (32 lane slots)
       // row sum of m (a - b)^2 = sum a^2 + sum (m b)^2 - 2 sum a b, with sum a^2 precomputed;
-      // two independent accumulator chains per term
-      int sbb0 = 0, sbb1 = 0, sab0 = 0, sab1 = 0;
+      // kChains independent accumulator chains per term
+      constexpr int kChains = WPR >= 8 ? 4 : 2;
+      int sbb[kChains], sab[kChains];
+#pragma unroll
+      for (int u = 0; u < kChains; ++u) sbb[u] = sab[u] = 0;
       const int4 *amq = reinterpret_cast<const int4 *>(&am[q][r * WPR]);
 #pragma unroll
       for (int v = 0; v < WPR; v += 2) {
         const int4 x = amq[v >> 1];  // (a_v, m_v, a_v+1, m_v+1)
         const int b0 = hw[v], b1 = hw[v + 1];
         const int bm0 = b0 & x.y, bm1 = b1 & x.w;
-        sbb0 = __dp4a(bm0, bm0, sbb0);
-        sab0 = __dp4a(x.x, b0, sab0);
-        sbb1 = __dp4a(bm1, bm1, sbb1);
-        sab1 = __dp4a(x.z, b1, sab1);
+        const int u = (v >> 1) % (kChains / 2) * 2;
+        sbb[u] = __dp4a(bm0, bm0, sbb[u]);
+        sab[u] = __dp4a(x.x, b0, sab[u]);
+        sbb[u + 1] = __dp4a(bm1, bm1, sbb[u + 1]);
+        sab[u + 1] = __dp4a(x.z, b1, sab[u + 1]);
+      }
+      int sb = 0, sa = 0;
+#pragma unroll
+      for (int u = 0; u < kChains; ++u) {
+        sb += sbb[u];
+        sa += sab[u];
       }
       if ((use >> q) & 1u) {
-        acc[q] += wrow[q][r] + (sbb0 + sbb1) - 2 * (sab0 + sab1);
+        acc[q] += wrow[q][r] + sb - 2 * sa;
         if (acc[q] > thr_s[q]) alive &= ~(1u << q);
       }
     }
@@ -524,7 +541,7 @@ __global__ void k_distances(const uint16_t *__restrict__ nimg, int64_t Q,
 bool dense_supported(int N) { return N == 8 || N == 16 || N == 32 || N == 64 || N == 128; }
 
 template <int N>
-cudaError_t launch_dense(const int8_t *nd, const int8_t *nm, const int *nw, int64_t Q,
+cudaError_t launch_dense(const int8_t *nd, const int8_t *nm, const int *nrs, const int *nw, int64_t Q,
                          const int8_t *hd, const int *hw, int64_t H, const int64_t *dt,
                          const int *nf, int *rank, unsigned long long *best,
                          unsigned long long *counters, cudaStream_t st) {
@@ -539,8 +556,8 @@ cudaError_t launch_dense(const int8_t *nd, const int8_t *nm, const int *nw, int6
   constexpr int64_t kMaxGrid = 0x7fffffffll;
   for (int64_t t0 = 0; t0 < total; t0 += kMaxGrid) {
     const int64_t n = total - t0 < kMaxGrid ? total - t0 : kMaxGrid;
-    k_dense<N, kTQ><<<(unsigned)n, kDenseThreads, smem, st>>>(nd, nm, nw, Q, hd, hw, H, dt, nf,
-                                                             rank, best, counters, t0, tq, th);
+    k_dense<N, kTQ><<<(unsigned)n, kDenseThreads, smem, st>>>(nd, nm, nrs, nw, Q, hd, hw, H, dt,
+                                                             nf, rank, best, counters, t0, tq, th);
     count_launches(1);
   }
   return cudaGetLastError();
@@ -564,6 +581,7 @@ int64_t search_batch_workspace_bytes(int num_scenes, int64_t Q, int64_t H, int N
   c.take<int>(H);                        // scene of each haystack image
   c.take<int8_t>(packed ? Q * K : 0);    // needle deltas (packed CUDA-core form only)
   c.take<int8_t>(packed ? Q * K : 0);    // needle masks
+  c.take<int>(packed ? Q * N : 0);       // needle row sums of squared deltas
   c.take<int8_t>(packed ? (H + 31) / 32 * 32 * K : 0);  // haystack deltas (groups of 32)
   c.take<int>(Q);                        // needle wide flags
   c.take<int>(H);                        // haystack wide flags
@@ -600,6 +618,7 @@ cudaError_t launch_search_batch(const SearchScene *scenes, const SearchBatch &b,
   int *hscene = c.take<int>(H);
   int8_t *nd = c.take<int8_t>(dense ? Q * K : 0);
   int8_t *nm = c.take<int8_t>(dense ? Q * K : 0);
+  int *nrs = c.take<int>(dense ? Q * N : 0);
   int8_t *hd = c.take<int8_t>(dense ? (H + 31) / 32 * 32 * K : 0);
   int *nwide = c.take<int>(Q);
   int *hwide = c.take<int>(H);
@@ -655,16 +674,16 @@ cudaError_t launch_search_batch(const SearchScene *scenes, const SearchBatch &b,
     // single scene: launch-wide indices are the scene's own
     const SearchScene &s0 = scenes[0];
     k_encode<<<blocks_for(Q), 32 * wpb, 0, st>>>(s0.needles, Q, N, nd, nm, nwide, wn_list,
-                                                 counts + 0, 0);
+                                                 counts + 0, 0, nrs);
     k_encode<<<blocks_for(H), 32 * wpb, 0, st>>>(s0.haystack, H, N, hd, nullptr, hwide, wh_list,
-                                                 counts + 1, 1);
+                                                 counts + 1, 1, nullptr);
     count_launches(2);
     switch (N) {
-      case 8: e = launch_dense<8>(nd, nm, nwide, Q, hd, hwide, H, dt, nflags, rank, best, cnt, st); break;
-      case 16: e = launch_dense<16>(nd, nm, nwide, Q, hd, hwide, H, dt, nflags, rank, best, cnt, st); break;
-      case 32: e = launch_dense<32>(nd, nm, nwide, Q, hd, hwide, H, dt, nflags, rank, best, cnt, st); break;
-      case 64: e = launch_dense<64>(nd, nm, nwide, Q, hd, hwide, H, dt, nflags, rank, best, cnt, st); break;
-      default: e = launch_dense<128>(nd, nm, nwide, Q, hd, hwide, H, dt, nflags, rank, best, cnt, st); break;
+      case 8: e = launch_dense<8>(nd, nm, nrs, nwide, Q, hd, hwide, H, dt, nflags, rank, best, cnt, st); break;
+      case 16: e = launch_dense<16>(nd, nm, nrs, nwide, Q, hd, hwide, H, dt, nflags, rank, best, cnt, st); break;
+      case 32: e = launch_dense<32>(nd, nm, nrs, nwide, Q, hd, hwide, H, dt, nflags, rank, best, cnt, st); break;
+      case 64: e = launch_dense<64>(nd, nm, nrs, nwide, Q, hd, hwide, H, dt, nflags, rank, best, cnt, st); break;
+      default: e = launch_dense<128>(nd, nm, nrs, nwide, Q, hd, hwide, H, dt, nflags, rank, best, cnt, st); break;
     }
     if (e != cudaSuccess) return e;
     wide(0);
