@@ -25,7 +25,7 @@
 namespace rici {
 namespace {
 
-constexpr int kDenseThreads = 256;     // haystack images per dense tile
+constexpr int kDenseThreads = 512;     // haystack images per dense tile
 constexpr int64_t kBandH = 8;          // haystack tiles per band of the dense tile order
 constexpr int kWideThreads = 256;
 constexpr unsigned long long kNoBest = ~0ull;
@@ -188,7 +188,7 @@ __device__ __forceinline__ unsigned long long warp_min_u64(unsigned long long v)
 // Narrow x narrow pairs.  Block: kTQ needles (deltas + masks in shared memory) x
 // kDenseThreads haystack images (one per thread).
 template <int N, int kTQ>
-__global__ void __launch_bounds__(kDenseThreads) k_dense(
+__global__ void __launch_bounds__(kDenseThreads, N <= 64 ? 2 : 1) k_dense(
     const int8_t *__restrict__ ndelta, const int8_t *__restrict__ nmask,
     const int *__restrict__ nrowsq, const int *__restrict__ nwide, int64_t Q,
     const int8_t *__restrict__ hdelta,
@@ -206,20 +206,15 @@ __global__ void __launch_bounds__(kDenseThreads) k_dense(
   __shared__ unsigned rmask[N];    // needles of the tile with a non-zero delta in the row
   __shared__ int nrows_s;
   const int tid = threadIdx.x, lane = tid & 31;
-  // Tile order: bands of kBandH haystack tiles; within a band the haystack tile varies fastest,
-  // then the needle tile, so a band's haystack images are read from DRAM once and reused from L2
-  // by every needle tile.
-  int64_t qt, ht;
-  {
-    const int64_t L = tile0 + blockIdx.x;
-    const int64_t band = L / (kBandH * tiles_q), rem = L - band * (kBandH * tiles_q);
-    const int64_t h0 = band * kBandH;
-    const int64_t bh = tiles_h - h0 < kBandH ? tiles_h - h0 : kBandH;
-    qt = rem / bh;
-    ht = h0 + (rem - qt * bh);
-  }
+  // Work order: bands of kBandH haystack tiles.  A block holds one needle tile and sweeps the
+  // haystack tiles of one band; consecutive blocks take consecutive needle tiles of the same band,
+  // so a band's haystack images are read from DRAM once and reused from L2 by every needle tile,
+  // and the needle tile's set-up (shared-memory fill, row order) is paid once per band.
+  const int64_t L = tile0 + blockIdx.x;
+  const int64_t band = L / tiles_q, qt = L - band * tiles_q;
+  const int64_t h0 = band * kBandH;
+  const int64_t h1 = tiles_h - h0 < kBandH ? tiles_h : h0 + kBandH;
   const int64_t q0 = qt * kTQ;
-  const int64_t j = ht * kDenseThreads + tid;
 
   for (int x = tid; x < kTQ * (K / 4); x += kDenseThreads) {
     int q = x / (K / 4), wd = x - q * (K / 4);
@@ -273,96 +268,99 @@ __global__ void __launch_bounds__(kDenseThreads) k_dense(
   __syncthreads();
   const int nrows = nrows_s;
 
-  const bool valid = j < H && !hwide[j];
-  int acc[kTQ];
-  unsigned alive = 0;
+  for (int64_t ht = h0; ht < h1; ++ht) {
+    const int64_t j = ht * kDenseThreads + tid;
+    const bool valid = j < H && !hwide[j];
+    int acc[kTQ];
+    unsigned alive = 0;
 #pragma unroll
-  for (int q = 0; q < kTQ; ++q) {
-    acc[q] = 0;
-    if (valid && act_s[q]) alive |= 1u << q;
-  }
-  // this thread's image in the warp-interleaved layout (group of 32 images, chunks of CW words)
-  constexpr int CW = WPR < 4 ? WPR : 4;
-  const int *hgrp = reinterpret_cast<const int *>(hdelta) + (j >> 5) * (int64_t)(N * WPR * 32) +
-                    lane * CW;
-  unsigned long long pair_rows = 0, lane_slots = 0;
-  for (int i = 0; i < nrows; ++i) {
-    if (__ballot_sync(0xffffffffu, alive != 0) == 0) break;
-    const int r = ord[i];
-    const unsigned use = alive & rmask[r];
-    if (counters) pair_rows += __popc(use);
-    int hw[WPR];
-    if (use) {
-      const int *src = hgrp + r * (WPR * 32);
+    for (int q = 0; q < kTQ; ++q) {
+      acc[q] = 0;
+      if (valid && act_s[q]) alive |= 1u << q;
+    }
+    // this thread's image in the warp-interleaved layout (group of 32 images, chunks of CW words)
+    constexpr int CW = WPR < 4 ? WPR : 4;
+    const int *hgrp = reinterpret_cast<const int *>(hdelta) + (j >> 5) * (int64_t)(N * WPR * 32) +
+                      lane * CW;
+    unsigned long long pair_rows = 0, lane_slots = 0;
+    for (int i = 0; i < nrows; ++i) {
+      if (__ballot_sync(0xffffffffu, alive != 0) == 0) break;
+      const int r = ord[i];
+      const unsigned use = alive & rmask[r];
+      if (counters) pair_rows += __popc(use);
+      int hw[WPR];
+      if (use) {
+        const int *src = hgrp + r * (WPR * 32);
 #pragma unroll
-      for (int v = 0; v < WPR / CW; ++v) {
-        if constexpr (CW == 4) {
-          const int4 x = *reinterpret_cast<const int4 *>(src + v * 32 * CW);
-          hw[4 * v] = x.x;
-          hw[4 * v + 1] = x.y;
-          hw[4 * v + 2] = x.z;
-          hw[4 * v + 3] = x.w;
-        } else {
-          const int2 x = *reinterpret_cast<const int2 *>(src + v * 32 * CW);
-          hw[2 * v] = x.x;
-          hw[2 * v + 1] = x.y;
+        for (int v = 0; v < WPR / CW; ++v) {
+          if constexpr (CW == 4) {
+            const int4 x = *reinterpret_cast<const int4 *>(src + v * 32 * CW);
+            hw[4 * v] = x.x;
+            hw[4 * v + 1] = x.y;
+            hw[4 * v + 2] = x.z;
+            hw[4 * v + 3] = x.w;
+          } else {
+            const int2 x = *reinterpret_cast<const int2 *>(src + v * 32 * CW);
+            hw[2 * v] = x.x;
+            hw[2 * v + 1] = x.y;
+          }
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < kTQ; ++q) {
+        if (__ballot_sync(0xffffffffu, (use >> q) & 1u) == 0) continue;
+        if (counters) lane_slots += 1;  // one warp-wide needle-row iteration (32 lane slots)
+        // row sum of m (a - b)^2 = sum a^2 + sum (m b)^2 - 2 sum a b, with sum a^2 precomputed;
+        // kChains independent accumulator chains per term
+        constexpr int kChains = WPR >= 8 ? 4 : 2;
+        int sbb[kChains], sab[kChains];
+#pragma unroll
+        for (int u = 0; u < kChains; ++u) sbb[u] = sab[u] = 0;
+        const int4 *amq = reinterpret_cast<const int4 *>(&am[q][r * WPR]);
+#pragma unroll
+        for (int v = 0; v < WPR; v += 2) {
+          const int4 x = amq[v >> 1];  // (a_v, m_v, a_v+1, m_v+1)
+          const int b0 = hw[v], b1 = hw[v + 1];
+          const int bm0 = b0 & x.y, bm1 = b1 & x.w;
+          const int u = (v >> 1) % (kChains / 2) * 2;
+          sbb[u] = __dp4a(bm0, bm0, sbb[u]);
+          sab[u] = __dp4a(x.x, b0, sab[u]);
+          sbb[u + 1] = __dp4a(bm1, bm1, sbb[u + 1]);
+          sab[u + 1] = __dp4a(x.z, b1, sab[u + 1]);
+        }
+        int sb = 0, sa = 0;
+#pragma unroll
+        for (int u = 0; u < kChains; ++u) {
+          sb += sbb[u];
+          sa += sab[u];
+        }
+        if ((use >> q) & 1u) {
+          acc[q] += wrow[q][r] + sb - 2 * sa;
+          if (acc[q] > thr_s[q]) alive &= ~(1u << q);
         }
       }
     }
+    // count and top-1 candidates (pairs that never exceeded the threshold hold exact values)
 #pragma unroll
     for (int q = 0; q < kTQ; ++q) {
-      if (__ballot_sync(0xffffffffu, (use >> q) & 1u) == 0) continue;
-      if (counters) lane_slots += 1;  // one warp-wide needle-row iteration (32 lane slots)
-      // row sum of m (a - b)^2 = sum a^2 + sum (m b)^2 - 2 sum a b, with sum a^2 precomputed;
-      // kChains independent accumulator chains per term
-      constexpr int kChains = WPR >= 8 ? 4 : 2;
-      int sbb[kChains], sab[kChains];
+      if (!act_s[q]) continue;
+      const bool fin = (alive >> q) & 1u;
+      int c = fin && acc[q] < thr_s[q];
+      unsigned long long b = fin ? pack_best(acc[q], j) : kNoBest;
 #pragma unroll
-      for (int u = 0; u < kChains; ++u) sbb[u] = sab[u] = 0;
-      const int4 *amq = reinterpret_cast<const int4 *>(&am[q][r * WPR]);
-#pragma unroll
-      for (int v = 0; v < WPR; v += 2) {
-        const int4 x = amq[v >> 1];  // (a_v, m_v, a_v+1, m_v+1)
-        const int b0 = hw[v], b1 = hw[v + 1];
-        const int bm0 = b0 & x.y, bm1 = b1 & x.w;
-        const int u = (v >> 1) % (kChains / 2) * 2;
-        sbb[u] = __dp4a(bm0, bm0, sbb[u]);
-        sab[u] = __dp4a(x.x, b0, sab[u]);
-        sbb[u + 1] = __dp4a(bm1, bm1, sbb[u + 1]);
-        sab[u + 1] = __dp4a(x.z, b1, sab[u + 1]);
-      }
-      int sb = 0, sa = 0;
-#pragma unroll
-      for (int u = 0; u < kChains; ++u) {
-        sb += sbb[u];
-        sa += sab[u];
-      }
-      if ((use >> q) & 1u) {
-        acc[q] += wrow[q][r] + sb - 2 * sa;
-        if (acc[q] > thr_s[q]) alive &= ~(1u << q);
+      for (int d = 16; d > 0; d >>= 1) c += __shfl_down_sync(0xffffffffu, c, d);
+      b = warp_min_u64(b);
+      if (lane == 0) {
+        if (c) atomicAdd(&rank[q0 + q], c);
+        if (b != kNoBest) atomicMin(&best[q0 + q], b);
       }
     }
-  }
-  // count and top-1 candidates (pairs that never exceeded the threshold hold exact values)
+    if (counters) {
 #pragma unroll
-  for (int q = 0; q < kTQ; ++q) {
-    if (!act_s[q]) continue;
-    const bool fin = (alive >> q) & 1u;
-    int c = fin && acc[q] < thr_s[q];
-    unsigned long long b = fin ? pack_best(acc[q], j) : kNoBest;
-#pragma unroll
-    for (int d = 16; d > 0; d >>= 1) c += __shfl_down_sync(0xffffffffu, c, d);
-    b = warp_min_u64(b);
-    if (lane == 0) {
-      if (c) atomicAdd(&rank[q0 + q], c);
-      if (b != kNoBest) atomicMin(&best[q0 + q], b);
+      for (int d = 16; d > 0; d >>= 1) pair_rows += __shfl_down_sync(0xffffffffu, pair_rows, d);
+      if (lane == 0 && pair_rows) atomicAdd(counters, pair_rows);
+      if (lane == 0 && lane_slots) atomicAdd(counters + 3, 32ull * lane_slots);
     }
-  }
-  if (counters) {
-#pragma unroll
-    for (int d = 16; d > 0; d >>= 1) pair_rows += __shfl_down_sync(0xffffffffu, pair_rows, d);
-    if (lane == 0 && pair_rows) atomicAdd(counters, pair_rows);
-    if (lane == 0 && lane_slots) atomicAdd(counters + 3, 32ull * lane_slots);
   }
 }
 
@@ -552,7 +550,7 @@ cudaError_t launch_dense(const int8_t *nd, const int8_t *nm, const int *nrs, con
   if (e != cudaSuccess) return e;
   const int64_t th = (H + kDenseThreads - 1) / kDenseThreads;
   const int64_t tq = (Q + kTQ - 1) / kTQ;
-  const int64_t total = th * tq;
+  const int64_t total = (th + kBandH - 1) / kBandH * tq;
   constexpr int64_t kMaxGrid = 0x7fffffffll;
   for (int64_t t0 = 0; t0 < total; t0 += kMaxGrid) {
     const int64_t n = total - t0 < kMaxGrid ? total - t0 : kMaxGrid;
