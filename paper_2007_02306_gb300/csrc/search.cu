@@ -26,7 +26,7 @@ namespace rici {
 namespace {
 
 constexpr int kDenseThreads = 512;     // haystack images per dense tile
-constexpr int64_t kBandH = 8;          // haystack tiles per band of the dense tile order
+constexpr int64_t kBandMax = 8;        // haystack tiles per band of the dense work order
 constexpr int kWideThreads = 256;
 constexpr unsigned long long kNoBest = ~0ull;
 
@@ -194,7 +194,8 @@ __global__ void __launch_bounds__(kDenseThreads, N <= 64 ? 2 : 1) k_dense(
     const int8_t *__restrict__ hdelta,
     const int *__restrict__ hwide, int64_t H, const int64_t *__restrict__ dtrue,
     const int *__restrict__ nflags, int *__restrict__ rank, unsigned long long *__restrict__ best,
-    unsigned long long *__restrict__ counters, int64_t tile0, int64_t tiles_q, int64_t tiles_h) {
+    unsigned long long *__restrict__ counters, int64_t tile0, int64_t tiles_q, int64_t tiles_h,
+    int64_t band_h) {
   constexpr int WPR = N / 4;  // 32-bit words per row
   constexpr int K = N * N;
   extern __shared__ int2 am_raw[];  // [kTQ][K/4] (needle delta word, mask word)
@@ -206,14 +207,14 @@ __global__ void __launch_bounds__(kDenseThreads, N <= 64 ? 2 : 1) k_dense(
   __shared__ unsigned rmask[N];    // needles of the tile with a non-zero delta in the row
   __shared__ int nrows_s;
   const int tid = threadIdx.x, lane = tid & 31;
-  // Work order: bands of kBandH haystack tiles.  A block holds one needle tile and sweeps the
+  // Work order: bands of band_h haystack tiles.  A block holds one needle tile and sweeps the
   // haystack tiles of one band; consecutive blocks take consecutive needle tiles of the same band,
   // so a band's haystack images are read from DRAM once and reused from L2 by every needle tile,
   // and the needle tile's set-up (shared-memory fill, row order) is paid once per band.
   const int64_t L = tile0 + blockIdx.x;
   const int64_t band = L / tiles_q, qt = L - band * tiles_q;
-  const int64_t h0 = band * kBandH;
-  const int64_t h1 = tiles_h - h0 < kBandH ? tiles_h : h0 + kBandH;
+  const int64_t h0 = band * band_h;
+  const int64_t h1 = tiles_h - h0 < band_h ? tiles_h : h0 + band_h;
   const int64_t q0 = qt * kTQ;
 
   for (int x = tid; x < kTQ * (K / 4); x += kDenseThreads) {
@@ -550,12 +551,19 @@ cudaError_t launch_dense(const int8_t *nd, const int8_t *nm, const int *nrs, con
   if (e != cudaSuccess) return e;
   const int64_t th = (H + kDenseThreads - 1) / kDenseThreads;
   const int64_t tq = (Q + kTQ - 1) / kTQ;
-  const int64_t total = (th + kBandH - 1) / kBandH * tq;
+  // bands as long as possible while the grid still gives every SM a few waves of blocks
+  int dev = 0, sms = 152;
+  if (cudaGetDevice(&dev) == cudaSuccess)
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  int64_t band_h = th * tq / ((int64_t)sms * 2 * 4);
+  band_h = band_h < 1 ? 1 : (band_h > kBandMax ? kBandMax : band_h);
+  const int64_t total = (th + band_h - 1) / band_h * tq;
   constexpr int64_t kMaxGrid = 0x7fffffffll;
   for (int64_t t0 = 0; t0 < total; t0 += kMaxGrid) {
     const int64_t n = total - t0 < kMaxGrid ? total - t0 : kMaxGrid;
     k_dense<N, kTQ><<<(unsigned)n, kDenseThreads, smem, st>>>(nd, nm, nrs, nw, Q, hd, hw, H, dt,
-                                                             nf, rank, best, counters, t0, tq, th);
+                                                             nf, rank, best, counters, t0, tq, th,
+                                                             band_h);
     count_launches(1);
   }
   return cudaGetLastError();
