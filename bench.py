@@ -52,6 +52,13 @@ MACS_PER_TERM = 2
 # dp4a instructions per SM per clock: half the 128 FP32 lanes (a microbenchmark of independent
 # dp4a chains measured 61.3 per SM per clock at 2070 MHz; FFMA measured 117.3)
 DP4A_PER_SM_CLK = 64
+# DRAM bytes (read + write) per launch from one ncu capture of the current kernels (dram__bytes_read
+# and dram__bytes_write; commands in profiles/): k_dense at the full clutter-scene size (one-pass
+# capture), k_generate on a 40,000-origin launch scaled by the number of origins (its traffic is
+# the images it writes plus a small read of the triangle records).  Set to None when a kernel
+# changes until it is captured again.
+TRAFFIC_DENSE_FULL = 2.97e9 + 5.5e6
+TRAFFIC_GEN_PER_ORIGIN = (23.6e6 + 278.7e6) / 40000
 
 
 def parse():
@@ -493,7 +500,8 @@ def main():
         "peak": mac_peak_gops,
         "work": f"{scnt[0]} (pair, row) evaluations x {N_RES - 1} masked squared differences x "
                 f"{MACS_PER_TERM} int8 multiply-adds",
-        "traffic": None,
+        "traffic": (TRAFFIC_DENSE_FULL if not (args.haystack_limit or args.needle_limit)
+                    else None),
         "peak_kind": f"derived: {sms} SMs x {DP4A_PER_SM_CLK} dp4a per clock x 4 MACs x "
                      f"{clk_mhz:.0f} MHz (median SM clock)",
         "measured_dp4a_per_sm_per_clk": dp4a_rate / sms / (clk_mhz * 1e6),
@@ -506,7 +514,7 @@ def main():
             "work": f"{F_PROJ} ops x 3 vertices per crossing (origin, triangle) pair + {F_LAYER} "
                     "ops per (origin, triangle, layer) crossing, counted by the oracle on 32 "
                     "sampled origins and scaled to all haystack origins",
-            "traffic": None,
+            "traffic": (TRAFFIC_GEN_PER_ORIGIN * V if TRAFFIC_GEN_PER_ORIGIN else None),
         }
     for r in rooflines.values():
         r["frac"] = r["achieved"] / r["peak"]
