@@ -238,38 +238,60 @@ def batched_comparison(p, torch, dev, stream, args, n_scenes=24, needles=256):
             p.rici_generate(x["V"], x["Nrm"], x["T"], x["oh"], R_SUP, N_RES, out=g1["out"])
             p.crss_search(g0["out"], g1["out"], x["m"], mode=p.SEARCH_TENSOR)
 
-    cs = torch.cuda.Stream(device=dev)
-    cs.wait_stream(stream)
-    with torch.cuda.stream(cs):
-        run_batched()
-    stream.wait_stream(cs)
-    torch.cuda.synchronize()
-    graph = torch.cuda.CUDAGraph()
-    with torch.cuda.graph(graph):
-        run_batched()
+    def capture():
+        cs = torch.cuda.Stream(device=dev)
+        cs.wait_stream(stream)
+        with torch.cuda.stream(cs):
+            run_batched()
+        stream.wait_stream(cs)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            run_batched()
+        return g
+
+    # a graph replays the launch shapes in force when it was captured: one with the default
+    # tuning, one with the autotuned tuning (measured on the first scenes, fresh cache)
+    from paper_2007_02306_gb300 import autotune
+
+    p.set_tuning(None)
+    graph_default = capture()
+    t_tune = time.time()
+    with tempfile.TemporaryDirectory() as td:
+        tuning = autotune.tune_batch(gen, srch, R_SUP, N_RES, gpu_name=torch.cuda.get_device_name(dev),
+                                     sample=4, path=os.path.join(td, "tuning.json"))
+    t_tune = time.time() - t_tune
+    graph = capture()
     for _ in range(2):
         graph.replay()
         run_plain()
+        graph_default.replay()
     torch.cuda.synchronize()
     reps = max(3, args.steps)
-    t_b, t_p = [], []
+    t_b, t_p, t_d = [], [], []
     for _ in range(reps):
-        e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+        e0, e1, e2, e3 = (torch.cuda.Event(enable_timing=True) for _ in range(4))
         e0.record(stream)
         graph.replay()
         e1.record(stream)
         run_plain()
         e2.record(stream)
+        graph_default.replay()
+        e3.record(stream)
         torch.cuda.synchronize()
         t_b.append(e0.elapsed_time(e1))
         t_p.append(e1.elapsed_time(e2))
+        t_d.append(e2.elapsed_time(e3))
     st = p.sync_status()
+    p.set_tuning(None)
     images = sum(g["origins"].numel() for g in gen)
     pairs = sum(x["on"].numel() * x["oh"].numel() for x in xs)
     return {"scenes": n_scenes, "triangles": int(sum(s.num_triangles for s in scenes)),
             "images": int(images), "comparisons": int(pairs),
             "batched_graph_ms": statistics.mean(t_b), "per_scene_calls_ms": statistics.mean(t_p),
             "speedup": statistics.mean(t_p) / statistics.mean(t_b),
+            "batched_graph_default_tuning_ms": statistics.mean(t_d),
+            "autotuned": tuning, "autotune_s": t_tune,
             "batched_images_per_s": images / (statistics.mean(t_b) / 1e3), "status": st,
             "recipe": "synth.scene_batch(seed=41, 24 scenes, 10k-300k triangles each), 256 needles "
                       "per scene (target alone) vs all scene vertices, tensor-core search"}

@@ -231,6 +231,49 @@ RICI_API const char *rici_last_error_string(void);
 /* Number of CUDA kernels this library has enqueued in the calling process so far. */
 RICI_API int64_t rici_kernel_launches(void);
 
+/* ------------------------------------------------------------------ launch tuning
+ * Launch shapes of the kernels.  None of them changes a result: images, distances, ranks and
+ * top-1 are bit-identical for every valid setting; only the speed differs.  The setting is
+ * process-wide (every device and stream) and is read when a call launches its kernels.  The
+ * paper has no counterpart (it fixes one kernel configuration for its GPU). */
+typedef struct RiciTuning {
+  int32_t gen_cells_per_reach; /* 2 or 3: generation grid cells per triangle reach (the support
+                                  sphere's radius plus the largest binned triangle's); each
+                                  oriented point scans (2 x this + 1)^3 cells. Default 2. */
+  float gen_big_radius;        /* in [1/16, 1]: triangles whose bounding radius exceeds this
+                                  fraction of the support sphere's radius are checked by every
+                                  oriented point of their scene instead of being binned.
+                                  Default 0.25. */
+  int32_t gen_warps;           /* 4 or 8 warps per oriented point. Default 4. */
+  int32_t tc_group_m;          /* 1..64: needle tiles of 128 that the tensor-core search sweeps
+                                  together over the haystack (L2 reuse). Default 8. */
+} RiciTuning;
+
+/* Sets the process-wide tuning; NULL restores the defaults.  RICI_ERR_INVALID_ARGUMENT when a
+ * field is out of range (nothing changes then). */
+RICI_API int rici_set_tuning(const RiciTuning *tuning);
+
+/* Copies the tuning in force to *tuning (RICI_ERR_INVALID_ARGUMENT for NULL). */
+RICI_API int rici_get_tuning(RiciTuning *tuning);
+
+/* Autotuner of the batched run.  Runs rici_generate_batch on the given scenes under each candidate
+ * generation setting (gen_cells_per_reach in {2,3} x gen_big_radius in {1/8, 1/4, 1/2} x
+ * gen_warps in {4,8}; the other fields as in force), one untimed warm-up and `repeats` (1..100)
+ * runs timed with CUDA events on `stream`, and writes the fastest setting to *best and its mean
+ * time in milliseconds to *best_ms (may be NULL).  The scenes' output images are written by every
+ * run (with identical results).  Synchronises the stream; the tuning in force is restored, not
+ * changed: apply *best with rici_set_tuning.  Arguments as for rici_generate_batch. */
+RICI_API int rici_autotune_generate_batch(const RiciGenerateScene *scenes, int32_t num_scenes,
+                                          float support_radius, int32_t resolution,
+                                          void *workspace, int64_t workspace_bytes, void *stream,
+                                          int32_t repeats, RiciTuning *best, float *best_ms);
+
+/* The same for crss_search_batch in RICI_SEARCH_TENSOR form over tc_group_m in {2,4,8,16,32}. */
+RICI_API int rici_autotune_search_batch(const RiciSearchScene *scenes, int32_t num_scenes,
+                                        int32_t resolution, void *workspace,
+                                        int64_t workspace_bytes, void *stream, int32_t repeats,
+                                        RiciTuning *best, float *best_ms);
+
 /* Measures, on the current device and the given stream, how many dp4a instructions (four int8
  * multiply-adds into an int32 each; the arithmetic of the CUDA-core search) the whole GPU issues
  * per second, running independent accumulator chains on every SM; the result goes to

@@ -104,6 +104,14 @@ def load_library(path: str | None = None):
         lib.rici_last_error_string.restype = ctypes.c_char_p
         lib.rici_kernel_launches.argtypes = []
         lib.rici_kernel_launches.restype = i64
+        lib.rici_set_tuning.argtypes = [P]
+        lib.rici_set_tuning.restype = ctypes.c_int
+        lib.rici_get_tuning.argtypes = [P]
+        lib.rici_get_tuning.restype = ctypes.c_int
+        lib.rici_autotune_generate_batch.argtypes = [P, i32, f32, i32, P, i64, P, i32, P, P]
+        lib.rici_autotune_generate_batch.restype = ctypes.c_int
+        lib.rici_autotune_search_batch.argtypes = [P, i32, i32, P, i64, P, i32, P, P]
+        lib.rici_autotune_search_batch.restype = ctypes.c_int
         lib.rici_measure_dp4a_rate.argtypes = [P, ctypes.POINTER(ctypes.c_double)]
         lib.rici_measure_dp4a_rate.restype = ctypes.c_int
         lib.rici_version.argtypes = []
@@ -240,6 +248,21 @@ def rici_generate_batch(scenes, support_radius: float, resolution: int, *, works
     """
     lib = load_library()
     N = int(resolution)
+    arr, outs = _gen_scene_array(scenes, N)
+    nb = lib.rici_generate_batch_workspace_size(arr, len(scenes), N)
+    if nb < 0:
+        _check(1)
+    dev = outs[0].device if outs else torch.device("cuda")
+    ws = workspace_tensor if workspace_tensor is not None else workspace(dev, nb)
+    if ws.numel() < nb:
+        raise ValueError(f"workspace_tensor needs {nb} bytes")
+    with torch.cuda.device(dev):
+        _check(lib.rici_generate_batch(arr, len(scenes), float(support_radius), N, _ptr(ws),
+                                       ws.numel(), _stream_handle(stream)))
+    return outs
+
+
+def _gen_scene_array(scenes, N):
     arr = (_GenScene * max(1, len(scenes)))()
     outs = []
     for k, sc in enumerate(scenes):
@@ -254,17 +277,7 @@ def rici_generate_batch(scenes, support_radius: float, resolution: int, *, works
         outs.append(out)
         arr[k] = _GenScene(_ptr0(v), _ptr0(n), v.shape[0], _ptr0(t), t.shape[0], _ptr0(o), o.numel(),
                            _ptr0(out))
-    nb = lib.rici_generate_batch_workspace_size(arr, len(scenes), N)
-    if nb < 0:
-        _check(1)
-    dev = outs[0].device if outs else torch.device("cuda")
-    ws = workspace_tensor if workspace_tensor is not None else workspace(dev, nb)
-    if ws.numel() < nb:
-        raise ValueError(f"workspace_tensor needs {nb} bytes")
-    with torch.cuda.device(dev):
-        _check(lib.rici_generate_batch(arr, len(scenes), float(support_radius), N, _ptr(ws),
-                                       ws.numel(), _stream_handle(stream)))
-    return outs
+    return arr, outs
 
 
 def generate_batch_workspace_bytes(scenes, resolution: int) -> int:
@@ -287,6 +300,21 @@ def crss_search_batch(scenes, resolution: int, *, mode: int = SEARCH_TENSOR, wor
     """
     lib = load_library()
     N = int(resolution)
+    arr, res = _search_scene_array(scenes, outputs)
+    nb = lib.crss_search_batch_workspace_size(arr, len(scenes), N, int(mode))
+    if nb < 0:
+        _check(1)
+    dev = scenes[0]["needles"].device if scenes else torch.device("cuda")
+    ws = workspace_tensor if workspace_tensor is not None else workspace(dev, nb)
+    if ws.numel() < nb:
+        raise ValueError(f"workspace_tensor needs {nb} bytes")
+    with torch.cuda.device(dev):
+        _check(lib.crss_search_batch(arr, len(scenes), N, int(mode), _ptr(ws), ws.numel(),
+                                     _stream_handle(stream)))
+    return res
+
+
+def _search_scene_array(scenes, outputs=None):
     arr = (_SearchScene * max(1, len(scenes)))()
     res = []
     for k, sc in enumerate(scenes):
@@ -305,17 +333,7 @@ def crss_search_batch(scenes, resolution: int, *, mode: int = SEARCH_TENSOR, wor
         res.append(r)
         arr[k] = _SearchScene(_ptr0(q), q.shape[0], _ptr0(h), h.shape[0], _ptr0(m),
                               _ptr0(r["rank"]), _ptr0(r["true_distance"]), _ptr0(r["top1"]))
-    nb = lib.crss_search_batch_workspace_size(arr, len(scenes), N, int(mode))
-    if nb < 0:
-        _check(1)
-    dev = scenes[0]["needles"].device if scenes else torch.device("cuda")
-    ws = workspace_tensor if workspace_tensor is not None else workspace(dev, nb)
-    if ws.numel() < nb:
-        raise ValueError(f"workspace_tensor needs {nb} bytes")
-    with torch.cuda.device(dev):
-        _check(lib.crss_search_batch(arr, len(scenes), N, int(mode), _ptr(ws), ws.numel(),
-                                     _stream_handle(stream)))
-    return res
+    return arr, res
 
 
 def search_batch_workspace_bytes(scenes, resolution: int, mode: int = SEARCH_TENSOR) -> int:
@@ -350,3 +368,73 @@ def measure_dp4a_rate(stream=None) -> float:
     out = ctypes.c_double(0.0)
     _check(lib.rici_measure_dp4a_rate(_stream_handle(stream), ctypes.byref(out)))
     return float(out.value)
+
+
+class _Tuning(ctypes.Structure):
+    _fields_ = [("gen_cells_per_reach", ctypes.c_int32), ("gen_big_radius", ctypes.c_float),
+                ("gen_warps", ctypes.c_int32), ("tc_group_m", ctypes.c_int32)]
+
+
+TUNING_FIELDS = tuple(f for f, _ in _Tuning._fields_)
+
+
+def _tuning_dict(t: _Tuning) -> dict:
+    return {f: (float(getattr(t, f)) if f == "gen_big_radius" else int(getattr(t, f)))
+            for f in TUNING_FIELDS}
+
+
+def get_tuning() -> dict:
+    """The process-wide launch tuning in force (see RiciTuning in include/rici.h)."""
+    t = _Tuning()
+    _check(load_library().rici_get_tuning(ctypes.byref(t)))
+    return _tuning_dict(t)
+
+
+def set_tuning(tuning=None) -> None:
+    """Set the launch tuning (a dict with every field of RiciTuning); None restores defaults."""
+    lib = load_library()
+    if tuning is None:
+        _check(lib.rici_set_tuning(None))
+        return
+    missing = [f for f in TUNING_FIELDS if f not in tuning]
+    if missing:
+        raise ValueError(f"tuning lacks {missing}")
+    t = _Tuning(*(tuning[f] for f in TUNING_FIELDS))
+    _check(lib.rici_set_tuning(ctypes.byref(t)))
+
+
+def autotune_generate_batch(scenes, support_radius: float, resolution: int, *, repeats: int = 1,
+                            stream=None):
+    """Time every candidate generation tuning on these scenes; returns (best tuning, ms)."""
+    lib = load_library()
+    N = int(resolution)
+    arr, outs = _gen_scene_array(scenes, N)
+    nb = lib.rici_generate_batch_workspace_size(arr, len(scenes), N)
+    if nb < 0:
+        _check(1)
+    dev = outs[0].device if outs else torch.device("cuda")
+    ws = workspace(dev, nb)
+    best, ms = _Tuning(), ctypes.c_float(0.0)
+    with torch.cuda.device(dev):
+        _check(lib.rici_autotune_generate_batch(arr, len(scenes), float(support_radius), N, _ptr(ws),
+                                                ws.numel(), _stream_handle(stream), int(repeats),
+                                                ctypes.byref(best), ctypes.byref(ms)))
+    return _tuning_dict(best), float(ms.value)
+
+
+def autotune_search_batch(scenes, resolution: int, *, repeats: int = 1, stream=None):
+    """Time every candidate tensor-core search tuning on these scenes; returns (best, ms)."""
+    lib = load_library()
+    N = int(resolution)
+    arr, _ = _search_scene_array(scenes)
+    nb = lib.crss_search_batch_workspace_size(arr, len(scenes), N, SEARCH_TENSOR)
+    if nb < 0:
+        _check(1)
+    dev = scenes[0]["needles"].device if scenes else torch.device("cuda")
+    ws = workspace(dev, nb)
+    best, ms = _Tuning(), ctypes.c_float(0.0)
+    with torch.cuda.device(dev):
+        _check(lib.rici_autotune_search_batch(arr, len(scenes), N, _ptr(ws), ws.numel(),
+                                              _stream_handle(stream), int(repeats),
+                                              ctypes.byref(best), ctypes.byref(ms)))
+    return _tuning_dict(best), float(ms.value)

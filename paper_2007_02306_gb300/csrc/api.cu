@@ -121,6 +121,89 @@ cudaError_t status_word_address(int **address) {
 
 }  // namespace rici
 
+namespace rici {
+namespace {
+std::mutex g_tune_mu;
+const Tuning kDefaultTuning = {2, 0.25f, 4, 8};
+Tuning g_tuning = kDefaultTuning;
+
+bool tuning_valid(const RiciTuning &t) {
+  return (t.gen_cells_per_reach == 2 || t.gen_cells_per_reach == 3) &&
+         t.gen_big_radius >= 0.0625f && t.gen_big_radius <= 1.0f &&
+         (t.gen_warps == 4 || t.gen_warps == 8) && t.tc_group_m >= 1 && t.tc_group_m <= 64;
+}
+
+RiciTuning to_public(const Tuning &t) {
+  RiciTuning r;
+  memset(&r, 0, sizeof(r));
+  r.gen_cells_per_reach = t.gen_cells_per_reach;
+  r.gen_big_radius = t.gen_big_radius;
+  r.gen_warps = t.gen_warps;
+  r.tc_group_m = t.tc_group_m;
+  return r;
+}
+
+Tuning from_public(const RiciTuning &r) {
+  return Tuning{r.gen_cells_per_reach, r.gen_big_radius, r.gen_warps, r.tc_group_m};
+}
+
+void store_tuning(const Tuning &t) {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tuning = t;
+}
+
+// Times `run` under each candidate tuning (one untimed warm-up, then `repeats` timed runs with
+// CUDA events on the stream) and reports the fastest.  The tuning in force before the call is
+// restored whatever happens.
+template <class Run>
+int autotune(const std::vector<Tuning> &cands, int32_t repeats, void *stream, Run run,
+             RiciTuning *best, float *best_ms) {
+  if (!best) return fail(RICI_ERR_INVALID_ARGUMENT, "null output pointer");
+  if (repeats < 1 || repeats > 100) return fail(RICI_ERR_INVALID_ARGUMENT, "repeats in [1, 100]");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const Tuning saved = current_tuning();
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  cudaError_t e;
+  if ((e = cudaEventCreate(&e0)) != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
+  if ((e = cudaEventCreate(&e1)) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return cuda_fail(e, "cudaEventCreate");
+  }
+  int rc = RICI_OK;
+  float best_t = 0.0f;
+  Tuning best_c = saved;
+  for (size_t i = 0; i < cands.size() && rc == RICI_OK; ++i) {
+    store_tuning(cands[i]);
+    if ((rc = run()) != RICI_OK) break;
+    if ((e = cudaEventRecord(e0, st)) != cudaSuccess) { rc = cuda_fail(e, "event"); break; }
+    for (int r = 0; r < repeats && rc == RICI_OK; ++r) rc = run();
+    if (rc != RICI_OK) break;
+    if ((e = cudaEventRecord(e1, st)) != cudaSuccess) { rc = cuda_fail(e, "event"); break; }
+    if ((e = cudaEventSynchronize(e1)) != cudaSuccess) { rc = cuda_fail(e, "event sync"); break; }
+    float ms = 0.0f;
+    if ((e = cudaEventElapsedTime(&ms, e0, e1)) != cudaSuccess) { rc = cuda_fail(e, "elapsed"); break; }
+    ms /= (float)repeats;
+    if (i == 0 || ms < best_t) {
+      best_t = ms;
+      best_c = cands[i];
+    }
+  }
+  store_tuning(saved);
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (rc != RICI_OK) return rc;
+  *best = to_public(best_c);
+  if (best_ms) *best_ms = best_t;
+  return RICI_OK;
+}
+}  // namespace
+
+Tuning current_tuning() {
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  return g_tuning;
+}
+}  // namespace rici
+
 using namespace rici;
 
 extern "C" {
@@ -450,5 +533,63 @@ int rici_measure_dp4a_rate(void *stream, double *dp4a_per_second) {
 }
 
 const char *rici_version(void) { return "rici-gb300 0.1 (sm_103a)"; }
+
+int rici_set_tuning(const RiciTuning *tuning) {
+  if (!tuning) {
+    store_tuning(kDefaultTuning);
+    return RICI_OK;
+  }
+  if (!tuning_valid(*tuning))
+    return fail(RICI_ERR_INVALID_ARGUMENT,
+                "tuning out of range (cells per reach 2|3, big radius [1/16,1], warps 4|8, "
+                "group 1..64)");
+  store_tuning(from_public(*tuning));
+  return RICI_OK;
+}
+
+int rici_get_tuning(RiciTuning *tuning) {
+  if (!tuning) return fail(RICI_ERR_INVALID_ARGUMENT, "null output pointer");
+  *tuning = to_public(current_tuning());
+  return RICI_OK;
+}
+
+int rici_autotune_generate_batch(const RiciGenerateScene *scenes, int32_t num_scenes,
+                                 float support_radius, int32_t resolution, void *workspace,
+                                 int64_t workspace_bytes, void *stream, int32_t repeats,
+                                 RiciTuning *best, float *best_ms) {
+  t_last_error.clear();
+  std::vector<Tuning> cands;
+  const Tuning base = current_tuning();
+  const int cells[] = {2, 3};
+  const float big[] = {0.125f, 0.25f, 0.5f};
+  const int warps[] = {4, 8};
+  for (int c : cells)
+    for (float b : big)
+      for (int w : warps) cands.push_back(Tuning{c, b, w, base.tc_group_m});
+  return autotune(
+      cands, repeats, stream,
+      [&]() {
+        return rici_generate_batch(scenes, num_scenes, support_radius, resolution, workspace,
+                                   workspace_bytes, stream);
+      },
+      best, best_ms);
+}
+
+int rici_autotune_search_batch(const RiciSearchScene *scenes, int32_t num_scenes,
+                               int32_t resolution, void *workspace, int64_t workspace_bytes,
+                               void *stream, int32_t repeats, RiciTuning *best, float *best_ms) {
+  t_last_error.clear();
+  std::vector<Tuning> cands;
+  const Tuning base = current_tuning();
+  for (int g : {2, 4, 8, 16, 32})
+    cands.push_back(Tuning{base.gen_cells_per_reach, base.gen_big_radius, base.gen_warps, g});
+  return autotune(
+      cands, repeats, stream,
+      [&]() {
+        return crss_search_batch(scenes, num_scenes, resolution, RICI_SEARCH_TENSOR, workspace,
+                                 workspace_bytes, stream);
+      },
+      best, best_ms);
+}
 
 }  // extern "C"

@@ -95,6 +95,16 @@ struct SearchScene {
   int32_t tiles_m, tiles_n;
 };
 
+// Launch shapes that do not change any result (set through rici_set_tuning; see RiciTuning).
+struct Tuning {
+  int gen_cells_per_reach;  // generation grid: cells per triangle reach (2 or 3)
+  float gen_big_radius;     // triangles wider than this fraction of the support sphere are
+                            // listed once per scene instead of being binned
+  int gen_warps;            // warps per oriented point (4 or 8)
+  int tc_group_m;           // tensor-core needle tiles swept together over the haystack
+};
+Tuning current_tuning();
+
 struct SearchBatch {
   int num_scenes;
   int64_t Qtot, Htot, Hmax, tiles_total;

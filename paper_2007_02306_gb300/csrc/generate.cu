@@ -32,10 +32,8 @@ constexpr float kU = 5.9604644775390625e-08f;  // 2^-24: unit roundoff of FP32
 constexpr float kSafety = 2.0f;                // multiplies every derived error bound
 constexpr uint32_t kSkip = 0xFFFFFFFEu;
 constexpr float kCellClamp = 1048576.0f;  // |cell coordinate| limit (2^20)
-constexpr int kWarps = 4;
 constexpr int kSlot = 25;  // words per staged triangle (odd stride: conflict-free lookups)
 constexpr int kScanItems = 2048;
-constexpr int kNeigh = 125;  // 5 x 5 x 5 neighbouring cells
 constexpr int kPerWarp = 64 + 32 + 64 + 64 + 32 * kSlot;  // shared words per warp
 
 __host__ __device__ inline uint32_t bucket_count(int64_t nt) {
@@ -269,6 +267,7 @@ struct KArgs {
   float alpha_cull;  // pretest radius limit (alpha_{N-1} plus margin)
   float beta_cull;   // pretest height limit (beta_{N-1} plus margin)
   int mode;
+  int nhalf;        // neighbourhood half-width in cells (cell edge > reach / nhalf)
   unsigned long long *counters;
   int *status;
 };
@@ -280,7 +279,7 @@ struct Shared {
   float *a2f;    // alpha_c^2 rounded to FP32
   float *bf;     // beta_r rounded to FP32
   double *fr;    // S (3 doubles), Nax, Nay, Nbx, Nbz
-  int *buckets;  // neighbour buckets (kNeigh cells + the big list)
+  int *buckets;  // neighbour buckets ((2 nhalf + 1)^3 cells + the big list)
   int *bdup;     // 1: skip this entry (out of reach or repeated bucket)
   int *wq;       // this warp's candidate queue [64]
   int *wst;      // this warp's item starts [32]
@@ -503,8 +502,9 @@ __global__ void __launch_bounds__(NW * 32) k_generate(KArgs a) {
     s.a2f = reinterpret_cast<float *>(s.fr + 8);
     s.bf = s.a2f + N;
     s.buckets = reinterpret_cast<int *>(s.bf + N);
-    s.bdup = s.buckets + kNeigh + 1;
-    int *wbase = s.bdup + kNeigh + 1;
+    const int nn = (2 * a.nhalf + 1) * (2 * a.nhalf + 1) * (2 * a.nhalf + 1);
+    s.bdup = s.buckets + nn + 1;
+    int *wbase = s.bdup + nn + 1;
     s.wq = wbase + warp * kPerWarp;
     s.wst = s.wq + 64;
     s.bq_rec = s.wst + 32;
@@ -568,30 +568,31 @@ __global__ void __launch_bounds__(NW * 32) k_generate(KArgs a) {
     s.fr[5] = Nbx;
     s.fr[6] = Nbz;
   }
-  // neighbourhood: the 5 x 5 x 5 cells around the spin vertex's cell (cell edge > reach / 2).
-  // A triangle binned in a cell (by its bounding-sphere centre) can reach the support volume only
-  // if the cell's box lies within `reach` of the spin vertex; farther cells are skipped, and cells
-  // that hash to an already listed bucket are listed once.
-  if (tid < kNeigh) {
-    const int ix = cell_coord(Sx, a.inv_cell) + tid % 5 - 2;
-    const int iy = cell_coord(Sy, a.inv_cell) + (tid / 5) % 5 - 2;
-    const int iz = cell_coord(Sz, a.inv_cell) + tid / 25 - 2;
+  // neighbourhood: the (2 nhalf + 1)^3 cells around the spin vertex's cell (cell edge > reach /
+  // nhalf).  A triangle binned in a cell (by its bounding-sphere centre) can reach the support
+  // volume only if the cell's box lies within `reach` of the spin vertex; farther cells are
+  // skipped, and cells that hash to an already listed bucket are listed once.
+  const int nw_ = 2 * a.nhalf + 1, nneigh = nw_ * nw_ * nw_;
+  for (int cidx = tid; cidx < nneigh; cidx += NW * 32) {
+    const int ix = cell_coord(Sx, a.inv_cell) + cidx % nw_ - a.nhalf;
+    const int iy = cell_coord(Sy, a.inv_cell) + (cidx / nw_) % nw_ - a.nhalf;
+    const int iz = cell_coord(Sz, a.inv_cell) + cidx / (nw_ * nw_) - a.nhalf;
     const float c = a.cell;
     const float gx = fmaxf(fmaxf((float)ix * c - Sx, Sx - (float)(ix + 1) * c), 0.0f);
     const float gy = fmaxf(fmaxf((float)iy * c - Sy, Sy - (float)(iy + 1) * c), 0.0f);
     const float gz = fmaxf(fmaxf((float)iz * c - Sz, Sz - (float)(iz + 1) * c), 0.0f);
     const bool near = gx * gx + gy * gy + gz * gz <= a.reach * a.reach;
-    s.buckets[tid] = near ? (int)(bucket_off + cell_hash(ix, iy, iz, nbuckets - 1)) : -1;
+    s.buckets[cidx] = near ? (int)(bucket_off + cell_hash(ix, iy, iz, nbuckets - 1)) : -1;
   }
-  if (tid == 0) s.buckets[kNeigh] = (int)(bucket_off + nbuckets);  // the scene's big list
+  if (tid == 0) s.buckets[nneigh] = (int)(bucket_off + nbuckets);  // the scene's big list
   __syncthreads();
-  if (tid < kNeigh) {
-    const int b = s.buckets[tid];
-    bool dup = false;
-    for (int k = 0; k < tid && !dup; ++k) dup = s.buckets[k] == b;
-    s.bdup[tid] = (b < 0 || dup) ? 1 : 0;
+  for (int cidx = tid; cidx < nneigh; cidx += NW * 32) {
+    const int b = s.buckets[cidx];
+    bool dup = b < 0;
+    for (int k = 0; k < cidx && !dup; ++k) dup = s.buckets[k] == b;
+    s.bdup[cidx] = dup ? 1 : 0;
   }
-  if (tid == 0) s.bdup[kNeigh] = 0;
+  if (tid == 0) s.bdup[nneigh] = 0;
   __syncthreads();
 
   const float fax = __double2float_rn(s.fr[3]), fay = __double2float_rn(s.fr[4]);
@@ -763,7 +764,7 @@ __global__ void __launch_bounds__(NW * 32) k_generate(KArgs a) {
   };
 
   // ---- stream candidates of the listed neighbouring cells and the scene's big list
-  for (int nb = 0; nb <= kNeigh; ++nb) {
+  for (int nb = 0; nb <= nneigh; ++nb) {
     if (s.bdup[nb]) continue;
     const int64_t b = s.buckets[nb];
     const int64_t beg = a.starts[b], end = a.starts[b + 1];
@@ -837,13 +838,30 @@ __global__ void __launch_bounds__(NW * 32) k_generate(KArgs a) {
   }
 }
 
-size_t generate_smem_bytes(int N) {
+size_t generate_smem_bytes(int N, int nhalf, int warps) {
+  const int nn = (2 * nhalf + 1) * (2 * nhalf + 1) * (2 * nhalf + 1);
   size_t b = ((size_t)N * N * 4 + 15) & ~(size_t)15;
   b += (size_t)(2 * N + 8) * sizeof(double);
   b += (size_t)(2 * N) * sizeof(float);
-  b += 2 * (kNeigh + 1) * sizeof(int);
-  b += (size_t)kWarps * kPerWarp * 4;
+  b += 2 * (size_t)(nn + 1) * sizeof(int);
+  b += (size_t)warps * kPerWarp * 4;
   return b;
+}
+
+template <int NW>
+cudaError_t launch_k_generate(const KArgs &k, int64_t total_origins, cudaStream_t st) {
+  const size_t smem = generate_smem_bytes(k.N, k.nhalf, NW);
+  cudaError_t e = cudaFuncSetAttribute(k_generate<NW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  for (int64_t o0 = 0; o0 < total_origins; o0 += 0x7fffffff) {
+    const int64_t cnt = total_origins - o0 < 0x7fffffff ? total_origins - o0 : 0x7fffffff;
+    KArgs kk = k;
+    kk.origin_base = o0;
+    k_generate<NW><<<(unsigned)cnt, NW * 32, smem, st>>>(kk);
+    count_launches(1);
+  }
+  return cudaGetLastError();
 }
 
 }  // namespace
@@ -894,12 +912,13 @@ cudaError_t launch_generate_batch(const GenScene *scenes, const GenerateBatch &g
   const double amax = R * (2.0 * N - 1.0) / (2.0 * N);
   const double bmax = R * (N - 1.0) / (2.0 * N);
   const double rho = sqrt(amax * amax + bmax * bmax) * (1.0 + 1.0 / 1024.0) + 1e-3 * R;
+  const Tuning tu = current_tuning();
   GridParams gp;
-  gp.r_big = (float)(0.25 * rho);
+  gp.r_big = (float)(tu.gen_big_radius * rho);
   // a triangle (centre c, radius <= r_big) reaching the support volume has |c - S| <= reach;
-  // with cell > reach / 2 its cell lies within +-2 cells of the spin vertex's cell
+  // with cell > reach / nhalf its cell lies within +-nhalf cells of the spin vertex's cell
   const double reach = (rho + gp.r_big) * 1.001;
-  const double cell = 0.5 * reach * 1.01;
+  const double cell = reach / tu.gen_cells_per_reach * 1.01;
   gp.inv_cell = (float)(1.0 / cell);
   gp.mask = 0;
 
@@ -934,20 +953,11 @@ cudaError_t launch_generate_batch(const GenScene *scenes, const GenerateBatch &g
   k.alpha_cull = (float)(amax * (1.0 + 1.0 / 1024.0) + 1e-3 * R);
   k.beta_cull = (float)(bmax * (1.0 + 1.0 / 1024.0) + 1e-3 * R);
   k.mode = g.mode;
+  k.nhalf = tu.gen_cells_per_reach;
   k.counters = reinterpret_cast<unsigned long long *>(g.counters);
   k.status = g.status;
-  const size_t smem = generate_smem_bytes(N);
-  if ((e = cudaFuncSetAttribute(k_generate<kWarps>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                (int)smem)) != cudaSuccess)
-    return e;
-  for (int64_t o0 = 0; o0 < g.total_origins; o0 += 0x7fffffff) {
-    const int64_t cnt = g.total_origins - o0 < 0x7fffffff ? g.total_origins - o0 : 0x7fffffff;
-    KArgs kk = k;
-    kk.origin_base = o0;
-    k_generate<kWarps><<<(unsigned)cnt, kWarps * 32, smem, st>>>(kk);
-    count_launches(1);
-  }
-  return cudaGetLastError();
+  return tu.gen_warps == 8 ? launch_k_generate<8>(k, g.total_origins, st)
+                           : launch_k_generate<4>(k, g.total_origins, st);
 }
 
 cudaError_t launch_generate(const GenerateArgs &a, void *ws, cudaStream_t st) {

@@ -33,7 +33,6 @@ constexpr int kBM = 128;          // needles per tile (TMEM lanes)
 constexpr int kBN = 256;          // haystack images per tile (TMEM columns per buffer)
 constexpr int kBK = 64;           // fp16 elements per k-block (one 128-byte swizzle row)
 constexpr int kStages = 4;
-constexpr int kGroupM = 8;        // M tiles swept together over N (L2 reuse)
 constexpr int kTcThreads = 192;   // 6 warps
 constexpr uint32_t kStageA = kBM * kBK * 2;  // 16 KB
 constexpr uint32_t kStageB = kBN * kBK * 2;  // 32 KB
@@ -239,6 +238,7 @@ struct TcArgs {
   unsigned long long *best;
   int *status;
   int withhold_first_load;  // test hook: CTA 0 never issues its first stage (its waits time out)
+  int group_m;              // needle tiles per group of the tile order
 };
 
 // A tile of one scene: needle rows [qbeg + 128 m, ...), haystack columns [hbeg + 256 n, ...),
@@ -249,7 +249,8 @@ struct TcTile {
   int64_t Q, H;
 };
 
-__device__ __forceinline__ TcTile tile_of(const SearchScene *tab, int ns, int64_t t) {
+// Needle tiles are swept in groups of group_m over the scene's haystack tiles (L2 reuse).
+__device__ __forceinline__ TcTile tile_of(const SearchScene *tab, int ns, int64_t t, int group_m) {
   int lo = 0, hi = ns - 1;
   while (lo < hi) {  // last scene whose first tile is <= t (empty scenes own no tile)
     const int mid = (lo + hi + 1) >> 1;
@@ -258,13 +259,13 @@ __device__ __forceinline__ TcTile tile_of(const SearchScene *tab, int ns, int64_
   const SearchScene &sc = tab[lo];
   const int64_t tl = t - sc.tile_off;
   const int tiles_m = sc.tiles_m, tiles_n = sc.tiles_n;
-  const int64_t per_group = (int64_t)kGroupM * tiles_n;
+  const int64_t per_group = (int64_t)group_m * tiles_n;
   const int64_t g = tl / per_group;
   const int64_t r = tl - g * per_group;
-  const int64_t gm = min((int64_t)kGroupM, (int64_t)tiles_m - g * kGroupM);
+  const int64_t gm = min((int64_t)group_m, (int64_t)tiles_m - g * group_m);
   TcTile tt;
   tt.n = r / gm;
-  tt.m = g * kGroupM + r % gm;
+  tt.m = g * group_m + r % gm;
   tt.qbeg = sc.qoff;
   tt.hbeg = sc.hoff;
   tt.Q = sc.Q;
@@ -323,7 +324,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       uint32_t it = 0;
       bool ok = true;
       for (int64_t t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
-        const TcTile tt = tile_of(a.tab, a.num_scenes, t);
+        const TcTile tt = tile_of(a.tab, a.num_scenes, t, a.group_m);
         const int ya = (int)(tt.qbeg + tt.m * kBM), yb = (int)(tt.hbeg + tt.n * kBN);
         for (int kb = 0; kb < kblocks; ++kb, ++it) {
           const uint32_t s = it % kStages, round = it / kStages;
@@ -383,7 +384,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const int row = quarter * 32 + lane;
     uint32_t lt = 0;
     for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x, ++lt) {
-      const TcTile tt = tile_of(a.tab, a.num_scenes, t);
+      const TcTile tt = tile_of(a.tab, a.num_scenes, t, a.group_m);
       const uint32_t buf = lt & 1, use = lt >> 1;
       // warp-uniform outcome before the .sync.aligned TMEM loads
       const bool ready = __all_sync(0xffffffffu, mbar_wait(&tfull[buf], use & 1, a.status, abort_flag));
@@ -529,6 +530,7 @@ cudaError_t launch_tc_encode_and_rank(const SearchScene *tab, int num_scenes, co
   a.best = best;
   a.status = status;
   a.withhold_first_load = test_withhold;
+  a.group_m = current_tuning().tc_group_m;
   const size_t smem = 1024 + kStages * (kStageA + kStageB) + 256;
   if ((e = cudaFuncSetAttribute(k_tc_rank, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)smem)) != cudaSuccess)
