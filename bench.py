@@ -70,6 +70,8 @@ def parse():
     ap.add_argument("--search-mode", type=int, default=1)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default launch tuning instead of autotuning the generation")
     ap.add_argument("--cpu-origins", type=int, default=96)
     ap.add_argument("--cpu-needle-origins", type=int, default=48)
     ap.add_argument("--cpu-needles", type=int, default=12)
@@ -254,6 +256,7 @@ def batched_comparison(p, torch, dev, stream, args, n_scenes=24, needles=256):
     # tuning, one with the autotuned tuning (measured on the first scenes, fresh cache)
     from paper_2007_02306_gb300 import autotune
 
+    prev_tuning = p.get_tuning()
     p.set_tuning(None)
     graph_default = capture()
     t_tune = time.time()
@@ -283,7 +286,7 @@ def batched_comparison(p, torch, dev, stream, args, n_scenes=24, needles=256):
         t_p.append(e1.elapsed_time(e2))
         t_d.append(e2.elapsed_time(e3))
     st = p.sync_status()
-    p.set_tuning(None)
+    p.set_tuning(prev_tuning)
     images = sum(g["origins"].numel() for g in gen)
     pairs = sum(x["on"].numel() * x["oh"].numel() for x in xs)
     return {"scenes": n_scenes, "triangles": int(sum(s.num_triangles for s in scenes)),
@@ -375,6 +378,21 @@ def main():
         p.rici_generate(vert, norm, tri_t, on, R_SUP, N_RES, out=needles)
         p.rici_generate(vert, norm, tri, oh, R_SUP, N_RES, out=hay)
         return p.crss_search(needles, hay, match, mode=args.search_mode)
+
+    # launch tuning of the generation kernels, measured on this workload (fresh cache)
+    tune_s = 0.0
+    if not args.no_autotune:
+        from paper_2007_02306_gb300 import autotune
+
+        t0 = time.time()
+        with tempfile.TemporaryDirectory() as td:
+            autotune.tune_batch(
+                [{"vertices": vert, "normals": norm, "triangles": tri_t, "origins": on, "out": needles},
+                 {"vertices": vert, "normals": norm, "triangles": tri, "origins": oh, "out": hay}],
+                [], R_SUP, N_RES, gpu_name=torch.cuda.get_device_name(dev), sample=2, repeats=2,
+                path=os.path.join(td, "tuning.json"))
+        tune_s = time.time() - t0
+    step_tuning = p.get_tuning()
 
     for _ in range(args.warmup):
         step()
@@ -580,6 +598,8 @@ def main():
                                 "lane_utilisation": scnt[0] / scnt[3] if scnt[3] else None},
             "search_tensor_core": tc,
             "batched_run": batched,
+            "tuning": step_tuning,
+            "autotune_s": tune_s,
         },
         "roofline": roof,
         "rooflines": rooflines,
