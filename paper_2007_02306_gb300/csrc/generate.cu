@@ -282,7 +282,7 @@ struct Shared {
   int *buckets;  // neighbour buckets ((2 nhalf + 1)^3 cells + the big list)
   int *bdup;     // 1: skip this entry (out of reach or repeated bucket)
   int *wq;       // this warp's candidate queue [64]
-  int *wst;      // this warp's item starts [32]
+  int *wst;      // this warp's item-owner marks for the current 32 items [32]
   int *bq_rec;   // this warp's FP64 queue: triangle record [64]
   int *bq_r;     // this warp's FP64 queue: layer [64]
   float *slots;  // this warp's staged triangles [32][kSlot]
@@ -295,14 +295,14 @@ enum {
 };
 constexpr int kAll64 = 1;
 
-__device__ __forceinline__ int lower_count_f(float x, const float *a2f, int N, float scale) {
-  // number of columns c with a2f[c] <= x
-  float s = x > 0.0f ? x * rsqrtf(x) * scale : 0.0f;  // estimate only, corrected below
-  float fc = floorf((s + 1.0f) * 0.5f);
-  int c = (fc >= (float)N) ? N : ((fc > 0.0f) ? (int)fc : 0);
-  while (c < N && a2f[c] <= x) ++c;
-  while (c > 0 && a2f[c - 1] > x) --c;
-  return c;
+// Estimate of the number of columns c with alpha_c^2 <= x (alpha_c = R (2c+1) / 2N, so the count
+// is floor(N sqrt(x) / R + 1/2)), in [0, N].  Off by one at most, and only within a few ulps of a
+// column boundary: every caller then checks the margins to both neighbouring columns, a check that
+// fails (sends the item to FP64) whenever the estimate is not the exact count.
+__device__ __forceinline__ int count_estimate_f(float x, int N, float scale) {
+  const float s = x > 0.0f ? x * rsqrtf(x) * scale : 0.0f;
+  const float fc = floorf((s + 1.0f) * 0.5f);
+  return (fc >= (float)N) ? N : ((fc > 0.0f) ? (int)fc : 0);
 }
 
 __device__ __forceinline__ int lower_count_d(double x, const double *a2d, int N) {
@@ -427,8 +427,9 @@ __device__ __forceinline__ int layer_fp32(const float *__restrict__ bf, const fl
   const float A1 = fabsf(E1x) + fabsf(E1y) + 2.0f * dE;
   const float de0 = kSafety * (2.0f * A0 * dE + 3.01f * kU * e0) + 1e-37f;
   const float de1 = kSafety * (2.0f * A1 * dE + 3.01f * kU * e1) + 1e-37f;
-  int c0 = lower_count_f(e0, a2f, N, scale), c1 = lower_count_f(e1, a2f, N, scale);
-  // the two columns around each transition must be decided with certainty
+  int c0 = count_estimate_f(e0, N, scale), c1 = count_estimate_f(e1, N, scale);
+  // the two columns around each transition must be decided with certainty (this also rejects a
+  // wrong estimate: one of the two differences is then <= 0)
   if (c0 > 0 && e0 - a2f[c0 - 1] <= de0 + kU * a2f[c0 - 1]) return 2;
   if (c0 < N && a2f[c0] - e0 <= de0 + kU * a2f[c0]) return 2;
   if (c1 > 0 && e1 - a2f[c1 - 1] <= de1 + kU * a2f[c1 - 1]) return 2;
@@ -453,14 +454,17 @@ __device__ __forceinline__ int layer_fp32(const float *__restrict__ bf, const fl
       // known to 2 h dh + dh^2 plus the rounding of the cross product, |D|^2 and the quotient.
       float cr = __fmaf_rn(E0x, Dy, -__fmul_rn(E0y, Dx));
       float dd = __fmaf_rn(Dx, Dx, __fmul_rn(Dy, Dy));
-      float h2 = __fdiv_rn(__fmul_rn(cr, cr), dd);
-      const float h = sqrtf(h2);
+      if (!(dd >= 1e-30f && dd <= 1e30f)) return 2;  // keep the fast quotient in its range
+      // fast quotient (at most 2 ulp = 4 kU relative from the rounded operands) and fast root
+      // (used in the bound only, raised by 1e-6 relative to cover its own error)
+      float h2 = __fdividef(__fmul_rn(cr, cr), dd);
+      const float h = h2 > 0.0f ? h2 * rsqrtf(h2) * 1.000001f : 0.0f;
       const float dh = 1.5f * (dE + kU * B);
       const float rb = B * rsqrtf(dd);  // (|Dx| + |Dy| + 2 dD) / |D|
       const float dq = kSafety * (2.0f * h * dh + 2.0f * dh * dh + 4.0f * kU * h * A0 * rb +
-                                  2.0f * kU * h2 * (1.0f + rb * rb)) + 1e-37f;
+                                  2.0f * kU * h2 * (1.0f + rb * rb) + 4.0f * kU * h2) + 1e-37f;
       if (!(dq < 1e30f)) return 2;
-      const int cs = lower_count_f(h2, a2f, N, scale);  // first column with alpha^2 > h^2
+      const int cs = count_estimate_f(h2, N, scale);  // first column with alpha^2 > h^2
       if (cs >= lo) {
         if (h2 - a2f[lo - 1] <= dq + kU * a2f[lo - 1]) return 2;
       } else {
@@ -725,21 +729,30 @@ __global__ void __launch_bounds__(NW * 32) k_generate(KArgs a) {
       if (lane >= d) incl += y;
     }
     const int total = __shfl_sync(0xffffffffu, incl, 31);
-    s.wst[lane] = incl - nlay;
+    const int first = incl - nlay;  // this lane's triangle owns items [first, first + nlay)
     n_tri += nlay > 0;
-    __syncwarp();
     for (int base = 0; base < total; base += 32) {
       const int it = base + lane;
       const bool act = it < total;
+      // owner of each item of this window: every triangle marks the first window position it
+      // owns (positions are distinct), and a running maximum carries the mark to the positions
+      // that follow (owners' lanes increase with their first item)
+      s.wst[lane] = -1;
+      __syncwarp();
+      const int d = first - base;
+      if (nlay > 0 && d < 32 && d + nlay > 0) s.wst[d > 0 ? d : 0] = lane;
+      __syncwarp();
+      int owner = s.wst[lane];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, owner, o);
+        if (lane >= o) owner = max(owner, y);
+      }
+      const int ofirst = __shfl_sync(0xffffffffu, first, owner < 0 ? 0 : owner);
       int res = 0, r = 0, rec = 0, lo = 0, hi = 0, dlo = 0;
       if (act) {
-        int lo_ = 0, hi_ = cnt - 1;
-        while (lo_ < hi_) {
-          int mid = (lo_ + hi_ + 1) >> 1;
-          if (s.wst[mid] <= it) lo_ = mid; else hi_ = mid - 1;
-        }
-        const float *ts = s.slots + lo_ * kSlot;
-        r = __float_as_int(ts[SRLO]) + (it - s.wst[lo_]);
+        const float *ts = s.slots + owner * kSlot;
+        r = __float_as_int(ts[SRLO]) + (it - ofirst);
         rec = __float_as_int(ts[SREC]);
         const int flags = __float_as_int(ts[SFLAGS]);
         bool band = (flags & kAll64) || r == __float_as_int(ts[SBAND]) ||
