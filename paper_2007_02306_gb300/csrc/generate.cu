@@ -268,6 +268,7 @@ struct KArgs {
   float beta_cull;   // pretest height limit (beta_{N-1} plus margin)
   int mode;
   int nhalf;        // neighbourhood half-width in cells (cell edge > reach / nhalf)
+  float r_big;      // largest bounding radius of a binned triangle
   unsigned long long *counters;
   int *status;
 };
@@ -573,10 +574,21 @@ __global__ void __launch_bounds__(NW * 32) k_generate(KArgs a) {
     s.fr[6] = Nbz;
   }
   // neighbourhood: the (2 nhalf + 1)^3 cells around the spin vertex's cell (cell edge > reach /
-  // nhalf).  A triangle binned in a cell (by its bounding-sphere centre) can reach the support
-  // volume only if the cell's box lies within `reach` of the spin vertex; farther cells are
-  // skipped, and cells that hash to an already listed bucket are listed once.
+  // nhalf).  A triangle binned in a cell (by its bounding-sphere centre, radius <= r_big) can
+  // reach the support volume only if the cell's box lies within `reach` of the spin vertex and
+  // the box's bounding sphere lies within r_big of the support cylinder (axis along the normal);
+  // other cells are skipped, and cells that hash to an already listed bucket are listed once.
   const int nw_ = 2 * a.nhalf + 1, nneigh = nw_ * nw_ * nw_;
+  float ux = 0.0f, uy = 0.0f, uz = 1.0f;  // axis direction (identity rule for a zero normal)
+  {
+    const float n2 = nxf * nxf + nyf * nyf + nzf * nzf;
+    if (n2 > 1e-30f) {
+      const float inv = rsqrtf(n2);
+      ux = nxf * inv;
+      uy = nyf * inv;
+      uz = nzf * inv;
+    }
+  }
   for (int cidx = tid; cidx < nneigh; cidx += NW * 32) {
     const int ix = cell_coord(Sx, a.inv_cell) + cidx % nw_ - a.nhalf;
     const int iy = cell_coord(Sy, a.inv_cell) + (cidx / nw_) % nw_ - a.nhalf;
@@ -585,7 +597,16 @@ __global__ void __launch_bounds__(NW * 32) k_generate(KArgs a) {
     const float gx = fmaxf(fmaxf((float)ix * c - Sx, Sx - (float)(ix + 1) * c), 0.0f);
     const float gy = fmaxf(fmaxf((float)iy * c - Sy, Sy - (float)(iy + 1) * c), 0.0f);
     const float gz = fmaxf(fmaxf((float)iz * c - Sz, Sz - (float)(iz + 1) * c), 0.0f);
-    const bool near = gx * gx + gy * gy + gz * gz <= a.reach * a.reach;
+    // box centre relative to the spin vertex, its axial and radial distances to the axis
+    const float hb = 0.8660254f * c * 1.001f + 1e-3f * c;  // half diagonal (+ cell rounding)
+    const float cx = ((float)ix + 0.5f) * c - Sx, cy = ((float)iy + 0.5f) * c - Sy,
+                cz = ((float)iz + 0.5f) * c - Sz;
+    const float ax = fabsf(cx * ux + cy * uy + cz * uz);
+    const float rad2 = cx * cx + cy * cy + cz * cz - ax * ax;
+    const float marg = hb + a.r_big + 1e-3f * a.reach + 1e-5f * (fabsf(cx) + fabsf(cy) + fabsf(cz));
+    const float rl = a.alpha_cull + marg;
+    const bool near = gx * gx + gy * gy + gz * gz <= a.reach * a.reach &&
+                      ax <= a.beta_cull + marg && rad2 <= rl * rl;
     s.buckets[cidx] = near ? (int)(bucket_off + cell_hash(ix, iy, iz, nbuckets - 1)) : -1;
   }
   if (tid == 0) s.buckets[nneigh] = (int)(bucket_off + nbuckets);  // the scene's big list
@@ -967,6 +988,7 @@ cudaError_t launch_generate_batch(const GenScene *scenes, const GenerateBatch &g
   k.beta_cull = (float)(bmax * (1.0 + 1.0 / 1024.0) + 1e-3 * R);
   k.mode = g.mode;
   k.nhalf = tu.gen_cells_per_reach;
+  k.r_big = gp.r_big;
   k.counters = reinterpret_cast<unsigned long long *>(g.counters);
   k.status = g.status;
   return tu.gen_warps == 8 ? launch_k_generate<8>(k, g.total_origins, st)
