@@ -280,8 +280,10 @@ struct Shared {
   float *a2f;    // alpha_c^2 rounded to FP32
   float *bf;     // beta_r rounded to FP32
   double *fr;    // S (3 doubles), Nax, Nay, Nbx, Nbz
-  int *buckets;  // neighbour buckets ((2 nhalf + 1)^3 cells + the big list)
-  int *bdup;     // 1: skip this entry (out of reach or repeated bucket)
+  int *buckets;  // neighbour buckets ((2 nhalf + 1)^3 cells + the big list), then the first
+                 // candidate of each
+  int *bdup;     // 1: skip this entry (out of reach or repeated bucket), then the end of its
+                 // candidate range (= its first candidate for a skipped entry)
   int *wq;       // this warp's candidate queue [64]
   int *wst;      // this warp's item-owner marks for the current 32 items [32]
   int *bq_rec;   // this warp's FP64 queue: triangle record [64]
@@ -619,6 +621,18 @@ __global__ void __launch_bounds__(NW * 32) k_generate(KArgs a) {
   }
   if (tid == 0) s.bdup[nneigh] = 0;
   __syncthreads();
+  // candidate range of every listed bucket, fetched once per block
+  for (int cidx = tid; cidx <= nneigh; cidx += NW * 32) {
+    int beg = 0, end = 0;
+    if (!s.bdup[cidx]) {
+      const int b = s.buckets[cidx];
+      beg = a.starts[b];
+      end = a.starts[b + 1];
+    }
+    s.buckets[cidx] = beg;
+    s.bdup[cidx] = end;
+  }
+  __syncthreads();
 
   const float fax = __double2float_rn(s.fr[3]), fay = __double2float_rn(s.fr[4]);
   const float fbx = __double2float_rn(s.fr[5]), fbz = __double2float_rn(s.fr[6]);
@@ -799,9 +813,7 @@ __global__ void __launch_bounds__(NW * 32) k_generate(KArgs a) {
 
   // ---- stream candidates of the listed neighbouring cells and the scene's big list
   for (int nb = 0; nb <= nneigh; ++nb) {
-    if (s.bdup[nb]) continue;
-    const int64_t b = s.buckets[nb];
-    const int64_t beg = a.starts[b], end = a.starts[b + 1];
+    const int64_t beg = s.buckets[nb], end = s.bdup[nb];
     for (int64_t base = beg + warp * 32; base < end; base += NW * 32) {
       const int64_t t = base + lane;
       bool pass = false;
