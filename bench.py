@@ -52,13 +52,13 @@ MACS_PER_TERM = 2
 # dp4a instructions per SM per clock: half the 128 FP32 lanes (a microbenchmark of independent
 # dp4a chains measured 61.3 per SM per clock at 2070 MHz; FFMA measured 117.3)
 DP4A_PER_SM_CLK = 64
-# DRAM bytes (read + write) per launch from one ncu capture of the current kernels (dram__bytes_read
-# and dram__bytes_write; commands in profiles/): k_dense at the full clutter-scene size (one-pass
-# capture), k_generate on a 40,000-origin launch scaled by the number of origins (its traffic is
-# the images it writes plus a small read of the triangle records).  Set to None when a kernel
-# changes until it is captured again.
+# DRAM bytes (read + write) per launch from one-pass ncu captures (dram__bytes_read and
+# dram__bytes_write; commands in profiles/) of the current kernels at the full clutter-scene
+# size: k_dense (the search) and k_generate (the haystack images; its traffic is the 8 KB image
+# of each origin plus a small read of triangle records, so it is the same for every launch
+# tuning).  Set to None when a kernel changes until it is captured again.
 TRAFFIC_DENSE_FULL = 2.97e9 + 5.5e6
-TRAFFIC_GEN_PER_ORIGIN = (23.6e6 + 278.7e6) / 40000
+TRAFFIC_GEN_FULL = 56.78e6 + 905.67e6
 
 
 def parse():
@@ -554,7 +554,8 @@ def main():
             "work": f"{F_PROJ} ops x 3 vertices per crossing (origin, triangle) pair + {F_LAYER} "
                     "ops per (origin, triangle, layer) crossing, counted by the oracle on 32 "
                     "sampled origins and scaled to all haystack origins",
-            "traffic": (TRAFFIC_GEN_PER_ORIGIN * V if TRAFFIC_GEN_PER_ORIGIN else None),
+            "traffic": (TRAFFIC_GEN_FULL if not (args.haystack_limit or args.needle_limit)
+                        else None),
         }
     for r in rooflines.values():
         r["frac"] = r["achieved"] / r["peak"]
