@@ -195,12 +195,14 @@ def cpu_baseline(scene, args, steps: int = 1):
     return est, threads, sample
 
 
-def batched_comparison(p, torch, dev, stream, args, n_scenes=24, needles=256):
+def batched_comparison(p, torch, dev, stream, args, n_scenes=24, needles=256, seed=41,
+                       tri_lo=2000, tri_hi=60_000, total_lo=10_000, total_hi=300_000):
     """Batched run of many uneven scenes (one set of launches, replayed from a CUDA graph)
     against one plain generate/generate/search call sequence per scene."""
     import synth
 
-    scenes = synth.scene_batch(seed=41, n_scenes=n_scenes, tri_hi=60_000, total_hi=300_000)
+    scenes = synth.scene_batch(seed=seed, n_scenes=n_scenes, tri_lo=tri_lo, tri_hi=tri_hi,
+                               total_lo=total_lo, total_hi=total_hi)
     rng = np.random.default_rng(2)
     d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)  # noqa: E731
     xs = []
@@ -296,8 +298,9 @@ def batched_comparison(p, torch, dev, stream, args, n_scenes=24, needles=256):
             "batched_graph_default_tuning_ms": statistics.mean(t_d),
             "autotuned": tuning, "autotune_s": t_tune,
             "batched_images_per_s": images / (statistics.mean(t_b) / 1e3), "status": st,
-            "recipe": "synth.scene_batch(seed=41, 24 scenes, 10k-300k triangles each), 256 needles "
-                      "per scene (target alone) vs all scene vertices, tensor-core search"}
+            "recipe": f"synth.scene_batch(seed={seed}, {n_scenes} scenes, {total_lo}-{total_hi} "
+                      f"triangles each), {needles} needles per scene (target alone) vs all scene "
+                      "vertices, tensor-core search"}
 
 
 def run_reference(args):
@@ -467,9 +470,13 @@ def main():
         tc = {"ms": statistics.mean(tc_ms), "comparisons_per_s": pairs / (statistics.mean(tc_ms) / 1e3),
               "same_ranks_as_cuda_core": same, "status": st}
 
-    batched = None
+    batched = batched_small = None
     if args.batched_compare and rank == 0:
         batched = batched_comparison(p, torch, dev, stream, args)
+        # many small scenes: where one set of launches per batch matters most
+        batched_small = batched_comparison(p, torch, dev, stream, args, n_scenes=256, needles=64,
+                                           seed=42, tri_lo=500, tri_hi=5000, total_lo=2000,
+                                           total_hi=12_000)
 
     # e2e: same step from pinned host buffers, host<->device copies inside the timed region
     e2e = None
@@ -599,6 +606,7 @@ def main():
                                 "lane_utilisation": scnt[0] / scnt[3] if scnt[3] else None},
             "search_tensor_core": tc,
             "batched_run": batched,
+            "batched_run_small_scenes": batched_small,
             "tuning": step_tuning,
             "autotune_s": tune_s,
         },
