@@ -42,9 +42,14 @@ WORKLOAD = ("clutter scene: displaced icosphere target (subdivision 5, 20,480 tr
             "uint16 at R=0.3 for the 10,242 target vertices (target alone) and all 114,892 scene "
             "vertices; CUDA-core CRSS search of every needle against every haystack image, ranks")
 
-# FP32-pipe operations of the definition per unit of generation work:
-F_PROJ = 15   # per projected vertex of an (origin, triangle) pair that crosses a layer
-F_LAYER = 40  # per (origin, triangle, layer) crossing: slicing + segment quantities + boundaries
+# FP32-pipe operations of the definition per unit of generation work: the projection of one
+# vertex (Eqs. relativeLocation, firstRotation, secondRotation: 3 subtractions and 6 multiply-adds
+# with their roundings, counted as 15 operations) for each vertex of an (origin, triangle) pair
+# that crosses a layer, and per (origin, triangle, layer) crossing the slicing of two edges, the
+# segment quantities |E0|^2, |E1|^2, E0.D, E1.D, E0 x D, |D|^2 and the interval boundaries of
+# Section 3.1.2 (counted as 40 operations)
+F_PROJ = 15
+F_LAYER = 40
 # int8 multiply-adds per masked squared difference in the expanded form m(a-b)^2 =
 # a^2 - 2ab + (mb)^2 with sum a^2 per row precomputed: one for a*b and one for (mb)*(mb); dp4a
 # performs four of them per instruction.
