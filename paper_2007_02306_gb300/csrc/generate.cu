@@ -865,6 +865,42 @@ __global__ void __launch_bounds__(NW * 32) k_generate(KArgs a) {
   // ---- prefix-sum each row of the difference image, saturate, store uint16
   uint16_t *out = out_img;
   const int cpl = (N + 31) / 32;
+  if ((N == 64 || N == 128) && (reinterpret_cast<uintptr_t>(out) & 7) == 0) {
+    // each lane owns 2 (N = 64) or 4 (N = 128) consecutive columns: one vector load of the
+    // difference row and one 32- or 64-bit store of the packed counts
+    for (int r = warp; r < N; r += NW) {
+      const int *row = s.diff + r * N;
+      int v0, v1, v2 = 0, v3 = 0;
+      if (cpl == 2) {
+        const int2 x = *reinterpret_cast<const int2 *>(row + 2 * lane);
+        v0 = x.x;
+        v1 = x.y;
+      } else {
+        const int4 x = *reinterpret_cast<const int4 *>(row + 4 * lane);
+        v0 = x.x;
+        v1 = x.y;
+        v2 = x.z;
+        v3 = x.w;
+      }
+      const int sum = v0 + v1 + v2 + v3;
+      int incl = sum;
+#pragma unroll
+      for (int d = 1; d < 32; d <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, d);
+        if (lane >= d) incl += y;
+      }
+      const int p0 = incl - sum + v0, p1 = p0 + v1, p2 = p1 + v2, p3 = p2 + v3;
+      const uint32_t w0 = (uint32_t)min(max(p0, 0), 65535) | ((uint32_t)min(max(p1, 0), 65535) << 16);
+      if (cpl == 2) {
+        *reinterpret_cast<uint32_t *>(out + r * N + 2 * lane) = w0;
+      } else {
+        const uint32_t w1 =
+            (uint32_t)min(max(p2, 0), 65535) | ((uint32_t)min(max(p3, 0), 65535) << 16);
+        *reinterpret_cast<uint2 *>(out + r * N + 4 * lane) = make_uint2(w0, w1);
+      }
+    }
+    return;
+  }
   for (int r = warp; r < N; r += NW) {
     const int *row = s.diff + r * N;
     const int c0 = lane * cpl, c1 = min(N, c0 + cpl);

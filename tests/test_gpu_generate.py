@@ -185,3 +185,21 @@ def test_clutter_scene_full_size_sampled_origins(rici, oracle_mod):
     assert np.array_equal(pick(nd, ts).cpu().numpy(), ref_t)
     c = cnt.cpu().numpy()
     assert c[1] > 0 and c[2] < c[1] * 0.02, f"FP64 band fraction too high: {c}"
+
+
+@pytest.mark.parametrize("N", [64, 128])
+def test_unaligned_output_buffer(rici, oracle_mod, N):
+    """Output rows start 2 bytes off an 8-byte boundary: the scalar store path, same images."""
+    import torch
+
+    s = synth.tiny_scene()
+    o = np.arange(0, s.num_vertices, 5, dtype=np.int32)
+    base = torch.zeros(len(o) * N * N + 1, dtype=torch.int16, device="cuda")
+    out = base[1:].view(len(o), N, N).view(torch.uint16)
+    assert out.data_ptr() % 8 == 2
+    rici.rici_generate(dev(s.vertices), dev(s.normals), dev(s.triangles), dev(o), 0.3, N, out=out)
+    assert rici.sync_status() == 0
+    got = out.view(torch.int16).cpu().numpy().view(np.uint16)
+    want = oracle_mod.rici_fp64(s.vertices, s.normals, s.triangles, o, 0.3, N)
+    assert np.array_equal(got, want)
+    assert base[0].item() == 0  # nothing written before the buffer
