@@ -2,17 +2,19 @@
 //
 // Pipeline per rici_generate call (all on the caller's stream, no host synchronisation):
 //   1. k_tri_bin      bounding sphere of every triangle; bin it into a hashed uniform grid
-//                     (cell = 1.25 x the support sphere) or into a "big" list.
+//                     (cell edge = reach / 2 or / 3, reach = support sphere + largest binned
+//                     triangle radius) or, for wide triangles, into its scene's "big" list.
 //   2. scan           bucket counts -> bucket starts.
 //   3. k_tri_scatter  64-byte triangle records (sphere, FP32 vertices, global indices) in
 //                     bucket order, so candidates of one cell are contiguous.
-//   4. k_generate     one CTA per oriented point.  Its warps stream the triangles of the 27
-//                     neighbouring cells (plus the big list), cull them against the support
+//   4. k_generate     one CTA per oriented point.  Its warps stream the triangles of the
+//                     5^3 or 7^3 neighbouring cells that lie within reach of the spin vertex
+//                     and of the support cylinder (plus the big list), cull them against the
 //                     cylinder, project the survivors (Eqs. relativeLocation..secondRotation)
 //                     and split the (triangle, layer) work evenly over the 32 lanes.  Each
 //                     layer's single/double crossing radii (Section 3.1.2) become column
 //                     intervals added to a shared-memory difference image, which is prefix
-//                     summed, saturated and stored as uint16.
+//                     summed, saturated and stored as packed uint16 (32- or 64-bit stores).
 //
 // Exactness: the FP32 path carries a forward error bound for every predicate (vertex side
 // of a layer, |E|^2 against alpha^2, the signs of E0.D and E1.D, alpha^2 |D|^2 against

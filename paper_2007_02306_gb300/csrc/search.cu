@@ -6,14 +6,18 @@
 // minimal d(i,j).  Everything is integer arithmetic, so results are exact.
 //
 // Stages:
-//   k_encode        per image: int8 column deltas (delta of column 0 := 0) and, for needles,
-//                   a byte mask of the non-zero deltas; images with any |delta| > 127 are
-//                   "wide" and listed separately.
+//   k_encode        per image: int8 column deltas (delta of column 0 := 0); for needles also
+//                   a byte mask of the non-zero deltas and per-row sums of squared deltas, for
+//                   the haystack a warp-interleaved layout (32 images per group, 16-byte chunks
+//                   chunk-major); images with any |delta| > 127 are "wide" and listed apart.
 //   k_true_distance d(i, match_i) in int64 straight from the uint16 images.
-//   k_dense         narrow x narrow pairs on CUDA cores.  Per 4 packed deltas the masked sum
-//                   of squares m(a-b)^2 = a^2 - 2ab + (mb)^2 runs as three dp4a; each per-word
-//                   sum is >= 0, so partial sums are monotone and a pair stops once it exceeds
+//   k_dense         narrow x narrow pairs on CUDA cores.  Per row, sum m(a-b)^2 =
+//                   sum a^2 + sum (mb)^2 - 2 sum ab with sum a^2 precomputed and the other two
+//                   as dp4a over 4 packed deltas (plus one AND for mb); each row's sum is >= 0,
+//                   so partial sums are monotone and a pair stops once it exceeds
 //                   d(i, match_i) (the early exit of Section 4.4, which never changes a rank).
+//                   A block keeps 8 needles in shared memory and sweeps a band of haystack
+//                   tiles (512 images each, one per thread), rows heaviest first.
 //   k_wide          pairs with a wide side: Listing 1 over the needle's non-zero deltas in
 //                   int64, reading the uint16 images.
 //   k_finalize / k_top1_exact   combine counts and top-1 candidates.
