@@ -229,9 +229,9 @@ int rici_generate_ex(const float *vertices, const float *normals, int64_t num_ve
   if (mode != RICI_GEN_DEFAULT && mode != RICI_GEN_FP64)
     return fail(RICI_ERR_INVALID_ARGUMENT, "unknown generation mode %d", mode);
   if (num_origins == 0) return RICI_OK;
-  DeviceState *d;
+  DeviceState *d = nullptr;
   if ((rc = device_state(&d))) return rc;
-  void *ws;
+  void *ws = nullptr;
   if ((rc = resolve_workspace(d, workspace, workspace_bytes,
                               generate_workspace_bytes(num_triangles), &ws)))
     return rc;
@@ -295,10 +295,10 @@ int crss_search_ex(const uint16_t *needles, int64_t num_needles, const uint16_t 
     return fail(RICI_ERR_OUT_TOO_LARGE, "more than 2^31-1 needles or haystack images");
   if (out_distances && (double)num_needles * (double)num_haystack > (double)(int64_t(1) << 28))
     return fail(RICI_ERR_OUT_TOO_LARGE, "distance matrix larger than 2^28 entries");
-  DeviceState *d;
+  DeviceState *d = nullptr;
   int rc;
   if ((rc = device_state(&d))) return rc;
-  void *ws;
+  void *ws = nullptr;
   if ((rc = resolve_workspace(d, workspace, workspace_bytes,
                               search_workspace_bytes(num_needles, num_haystack, resolution, mode),
                               &ws)))
@@ -377,7 +377,7 @@ static int build_gen_batch(const RiciGenerateScene *scenes, int32_t ns, int32_t 
 int64_t rici_generate_batch_workspace_size(const RiciGenerateScene *scenes, int32_t num_scenes,
                                            int32_t resolution) {
   std::vector<GenScene> tab;
-  GenerateBatch b;
+  GenerateBatch b{};
   if (build_gen_batch(scenes, num_scenes, resolution, &tab, &b)) return -1;
   return generate_batch_workspace_bytes(num_scenes > 0 ? num_scenes : 1, b.total_tris,
                                         b.total_buckets);
@@ -390,13 +390,13 @@ int rici_generate_batch(const RiciGenerateScene *scenes, int32_t num_scenes, flo
   if (!(support_radius > 0.0f) || !isfinite(support_radius))
     return fail(RICI_ERR_INVALID_ARGUMENT, "support_radius must be positive and finite");
   std::vector<GenScene> tab;
-  GenerateBatch b;
+  GenerateBatch b{};
   int rc = build_gen_batch(scenes, num_scenes, resolution, &tab, &b);
   if (rc) return rc;
   if (b.total_origins == 0) return RICI_OK;
-  DeviceState *d;
+  DeviceState *d = nullptr;
   if ((rc = device_state(&d))) return rc;
-  void *ws;
+  void *ws = nullptr;
   if ((rc = resolve_workspace(d, workspace, workspace_bytes,
                               generate_batch_workspace_bytes(num_scenes, b.total_tris,
                                                              b.total_buckets),
@@ -462,7 +462,7 @@ static int build_search_batch(const RiciSearchScene *scenes, int32_t ns, int32_t
 int64_t crss_search_batch_workspace_size(const RiciSearchScene *scenes, int32_t num_scenes,
                                          int32_t resolution, int32_t mode) {
   std::vector<SearchScene> tab;
-  SearchBatch b;
+  SearchBatch b{};
   if (build_search_batch(scenes, num_scenes, resolution, mode, &tab, &b)) return -1;
   return search_batch_workspace_bytes(num_scenes > 0 ? num_scenes : 1, b.Qtot, b.Htot, resolution,
                                       b.mode);
@@ -472,13 +472,13 @@ int crss_search_batch(const RiciSearchScene *scenes, int32_t num_scenes, int32_t
                       int32_t mode, void *workspace, int64_t workspace_bytes, void *stream) {
   t_last_error.clear();
   std::vector<SearchScene> tab;
-  SearchBatch b;
+  SearchBatch b{};
   int rc = build_search_batch(scenes, num_scenes, resolution, mode, &tab, &b);
   if (rc) return rc;
   if (b.Qtot == 0) return RICI_OK;
-  DeviceState *d;
+  DeviceState *d = nullptr;
   if ((rc = device_state(&d))) return rc;
-  void *ws;
+  void *ws = nullptr;
   if ((rc = resolve_workspace(d, workspace, workspace_bytes,
                               search_batch_workspace_bytes(num_scenes, b.Qtot, b.Htot, resolution,
                                                            b.mode),
@@ -492,7 +492,7 @@ int crss_search_batch(const RiciSearchScene *scenes, int32_t num_scenes, int32_t
 }
 
 int rici_sync_status(void *stream, int32_t *device_status) {
-  DeviceState *d;
+  DeviceState *d = nullptr;
   int rc;
   if ((rc = device_state(&d))) return rc;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -508,7 +508,7 @@ int rici_sync_status(void *stream, int32_t *device_status) {
 }
 
 int rici_release_workspace(void) {
-  DeviceState *d;
+  DeviceState *d = nullptr;
   int rc;
   if ((rc = device_state(&d))) return rc;
   std::lock_guard<std::mutex> lk(g_mu);
