@@ -34,9 +34,11 @@ constexpr float kU = 5.9604644775390625e-08f;  // 2^-24: unit roundoff of FP32
 constexpr float kSafety = 2.0f;                // multiplies every derived error bound
 constexpr uint32_t kSkip = 0xFFFFFFFEu;
 constexpr float kCellClamp = 1048576.0f;  // |cell coordinate| limit (2^20)
-constexpr int kSlot = 25;  // words per staged triangle (odd stride: conflict-free lookups)
+constexpr int kSlot = 21;  // words per staged triangle (odd stride: conflict-free lookups)
 constexpr int kScanItems = 2048;
-constexpr int kPerWarp = 64 + 32 + 64 + 64 + 32 * kSlot;  // shared words per warp
+// shared words per warp: candidate queue, FP64 queue (triangle records, then their layers as
+// bytes), staged triangles
+constexpr int kPerWarp = 64 + 64 + 16 + 32 * kSlot;
 
 __host__ __device__ inline uint32_t bucket_count(int64_t nt) {
   uint32_t b = 1024;
@@ -287,18 +289,22 @@ struct Shared {
   int *bdup;     // 1: skip this entry (out of reach or repeated bucket), then the end of its
                  // candidate range (= its first candidate for a skipped entry)
   int *wq;       // this warp's candidate queue [64]
-  int *wst;      // this warp's item-owner marks for the current 32 items [32]
+  int *wst;      // this warp's item-owner marks for the current 32 items [32] (aliases the first
+                 // half of wq, which is free once a batch's triangles are staged)
   int *bq_rec;   // this warp's FP64 queue: triangle record [64]
-  int *bq_r;     // this warp's FP64 queue: layer [64]
+  unsigned char *bq_r;  // this warp's FP64 queue: layer [64]
   float *slots;  // this warp's staged triangles [32][kSlot]
 };
 
 // slot layout (words)
 enum {
-  SX = 0, SY = 3, SZ = 6, SGID = 9, SDE = 12, SRLO = 15, SBAND = 16, SFLAGS = 19, SREC = 20,
-  SINV = 21  // 1 / (z_j - z_i) of edge k (opposite vertex k, i < j local indices)
+  SX = 0, SY = 3, SZ = 6, SGID = 9, SDE = 12,
+  SINV = 15,   // 1 / (z_j - z_i) of edge k (opposite vertex k, i < j local indices)
+  SMETA = 18,  // first layer (bits 0-7), side-band layer of each vertex (bits 8-15, 16-23,
+               // 24-31; kNoBand for none; kAllBand in bits 8-15: every layer goes to FP64)
+  SREC = 19
 };
-constexpr int kAll64 = 1;
+constexpr unsigned kNoBand = 0xFF, kAllBand = 0xFE;
 
 // Estimate of the number of columns c with alpha_c^2 <= x (alpha_c = R (2c+1) / 2N, so the count
 // is floor(N sqrt(x) / R + 1/2)), in [0, N].  Off by one at most, and only within a few ulps of a
@@ -494,7 +500,7 @@ __device__ __forceinline__ void add_intervals(int *row, int N, int lo, int hi, i
 }
 
 template <int NW>
-__global__ void __launch_bounds__(NW * 32) k_generate(KArgs a) {
+__global__ void __launch_bounds__(NW * 32, NW == 4 ? 7 : 3) k_generate(KArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int N = a.N;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -515,10 +521,10 @@ __global__ void __launch_bounds__(NW * 32) k_generate(KArgs a) {
     s.bdup = s.buckets + nn + 1;
     int *wbase = s.bdup + nn + 1;
     s.wq = wbase + warp * kPerWarp;
-    s.wst = s.wq + 64;
-    s.bq_rec = s.wst + 32;
-    s.bq_r = s.bq_rec + 64;
-    s.slots = reinterpret_cast<float *>(s.bq_r + 64);
+    s.wst = s.wq;
+    s.bq_rec = s.wq + 64;
+    s.bq_r = reinterpret_cast<unsigned char *>(s.bq_rec + 64);
+    s.slots = reinterpret_cast<float *>(s.bq_rec + 64 + 16);
   }
 
   const int64_t og = a.origin_base + o;  // launch-wide origin index
@@ -719,7 +725,7 @@ __global__ void __launch_bounds__(NW * 32) k_generate(KArgs a) {
         nlay = max(0, r_hi - r_lo + 1);
       }
       if (nlay > 0) {
-        int flags = (fp64_only || dside >= 0.25f * spacing) ? kAll64 : 0;
+        unsigned meta = (unsigned)r_lo;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
           sl[SX + k] = tx[k];
@@ -728,13 +734,14 @@ __global__ void __launch_bounds__(NW * 32) k_generate(KArgs a) {
           // side band: the one layer a vertex could be ambiguous against
           float fr_ = rintf((tz[k] * scale + (float)(N - 1)) * 0.5f);
           int rk = fr_ <= 0.0f ? 0 : (fr_ >= (float)(N - 1) ? N - 1 : (int)fr_);
-          int band = -1;
+          unsigned band = kNoBand;
           for (int d = -1; d <= 1; ++d) {
             int rr = rk + d;
-            if (rr >= 0 && rr < N && fabsf(tz[k] - s.bf[rr]) <= dside) band = rr;
+            if (rr >= 0 && rr < N && fabsf(tz[k] - s.bf[rr]) <= dside) band = (unsigned)rr;
           }
-          sl[SBAND + k] = __int_as_float(band);
+          meta |= band << (8 * (k + 1));
         }
+        if (fp64_only || dside >= 0.25f * spacing) meta = (meta & ~0xff00u) | (kAllBand << 8);
         sl[SGID + 0] = r3.y;
         sl[SGID + 1] = r3.z;
         sl[SGID + 2] = r3.w;
@@ -753,8 +760,7 @@ __global__ void __launch_bounds__(NW * 32) k_generate(KArgs a) {
           sl[SDE + k] = (den > eden && de < 1e30f) ? de : __int_as_float(0x7f800000);
           sl[SINV + k] = __frcp_rn(tz[j] - tz[i]);
         }
-        sl[SRLO] = __int_as_float(r_lo);
-        sl[SFLAGS] = __int_as_float(flags);
+        sl[SMETA] = __uint_as_float(meta);
         sl[SREC] = __int_as_float(rec);
       }
     }
@@ -789,11 +795,12 @@ __global__ void __launch_bounds__(NW * 32) k_generate(KArgs a) {
       int res = 0, r = 0, rec = 0, lo = 0, hi = 0, dlo = 0;
       if (act) {
         const float *ts = s.slots + owner * kSlot;
-        r = __float_as_int(ts[SRLO]) + (it - ofirst);
+        const unsigned meta = __float_as_uint(ts[SMETA]);
+        r = (int)(meta & 0xffu) + (it - ofirst);
         rec = __float_as_int(ts[SREC]);
-        const int flags = __float_as_int(ts[SFLAGS]);
-        bool band = (flags & kAll64) || r == __float_as_int(ts[SBAND]) ||
-                    r == __float_as_int(ts[SBAND + 1]) || r == __float_as_int(ts[SBAND + 2]);
+        const unsigned b0 = (meta >> 8) & 0xffu;
+        const bool band = b0 == kAllBand || r == (int)b0 || r == (int)((meta >> 16) & 0xffu) ||
+                          r == (int)(meta >> 24);
         res = band ? 2 : layer_fp32(s.bf, s.a2f, N, ts, r, scale, lo, hi, dlo);
         ++n_items;
       }
