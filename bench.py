@@ -99,6 +99,24 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(x: float, device) -> float:
+    """The largest value over all ranks (a job's step time is its slowest rank's); x itself when
+    no process group is running or it has one rank."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank: float, ms: float, world: int) -> float:
+    """Whole-job throughput: every rank processes units_per_rank in ms (the max over ranks)."""
+    return world * units_per_rank / (ms / 1e3)
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -445,14 +463,10 @@ def main():
     t_hy = [ev[k][1].elapsed_time(ev[k][2]) for k in range(args.steps)]
     t_se = [ev[k][2].elapsed_time(ev[k][3]) for k in range(args.steps)]
     ms = [a + b + c for a, b, c in zip(t_nd, t_hy, t_se)]
-    ms_step = statistics.mean(ms)
-    if world > 1:
-        t = torch.tensor([ms_step], device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        ms_step = float(t.item())
+    ms_step = max_over_ranks(statistics.mean(ms), dev)
     images = V + Vt
     pairs = V * Vt
-    value = world * images / (ms_step / 1e3)
+    value = job_rate(images, ms_step, world)
 
     # tensor-core form of the same search (exact fp16 tcgen05 GEMM), timed separately
     tc = None
@@ -511,14 +525,10 @@ def main():
             torch.cuda.synchronize()
             if k > 0:  # first pass warms the copy path
                 e2e_ms.append(a0.elapsed_time(a1))
-        e_ms = statistics.mean(e2e_ms)
-        if world > 1:
-            t = torch.tensor([e_ms], device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            e_ms = float(t.item())
+        e_ms = max_over_ranks(statistics.mean(e2e_ms), dev)
         h2d = sum(x.numel() * x.element_size() for x in (h_vert, h_norm, h_tri, h_oh, h_on, h_match))
         d2h = Vt * (4 + 4 + 8)
-        e2e = {"value": world * images / (e_ms / 1e3), "unit": "images/s",
+        e2e = {"value": job_rate(images, e_ms, world), "unit": "images/s",
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e_ms}
 
     pk, pk_kind = peaks()
