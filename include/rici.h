@@ -274,6 +274,19 @@ RICI_API int rici_autotune_search_batch(const RiciSearchScene *scenes, int32_t n
                                         int64_t workspace_bytes, void *stream, int32_t repeats,
                                         RiciTuning *best, float *best_ms);
 
+/* Projection of points into the frame of one oriented point with the generation kernel's FP32
+ * stage, for checking that stage against an FP32 restatement: frame coefficients of Eq.
+ * rotationCoefficients in FP64 (second pair on the rotated x, identity rule for zero pairs)
+ * rounded to FP32, then Eqs. relativeLocation, firstRotation and secondRotation in FP32 with
+ *   P' = P - S; P''x = fma(Nay, P'y, Nax*P'x); P''y = fma(Nax, P'y, -(Nay*P'x));
+ *   Tx = fma(Nbz, P''x, -(Nbx*P'z)); Ty = P''y; Tz = fma(Nbx, P''x, Nbz*P'z)
+ * (each product and sum rounded once).  points: device [n][3] float; spin_vertex, spin_normal:
+ * device float[3]; out: device [n][3] float (Tx, Ty, Tz; alpha^2 = Tx^2 + Ty^2, beta = Tz).
+ * Asynchronous on `stream`.  RICI_ERR_INVALID_ARGUMENT for a negative count or a null pointer
+ * (n = 0 is a no-op), RICI_ERR_CUDA on a launch failure. */
+RICI_API int rici_project_fp32(const float *points, int64_t num_points, const float *spin_vertex,
+                               const float *spin_normal, float *out, void *stream);
+
 /* Measures, on the current device and the given stream, how many dp4a instructions (four int8
  * multiply-adds into an int32 each; the arithmetic of the CUDA-core search) the whole GPU issues
  * per second, running independent accumulator chains on every SM; the result goes to

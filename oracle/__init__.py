@@ -57,6 +57,10 @@ def _load():
             lib.oracle_max_threads.restype = ctypes.c_int
             lib.oracle_project_fp64.argtypes = [P, i64, P, P, P]
             lib.oracle_project_fp64.restype = None
+            lib.oracle_project_fp32.argtypes = [P, i64, P, P, P]
+            lib.oracle_project_fp32.restype = None
+            lib.oracle_rici_fp32.argtypes = [P, P, i64, P, i64, P, i64, f32, i32, P, i32, P]
+            lib.oracle_rici_fp32.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -100,6 +104,39 @@ def project_fp64(points, spin_vertex, spin_normal):
     out = np.zeros((p.shape[0], 3), np.float64)
     lib.oracle_project_fp64(_ptr(p), p.shape[0], _ptr(s), _ptr(n), _ptr(out))
     return out
+
+
+def project_fp32(points, spin_vertex, spin_normal):
+    """(Tx, Ty, Tz) float32 [n, 3] in the FP32 same-operation-order mode (frame in FP64, rounded
+    to float; projection in float with explicit fmaf)."""
+    lib = _load()
+    p = np.ascontiguousarray(points, dtype=np.float32).reshape(-1, 3)
+    s = np.ascontiguousarray(spin_vertex, dtype=np.float32).reshape(3)
+    n = np.ascontiguousarray(spin_normal, dtype=np.float32).reshape(3)
+    out = np.zeros((p.shape[0], 3), np.float32)
+    lib.oracle_project_fp32(_ptr(p), p.shape[0], _ptr(s), _ptr(n), _ptr(out))
+    return out
+
+
+def rici_fp32(vertices, normals, triangles, origins, support_radius: float, resolution: int,
+              num_threads: int = 0):
+    """Images of the FP32 same-operation-order mode and its counters: FP32 crossings and the
+    (origin, triangle, layer) items whose counts differ from the FP64 definition."""
+    lib = _load()
+    v = np.ascontiguousarray(vertices, dtype=np.float32).reshape(-1, 3)
+    n = np.ascontiguousarray(normals, dtype=np.float32).reshape(-1, 3)
+    t = np.ascontiguousarray(triangles, dtype=np.int32).reshape(-1, 3)
+    o = np.ascontiguousarray(origins, dtype=np.int32).reshape(-1)
+    if n.shape != v.shape:
+        raise ValueError("normals must match vertices")
+    N = int(resolution)
+    out = np.zeros((o.size, N, N), dtype=np.uint16)
+    cnt = np.zeros(2, dtype=np.int64)
+    rc = lib.oracle_rici_fp32(_ptr(v), _ptr(n), v.shape[0], _ptr(t), t.shape[0], _ptr(o), o.size,
+                              float(support_radius), N, _ptr(out), int(num_threads), _ptr(cnt))
+    if rc != 0:
+        raise ValueError(f"oracle_rici_fp32 failed with status {rc}")
+    return out, {"crossings": int(cnt[0]), "items_differing_from_fp64": int(cnt[1])}
 
 
 def crss(needle, haystack) -> int:

@@ -22,6 +22,9 @@
  *                              triangle with the plane of a circle layer; single crossings for
  *                              radii between |E0| and |E1|; double crossings between |C| and
  *                              min(|E0|,|E1|) when the closest point C lies inside the segment)
+ *  - oracle_project_fp32 / oracle_rici_fp32: the same steps in single precision in one fixed
+ *    operation order (see the comment above those functions), with a count of the items whose
+ *    counts differ from the FP64 definition;
  *  - oracle_crss: the clutter-resistant distance of Listing 1 / Eq. distanceFunctionExpression,
  *    in int64.
  *  - oracle_crss_search: per needle, the distance to its true match, the rank of that match
@@ -278,6 +281,182 @@ int oracle_crss_search(const uint16_t *needles, int64_t num_needles, const uint1
         if (out_top1) out_top1[i] = (int32_t)best_j;
     }
     return ORACLE_OK;
+}
+
+/*
+ * FP32 same-operation-order mode.  The frame coefficients are the FP64 ones above, rounded to
+ * float; projection, slicing and the segment quantities are evaluated in float in one fixed
+ * operation order, every multiply-add written as an explicit fmaf (contraction is off, so
+ * nothing else fuses):
+ *   P' = P - S;  P''x = fmaf(Nay, P'y, Nax*P'x);  P''y = fmaf(Nax, P'y, -(Nay*P'x));
+ *   Tx = fmaf(Nbz, P''x, -(Nbx*P'z));  Ty = P''y;  Tz = fmaf(Nbx, P''x, Nbz*P'z);
+ *   a crossed edge (i, j), i < j in the triangle's own vertex order:
+ *     lambda = (beta - Tz_i) * (1 / (Tz_j - Tz_i)),  E = fmaf(lambda, T_j - T_i, T_i);
+ *   e = fmaf(Ex, Ex, Ey*Ey); D = E1 - E0; d0 = fmaf(E0x, Dx, E0y*Dy); d1 likewise;
+ *   cr = fmaf(E0x, Dy, -(E0y*Dx)); dd = fmaf(Dx, Dx, Dy*Dy);
+ * and the predicates of steps 2-6 compare them with the FP32 roundings of alpha_c^2 and beta_r.
+ * E0 and E1 keep the roles of reading (7).  This is not the definition (reading (7) evaluates
+ * each edge from its lower global index, in FP64); it is the arithmetic a single-precision
+ * implementation of the method performs, used to measure how often single precision alone
+ * would decide a count differently from the FP64 definition.
+ */
+static void project_point_fp32(const float *P, const float S[3], float ax, float ay, float bx,
+                               float bz, float T[3]) {
+    float px = P[0] - S[0], py = P[1] - S[1], pz = P[2] - S[2];
+    float qx = fmaf(ay, py, ax * px);
+    float qy = fmaf(ax, py, -(ay * px));
+    T[0] = fmaf(bz, qx, -(bx * pz));
+    T[1] = qy;
+    T[2] = fmaf(bx, qx, bz * pz);
+}
+
+void oracle_project_fp32(const float *points, int64_t n, const float *spin_vertex,
+                         const float *spin_normal, float *out) {
+    double Nax, Nay, Nbx, Nbz;
+    frame_coefficients(spin_normal[0], spin_normal[1], spin_normal[2], &Nax, &Nay, &Nbx, &Nbz);
+    for (int64_t k = 0; k < n; k++)
+        project_point_fp32(points + 3 * k, spin_vertex, (float)Nax, (float)Nay, (float)Nbx,
+                           (float)Nbz, out + 3 * k);
+}
+
+/* Row increments of one triangle in one layer, single precision (order above). */
+static int count_layer_fp32(const float T[3][3], const int32_t gid[3], float beta,
+                            const float *alpha2, int32_t N, int64_t *row) {
+    int s0 = T[0][2] >= beta, s1 = T[1][2] >= beta, s2 = T[2][2] >= beta;
+    if (s0 == s1 && s1 == s2) return 0;
+    int lone = (s0 != s1 && s0 != s2) ? 0 : ((s1 != s0 && s1 != s2) ? 1 : 2);
+    int oa = lone == 0 ? 1 : 0, ob = lone == 2 ? 1 : 2;
+    int ia = lone < oa ? lone : oa, ja = lone < oa ? oa : lone;
+    int ib = lone < ob ? lone : ob, jb = lone < ob ? ob : lone;
+    float la = (beta - T[ia][2]) * (1.0f / (T[ja][2] - T[ia][2]));
+    float lb = (beta - T[ib][2]) * (1.0f / (T[jb][2] - T[ib][2]));
+    float Ea[2] = {fmaf(la, T[ja][0] - T[ia][0], T[ia][0]), fmaf(la, T[ja][1] - T[ia][1], T[ia][1])};
+    float Eb[2] = {fmaf(lb, T[jb][0] - T[ib][0], T[ib][0]), fmaf(lb, T[jb][1] - T[ib][1], T[ib][1])};
+    int32_t ua = gid[lone] < gid[oa] ? gid[lone] : gid[oa], va = gid[lone] < gid[oa] ? gid[oa] : gid[lone];
+    int32_t ub = gid[lone] < gid[ob] ? gid[lone] : gid[ob], vb = gid[lone] < gid[ob] ? gid[ob] : gid[lone];
+    const float *E0 = Ea, *E1 = Eb;
+    if (key_less(ub, vb, ua, va)) {
+        E0 = Eb;
+        E1 = Ea;
+    }
+    float e0 = fmaf(E0[0], E0[0], E0[1] * E0[1]);
+    float e1 = fmaf(E1[0], E1[0], E1[1] * E1[1]);
+    float Dx = E1[0] - E0[0], Dy = E1[1] - E0[1];
+    float d0 = fmaf(E0[0], Dx, E0[1] * Dy);
+    float d1 = fmaf(E1[0], Dx, E1[1] * Dy);
+    float cr = fmaf(E0[0], Dy, -(E0[1] * Dx));
+    float dd = fmaf(Dx, Dx, Dy * Dy);
+    for (int32_t c = 0; c < N; c++) {
+        int in0 = e0 >= alpha2[c], in1 = e1 >= alpha2[c];
+        if (in0 != in1)
+            row[c] += 1;
+        else if (in0 && in1 && d0 < 0.0f && d1 > 0.0f && alpha2[c] * dd > cr * cr)
+            row[c] += 2;
+    }
+    return 1;
+}
+
+/*
+ * Images of the FP32 same-order mode, plus counters: counters[0] = (origin, triangle, layer)
+ * crossings in FP32; counters[1] = items whose row increments differ between this mode and the
+ * FP64 definition (the items any single-precision evaluation must send to a wider precision).
+ */
+int oracle_rici_fp32(const float *vertices, const float *normals, int64_t num_vertices,
+                     const int32_t *triangles, int64_t num_triangles, const int32_t *origins,
+                     int64_t num_origins, float support_radius, int32_t resolution,
+                     uint16_t *out_images, int32_t num_threads, int64_t *counters) {
+    const int32_t N = resolution;
+    if (N < 1 || N > 1024 || !(support_radius > 0.0f) || num_vertices < 0 || num_triangles < 0 ||
+        num_origins < 0)
+        return ORACLE_BAD_ARGUMENT;
+    for (int64_t t = 0; t < 3 * num_triangles; t++)
+        if (triangles[t] < 0 || triangles[t] >= num_vertices) return ORACLE_BAD_INDEX;
+    for (int64_t o = 0; o < num_origins; o++)
+        if (origins[o] < 0 || origins[o] >= num_vertices) return ORACLE_BAD_INDEX;
+    const double R = (double)support_radius;
+    double *a2d = (double *)malloc(sizeof(double) * (size_t)N);
+    double *bd = (double *)malloc(sizeof(double) * (size_t)N);
+    float *a2f = (float *)malloc(sizeof(float) * (size_t)N);
+    float *bf = (float *)malloc(sizeof(float) * (size_t)N);
+    if (!a2d || !bd || !a2f || !bf) {
+        free(a2d);
+        free(bd);
+        free(a2f);
+        free(bf);
+        return ORACLE_NO_MEMORY;
+    }
+    for (int32_t i = 0; i < N; i++) {
+        double a = (R * (double)(2 * i + 1)) / (double)(2 * N);
+        a2d[i] = a * a;
+        bd[i] = (R * (double)(2 * i + 1 - N)) / (double)(2 * N);
+        a2f[i] = (float)a2d[i];
+        bf[i] = (float)bd[i];
+    }
+    int64_t crossings32 = 0, differing = 0;
+    int status = ORACLE_OK;
+#ifdef _OPENMP
+    if (num_threads > 0) omp_set_num_threads(num_threads);
+#pragma omp parallel reduction(+ : crossings32, differing)
+#endif
+    {
+        int64_t *img = (int64_t *)malloc(sizeof(int64_t) * (size_t)N * (size_t)N);
+        int64_t *r32 = (int64_t *)malloc(sizeof(int64_t) * (size_t)N);
+        int64_t *r64 = (int64_t *)malloc(sizeof(int64_t) * (size_t)N);
+        if (!img || !r32 || !r64) {
+#ifdef _OPENMP
+#pragma omp atomic write
+#endif
+            status = ORACLE_NO_MEMORY;
+        } else {
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 1)
+#endif
+            for (int64_t o = 0; o < num_origins; o++) {
+                memset(img, 0, sizeof(int64_t) * (size_t)N * (size_t)N);
+                const int32_t sv = origins[o];
+                const float Sf[3] = {vertices[3 * sv], vertices[3 * sv + 1], vertices[3 * sv + 2]};
+                const double S[3] = {Sf[0], Sf[1], Sf[2]};
+                double Nax, Nay, Nbx, Nbz;
+                frame_coefficients(normals[3 * sv], normals[3 * sv + 1], normals[3 * sv + 2], &Nax,
+                                   &Nay, &Nbx, &Nbz);
+                for (int64_t t = 0; t < num_triangles; t++) {
+                    float T32[3][3];
+                    double T64[3][3];
+                    int32_t gid[3];
+                    for (int k = 0; k < 3; k++) {
+                        gid[k] = triangles[3 * t + k];
+                        project_point_fp32(vertices + 3 * (int64_t)gid[k], Sf, (float)Nax,
+                                           (float)Nay, (float)Nbx, (float)Nbz, T32[k]);
+                        project_point(vertices + 3 * (int64_t)gid[k], S, Nax, Nay, Nbx, Nbz, T64[k]);
+                    }
+                    for (int32_t r = 0; r < N; r++) {
+                        memset(r32, 0, sizeof(int64_t) * (size_t)N);
+                        memset(r64, 0, sizeof(int64_t) * (size_t)N);
+                        int64_t dummy = 0;
+                        crossings32 += count_layer_fp32(T32, gid, bf[r], a2f, N, r32);
+                        count_layer(T64, gid, bd[r], a2d, N, r64, &dummy);
+                        if (memcmp(r32, r64, sizeof(int64_t) * (size_t)N) != 0) differing++;
+                        for (int32_t c = 0; c < N; c++) img[(int64_t)r * N + c] += r32[c];
+                    }
+                }
+                uint16_t *out = out_images + o * (int64_t)N * N;
+                for (int64_t b = 0; b < (int64_t)N * N; b++)
+                    out[b] = (uint16_t)(img[b] > 65535 ? 65535 : img[b]);
+            }
+        }
+        free(img);
+        free(r32);
+        free(r64);
+    }
+    free(a2d);
+    free(bd);
+    free(a2f);
+    free(bf);
+    if (counters) {
+        counters[0] = crossings32;
+        counters[1] = differing;
+    }
+    return status;
 }
 
 int oracle_max_threads(void) {

@@ -104,6 +104,8 @@ def load_library(path: str | None = None):
         lib.rici_last_error_string.restype = ctypes.c_char_p
         lib.rici_kernel_launches.argtypes = []
         lib.rici_kernel_launches.restype = i64
+        lib.rici_project_fp32.argtypes = [P, i64, P, P, P, P]
+        lib.rici_project_fp32.restype = ctypes.c_int
         lib.rici_set_tuning.argtypes = [P]
         lib.rici_set_tuning.restype = ctypes.c_int
         lib.rici_get_tuning.argtypes = [P]
@@ -438,3 +440,18 @@ def autotune_search_batch(scenes, resolution: int, *, repeats: int = 1, stream=N
                                               _stream_handle(stream), int(repeats),
                                               ctypes.byref(best), ctypes.byref(ms)))
     return _tuning_dict(best), float(ms.value)
+
+
+def project_fp32(points, spin_vertex, spin_normal, stream=None):
+    """The generation kernel's FP32 projection of points [n, 3] into one oriented point's frame."""
+    lib = load_library()
+    pts = _need(points, torch.float32, "points")
+    sv = _need(spin_vertex, torch.float32, "spin_vertex")
+    sn = _need(spin_normal, torch.float32, "spin_normal")
+    if pts.dim() != 2 or pts.shape[1] != 3 or sv.numel() != 3 or sn.numel() != 3:
+        raise ValueError("points must be [n, 3]; spin_vertex and spin_normal 3 floats")
+    out = torch.empty_like(pts)
+    with torch.cuda.device(pts.device):
+        _check(lib.rici_project_fp32(_ptr(pts), pts.shape[0], _ptr(sv), _ptr(sn), _ptr(out),
+                                     _stream_handle(stream)))
+    return out

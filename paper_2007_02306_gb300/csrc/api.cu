@@ -525,6 +525,19 @@ const char *rici_last_error_string(void) { return t_last_error.c_str(); }
 
 int64_t rici_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
 
+int rici_project_fp32(const float *points, int64_t num_points, const float *spin_vertex,
+                      const float *spin_normal, float *out, void *stream) {
+  t_last_error.clear();
+  if (num_points < 0) return fail(RICI_ERR_INVALID_ARGUMENT, "negative point count");
+  if (num_points == 0) return RICI_OK;
+  if (!points || !spin_vertex || !spin_normal || !out)
+    return fail(RICI_ERR_INVALID_ARGUMENT, "null pointer");
+  cudaError_t e = launch_project_fp32(points, num_points, spin_vertex, spin_normal, out,
+                                      static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "rici_project_fp32 launch");
+  return RICI_OK;
+}
+
 int rici_measure_dp4a_rate(void *stream, double *dp4a_per_second) {
   if (!dp4a_per_second) return fail(RICI_ERR_INVALID_ARGUMENT, "null output pointer");
   cudaError_t e = measure_dp4a_rate(static_cast<cudaStream_t>(stream), dp4a_per_second);

@@ -156,6 +156,10 @@ void count_launches(int64_t n);
 // Device address of the status word on the current device.
 cudaError_t status_word_address(int **address);
 
+// The generation kernel's FP32 projection stage for n points (frame in FP64, rounded to FP32).
+cudaError_t launch_project_fp32(const float *pts, int64_t n, const float *sv, const float *sn,
+                                float *out, cudaStream_t st);
+
 // Measured whole-device dp4a issue rate (instructions per second), for roofline peaks.
 cudaError_t measure_dp4a_rate(cudaStream_t st, double *per_second);
 

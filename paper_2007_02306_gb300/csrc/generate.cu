@@ -326,6 +326,62 @@ __device__ __forceinline__ int lower_count_d(double x, const double *a2d, int N)
   return lo;
 }
 
+// Eq. rotationCoefficients (second pair on the rotated x component) with the identity rule,
+// in FP64 with the definition's operation order: fr = (Nax, Nay, Nbx, Nbz).
+__device__ __forceinline__ void frame_fp64(float nxf, float nyf, float nzf, double *fr) {
+  const double nx = nxf, ny = nyf, nz = nzf;
+  const double h = __dsqrt_rn(__dadd_rn(__dmul_rn(nx, nx), __dmul_rn(ny, ny)));
+  double Nax = 1.0, Nay = 0.0;
+  if (h != 0.0) {
+    Nax = __ddiv_rn(nx, h);
+    Nay = __ddiv_rn(ny, h);
+  }
+  const double n2x = __dadd_rn(__dmul_rn(Nax, nx), __dmul_rn(Nay, ny));
+  const double g = __dsqrt_rn(__dadd_rn(__dmul_rn(n2x, n2x), __dmul_rn(nz, nz)));
+  double Nbx = 0.0, Nbz = 1.0;
+  if (g != 0.0) {
+    Nbx = __ddiv_rn(n2x, g);
+    Nbz = __ddiv_rn(nz, g);
+  }
+  fr[0] = Nax;
+  fr[1] = Nay;
+  fr[2] = Nbx;
+  fr[3] = Nbz;
+}
+
+// Eqs. relativeLocation, firstRotation, secondRotation in FP32 with explicit roundings (the
+// frame coefficients rounded to FP32).  Returns |dx| + |dy| + |dz|, the scale of the error bound
+// |T32 - T64| <= 10 u (|dx| + |dy| + |dz|) used by the generation kernel.
+__device__ __forceinline__ float project_fp32(float px, float py, float pz, float Sx, float Sy,
+                                              float Sz, float fax, float fay, float fbx,
+                                              float fbz, float &tx, float &ty, float &tz) {
+  const float dx = __fsub_rn(px, Sx), dy = __fsub_rn(py, Sy), dz = __fsub_rn(pz, Sz);
+  const float qx = __fmaf_rn(fay, dy, __fmul_rn(fax, dx));
+  const float qy = __fmaf_rn(fax, dy, -__fmul_rn(fay, dx));
+  tx = __fmaf_rn(fbz, qx, -__fmul_rn(fbx, dz));
+  ty = qy;
+  tz = __fmaf_rn(fbx, qx, __fmul_rn(fbz, dz));
+  return fabsf(dx) + fabsf(dy) + fabsf(dz);
+}
+
+// Projection of n points into one oriented point's frame with the generation kernel's FP32
+// stage (one thread per point; each computes the frame).
+__global__ void k_project_fp32(const float *__restrict__ pts, int64_t n, const float *__restrict__ sv,
+                               const float *__restrict__ sn, float *__restrict__ out) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n;
+       k += (int64_t)gridDim.x * blockDim.x) {
+    double fr[4];
+    frame_fp64(sn[0], sn[1], sn[2], fr);
+    float tx, ty, tz;
+    project_fp32(pts[3 * k], pts[3 * k + 1], pts[3 * k + 2], sv[0], sv[1], sv[2],
+                 __double2float_rn(fr[0]), __double2float_rn(fr[1]), __double2float_rn(fr[2]),
+                 __double2float_rn(fr[3]), tx, ty, tz);
+    out[3 * k] = tx;
+    out[3 * k + 1] = ty;
+    out[3 * k + 2] = tz;
+  }
+}
+
 __device__ __forceinline__ void project64(float px, float py, float pz, const double *fr,
                                           double T[3]) {
   double dx = __dsub_rn((double)px, fr[0]);
@@ -560,28 +616,10 @@ __global__ void __launch_bounds__(NW * 32, NW == 4 ? 7 : 3) k_generate(KArgs a) 
     s.bf[i] = __double2float_rn(b);
   }
   if (tid == 0) {
-    // Eq. rotationCoefficients (second pair on the rotated x) with the identity rule
-    double nx = nxf, ny = nyf, nz = nzf;
-    double h = __dsqrt_rn(__dadd_rn(__dmul_rn(nx, nx), __dmul_rn(ny, ny)));
-    double Nax = 1.0, Nay = 0.0;
-    if (h != 0.0) {
-      Nax = __ddiv_rn(nx, h);
-      Nay = __ddiv_rn(ny, h);
-    }
-    double n2x = __dadd_rn(__dmul_rn(Nax, nx), __dmul_rn(Nay, ny));
-    double g = __dsqrt_rn(__dadd_rn(__dmul_rn(n2x, n2x), __dmul_rn(nz, nz)));
-    double Nbx = 0.0, Nbz = 1.0;
-    if (g != 0.0) {
-      Nbx = __ddiv_rn(n2x, g);
-      Nbz = __ddiv_rn(nz, g);
-    }
     s.fr[0] = Sx;
     s.fr[1] = Sy;
     s.fr[2] = Sz;
-    s.fr[3] = Nax;
-    s.fr[4] = Nay;
-    s.fr[5] = Nbx;
-    s.fr[6] = Nbz;
+    frame_fp64(nxf, nyf, nzf, s.fr + 3);
   }
   // neighbourhood: the (2 nhalf + 1)^3 cells around the spin vertex's cell (cell edge > reach /
   // nhalf).  A triangle binned in a cell (by its bounding-sphere centre, radius <= r_big) can
@@ -690,17 +728,9 @@ __global__ void __launch_bounds__(NW * 32, NW == 4 ? 7 : 3) k_generate(KArgs a) 
       float P[9] = {r1.x, r1.y, r1.z, r1.w, r2.x, r2.y, r2.z, r2.w, r3.x};
       float tx[3], ty[3], tz[3], M = 0.0f;
 #pragma unroll
-      for (int k = 0; k < 3; ++k) {
-        // Eqs. relativeLocation, firstRotation, secondRotation in FP32 (explicit roundings)
-        float dx = __fsub_rn(P[3 * k], Sx), dy = __fsub_rn(P[3 * k + 1], Sy),
-              dz = __fsub_rn(P[3 * k + 2], Sz);
-        float qx = __fmaf_rn(fay, dy, __fmul_rn(fax, dx));
-        float qy = __fmaf_rn(fax, dy, -__fmul_rn(fay, dx));
-        tx[k] = __fmaf_rn(fbz, qx, -__fmul_rn(fbx, dz));
-        ty[k] = qy;
-        tz[k] = __fmaf_rn(fbx, qx, __fmul_rn(fbz, dz));
-        M = fmaxf(M, fabsf(dx) + fabsf(dy) + fabsf(dz));
-      }
+      for (int k = 0; k < 3; ++k)
+        M = fmaxf(M, project_fp32(P[3 * k], P[3 * k + 1], P[3 * k + 2], Sx, Sy, Sz, fax, fay, fbx,
+                                  fbz, tx[k], ty[k], tz[k]));
       // |T32 - T64| <= dT for every coordinate (first-order bound 7uM, 10uM with slack)
       const float dT = 10.0f * kU * M + 1e-37f;
       const float dside = kSafety * (dT + kU * R);
@@ -958,6 +988,15 @@ cudaError_t launch_k_generate(const KArgs &k, int64_t total_origins, cudaStream_
 }  // namespace
 
 uint32_t generate_bucket_count(int64_t nt) { return bucket_count(nt); }
+
+cudaError_t launch_project_fp32(const float *pts, int64_t n, const float *sv, const float *sn,
+                                float *out, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  const int64_t want = (n + 255) / 256;
+  k_project_fp32<<<(unsigned)(want < 152 * 16 ? want : 152 * 16), 256, 0, st>>>(pts, n, sv, sn, out);
+  count_launches(1);
+  return cudaGetLastError();
+}
 
 int64_t generate_batch_workspace_bytes(int num_scenes, int64_t total_tris, int64_t total_buckets) {
   Carver c(nullptr);
