@@ -104,3 +104,23 @@ def dyadic_mesh(rng: np.random.Generator, n_tris: int, n_verts: int, scale_bits:
     v = rng.integers(-lim, lim + 1, size=(n_verts, 3)).astype(np.float64) / q
     t = np.stack([rng.choice(n_verts, 3, replace=False) for _ in range(n_tris)]).astype(np.int32)
     return v.astype(np.float32), t
+
+
+def radius_tie_scene(R=0.3, N=64):
+    """A triangle with a vertical edge at distance x from the axis, where x^2 lies just below
+    alpha_c^2 in exact arithmetic but rounds to the same FP32 value as alpha_c^2: the circle of
+    column c misses the edge in FP64 and touches it in FP32 (origin at 0 with normal +z, where
+    both precisions project every vertex exactly)."""
+    R = float(np.float32(R))  # the support radius is passed as an FP32 value
+    for c in range(N):
+        a2d = ((R * (2 * c + 1)) / (2 * N)) ** 2
+        a2f = np.float32(a2d)
+        x = np.float32(np.sqrt(a2d))
+        for _ in range(64):
+            if float(x) ** 2 < a2d and np.float32(float(x) ** 2) == a2f:
+                v = np.array([[0, 0, 0], [x, 0, -0.01], [x, 0, 0.01], [x + 0.05, 0.04, 0.0]],
+                             np.float32)
+                n = np.tile(np.array([0.0, 0.0, 1.0], np.float32), (4, 1))
+                return v, n, np.array([[1, 2, 3]], np.int32), c
+            x = np.nextafter(x, np.float32(0))
+    raise AssertionError("no near-tie found")

@@ -41,9 +41,9 @@ def test_projection_bit_exact(rici, oracle_mod, normal):
 def test_near_tie_follows_fp64(rici, oracle_mod):
     import torch
 
-    from test_oracle_fp32_pins import tie_scene
+    from synth import fixtures as F
 
-    v, n, t, c = tie_scene()
+    v, n, t, c = F.radius_tie_scene()
     o = np.array([0], np.int32)
     d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()  # noqa: E731
     img = rici.rici_generate(d(v), d(n), d(t), d(o), 0.3, 64)

@@ -10,6 +10,8 @@
 """
 import numpy as np
 
+from synth import fixtures as F
+
 U = 2.0 ** -24
 
 
@@ -51,28 +53,8 @@ def test_exact_inputs_give_identical_images(oracle_mod):
     assert np.array_equal(got, want)
 
 
-def tie_scene(R=0.3, N=64):
-    """A triangle with a vertical edge at distance x from the axis, where x^2 lies just below
-    alpha_c^2 in exact arithmetic but rounds to the same FP32 value as alpha_c^2: the circle of
-    column c misses the edge in FP64 and touches it in FP32 (origin at 0 with normal +z, where
-    both precisions project every vertex exactly)."""
-    R = float(np.float32(R))  # the support radius is passed as an FP32 value
-    for c in range(N):
-        a2d = ((R * (2 * c + 1)) / (2 * N)) ** 2
-        a2f = np.float32(a2d)
-        x = np.float32(np.sqrt(a2d))
-        for _ in range(64):
-            if float(x) ** 2 < a2d and np.float32(float(x) ** 2) == a2f:
-                v = np.array([[0, 0, 0], [x, 0, -0.01], [x, 0, 0.01], [x + 0.05, 0.04, 0.0]],
-                             np.float32)
-                n = np.tile(np.array([0.0, 0.0, 1.0], np.float32), (4, 1))
-                return v, n, np.array([[1, 2, 3]], np.int32), c
-            x = np.nextafter(x, np.float32(0))
-    raise AssertionError("no near-tie found")
-
-
 def test_fp32_alone_decides_a_near_tie_differently(oracle_mod):
-    v, n, t, c = tie_scene()
+    v, n, t, c = F.radius_tie_scene()
     o = np.array([0], np.int32)
     want = oracle_mod.rici_fp64(v, n, t, o, 0.3, 64)
     got, cnt = oracle_mod.rici_fp32(v, n, t, o, 0.3, 64)
