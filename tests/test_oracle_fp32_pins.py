@@ -4,9 +4,9 @@
   |T32 - T64| <= 10 u (|dx| + |dy| + |dz|), u = 2^-24, on random points and normals.
 - With an axis-aligned normal and a mesh on a coarse dyadic grid every FP32 operation is exact,
   so the FP32 images equal the FP64 definition and no item differs.
-- A vertex placed just below the FP32 rounding of a layer height but above its FP64 value is on
-  different sides in the two precisions: the FP32 mode must report the item as differing and its
-  image must differ from the FP64 image in that row.
+- A vertical edge whose squared distance to the axis lies just below a bin's alpha^2 but rounds
+  onto it in FP32 is outside that circle in FP64 and on it in FP32: the FP32 mode must report the
+  item as differing and its image must differ from the FP64 image in that column.
 """
 import numpy as np
 
