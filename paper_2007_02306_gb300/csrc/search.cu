@@ -191,7 +191,7 @@ __device__ __forceinline__ unsigned long long warp_min_u64(unsigned long long v)
 
 // Narrow x narrow pairs.  Block: kTQ needles (deltas + masks in shared memory) x
 // kDenseThreads haystack images (one per thread).
-template <int N, int kTQ>
+template <int N, int kTQ, bool kCount>
 __global__ void __launch_bounds__(kDenseThreads, N <= 64 ? 2 : 1) k_dense(
     const int8_t *__restrict__ ndelta, const int8_t *__restrict__ nmask,
     const int *__restrict__ nrowsq, const int *__restrict__ nwide, int64_t Q,
@@ -292,7 +292,7 @@ __global__ void __launch_bounds__(kDenseThreads, N <= 64 ? 2 : 1) k_dense(
       if (__ballot_sync(0xffffffffu, alive != 0) == 0) break;
       const int r = ord[i];
       const unsigned use = alive & rmask[r];
-      if (counters) pair_rows += __popc(use);
+      if (kCount) pair_rows += __popc(use);
       int hw[WPR];
       if (use) {
         const int *src = hgrp + r * (WPR * 32);
@@ -314,7 +314,7 @@ __global__ void __launch_bounds__(kDenseThreads, N <= 64 ? 2 : 1) k_dense(
 #pragma unroll
       for (int q = 0; q < kTQ; ++q) {
         if (__ballot_sync(0xffffffffu, (use >> q) & 1u) == 0) continue;
-        if (counters) lane_slots += 1;  // one warp-wide needle-row iteration (32 lane slots)
+        if (kCount) lane_slots += 1;  // one warp-wide needle-row iteration (32 lane slots)
         // row sum of m (a - b)^2 = sum a^2 + sum (m b)^2 - 2 sum a b, with sum a^2 precomputed;
         // kChains independent accumulator chains per term
         constexpr int kChains = WPR >= 8 ? 4 : 2;
@@ -360,7 +360,7 @@ __global__ void __launch_bounds__(kDenseThreads, N <= 64 ? 2 : 1) k_dense(
         if (b != kNoBest) atomicMin(&best[q0 + q], b);
       }
     }
-    if (counters) {
+    if (kCount) {
 #pragma unroll
       for (int d = 16; d > 0; d >>= 1) pair_rows += __shfl_down_sync(0xffffffffu, pair_rows, d);
       if (lane == 0 && pair_rows) atomicAdd(counters, pair_rows);
@@ -550,8 +550,8 @@ cudaError_t launch_dense(const int8_t *nd, const int8_t *nm, const int *nrs, con
                          unsigned long long *counters, cudaStream_t st) {
   constexpr int kTQ = N <= 64 ? 8 : 4;
   const size_t smem = sizeof(int2) * kTQ * (N * N / 4);
-  cudaError_t e = cudaFuncSetAttribute(k_dense<N, kTQ>,
-                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  auto kern = counters ? k_dense<N, kTQ, true> : k_dense<N, kTQ, false>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int64_t th = (H + kDenseThreads - 1) / kDenseThreads;
   const int64_t tq = (Q + kTQ - 1) / kTQ;
@@ -565,9 +565,8 @@ cudaError_t launch_dense(const int8_t *nd, const int8_t *nm, const int *nrs, con
   constexpr int64_t kMaxGrid = 0x7fffffffll;
   for (int64_t t0 = 0; t0 < total; t0 += kMaxGrid) {
     const int64_t n = total - t0 < kMaxGrid ? total - t0 : kMaxGrid;
-    k_dense<N, kTQ><<<(unsigned)n, kDenseThreads, smem, st>>>(nd, nm, nrs, nw, Q, hd, hw, H, dt,
-                                                             nf, rank, best, counters, t0, tq, th,
-                                                             band_h);
+    kern<<<(unsigned)n, kDenseThreads, smem, st>>>(nd, nm, nrs, nw, Q, hd, hw, H, dt, nf, rank,
+                                                   best, counters, t0, tq, th, band_h);
     count_launches(1);
   }
   return cudaGetLastError();
