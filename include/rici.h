@@ -58,7 +58,8 @@ extern "C" {
 #define RICI_GEN_FP64 1      /* every (triangle, layer) evaluated in FP64 (slow reference mode) */
 
 /* Search modes (crss_search). */
-#define RICI_SEARCH_DEFAULT 0   /* fastest exact form available */
+#define RICI_SEARCH_DEFAULT 0   /* fastest exact form available: RICI_SEARCH_TENSOR where it
+                                   applies (N in 8..128, powers of two), else CUDA cores */
 #define RICI_SEARCH_CUDA_CORE 1 /* Listing 1 per pair on CUDA cores, early exit */
 #define RICI_SEARCH_EXACT_SLOW 2 /* generic int64 per-pair kernel for every pair (test reference) */
 #define RICI_SEARCH_TENSOR 3    /* exact fp16 tcgen05 GEMM of the expanded distance (N in 8..128,

@@ -582,7 +582,8 @@ void search_tiles(int64_t Q, int64_t H, int32_t *tiles_m, int32_t *tiles_n) {
 int64_t search_batch_workspace_bytes(int num_scenes, int64_t Q, int64_t H, int N, int mode) {
   const int64_t K = (int64_t)N * N;
   mode &= 0xff;
-  const bool tensor = mode == RICI_SEARCH_TENSOR && tc_supported(N);
+  const bool tensor =
+      (mode == RICI_SEARCH_TENSOR || mode == RICI_SEARCH_DEFAULT) && tc_supported(N);
   const bool packed = !tensor && mode != RICI_SEARCH_EXACT_SLOW && dense_supported(N);
   Carver c(nullptr);
   c.take<SearchScene>(num_scenes);
@@ -618,7 +619,8 @@ cudaError_t launch_search_batch(const SearchScene *scenes, const SearchBatch &b,
   if (Q == 0) return cudaSuccess;
   const int withhold = (b.mode & RICI_SEARCH_TEST_WITHHOLD_LOAD) ? 1 : 0;
   const int mode = b.mode & 0xff;
-  const bool tensor = mode == RICI_SEARCH_TENSOR && tc_supported(N);
+  const bool tensor =
+      (mode == RICI_SEARCH_TENSOR || mode == RICI_SEARCH_DEFAULT) && tc_supported(N);
   const bool dense = !tensor && mode != RICI_SEARCH_EXACT_SLOW && dense_supported(N) &&
                      b.num_scenes == 1;
   Carver c(ws);
