@@ -19,6 +19,7 @@ samples of the same workload and extrapolates to the full step.
 from __future__ import annotations
 
 import argparse
+import hashlib
 import json
 import os
 import statistics
@@ -90,6 +91,14 @@ def parse():
     ap.add_argument("--needle-limit", type=int, default=0,
                     help="use only the first Q target vertices as needles (small profiling case)")
     return ap.parse_args()
+
+
+def input_digest(scene) -> str:
+    """First 16 hex digits of the SHA-256 of the scene's vertex, normal and triangle arrays."""
+    h = hashlib.sha256()
+    for a in (scene.vertices, scene.normals, scene.triangles):
+        h.update(np.ascontiguousarray(a).tobytes())
+    return h.hexdigest()[:16]
 
 
 def dist_env():
@@ -606,6 +615,7 @@ def main():
         "config": {"workload": WORKLOAD, "resolution": N_RES, "support_radius": R_SUP,
                    "triangles": T, "needles": Vt, "haystack": V, "comparisons": pairs, "seed": SEED,
                    "search_mode": args.search_mode,
+                   "input_sha256": input_digest(scene),
                    "l2": "flushed by a 512 MB device write before every timed step",
                    "parallelism": f"replicas x{world}"},
         "breakdown": {
@@ -615,7 +625,8 @@ def main():
             "generation_images_per_s": images / ((statistics.mean(t_nd) + gen_ms) / 1e3),
             "search_comparisons_per_s": pairs / (se_ms / 1e3),
             "generation_counters": {"triangles_processed": gcnt[0], "layer_items": gcnt[1],
-                                    "fp64_band_items": gcnt[2], "cull_candidates": gcnt[3]},
+                                    "fp64_band_items": gcnt[2], "cull_candidates": gcnt[3],
+                                    "fp64_band_rate": gcnt[2] / gcnt[1] if gcnt[1] else None},
             "search_counters": {"pair_rows": scnt[0], "wide_pairs": scnt[1],
                                 "wide_terms": scnt[2], "lane_slots": scnt[3],
                                 "lane_utilisation": scnt[0] / scnt[3] if scnt[3] else None},
