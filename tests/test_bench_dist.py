@@ -58,3 +58,14 @@ def test_single_process_passes_values_through():
 
     assert bench.max_over_ranks(3.5, "cpu") == 3.5
     assert bench.job_rate(500.0, 250.0, 1) == pytest.approx(2000.0)
+
+
+def test_input_digest_is_deterministic():
+    sys.path.insert(0, ROOT)
+    import bench
+    import synth
+
+    a = bench.input_digest(synth.tiny_scene(seed=1))
+    assert a == bench.input_digest(synth.tiny_scene(seed=1))
+    assert a != bench.input_digest(synth.tiny_scene(seed=2))
+    assert len(a) == 16
