@@ -2,7 +2,8 @@
 
 Under torchrun every rank runs one replica of the step and the job's step time is the slowest
 rank's; the whole-job rate is world x units per rank / that time.  Two spawned gloo ranks with
-different times must both see the maximum, and the rate must follow from it.
+different times must both see the maximum, and the rate must follow from it.  The scene digest
+the benchmark records must depend on the seed only.
 """
 import os
 import socket
