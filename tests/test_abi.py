@@ -108,3 +108,12 @@ def test_binding_fails_loudly_without_library(tmp_path):
             binding.load_library(str(tmp_path / "missing.so"))
     finally:
         binding._lib = saved
+
+
+def test_projection_and_tuning_reject_bad_arguments_on_host(lib):
+    dummy = ctypes.c_void_p(16)
+    assert lib.rici_project_fp32(dummy, -1, dummy, dummy, dummy, None) == 1
+    assert lib.rici_project_fp32(None, 4, dummy, dummy, dummy, None) == 1
+    assert lib.rici_project_fp32(dummy, 0, None, None, None, None) == 0
+    assert lib.rici_get_tuning(None) == 1
+    assert lib.rici_measure_dp4a_rate(None, None) == 1
