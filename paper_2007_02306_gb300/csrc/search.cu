@@ -292,6 +292,7 @@ __global__ void __launch_bounds__(kDenseThreads, N <= 64 ? 2 : 1) k_dense(
       if (__ballot_sync(0xffffffffu, alive != 0) == 0) break;
       const int r = ord[i];
       const unsigned use = alive & rmask[r];
+      const unsigned wuse = __reduce_or_sync(0xffffffffu, use);  // needles any lane still needs
       if (kCount) pair_rows += __popc(use);
       int hw[WPR];
       if (use) {
@@ -313,7 +314,7 @@ __global__ void __launch_bounds__(kDenseThreads, N <= 64 ? 2 : 1) k_dense(
       }
 #pragma unroll
       for (int q = 0; q < kTQ; ++q) {
-        if (__ballot_sync(0xffffffffu, (use >> q) & 1u) == 0) continue;
+        if (((wuse >> q) & 1u) == 0) continue;
         if (kCount) lane_slots += 1;  // one warp-wide needle-row iteration (32 lane slots)
         // row sum of m (a - b)^2 = sum a^2 + sum (m b)^2 - 2 sum a b, with sum a^2 precomputed;
         // kChains independent accumulator chains per term
