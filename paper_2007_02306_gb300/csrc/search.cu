@@ -276,11 +276,11 @@ __global__ void __launch_bounds__(kDenseThreads, N <= 64 ? 2 : 1) k_dense(
   for (int64_t ht = h0; ht < h1; ++ht) {
     const int64_t j = ht * kDenseThreads + tid;
     const bool valid = j < H && !hwide[j];
-    int acc[kTQ];
+    int acc[kTQ];  // partial distance minus the needle's true distance (exit once > 0)
     unsigned alive = 0;
 #pragma unroll
     for (int q = 0; q < kTQ; ++q) {
-      acc[q] = 0;
+      acc[q] = -thr_s[q];
       if (valid && act_s[q]) alive |= 1u << q;
     }
     // this thread's image in the warp-interleaved layout (group of 32 images, chunks of CW words)
@@ -342,7 +342,7 @@ __global__ void __launch_bounds__(kDenseThreads, N <= 64 ? 2 : 1) k_dense(
         }
         if ((use >> q) & 1u) {
           acc[q] += wrow[q][r] + sb - 2 * sa;
-          if (acc[q] > thr_s[q]) alive &= ~(1u << q);
+          if (acc[q] > 0) alive &= ~(1u << q);
         }
       }
     }
@@ -351,8 +351,8 @@ __global__ void __launch_bounds__(kDenseThreads, N <= 64 ? 2 : 1) k_dense(
     for (int q = 0; q < kTQ; ++q) {
       if (!act_s[q]) continue;
       const bool fin = (alive >> q) & 1u;
-      int c = fin && acc[q] < thr_s[q];
-      unsigned long long b = fin ? pack_best(acc[q], j) : kNoBest;
+      int c = fin && acc[q] < 0;
+      unsigned long long b = fin ? pack_best(acc[q] + thr_s[q], j) : kNoBest;
 #pragma unroll
       for (int d = 16; d > 0; d >>= 1) c += __shfl_down_sync(0xffffffffu, c, d);
       b = warp_min_u64(b);
