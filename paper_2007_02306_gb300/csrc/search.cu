@@ -16,8 +16,9 @@
 //                   as dp4a over 4 packed deltas (plus one AND for mb); each row's sum is >= 0,
 //                   so partial sums are monotone and a pair stops once it exceeds
 //                   d(i, match_i) (the early exit of Section 4.4, which never changes a rank).
-//                   A block keeps 8 needles in shared memory and sweeps a band of haystack
-//                   tiles (512 images each, one per thread), rows heaviest first.
+//                   A block keeps 4 needles in shared memory and sweeps a band of haystack
+//                   tiles (2,048 images each, four per thread at N <= 64), rows heaviest
+//                   first; each broadcast needle word serves all of a thread's images.
 //   k_wide          pairs with a wide side: Listing 1 over the needle's non-zero deltas in
 //                   int64, reading the uint16 images.
 //   k_finalize / k_top1_exact   combine counts and top-1 candidates.
@@ -29,7 +30,7 @@
 namespace rici {
 namespace {
 
-constexpr int kDenseThreads = 512;     // haystack images per dense tile
+constexpr int kDenseThreads = 512;     // threads of a dense block
 constexpr int64_t kBandMax = 8;        // haystack tiles per band of the dense work order
 constexpr int kWideThreads = 256;
 constexpr unsigned long long kNoBest = ~0ull;
@@ -190,9 +191,9 @@ __device__ __forceinline__ unsigned long long warp_min_u64(unsigned long long v)
 }
 
 // Narrow x narrow pairs.  Block: kTQ needles (deltas + masks in shared memory) x
-// kDenseThreads haystack images (one per thread).
-template <int N, int kTQ, bool kCount>
-__global__ void __launch_bounds__(kDenseThreads, N <= 64 ? 2 : 1) k_dense(
+// kDenseThreads * kImg haystack images (kImg per thread, in consecutive groups of 32).
+template <int N, int kTQ, int kImg, bool kCount>
+__global__ void __launch_bounds__(kDenseThreads, N * kImg <= 64 ? 2 : 1) k_dense(
     const int8_t *__restrict__ ndelta, const int8_t *__restrict__ nmask,
     const int *__restrict__ nrowsq, const int *__restrict__ nwide, int64_t Q,
     const int8_t *__restrict__ hdelta,
@@ -273,76 +274,102 @@ __global__ void __launch_bounds__(kDenseThreads, N <= 64 ? 2 : 1) k_dense(
   __syncthreads();
   const int nrows = nrows_s;
 
+  constexpr int kTile = kDenseThreads * kImg;  // haystack images per tile
+  constexpr int CW = WPR < 4 ? WPR : 4;
+  constexpr int64_t kGroupWords = (int64_t)N * WPR * 32;  // one group of 32 interleaved images
+  const int warp = tid >> 5;
   for (int64_t ht = h0; ht < h1; ++ht) {
-    const int64_t j = ht * kDenseThreads + tid;
-    const bool valid = j < H && !hwide[j];
-    int acc[kTQ];  // partial distance minus the needle's true distance (exit once > 0)
-    unsigned alive = 0;
+    // this thread's images: j0 + 32 k, k < kImg (a warp owns kImg consecutive groups of 32)
+    const int64_t j0 = ht * kTile + (int64_t)warp * (32 * kImg) + lane;
+    int acc[kImg][kTQ];  // partial distance minus the needle's true distance (exit once > 0)
+    unsigned alive[kImg];
 #pragma unroll
-    for (int q = 0; q < kTQ; ++q) {
-      acc[q] = -thr_s[q];
-      if (valid && act_s[q]) alive |= 1u << q;
+    for (int k = 0; k < kImg; ++k) {
+      const int64_t j = j0 + 32 * k;
+      const bool valid = j < H && !hwide[j];
+      alive[k] = 0;
+#pragma unroll
+      for (int q = 0; q < kTQ; ++q) {
+        acc[k][q] = -thr_s[q];
+        if (valid && act_s[q]) alive[k] |= 1u << q;
+      }
     }
-    // this thread's image in the warp-interleaved layout (group of 32 images, chunks of CW words)
-    constexpr int CW = WPR < 4 ? WPR : 4;
-    const int *hgrp = reinterpret_cast<const int *>(hdelta) + (j >> 5) * (int64_t)(N * WPR * 32) +
-                      lane * CW;
+    const int *hgrp = reinterpret_cast<const int *>(hdelta) + (j0 >> 5) * kGroupWords + lane * CW;
     unsigned long long pair_rows = 0, lane_slots = 0;
-    for (int i = 0; i < nrows; ++i) {
-      if (__ballot_sync(0xffffffffu, alive != 0) == 0) break;
-      const int r = ord[i];
-      const unsigned use = alive & rmask[r];
-      const unsigned wuse = __reduce_or_sync(0xffffffffu, use);  // needles any lane still needs
-      if (kCount) pair_rows += __popc(use);
-      int hw[WPR];
-      if (use) {
-        const int *src = hgrp + r * (WPR * 32);
+    int hw[kImg][WPR];
 #pragma unroll
-        for (int v = 0; v < WPR / CW; ++v) {
-          if constexpr (CW == 4) {
-            const int4 x = *reinterpret_cast<const int4 *>(src + v * 32 * CW);
-            hw[4 * v] = x.x;
-            hw[4 * v + 1] = x.y;
-            hw[4 * v + 2] = x.z;
-            hw[4 * v + 3] = x.w;
-          } else {
-            const int2 x = *reinterpret_cast<const int2 *>(src + v * 32 * CW);
-            hw[2 * v] = x.x;
-            hw[2 * v + 1] = x.y;
+    for (int k = 0; k < kImg; ++k)
+#pragma unroll
+      for (int v = 0; v < WPR; ++v) hw[k][v] = 0;
+    for (int i = 0; i < nrows; ++i) {
+      unsigned any = 0;
+#pragma unroll
+      for (int k = 0; k < kImg; ++k) any |= alive[k];
+      if (__ballot_sync(0xffffffffu, any != 0) == 0) break;
+      const int r = ord[i];
+      const unsigned rm = rmask[r];
+      unsigned use[kImg], uor = 0;
+#pragma unroll
+      for (int k = 0; k < kImg; ++k) {
+        use[k] = alive[k] & rm;
+        uor |= use[k];
+        if (kCount) pair_rows += __popc(use[k]);
+      }
+      const unsigned wuse = __reduce_or_sync(0xffffffffu, uor);  // needles any lane still needs
+#pragma unroll
+      for (int k = 0; k < kImg; ++k) {
+        if (use[k]) {
+          const int *src = hgrp + k * kGroupWords + r * (WPR * 32);
+#pragma unroll
+          for (int v = 0; v < WPR / CW; ++v) {
+            if constexpr (CW == 4) {
+              const int4 x = *reinterpret_cast<const int4 *>(src + v * 32 * CW);
+              hw[k][4 * v] = x.x;
+              hw[k][4 * v + 1] = x.y;
+              hw[k][4 * v + 2] = x.z;
+              hw[k][4 * v + 3] = x.w;
+            } else {
+              const int2 x = *reinterpret_cast<const int2 *>(src + v * 32 * CW);
+              hw[k][2 * v] = x.x;
+              hw[k][2 * v + 1] = x.y;
+            }
           }
         }
       }
 #pragma unroll
       for (int q = 0; q < kTQ; ++q) {
         if (((wuse >> q) & 1u) == 0) continue;
-        if (kCount) lane_slots += 1;  // one warp-wide needle-row iteration (32 lane slots)
+        if (kCount) lane_slots += kImg;  // kImg warp-wide needle-row iterations (32 lane slots each)
         // row sum of m (a - b)^2 = sum a^2 + sum (m b)^2 - 2 sum a b, with sum a^2 precomputed;
-        // kChains independent accumulator chains per term
-        constexpr int kChains = WPR >= 8 ? 4 : 2;
-        int sbb[kChains], sab[kChains];
+        // the (m b)^2 chain starts from the running value, and one chain per term and image
+        // suffices because the warps of the block hide the dp4a latency
+        const int w = wrow[q][r];
+        int sb[kImg], sa[kImg];
 #pragma unroll
-        for (int u = 0; u < kChains; ++u) sbb[u] = sab[u] = 0;
+        for (int k = 0; k < kImg; ++k) {
+          sb[k] = acc[k][q] + w;
+          sa[k] = 0;
+        }
         const int4 *amq = reinterpret_cast<const int4 *>(&am[q][r * WPR]);
 #pragma unroll
         for (int v = 0; v < WPR; v += 2) {
           const int4 x = amq[v >> 1];  // (a_v, m_v, a_v+1, m_v+1)
-          const int b0 = hw[v], b1 = hw[v + 1];
-          const int bm0 = b0 & x.y, bm1 = b1 & x.w;
-          const int u = (v >> 1) % (kChains / 2) * 2;
-          sbb[u] = __dp4a(bm0, bm0, sbb[u]);
-          sab[u] = __dp4a(x.x, b0, sab[u]);
-          sbb[u + 1] = __dp4a(bm1, bm1, sbb[u + 1]);
-          sab[u + 1] = __dp4a(x.z, b1, sab[u + 1]);
-        }
-        int sb = 0, sa = 0;
 #pragma unroll
-        for (int u = 0; u < kChains; ++u) {
-          sb += sbb[u];
-          sa += sab[u];
+          for (int k = 0; k < kImg; ++k) {
+            const int b0 = hw[k][v], b1 = hw[k][v + 1];
+            const int bm0 = b0 & x.y, bm1 = b1 & x.w;
+            sb[k] = __dp4a(bm0, bm0, sb[k]);
+            sa[k] = __dp4a(x.x, b0, sa[k]);
+            sb[k] = __dp4a(bm1, bm1, sb[k]);
+            sa[k] = __dp4a(x.z, b1, sa[k]);
+          }
         }
-        if ((use >> q) & 1u) {
-          acc[q] += wrow[q][r] + sb - 2 * sa;
-          if (acc[q] > 0) alive &= ~(1u << q);
+#pragma unroll
+        for (int k = 0; k < kImg; ++k) {
+          if ((use[k] >> q) & 1u) {
+            acc[k][q] = sb[k] - 2 * sa[k];
+            if (acc[k][q] > 0) alive[k] &= ~(1u << q);
+          }
         }
       }
     }
@@ -350,9 +377,15 @@ __global__ void __launch_bounds__(kDenseThreads, N <= 64 ? 2 : 1) k_dense(
 #pragma unroll
     for (int q = 0; q < kTQ; ++q) {
       if (!act_s[q]) continue;
-      const bool fin = (alive >> q) & 1u;
-      int c = fin && acc[q] < 0;
-      unsigned long long b = fin ? pack_best(acc[q] + thr_s[q], j) : kNoBest;
+      int c = 0;
+      unsigned long long b = kNoBest;
+#pragma unroll
+      for (int k = 0; k < kImg; ++k) {
+        const bool fin = (alive[k] >> q) & 1u;
+        c += fin && acc[k][q] < 0;
+        const unsigned long long bk = fin ? pack_best(acc[k][q] + thr_s[q], j0 + 32 * k) : kNoBest;
+        b = bk < b ? bk : b;
+      }
 #pragma unroll
       for (int d = 16; d > 0; d >>= 1) c += __shfl_down_sync(0xffffffffu, c, d);
       b = warp_min_u64(b);
@@ -549,12 +582,16 @@ cudaError_t launch_dense(const int8_t *nd, const int8_t *nm, const int *nrs, con
                          const int8_t *hd, const int *hw, int64_t H, const int64_t *dt,
                          const int *nf, int *rank, unsigned long long *best,
                          unsigned long long *counters, cudaStream_t st) {
-  constexpr int kTQ = N <= 64 ? 8 : 4;
+  // 4 needles x 4 haystack images per thread (N <= 64; 122 registers, one block per SM) is the
+  // fastest measured shape: each broadcast needle word serves four images, and the per-row
+  // bookkeeping is shared by 16 (needle, image) pairs
+  constexpr int kTQ = 4;
+  constexpr int kImg = N <= 64 ? 4 : 1;
   const size_t smem = sizeof(int2) * kTQ * (N * N / 4);
-  auto kern = counters ? k_dense<N, kTQ, true> : k_dense<N, kTQ, false>;
+  auto kern = counters ? k_dense<N, kTQ, kImg, true> : k_dense<N, kTQ, kImg, false>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  const int64_t th = (H + kDenseThreads - 1) / kDenseThreads;
+  const int64_t th = (H + kDenseThreads * kImg - 1) / (kDenseThreads * kImg);
   const int64_t tq = (Q + kTQ - 1) / kTQ;
   // bands as long as possible while the grid still gives every SM a few waves of blocks
   int dev = 0, sms = 152;

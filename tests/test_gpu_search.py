@@ -111,6 +111,45 @@ def test_tensor_ragged_tiles(rici, oracle_mod, Q, H):
     check(run(rici, nd, hay, m, mode=3), oracle_mod.crss_search(nd, hay, m))
 
 
+@pytest.mark.parametrize("N", [64, 32, 16])
+def test_dense_bands_and_ragged_tiles(rici, oracle_mod, N):
+    """CUDA-core form over many haystack tiles: bands of several tiles, a ragged last tile whose
+    tail ends inside a thread's image groups, and a partial last needle tile; needles sampled
+    from the first, middle and last needle tiles are checked against the oracle."""
+    Q, H = 3541, 2048 * 10 + 77
+    nd, hay, m = dataset(21, Q, H, N)
+    m[-1] = H - 1  # a true match in the last, ragged haystack group
+    nd[-1] = hay[H - 1]
+    rng = np.random.default_rng(22)
+    free = np.setdiff1d(np.arange(H), m)
+    pick = np.r_[0:4, 1500:1504, Q - 9:Q]
+
+    def stepped(img, rows, h):
+        # raise each listed row from its first non-zero delta on: that delta changes by h, so
+        # the clutter-resistant distance to img grows by h^2 per row
+        out = img.copy()
+        for r in rows:
+            nz = np.flatnonzero(np.diff(img[r].astype(np.int64))) + 1
+            if nz.size:
+                out[r, nz[0]:] += h
+        return out
+
+    # true matches a little off their needles, and closer copies spread over the haystack
+    # (one in the ragged tail), so the ranks are not all zero
+    for i, k in enumerate(pick):
+        hay[m[k]] = stepped(nd[k], range(3), 2)
+        spots = rng.choice(free, size=i % 4, replace=False)
+        if k == Q - 1:
+            spots = np.r_[spots, H - 2]
+        for pos in spots:
+            hay[pos] = stepped(nd[k], [5], 1)
+    got = run(rici, nd, hay, m, mode=1)
+    ref = oracle_mod.crss_search(nd[pick], hay, m[pick])
+    assert ref["rank"].max() >= 3
+    for k in ("true_distance", "rank", "top1"):
+        assert np.array_equal(got[k][pick], ref[k]), k
+
+
 def test_ties_keep_best_rank(rici, oracle_mod):
     nd, hay, m = dataset(4, 50, 500, 32)
     for k in range(0, 50, 3):  # duplicates of true matches elsewhere in the haystack
