@@ -17,7 +17,7 @@
 //                   so partial sums are monotone and a pair stops once it exceeds
 //                   d(i, match_i) (the early exit of Section 4.4, which never changes a rank).
 //                   A block keeps 4 needles in shared memory and sweeps a band of haystack
-//                   tiles (2,048 images each, four per thread at N <= 64), rows heaviest
+//                   tiles (1,024 images each, four per thread at N <= 64), rows heaviest
 //                   first; each broadcast needle word serves all of a thread's images.
 //   k_wide          pairs with a wide side: Listing 1 over the needle's non-zero deltas in
 //                   int64, reading the uint16 images.
@@ -30,7 +30,7 @@
 namespace rici {
 namespace {
 
-constexpr int kDenseThreads = 512;     // threads of a dense block
+constexpr int kDenseThreads = 256;     // threads of a dense block
 constexpr int64_t kBandMax = 8;        // haystack tiles per band of the dense work order
 constexpr int kWideThreads = 256;
 constexpr unsigned long long kNoBest = ~0ull;
@@ -193,7 +193,8 @@ __device__ __forceinline__ unsigned long long warp_min_u64(unsigned long long v)
 // Narrow x narrow pairs.  Block: kTQ needles (deltas + masks in shared memory) x
 // kDenseThreads * kImg haystack images (kImg per thread, in consecutive groups of 32).
 template <int N, int kTQ, int kImg, bool kCount>
-__global__ void __launch_bounds__(kDenseThreads, N * kImg <= 64 ? 2 : 1) k_dense(
+__global__ void __launch_bounds__(kDenseThreads, (N * kImg <= 64 ? 4 : 2) * 256 / kDenseThreads)
+    k_dense(
     const int8_t *__restrict__ ndelta, const int8_t *__restrict__ nmask,
     const int *__restrict__ nrowsq, const int *__restrict__ nwide, int64_t Q,
     const int8_t *__restrict__ hdelta,
@@ -366,10 +367,10 @@ __global__ void __launch_bounds__(kDenseThreads, N * kImg <= 64 ? 2 : 1) k_dense
         }
 #pragma unroll
         for (int k = 0; k < kImg; ++k) {
-          if ((use[k] >> q) & 1u) {
-            acc[k][q] = sb[k] - 2 * sa[k];
-            if (acc[k][q] > 0) alive[k] &= ~(1u << q);
-          }
+          // an image whose pair has exited keeps computing with stale deltas; its value is
+          // never read again, since only pairs still alive are counted
+          acc[k][q] = sb[k] - 2 * sa[k];
+          if (acc[k][q] > 0) alive[k] &= ~(1u << q);
         }
       }
     }
@@ -582,10 +583,10 @@ cudaError_t launch_dense(const int8_t *nd, const int8_t *nm, const int *nrs, con
                          const int8_t *hd, const int *hw, int64_t H, const int64_t *dt,
                          const int *nf, int *rank, unsigned long long *best,
                          unsigned long long *counters, cudaStream_t st) {
-  // 4 needles x 4 haystack images per thread (N <= 64; 122 registers, one block per SM) is the
-  // fastest measured shape: each broadcast needle word serves four images, and the per-row
-  // bookkeeping is shared by 16 (needle, image) pairs
-  constexpr int kTQ = 4;
+  // 4 needles x 4 haystack images per thread (N <= 64; 120 registers, two blocks of 256 threads
+  // per SM) is the fastest measured shape: each broadcast needle word serves four images, and
+  // the per-row bookkeeping is shared by 16 (needle, image) pairs
+  constexpr int kTQ = N <= 64 ? 4 : 2;  // N = 128: 64 KB of needle tile, two blocks per SM
   constexpr int kImg = N <= 64 ? 4 : 1;
   const size_t smem = sizeof(int2) * kTQ * (N * N / 4);
   auto kern = counters ? k_dense<N, kTQ, kImg, true> : k_dense<N, kTQ, kImg, false>;
