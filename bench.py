@@ -84,6 +84,10 @@ def parse():
     ap.add_argument("--cpu-haystack", type=int, default=24000)
     ap.add_argument("--tc-compare", type=int, default=1,
                     help="also time the tensor-core search on the same images (breakdown)")
+    ap.add_argument("--sparse-compare", type=int, default=1,
+                    help="also time the sparse-needle CUDA-core search on the same images")
+    ap.add_argument("--precision-compare", type=int, default=1,
+                    help="also time the three search forms on a precision-form image set sample")
     ap.add_argument("--batched-compare", type=int, default=1,
                     help="also time the batched multi-scene run (CUDA graph) against per-scene calls")
     ap.add_argument("--haystack-limit", type=int, default=0,
@@ -225,6 +229,43 @@ def cpu_baseline(scene, args, steps: int = 1):
               f"over all triangles) and {len(nd)} needles x {len(hay)} haystack images (int64 "
               f"Listing 1) per step, extrapolated to {Vt + V} images and {Vt * V} comparisons")
     return est, threads, sample
+
+
+def precision_form_comparison(p, torch, dev, stream, Q=16384, H=262144, seed=31, steps=3):
+    """The three exact search forms on a sample of the precision-form image set (heavy-tailed
+    RICI-like rows, needles copied before clutter is added to 30 % of the haystack)."""
+    import synth
+
+    nd, hay, m = synth.images.needle_haystack_set_torch(seed, Q, H, N_RES, dev)
+    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
+    out = {"recipe": f"synth.images.needle_haystack_set_torch(seed={seed}), {Q} needles x {H} "
+                     f"haystack images, N = {N_RES}", "comparisons": Q * H}
+    ref = None
+    for name, mode in (("tensor_core", p.SEARCH_TENSOR), ("cuda_core", p.SEARCH_CUDA_CORE),
+                       ("sparse_needle", p.SEARCH_SPARSE)):
+        r = p.crss_search(nd, hay, m, mode=mode)
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r = p.crss_search(nd, hay, m, mode=mode)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        same = None if ref is None else all(bool(torch.equal(r[k], ref[k]))
+                                            for k in ("rank", "true_distance", "top1"))
+        if ref is None:
+            ref = r
+        t = statistics.mean(ts)
+        out[name] = {"ms": t, "comparisons_per_s": Q * H / (t / 1e3),
+                     "same_ranks_as_tensor_core": same}
+    out["status"] = p.sync_status()
+    del nd, hay, m, ref, r, flush
+    torch.cuda.empty_cache()
+    return out
 
 
 def batched_comparison(p, torch, dev, stream, args, n_scenes=24, needles=256, seed=41,
@@ -498,6 +539,36 @@ def main():
         tc = {"ms": statistics.mean(tc_ms), "comparisons_per_s": pairs / (statistics.mean(tc_ms) / 1e3),
               "same_ranks_as_cuda_core": same, "status": st}
 
+    # sparse-needle form of the same search (CUDA cores, the needles' non-zero words only)
+    sp = None
+    if args.sparse_compare:
+        for _ in range(2):
+            p.crss_search(needles, hay, match, mode=p.SEARCH_SPARSE)
+        torch.cuda.synchronize()
+        sp_ms = []
+        for k in range(args.steps):
+            flush.zero_()
+            b0 = torch.cuda.Event(enable_timing=True)
+            b1 = torch.cuda.Event(enable_timing=True)
+            b0.record(stream)
+            rs = p.crss_search(needles, hay, match, mode=p.SEARCH_SPARSE)
+            b1.record(stream)
+            torch.cuda.synchronize()
+            sp_ms.append(b0.elapsed_time(b1))
+        same = all(bool(torch.equal(rs[k2], res[k2])) for k2 in ("rank", "true_distance", "top1"))
+        spc = torch.zeros(4, dtype=torch.int64, device=dev)
+        p.crss_search(needles, hay, match, mode=p.SEARCH_SPARSE, counters=spc)
+        spc = [int(x) for x in spc.cpu()]
+        st = p.sync_status()
+        sp = {"ms": statistics.mean(sp_ms),
+              "comparisons_per_s": pairs / (statistics.mean(sp_ms) / 1e3),
+              "same_ranks_as_cuda_core": same, "status": st,
+              "pair_words": spc[0], "lane_slots": spc[3],
+              "lane_utilisation": spc[0] / spc[3] if spc[3] else None}
+    precision = None
+    if args.precision_compare and rank == 0:
+        precision = precision_form_comparison(p, torch, dev, stream)
+
     batched = batched_small = None
     if args.batched_compare and rank == 0:
         batched = batched_comparison(p, torch, dev, stream, args)
@@ -603,6 +674,17 @@ def main():
         }
         rooflines["search_tensor_core"]["frac"] = (rooflines["search_tensor_core"]["achieved"] /
                                                    rooflines["search_tensor_core"]["peak"])
+    if sp is not None:
+        rooflines["search_sparse"] = {
+            "bound": "alu", "unit": "G int8-MAC/s",
+            "achieved": sp["pair_words"] * 4 * MACS_PER_TERM / (sp["ms"] / 1e3) / 1e9,
+            "peak": rooflines["search"]["peak"],
+            "work": f"{sp['pair_words']} (pair, needle word) evaluations x 4 masked squared "
+                    "differences x 2 int8 multiply-adds",
+            "traffic": None, "peak_kind": rooflines["search"]["peak_kind"],
+        }
+        rooflines["search_sparse"]["frac"] = (rooflines["search_sparse"]["achieved"] /
+                                              rooflines["search_sparse"]["peak"])
     dom = "search" if se_ms >= gen_ms or "generation" not in rooflines else "generation"
     roof = dict(rooflines[dom])
     roof["kernel"] = "k_dense (CUDA-core CRSS)" if dom == "search" else "k_generate"
@@ -631,6 +713,8 @@ def main():
                                 "wide_terms": scnt[2], "lane_slots": scnt[3],
                                 "lane_utilisation": scnt[0] / scnt[3] if scnt[3] else None},
             "search_tensor_core": tc,
+            "search_sparse_needle": sp,
+            "precision_form_sample": precision,
             "batched_run": batched,
             "batched_run_small_scenes": batched_small,
             "tuning": step_tuning,

@@ -65,6 +65,11 @@ extern "C" {
 #define RICI_SEARCH_TENSOR 3    /* exact fp16 tcgen05 GEMM of the expanded distance (N in 8..128,
                                    powers of two); pairs with |delta| > 32 on either side run in
                                    exact int64 on CUDA cores */
+#define RICI_SEARCH_SPARSE 4    /* Listing 1 over each needle's non-zero delta words only (the
+                                   positions where a != 0, Section 3.2), on CUDA cores: words
+                                   heaviest first, early exit after every word; single-scene
+                                   calls with N in {8,16,32,64,128} (other calls take the int64
+                                   kernel); fastest when needles are sparse */
 /* Test hook, OR-ed into RICI_SEARCH_TENSOR: one CTA of the tensor-core kernel withholds its
  * first tile load, so its bounded waits run out (about 2 s), RICI_ERR_TIMEOUT is raised in the
  * status word and the kernel returns; outputs of that call are unspecified. */
@@ -134,11 +139,13 @@ RICI_API int crss_search(const uint16_t *needles, int64_t num_needles, const uin
 
 /* As crss_search with optional device counters (NULL or int64[4]), added to:
  *   [0] (pair, row) evaluations by the packed CUDA-core kernel (each row = N-1 positions;
- *       rows after a pair's early exit are not evaluated),
+ *       rows after a pair's early exit are not evaluated); with RICI_SEARCH_SPARSE,
+ *       (pair, needle word) evaluations (each word = 4 positions of the needle, at least one
+ *       of them non-zero),
  *   [1] pairs evaluated by the int64 kernel (pairs with a delta outside int8),
  *   [2] needle non-zero positions evaluated by the int64 kernel,
- *   [3] lane slots the packed kernel spent on (pair, row) evaluations (32 per warp-wide
- *       needle-row iteration; [0] / [3] is its lane utilisation). */
+ *   [3] lane slots the packed kernel spent on those evaluations (32 per warp-wide iteration;
+ *       [0] / [3] is its lane utilisation). */
 RICI_API int crss_search_ex(const uint16_t *needles, int64_t num_needles,
                             const uint16_t *haystack, int64_t num_haystack, int32_t resolution,
                             const int64_t *true_match, int32_t *out_rank,

@@ -21,6 +21,7 @@ SEARCH_DEFAULT = 0
 SEARCH_CUDA_CORE = 1
 SEARCH_EXACT_SLOW = 2
 SEARCH_TENSOR = 3
+SEARCH_SPARSE = 4
 SEARCH_TEST_WITHHOLD_LOAD = 0x100  # test hook (see include/rici.h)
 
 ERR_INVALID_ARGUMENT = 1

@@ -25,6 +25,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "common.cuh"
 
 namespace rici {
@@ -51,9 +53,18 @@ __device__ __forceinline__ int64_t interleaved_offset(int64_t i, int N, int k) {
   return ((((g * N + r) * (WPR / CW) + v) * 32 + l) * CW + ww) * 4 + (c & 3);
 }
 
-// One warp per image.  interleave: write the deltas in the layout of interleaved_offset (the
-// haystack of the dense kernel) instead of image-major.  row_sq (optional): per row, the sum of
-// the squared (clamped) deltas, [n][N].
+// Byte offset of the delta at flat position k of image i in the word-major layout read by
+// k_sparse: 32 consecutive images form a group, and within a group word w (4 deltas) of the 32
+// images is stored contiguously (128 bytes), so the 32 lanes of a warp reading the same word of
+// their images make one coalesced access whatever the word.
+__device__ __forceinline__ int64_t word_major_offset(int64_t i, int N, int k) {
+  const int64_t g = i >> 5, l = i & 31;
+  return ((g * (N * N / 4) + (k >> 2)) * 32 + l) * 4 + (k & 3);
+}
+
+// One warp per image.  interleave: 0 image-major deltas; 1 the layout of interleaved_offset (the
+// haystack of the dense kernel); 2 the layout of word_major_offset (the haystack of k_sparse).
+// row_sq (optional): per row, the sum of the squared (clamped) deltas, [n][N].
 __global__ void k_encode(const uint16_t *__restrict__ imgs, int64_t n, int N,
                          int8_t *__restrict__ delta, int8_t *__restrict__ mask,
                          int *__restrict__ wide_flag, int *__restrict__ wide_list,
@@ -70,7 +81,10 @@ __global__ void k_encode(const uint16_t *__restrict__ imgs, int64_t n, int N,
       int d = delta_at(img, N, r, c);
       wide |= (d > 127 || d < -127);
       int dc = d > 127 ? 127 : (d < -127 ? -127 : d);
-      delta[interleave ? interleaved_offset(i, N, k) : i * K + k] = (int8_t)dc;
+      const int64_t off = interleave == 1   ? interleaved_offset(i, N, k)
+                          : interleave == 2 ? word_major_offset(i, N, k)
+                                            : i * K + k;
+      delta[off] = (int8_t)dc;
       if (mask) mask[i * K + k] = (int8_t)(d != 0 ? -1 : 0);
     }
     if (row_sq) {
@@ -404,6 +418,183 @@ __global__ void __launch_bounds__(kDenseThreads, (N * kImg <= 64 ? 4 : 2) * 256 
   }
 }
 
+// Sparse-needle form.  Listing 1 only touches positions where the needle's delta is non-zero, so
+// each needle is reduced to the list of its 32-bit words (4 deltas) holding a non-zero delta:
+// entry = (a word, mask word, byte offset of the word in the word-major haystack group,
+// sum of the word's squared deltas).  Each word adds m(a-b)^2 >= 0 over its 4 positions, so the
+// partial sum may be compared with d(i, match_i) after any word; words are listed heaviest
+// first (descending sum a^2, in 64 logarithmic classes) so that pairs pass the threshold sooner.
+// The order decides only when a pair stops, never its result.
+constexpr int kSparseWarps = 8;   // needles per block, one per warp
+constexpr int kSparseImg = 4;     // haystack images per lane
+constexpr int kSparseStep = 2;    // needle words per step over the first kSparseHead words
+constexpr int kSparseHead = 4;
+constexpr int kSparseStepLong = 4;  // needle words per step after them (loads of a step are in
+                                    // flight together)
+constexpr int64_t kSparseBandMax = 64;  // haystack tiles per band of the sparse work order
+
+__device__ __forceinline__ int sparse_class(int wsq) {  // 0 = heaviest
+  const int lg = 31 - __clz(wsq);
+  const int frac = lg >= 2 ? (wsq >> (lg - 2)) & 3 : (wsq << (2 - lg)) & 3;
+  return 63 - (4 * lg + frac);
+}
+
+// One warp per needle: the needle's non-zero words as sparse entries, heaviest class first
+// (order inside a class is arbitrary).  ent: [Q][K/4] int4 slabs; ecount[i] = entries of i.
+__global__ void __launch_bounds__(256) k_sparse_needles(const int8_t *__restrict__ nd,
+                                                        const int8_t *__restrict__ nm, int64_t Q,
+                                                        int N, int4 *__restrict__ ent,
+                                                        int *__restrict__ ecount) {
+  __shared__ int cls_n[8][64];
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+  const int64_t w0 = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+  const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  const int KW = N * N / 4;
+  int *cnt = cls_n[wib];
+  for (int64_t i = w0; i < Q; i += nw) {
+    const int *a32 = reinterpret_cast<const int *>(nd + i * (int64_t)N * N);
+    const int *m32 = reinterpret_cast<const int *>(nm + i * (int64_t)N * N);
+    cnt[lane] = 0;
+    cnt[lane + 32] = 0;
+    __syncwarp();
+    for (int w = lane; w < KW; w += 32) {
+      const int a = a32[w];
+      if (a != 0) atomicAdd(&cnt[sparse_class(__dp4a(a, a, 0))], 1);
+    }
+    __syncwarp();
+    // exclusive scan of the 64 class sizes (two per lane)
+    const int c0 = cnt[2 * lane], c1 = cnt[2 * lane + 1];
+    int incl = c0 + c1;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, d);
+      if (lane >= d) incl += y;
+    }
+    const int total = __shfl_sync(0xffffffffu, incl, 31);
+    __syncwarp();
+    cnt[2 * lane] = incl - c0 - c1;
+    cnt[2 * lane + 1] = incl - c1;
+    __syncwarp();
+    int4 *e = ent + i * (int64_t)KW;
+    for (int w = lane; w < KW; w += 32) {
+      const int a = a32[w];
+      if (a != 0) {
+        const int wsq = __dp4a(a, a, 0);
+        const int pos = atomicAdd(&cnt[sparse_class(wsq)], 1);
+        e[pos] = make_int4(a, m32[w], w * 128, wsq);
+      }
+    }
+    if (lane == 0) ecount[i] = total;
+    __syncwarp();
+  }
+}
+
+// Narrow needles x narrow haystack images over the needles' sparse entries.  Block: kSparseWarps
+// needles (one per warp) sweeping a band of haystack tiles of 32 * kSparseImg images; lane l of a
+// warp holds images j0 + l + 32 k.  Per step the warp reads kSparseStep entries (the same address
+// in every lane) and each lane gathers the entries' words of its images that are still alive
+// (one coalesced 128-byte access per warp and image slot).
+template <bool kCount>
+__global__ void __launch_bounds__(kSparseWarps * 32) k_sparse(
+    const int4 *__restrict__ ent, const int *__restrict__ ecount,
+    const int *__restrict__ nwide, int64_t Q, const int8_t *__restrict__ hword,
+    const int *__restrict__ hwide, int64_t H, int N, const int64_t *__restrict__ dtrue,
+    const int *__restrict__ nflags, int *__restrict__ rank, unsigned long long *__restrict__ best,
+    unsigned long long *__restrict__ counters, int64_t tile0, int64_t tiles_q, int64_t tiles_h,
+    int64_t band_h) {
+  constexpr int kTile = 32 * kSparseImg;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t L = tile0 + blockIdx.x;
+  const int64_t band = L / tiles_q, qt = L - band * tiles_q;
+  const int64_t h0 = band * band_h;
+  const int64_t h1 = tiles_h - h0 < band_h ? tiles_h : h0 + band_h;
+  const int64_t q = qt * kSparseWarps + warp;
+  if (q >= Q || nflags[q] != 0 || nwide[q]) return;  // the whole warp leaves; no block barrier follows
+  const int64_t tq = dtrue[q];
+  const int thr = tq > 0x7fffffffll ? 0x7fffffff : (int)tq;
+  const int KW = N * N / 4;
+  const int ne = ecount[q];
+  const int4 *e = ent + q * (int64_t)KW;
+  const int64_t gbytes = (int64_t)KW * 128;  // one group of 32 images
+  unsigned long long pair_words = 0, lane_slots = 0;
+  for (int64_t ht = h0; ht < h1; ++ht) {
+    const int64_t j0 = ht * kTile + lane;
+    int acc[kSparseImg];  // partial distance minus the needle's true distance (exit once > 0)
+    unsigned alive = 0;
+#pragma unroll
+    for (int k = 0; k < kSparseImg; ++k) {
+      const int64_t j = j0 + 32 * k;
+      acc[k] = -thr;
+      if (j < H && !hwide[j]) alive |= 1u << k;
+    }
+    const int8_t *hb = hword + (j0 >> 5) * gbytes + lane * 4;
+    // steps of S entries from e0 while any image of the warp is alive; returns where it stopped
+    auto steps = [&](auto step_tag, int e0, int e_end) {
+      constexpr int S = decltype(step_tag)::value;
+      for (; e0 < e_end; e0 += S) {
+        if (__ballot_sync(0xffffffffu, alive != 0) == 0) return ne;
+        int4 E[S];
+#pragma unroll
+        for (int u = 0; u < S; ++u)
+          E[u] = e0 + u < ne ? e[e0 + u] : make_int4(0, 0, 0, 0);  // a zero entry adds nothing
+        int b[S][kSparseImg];
+#pragma unroll
+        for (int u = 0; u < S; ++u)
+#pragma unroll
+          for (int k = 0; k < kSparseImg; ++k)
+            b[u][k] = (alive >> k) & 1u
+                          ? *reinterpret_cast<const int *>(hb + k * gbytes + E[u].z)
+                          : 0;
+        if (kCount) {
+          const int n = ne - e0 < S ? ne - e0 : S;
+          pair_words += (unsigned long long)__popc(alive) * n;
+          lane_slots += (unsigned long long)kSparseImg * n;
+        }
+#pragma unroll
+        for (int u = 0; u < S; ++u)
+#pragma unroll
+          for (int k = 0; k < kSparseImg; ++k) {
+            // m (a - b)^2 over the word = sum a^2 + sum (m b)^2 - 2 sum a b
+            const int bm = b[u][k] & E[u].y;
+            const int sq = __dp4a(bm, bm, acc[k] + E[u].w);
+            acc[k] = sq - 2 * __dp4a(E[u].x, b[u][k], 0);
+          }
+#pragma unroll
+        for (int k = 0; k < kSparseImg; ++k)
+          if (acc[k] > 0) alive &= ~(1u << k);  // images that have exited keep stale sums
+      }
+      return e0;
+    };
+    // short steps first (most pairs of sparse needles stop within a word or two), then longer
+    // steps with more loads in flight for the pairs that go on
+    const int e_mid = ne < kSparseHead ? ne : kSparseHead;
+    const int e1 = steps(std::integral_constant<int, kSparseStep>(), 0, e_mid);
+    steps(std::integral_constant<int, kSparseStepLong>(), e1, ne);
+    int c = 0;
+    unsigned long long bb = kNoBest;
+#pragma unroll
+    for (int k = 0; k < kSparseImg; ++k) {
+      const bool fin = (alive >> k) & 1u;
+      c += fin && acc[k] < 0;
+      const unsigned long long bk = fin ? pack_best(acc[k] + thr, j0 + 32 * k) : kNoBest;
+      bb = bk < bb ? bk : bb;
+    }
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) c += __shfl_down_sync(0xffffffffu, c, d);
+    bb = warp_min_u64(bb);
+    if (lane == 0) {
+      if (c) atomicAdd(&rank[q], c);
+      if (bb != kNoBest) atomicMin(&best[q], bb);
+    }
+  }
+  if (kCount) {  // lane_slots is the same in every lane of the warp
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) pair_words += __shfl_down_sync(0xffffffffu, pair_words, d);
+    if (lane == 0 && pair_words) atomicAdd(counters, pair_words);
+    if (lane == 0 && lane_slots) atomicAdd(counters + 3, 32ull * lane_slots);
+  }
+}
+
 // Pairs with a wide side, exact int64 (launch-wide indices; haystack restricted to the needle's
 // scene).  List mode:
 //   pass 0: needles = wide needle list, haystack = the needle's whole scene.
@@ -611,6 +802,30 @@ cudaError_t launch_dense(const int8_t *nd, const int8_t *nm, const int *nrs, con
   return cudaGetLastError();
 }
 
+cudaError_t launch_sparse(const int4 *ent, const int *ecount, const int *nw, int64_t Q,
+                          const int8_t *hd, const int *hw, int64_t H, int N, const int64_t *dt,
+                          const int *nf, int *rank, unsigned long long *best,
+                          unsigned long long *counters, cudaStream_t st) {
+  auto kern = counters ? k_sparse<true> : k_sparse<false>;
+  const int64_t th = (H + 32 * kSparseImg - 1) / (32 * kSparseImg);
+  const int64_t tq = (Q + kSparseWarps - 1) / kSparseWarps;
+  int dev = 0, sms = 152;
+  if (cudaGetDevice(&dev) == cudaSuccess)
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  // bands as long as possible while the grid still gives every SM several waves of blocks
+  int64_t band_h = th * tq / ((int64_t)sms * 8 * 4);
+  band_h = band_h < 1 ? 1 : (band_h > kSparseBandMax ? kSparseBandMax : band_h);
+  const int64_t total = (th + band_h - 1) / band_h * tq;
+  constexpr int64_t kMaxGrid = 0x7fffffffll;
+  for (int64_t t0 = 0; t0 < total; t0 += kMaxGrid) {
+    const int64_t n = total - t0 < kMaxGrid ? total - t0 : kMaxGrid;
+    kern<<<(unsigned)n, kSparseWarps * 32, 0, st>>>(ent, ecount, nw, Q, hd, hw, H, N, dt, nf, rank,
+                                                    best, counters, t0, tq, th, band_h);
+    count_launches(1);
+  }
+  return cudaGetLastError();
+}
+
 }  // namespace
 
 void search_tiles(int64_t Q, int64_t H, int32_t *tiles_m, int32_t *tiles_n) {
@@ -624,13 +839,14 @@ int64_t search_batch_workspace_bytes(int num_scenes, int64_t Q, int64_t H, int N
   const bool tensor =
       (mode == RICI_SEARCH_TENSOR || mode == RICI_SEARCH_DEFAULT) && tc_supported(N);
   const bool packed = !tensor && mode != RICI_SEARCH_EXACT_SLOW && dense_supported(N);
+  const bool sparse = packed && mode == RICI_SEARCH_SPARSE;
   Carver c(nullptr);
   c.take<SearchScene>(num_scenes);
   c.take<int>(Q);                        // scene of each needle
   c.take<int>(H);                        // scene of each haystack image
-  c.take<int8_t>(packed ? Q * K : 0);    // needle deltas (packed CUDA-core form only)
+  c.take<int8_t>(packed ? Q * K : 0);    // needle deltas (packed CUDA-core forms only)
   c.take<int8_t>(packed ? Q * K : 0);    // needle masks
-  c.take<int>(packed ? Q * N : 0);       // needle row sums of squared deltas
+  c.take<int>(packed && !sparse ? Q * N : 0);  // needle row sums of squared deltas (dense)
   c.take<int8_t>(packed ? (H + 31) / 32 * 32 * K : 0);  // haystack deltas (groups of 32)
   c.take<int>(Q);                        // needle wide flags
   c.take<int>(H);                        // haystack wide flags
@@ -642,6 +858,8 @@ int64_t search_batch_workspace_bytes(int num_scenes, int64_t Q, int64_t H, int N
   c.take<unsigned long long>(Q);         // packed best (distance, index)
   c.take<int64_t>(Q);                    // true distances
   c.take<int>(Q);                        // ranks
+  c.take<int4>(sparse ? Q * (K / 4) : 0);  // sparse needle entries (one slab per needle)
+  c.take<int>(sparse ? Q : 0);           // sparse entries per needle
   c.take<char>(tensor ? tc_workspace_bytes(Q, H, N) : 0);
   return c.off + 256;
 }
@@ -660,16 +878,18 @@ cudaError_t launch_search_batch(const SearchScene *scenes, const SearchBatch &b,
   const int mode = b.mode & 0xff;
   const bool tensor =
       (mode == RICI_SEARCH_TENSOR || mode == RICI_SEARCH_DEFAULT) && tc_supported(N);
-  const bool dense = !tensor && mode != RICI_SEARCH_EXACT_SLOW && dense_supported(N) &&
-                     b.num_scenes == 1;
+  const bool packed = !tensor && mode != RICI_SEARCH_EXACT_SLOW && dense_supported(N) &&
+                      b.num_scenes == 1;
+  const bool sparse = packed && mode == RICI_SEARCH_SPARSE;
+  const bool dense = packed && !sparse;
   Carver c(ws);
   SearchScene *tab = c.take<SearchScene>(b.num_scenes);
   int *qscene = c.take<int>(Q);
   int *hscene = c.take<int>(H);
-  int8_t *nd = c.take<int8_t>(dense ? Q * K : 0);
-  int8_t *nm = c.take<int8_t>(dense ? Q * K : 0);
+  int8_t *nd = c.take<int8_t>(packed ? Q * K : 0);
+  int8_t *nm = c.take<int8_t>(packed ? Q * K : 0);
   int *nrs = c.take<int>(dense ? Q * N : 0);
-  int8_t *hd = c.take<int8_t>(dense ? (H + 31) / 32 * 32 * K : 0);
+  int8_t *hd = c.take<int8_t>(packed ? (H + 31) / 32 * 32 * K : 0);
   int *nwide = c.take<int>(Q);
   int *hwide = c.take<int>(H);
   int *wn_list = c.take<int>(Q);
@@ -680,6 +900,8 @@ cudaError_t launch_search_batch(const SearchScene *scenes, const SearchBatch &b,
   unsigned long long *best = c.take<unsigned long long>(Q);
   int64_t *dt = c.take<int64_t>(Q);
   int *rank = c.take<int>(Q);
+  int4 *sent = c.take<int4>(sparse ? Q * (K / 4) : 0);
+  int *scount = c.take<int>(sparse ? Q : 0);
   char *tc_ws = tensor ? c.take<char>(tc_workspace_bytes(Q, H, N)) : nullptr;
 
   cudaError_t e;
@@ -736,6 +958,19 @@ cudaError_t launch_search_batch(const SearchScene *scenes, const SearchBatch &b,
       default: e = launch_dense<128>(nd, nm, nrs, nwide, Q, hd, hwide, H, dt, nflags, rank, best, cnt, st); break;
     }
     if (e != cudaSuccess) return e;
+    wide(0);
+    wide(1);
+  } else if (sparse) {
+    const SearchScene &s0 = scenes[0];
+    k_encode<<<blocks_for(Q), 32 * wpb, 0, st>>>(s0.needles, Q, N, nd, nm, nwide, wn_list,
+                                                 counts + 0, 0, nullptr);
+    k_encode<<<blocks_for(H), 32 * wpb, 0, st>>>(s0.haystack, H, N, hd, nullptr, hwide, wh_list,
+                                                 counts + 1, 2, nullptr);
+    k_sparse_needles<<<blocks_for(Q), 32 * wpb, 0, st>>>(nd, nm, Q, N, sent, scount);
+    count_launches(3);
+    if ((e = launch_sparse(sent, scount, nwide, Q, hd, hwide, H, N, dt, nflags, rank, best, cnt,
+                           st)) != cudaSuccess)
+      return e;
     wide(0);
     wide(1);
   } else {

@@ -57,6 +57,9 @@ def test_version_and_workspace_queries(lib):
     assert lib.rici_generate_workspace_size(10, 100, 5, 64) > 100 * 64
     assert lib.rici_generate_workspace_size(10, -1, 5, 64) == -1
     assert lib.crss_search_workspace_size(10, 100, 64, 0) >= 110 * 64 * 64
+    # sparse-needle form: a slab of N^2/4 16-byte entries per needle on top of the packed deltas
+    assert (lib.crss_search_workspace_size(10, 100, 64, 4)
+            >= lib.crss_search_workspace_size(10, 100, 64, 1) - 10 * 64 * 4 + 10 * 64 * 64 * 4)
     assert lib.crss_search_workspace_size(10, 100, 0, 0) == -1
 
 
@@ -83,6 +86,10 @@ def test_search_rejects_bad_arguments_on_host(lib):
     assert lib.crss_search(dummy, 1, dummy, 0, 64, None, dummy, None, None, None, 0, None, 0, None) == 1
     assert lib.crss_search(dummy, 1, dummy, 1, 1, None, dummy, None, None, None, 0, None, 0, None) == 1
     assert lib.crss_search(dummy, 1, dummy, 1, 64, None, dummy, None, None, None, 9, None, 0, None) == 1
+    assert lib.crss_search(dummy, 1, dummy, 1, 64, None, dummy, None, None, None, 5, None, 0, None) == 1
+    # the withheld-load hook is a tensor-core test bit: rejected with the sparse-needle form
+    assert lib.crss_search(dummy, 1, dummy, 1, 64, None, dummy, None, None, None, 0x104, None, 0,
+                           None) == 1
     # the withheld-load test bit is only accepted with the tensor-core form; other high bits never
     assert lib.crss_search(dummy, 1, dummy, 1, 64, None, dummy, None, None, None, 0x101, None, 0,
                            None) == 1

@@ -53,7 +53,7 @@ def dataset(seed, Q, H, N, **kw):
     return synth.images.needle_haystack_set(rng, Q, H, N, **kw)
 
 
-@pytest.mark.parametrize("mode", [0, 1, 2, 3])
+@pytest.mark.parametrize("mode", [0, 1, 2, 3, 4])
 def test_small_set_all_outputs(rici, oracle_mod, mode):
     nd, hay, m = dataset(1, 64, 700, 64)
     ref = oracle_mod.crss_search(nd, hay, m, return_distances=True)
@@ -62,14 +62,14 @@ def test_small_set_all_outputs(rici, oracle_mod, mode):
 
 
 @pytest.mark.parametrize("N", [8, 16, 32, 128, 12, 2])
-@pytest.mark.parametrize("mode", [1, 3])
+@pytest.mark.parametrize("mode", [1, 3, 4])
 def test_resolutions(rici, oracle_mod, N, mode):
     nd, hay, m = dataset(2, 40, 300, N)
     ref = oracle_mod.crss_search(nd, hay, m)
     check(run(rici, nd, hay, m, mode=mode), ref)
 
 
-@pytest.mark.parametrize("mode", [1, 3])
+@pytest.mark.parametrize("mode", [1, 3, 4])
 def test_heavy_tails_and_extremes(rici, oracle_mod, mode):
     rng = np.random.default_rng(3)
     nd, hay, m = synth.images.needle_haystack_set(rng, 60, 900, 64, tail_image_fraction=0.3,
@@ -112,8 +112,9 @@ def test_tensor_ragged_tiles(rici, oracle_mod, Q, H):
 
 
 @pytest.mark.parametrize("N", [64, 32, 16])
-def test_dense_bands_and_ragged_tiles(rici, oracle_mod, N):
-    """CUDA-core form over many haystack tiles: bands of several tiles, a ragged last tile whose
+@pytest.mark.parametrize("mode", [1, 4])
+def test_dense_bands_and_ragged_tiles(rici, oracle_mod, N, mode):
+    """CUDA-core forms (dense and sparse-needle) over many haystack tiles: bands of several tiles, a ragged last tile whose
     tail ends inside a thread's image groups, and a partial last needle tile; needles sampled
     from the first, middle and last needle tiles are checked against the oracle."""
     Q, H = 3541, 2048 * 10 + 77
@@ -143,19 +144,37 @@ def test_dense_bands_and_ragged_tiles(rici, oracle_mod, N):
             spots = np.r_[spots, H - 2]
         for pos in spots:
             hay[pos] = stepped(nd[k], [5], 1)
-    got = run(rici, nd, hay, m, mode=1)
+    got = run(rici, nd, hay, m, mode=mode)
     ref = oracle_mod.crss_search(nd[pick], hay, m[pick])
     assert ref["rank"].max() >= 3
     for k in ("true_distance", "rank", "top1"):
         assert np.array_equal(got[k][pick], ref[k]), k
 
 
-def test_ties_keep_best_rank(rici, oracle_mod):
+@pytest.mark.parametrize("mode", [1, 4])
+def test_degenerate_needles(rici, oracle_mod, mode):
+    """Needles with no non-zero delta (constant rows: distance 0 to everything), one non-zero
+    delta, a non-zero delta only in the last column, and one full row of +-127 deltas."""
+    N = 64
+    nd, hay, m = dataset(9, 12, 600, N)
+    nd[0] = 7                       # constant image: no entries
+    nd[1] = 0
+    nd[1, 30, 40:] = 3              # a single non-zero delta
+    nd[2] = 0
+    nd[2, 63, 63] = 5               # only the last column of the last row
+    nd[3, 5] = np.where(np.arange(N) % 2 == 0, 0, 127).astype(np.uint16)  # +-127 on a whole row
+    hay[m[0]] = 0
+    ref = oracle_mod.crss_search(nd, hay, m, return_distances=True)
+    check(run(rici, nd, hay, m, mode=mode, dist=True), ref, dist=True)
+
+
+@pytest.mark.parametrize("mode", [0, 1, 4])
+def test_ties_keep_best_rank(rici, oracle_mod, mode):
     nd, hay, m = dataset(4, 50, 500, 32)
     for k in range(0, 50, 3):  # duplicates of true matches elsewhere in the haystack
         hay[(m[k] + 17) % 500] = hay[m[k]]
     ref = oracle_mod.crss_search(nd, hay, m)
-    check(run(rici, nd, hay, m), ref)
+    check(run(rici, nd, hay, m, mode=mode), ref)
 
 
 def test_identity_match_default(rici, oracle_mod):
@@ -200,7 +219,7 @@ def test_single_haystack_and_single_needle(rici, oracle_mod):
     check(run(rici, nd, hay, m), oracle_mod.crss_search(nd, hay, m))
 
 
-@pytest.mark.parametrize("mode", [1, 3])
+@pytest.mark.parametrize("mode", [1, 3, 4])
 def test_clutter_scale_search_sampled_needles(rici, oracle_mod, mode):
     """Full benchmark size: 10,242 needles x 114,892 haystack images, N = 64."""
     Q, H = 10242, 114892

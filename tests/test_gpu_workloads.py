@@ -52,11 +52,13 @@ def test_precision_form_full_size(rici, oracle_mod):
     rng = np.random.default_rng(3)
     sample = np.unique(np.concatenate([[0, Q - 1], rng.integers(0, Q, 14)]))
     sampled_parity(oracle_mod, nd, hay, m, got, sample)
-    # every needle: the CUDA-core form gives the same ranks, distances and top-1
-    rc = rici.crss_search(nd, hay, m, mode=rici.SEARCH_CUDA_CORE)
-    assert rici.sync_status() == 0
-    for k in ("true_distance", "rank", "top1"):
-        assert torch.equal(rc[k], r[k]), k
+    # every needle: both CUDA-core forms give the same ranks, distances and top-1
+    for mode in (rici.SEARCH_CUDA_CORE, rici.SEARCH_SPARSE):
+        rc = rici.crss_search(nd, hay, m, mode=mode)
+        assert rici.sync_status() == 0
+        for k in ("true_distance", "rank", "top1"):
+            assert torch.equal(rc[k], r[k]), (mode, k)
+        del rc
     del nd, hay
 
 
