@@ -88,6 +88,8 @@ def parse():
                     help="also time the sparse-needle CUDA-core search on the same images")
     ap.add_argument("--precision-compare", type=int, default=1,
                     help="also time the three search forms on a precision-form image set sample")
+    ap.add_argument("--clutterbox-compare", type=int, default=1,
+                    help="also time a synthetic clutterbox experiment (Section 4.1) on the GPU path")
     ap.add_argument("--batched-compare", type=int, default=1,
                     help="also time the batched multi-scene run (CUDA graph) against per-scene calls")
     ap.add_argument("--haystack-limit", type=int, default=0,
@@ -264,6 +266,45 @@ def precision_form_comparison(p, torch, dev, stream, Q=16384, H=262144, seed=31,
                      "same_ranks_as_tensor_core": same}
     out["status"] = p.sync_status()
     del nd, hay, m, ref, r, flush
+    torch.cuda.empty_cache()
+    return out
+
+
+def clutterbox_experiment(p, torch, dev, stream, runs=4, n=10, seed=51, tri_lo=2000,
+                          tri_hi=20000, steps=3):
+    """Synthetic clutterbox runs (Section 4.1): every level of every run imaged by one batched
+    generation call and searched by one batched search call (tensor-core form)."""
+    import synth
+    from paper_2007_02306_gb300 import clutterbox
+
+    levels = [synth.scenes.clutterbox(seed + r, n=n, box_side=3.0, tri_lo=tri_lo, tri_hi=tri_hi)
+              for r in range(runs)]
+    prep = clutterbox.prepare(levels, dev)
+    clutterbox.run_prepared(prep, R_SUP, N_RES)
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        res = clutterbox.run_prepared(prep, R_SUP, N_RES)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    st = p.sync_status()
+    h = clutterbox.histograms(prep, res)
+    images = sum(sum(sz) for sz in prep["sizes"])
+    comparisons = sum(sz[0] * sum(sz) for sz in prep["sizes"])
+    t = statistics.mean(ts)
+    out = {"runs": runs, "levels": n, "box_side": 3.0, "images": images,
+           "comparisons": comparisons, "ms": t, "runs_per_s": runs / (t / 1e3),
+           "images_per_s": images / (t / 1e3),
+           "rank0_fraction_by_level": [float(x) for x in
+                                       np.mean([r["rank0_fraction"] for r in h], axis=0)],
+           "status": st,
+           "recipe": f"synth.scenes.clutterbox(seed={seed}..{seed + runs - 1}, n={n}, box side 3, "
+                     f"objects of {tri_lo}-{tri_hi} triangles), N = {N_RES}, R = {R_SUP}"}
+    del prep, res
     torch.cuda.empty_cache()
     return out
 
@@ -569,6 +610,10 @@ def main():
     if args.precision_compare and rank == 0:
         precision = precision_form_comparison(p, torch, dev, stream)
 
+    cbox = None
+    if args.clutterbox_compare and rank == 0:
+        cbox = clutterbox_experiment(p, torch, dev, stream)
+
     batched = batched_small = None
     if args.batched_compare and rank == 0:
         batched = batched_comparison(p, torch, dev, stream, args)
@@ -715,6 +760,7 @@ def main():
             "search_tensor_core": tc,
             "search_sparse_needle": sp,
             "precision_form_sample": precision,
+            "clutterbox": cbox,
             "batched_run": batched,
             "batched_run_small_scenes": batched_small,
             "tuning": step_tuning,

@@ -14,6 +14,10 @@ collection itself is replaced by displaced icospheres and tori):
   5k-50k triangles (log-uniform), centres uniform in [-1,1]^3 (box side 2).
 * ``large_scene``   a subdivision-7 target plus meshes up to ~5M triangles in total (about 40
   meshes), box side 4 with every bounding sphere inside the box (centres in [-1,1]^3).
+* ``clutterbox``    the levels of one clutterbox run (Section 4.1): n objects drawn from the
+  synthetic collection, each fitted to the unit sphere and placed in a box of side s with its
+  bounding sphere inside the box; level k is the combined mesh of the first k objects, the
+  reference object first.
 """
 from __future__ import annotations
 
@@ -140,3 +144,27 @@ def scene_batch(seed: int, n_scenes: int, tri_lo: int = 2000, tri_hi: int = 200_
             total += m.num_triangles
         out.append(assemble(placed))
     return out
+
+
+def clutterbox(seed: int, n: int = 10, box_side: float = 3.0, tri_lo: int = 2000,
+               tri_hi: int = 50_000):
+    """Levels 1..n of one clutterbox run (Section 4.1, steps 1-6a).
+
+    The n objects come from the synthetic collection (displaced icospheres and tori of
+    tri_lo..tri_hi triangles, log-uniform), each fitted to the unit sphere (step 3).  The
+    reference object is one of them chosen at random (step 4) and is placed first; then the
+    others follow in random order (step 6).  Every object gets a uniform random orientation and
+    a centre uniform in [-(s/2 - 1), s/2 - 1]^3, so its bounding sphere lies inside the box
+    (step 6a).  Returns [level_1, ..., level_n]; level k is the combined mesh of the first k
+    placed objects, so the reference object's vertex i is vertex i of every level, and level 1
+    (the reference alone) gives the reference descriptor set.
+    """
+    if box_side < 2.0:
+        raise ValueError("a unit sphere fits in the clutterbox only when its side is at least 2")
+    rng = np.random.Generator(np.random.PCG64(seed))
+    objects = [_clutter_mesh(rng, tri_lo, tri_hi) for _ in range(n)]
+    ref = int(rng.integers(n))
+    order = [ref] + [int(i) for i in rng.permutation([i for i in range(n) if i != ref])]
+    half = box_side / 2.0 - 1.0
+    placed = [_place(rng, objects[i], half) for i in order]
+    return [assemble(placed[:k]) for k in range(1, n + 1)]
