@@ -61,6 +61,8 @@ def _load():
             lib.oracle_project_fp32.restype = None
             lib.oracle_rici_fp32.argtypes = [P, P, i64, P, i64, P, i64, f32, i32, P, i32, P]
             lib.oracle_rici_fp32.restype = ctypes.c_int
+            lib.oracle_clutter_areas.argtypes = [P, P, i64, P, i64, P, i64, f32, i64, P, P, i32]
+            lib.oracle_clutter_areas.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -169,3 +171,33 @@ def crss_search(needles, haystack, true_match=None, return_distances: bool = Fal
     if dist is not None:
         out["distances"] = dist
     return out
+
+
+def clutter_areas(vertices, normals, triangles, origins, support_radius: float,
+                  object_vertices: int, num_threads: int = 0):
+    """Eq. clutter inputs per oriented point, FP64 brute force over every triangle: the surface
+    area inside the support volume (radius R around the normal axis, |beta| <= R/2) and the part
+    of it on triangles whose first vertex index is below ``object_vertices``.
+
+    Returns (area_all, area_object), float64 [O] each."""
+    lib = _load()
+    v = np.ascontiguousarray(vertices, dtype=np.float32).reshape(-1, 3)
+    n = np.ascontiguousarray(normals, dtype=np.float32).reshape(-1, 3)
+    t = np.ascontiguousarray(triangles, dtype=np.int32).reshape(-1, 3)
+    o = np.ascontiguousarray(origins, dtype=np.int32).reshape(-1)
+    a_all = np.zeros(o.shape[0], np.float64)
+    a_obj = np.zeros(o.shape[0], np.float64)
+    rc = lib.oracle_clutter_areas(_ptr(v), _ptr(n), v.shape[0], _ptr(t), t.shape[0], _ptr(o),
+                                  o.shape[0], float(support_radius), int(object_vertices),
+                                  _ptr(a_all), _ptr(a_obj), int(num_threads))
+    if rc != 0:
+        raise ValueError(f"oracle_clutter_areas failed with status {rc}")
+    return a_all, a_obj
+
+
+def clutter(vertices, normals, triangles, origins, support_radius: float, object_vertices: int):
+    """Eq. clutter per oriented point: (A_all - A_object) / A_all (NaN where A_all = 0)."""
+    a_all, a_obj = clutter_areas(vertices, normals, triangles, origins, support_radius,
+                                 object_vertices)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        return np.where(a_all > 0, (a_all - a_obj) / np.where(a_all > 0, a_all, 1.0), np.nan)

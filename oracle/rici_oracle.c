@@ -30,6 +30,9 @@
  *  - oracle_crss_search: per needle, the distance to its true match, the rank of that match
  *    (number of haystack images strictly closer, the tie rule of Section 4.2) and the top-1
  *    haystack index (smallest index among the minimal distances).
+ *  - oracle_clutter_areas: per oriented point, the surface area inside its support volume and
+ *    the part of it that belongs to the object of interest (Eq. clutter), brute force over
+ *    every triangle (see the comment above that function).
  *
  * Readings where the paper is silent or garbled (each listed with its reason in the design
  * notes):
@@ -475,4 +478,185 @@ void oracle_project_fp64(const float *points, int64_t n, const float *spin_verte
     double Nax, Nay, Nbx, Nbz;
     frame_coefficients(spin_normal[0], spin_normal[1], spin_normal[2], &Nax, &Nay, &Nbx, &Nbz);
     for (int64_t k = 0; k < n; k++) project_point(points + 3 * k, S, Nax, Nay, Nbx, Nbz, out + 3 * k);
+}
+
+/* ------------------------------------------------------------------------------------------
+ * Eq. clutter (Section 4.1): clutter = (A_all - A_object) / A_all, where A_all is the surface
+ * area of every triangle inside the support volume of an oriented point and A_object the part
+ * of it that belongs to the object of interest.
+ *
+ * Support volume: the cylinder swept by the image, radius R around the axis through the
+ * oriented point along its normal and heights |beta| <= R/2 (readings (1) and (2) above), in
+ * the frame of Eqs. relativeLocation..secondRotation: Tx^2 + Ty^2 <= R^2, |Tz| <= R/2.  The
+ * projection is a rotation, so areas measured in the frame are areas in the scene.
+ *
+ * Per triangle: clip it to the slab |Tz| <= R/2 (a convex polygon of up to 5 vertices); the
+ * part of that polygon inside the infinite cylinder is the part whose projection onto the
+ * (Tx, Ty) plane lies in the disk of radius R, so its area is area(projection n disk) / |cos|,
+ * with cos the z component of the triangle's unit normal.  Reading: planes with |cos| < 1e-7
+ * are treated as parallel to the axis; their part inside is the polygon between the two lines
+ * where the plane meets the cylinder, at the plane's mean distance from the axis.
+ * A triangle belongs to the object when its first vertex index is below object_vertices (the
+ * object's vertices come first).
+ * ---------------------------------------------------------------------------------------- */
+
+/* Signed area of the intersection of the triangle (0, a, b) with the disk |p| <= R: the segment
+ * a-b is cut where it crosses the circle; pieces inside the disk add the triangle (0, p, q),
+ * pieces outside add the circular sector between p and q. */
+static double sector_piece_area(double ax, double ay, double bx, double by, double R) {
+    const double dx = bx - ax, dy = by - ay;
+    const double A = dx * dx + dy * dy;
+    double ts[4];
+    int nt = 0;
+    ts[nt++] = 0.0;
+    if (A > 0.0) {
+        const double B = ax * dx + ay * dy;
+        const double C = ax * ax + ay * ay - R * R;
+        const double disc = B * B - A * C;
+        if (disc > 0.0) {
+            const double s = sqrt(disc);
+            const double t1 = (-B - s) / A, t2 = (-B + s) / A;
+            if (t1 > 0.0 && t1 < 1.0) ts[nt++] = t1;
+            if (t2 > 0.0 && t2 < 1.0) ts[nt++] = t2;
+        }
+    }
+    ts[nt++] = 1.0;
+    double sum = 0.0;
+    for (int i = 0; i + 1 < nt; i++) {
+        const double px = ax + ts[i] * dx, py = ay + ts[i] * dy;
+        const double qx = ax + ts[i + 1] * dx, qy = ay + ts[i + 1] * dy;
+        const double tm = 0.5 * (ts[i] + ts[i + 1]);
+        const double mx = ax + tm * dx, my = ay + tm * dy;
+        const double cross = px * qy - py * qx;
+        if (mx * mx + my * my <= R * R)
+            sum += 0.5 * cross;
+        else
+            sum += 0.5 * R * R * atan2(cross, px * qx + py * qy);
+    }
+    return sum;
+}
+
+/* Sutherland-Hodgman step: keep the part of the polygon where sign * z <= lim. */
+static int clip_height(const double (*in)[3], int n, double (*out)[3], double sign, double lim) {
+    int m = 0;
+    for (int i = 0; i < n; i++) {
+        const double *P = in[i], *Q = in[(i + 1) % n];
+        const double dp = lim - sign * P[2], dq = lim - sign * Q[2];
+        if (dp >= 0.0) {
+            out[m][0] = P[0];
+            out[m][1] = P[1];
+            out[m][2] = P[2];
+            m++;
+        }
+        if ((dp >= 0.0) != (dq >= 0.0)) {
+            const double t = dp / (dp - dq);
+            for (int k = 0; k < 3; k++) out[m][k] = P[k] + t * (Q[k] - P[k]);
+            m++;
+        }
+    }
+    return m;
+}
+
+/* Keep the part of a 2D polygon where sign * h <= lim. */
+static int clip_line(const double (*in)[2], int n, double (*out)[2], double sign, double lim) {
+    int m = 0;
+    for (int i = 0; i < n; i++) {
+        const double *P = in[i], *Q = in[(i + 1) % n];
+        const double dp = lim - sign * P[0], dq = lim - sign * Q[0];
+        if (dp >= 0.0) {
+            out[m][0] = P[0];
+            out[m][1] = P[1];
+            m++;
+        }
+        if ((dp >= 0.0) != (dq >= 0.0)) {
+            const double t = dp / (dp - dq);
+            out[m][0] = P[0] + t * (Q[0] - P[0]);
+            out[m][1] = P[1] + t * (Q[1] - P[1]);
+            m++;
+        }
+    }
+    return m;
+}
+
+/* Area of the part of one projected triangle inside the support volume. */
+static double support_area(const double T[3][3], double R) {
+    const double ux = T[1][0] - T[0][0], uy = T[1][1] - T[0][1], uz = T[1][2] - T[0][2];
+    const double vx = T[2][0] - T[0][0], vy = T[2][1] - T[0][1], vz = T[2][2] - T[0][2];
+    const double nx = uy * vz - uz * vy, ny = uz * vx - ux * vz, nz = ux * vy - uy * vx;
+    const double nn = sqrt(nx * nx + ny * ny + nz * nz);
+    if (nn == 0.0) return 0.0;
+    double a[6][3], b[6][3];
+    for (int k = 0; k < 3; k++)
+        for (int j = 0; j < 3; j++) a[k][j] = T[k][j];
+    int m = clip_height((const double(*)[3])a, 3, b, 1.0, 0.5 * R);
+    if (m < 3) return 0.0;
+    m = clip_height((const double(*)[3])b, m, a, -1.0, 0.5 * R);
+    if (m < 3) return 0.0;
+    const double cz = fabs(nz) / nn;
+    if (cz >= 1e-7) {
+        double s = 0.0;
+        for (int i = 0; i < m; i++)
+            s += sector_piece_area(a[i][0], a[i][1], a[(i + 1) % m][0], a[(i + 1) % m][1], R);
+        return fabs(s) / cz;
+    }
+    /* plane parallel to the axis: in-plane coordinates (h along the horizontal direction of
+     * the plane, z), inside where |h| <= sqrt(R^2 - p^2), p = distance of the plane from the
+     * axis */
+    const double hxy = sqrt(nx * nx + ny * ny);
+    const double ex = -ny / hxy, ey = nx / hxy, wx = nx / hxy, wy = ny / hxy;
+    double p = 0.0;
+    for (int i = 0; i < m; i++) p += a[i][0] * wx + a[i][1] * wy;
+    p /= (double)m;
+    if (fabs(p) >= R) return 0.0;
+    const double c = sqrt(R * R - p * p);
+    double h[7][2], g[7][2];
+    for (int i = 0; i < m; i++) {
+        h[i][0] = a[i][0] * ex + a[i][1] * ey;
+        h[i][1] = a[i][2];
+    }
+    int k = clip_line((const double(*)[2])h, m, g, 1.0, c);
+    if (k < 3) return 0.0;
+    k = clip_line((const double(*)[2])g, k, h, -1.0, c);
+    if (k < 3) return 0.0;
+    double s = 0.0;
+    for (int i = 0; i < k; i++) s += h[i][0] * h[(i + 1) % k][1] - h[(i + 1) % k][0] * h[i][1];
+    return 0.5 * fabs(s);
+}
+
+/* Per origin: area_all[o] = A_all, area_object[o] = A_object (brute force over all triangles). */
+int oracle_clutter_areas(const float *vertices, const float *normals, int64_t num_vertices,
+                         const int32_t *triangles, int64_t num_triangles, const int32_t *origins,
+                         int64_t num_origins, float support_radius, int64_t object_vertices,
+                         double *area_all, double *area_object, int32_t num_threads) {
+    if (!(support_radius > 0.0f) || num_vertices < 0 || num_triangles < 0 || num_origins < 0)
+        return ORACLE_BAD_ARGUMENT;
+    for (int64_t t = 0; t < 3 * num_triangles; t++)
+        if (triangles[t] < 0 || triangles[t] >= num_vertices) return ORACLE_BAD_INDEX;
+    for (int64_t o = 0; o < num_origins; o++)
+        if (origins[o] < 0 || origins[o] >= num_vertices) return ORACLE_BAD_INDEX;
+    const double R = (double)support_radius;
+#ifdef _OPENMP
+    if (num_threads > 0) omp_set_num_threads(num_threads);
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+    for (int64_t o = 0; o < num_origins; o++) {
+        const int32_t sv = origins[o];
+        const double S[3] = {vertices[3 * sv], vertices[3 * sv + 1], vertices[3 * sv + 2]};
+        double Nax, Nay, Nbx, Nbz;
+        frame_coefficients(normals[3 * sv], normals[3 * sv + 1], normals[3 * sv + 2], &Nax, &Nay,
+                           &Nbx, &Nbz);
+        double all = 0.0, obj = 0.0;
+        for (int64_t t = 0; t < num_triangles; t++) {
+            double T[3][3];
+            for (int k = 0; k < 3; k++)
+                project_point(vertices + 3 * (int64_t)triangles[3 * t + k], S, Nax, Nay, Nbx, Nbz,
+                              T[k]);
+            const double a = support_area((const double(*)[3])T, R);
+            all += a;
+            if (triangles[3 * t] < object_vertices) obj += a;
+        }
+        area_all[o] = all;
+        area_object[o] = obj;
+    }
+    return ORACLE_OK;
 }
