@@ -204,6 +204,33 @@ RICI_API int crss_search_batch(const RiciSearchScene *scenes, int32_t num_scenes
                                int64_t workspace_bytes, void *stream);
 
 /*
+ * rici_clutter — the clutter measure of Eq. clutter (Section 4.1) per oriented point:
+ * clutter = (A_all - A_object) / A_all, with A_all the surface area of the mesh inside the
+ * oriented point's support volume and A_object the part of it on the object of interest.
+ *
+ *   vertices, normals, triangles, origins, support_radius  as for rici_generate.  The support
+ *              volume is the cylinder of the image: radius R around the axis through the
+ *              oriented point along its normal, heights |beta| <= R/2 along that axis.
+ *   object_vertices  a triangle belongs to the object of interest when its first vertex index
+ *              is below this count (the object's vertices come first, as in a clutterbox
+ *              level); 0 counts no triangle, num_vertices every triangle.
+ *   out_area_all, out_area_object  [num_origins] float64 device arrays (caller-owned): A_all
+ *              and A_object, each the sum over triangles of the exact area of the triangle's
+ *              part inside the volume (FP64 closed form: slab clip, then the projection's area
+ *              within the disk over the cosine of the plane's tilt; planes within 1e-7 of
+ *              parallel to the axis are cut by the two lines where they meet the cylinder).
+ * Workspace: rici_clutter_workspace_size bytes, or NULL to use the library's own.
+ * Errors: as rici_generate (NaN outputs for an oriented point with a bad index or a
+ * non-finite coordinate).
+ */
+RICI_API int64_t rici_clutter_workspace_size(int64_t num_triangles);
+RICI_API int rici_clutter(const float *vertices, const float *normals, int64_t num_vertices,
+                          const int32_t *triangles, int64_t num_triangles, const int32_t *origins,
+                          int64_t num_origins, float support_radius, int64_t object_vertices,
+                          double *out_area_all, double *out_area_object, void *workspace,
+                          int64_t workspace_bytes, void *stream);
+
+/*
  * rici_generate_noalloc — rici_generate for callers that must not allocate device memory.
  * (An addition of this library; the paper has no counterpart.)
  *

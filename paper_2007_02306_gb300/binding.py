@@ -105,6 +105,10 @@ def load_library(path: str | None = None):
         lib.rici_last_error_string.restype = ctypes.c_char_p
         lib.rici_kernel_launches.argtypes = []
         lib.rici_kernel_launches.restype = i64
+        lib.rici_clutter_workspace_size.argtypes = [i64]
+        lib.rici_clutter_workspace_size.restype = i64
+        lib.rici_clutter.argtypes = [P, P, i64, P, i64, P, i64, f32, i64, P, P, P, i64, P]
+        lib.rici_clutter.restype = ctypes.c_int
         lib.rici_project_fp32.argtypes = [P, i64, P, P, P, P]
         lib.rici_project_fp32.restype = ctypes.c_int
         lib.rici_set_tuning.argtypes = [P]
@@ -196,6 +200,32 @@ def rici_generate(vertices, normals, triangles, origins, support_radius: float, 
                                     o.numel(), float(support_radius), N, _ptr(out), int(mode),
                                     _ptr(counters), _ptr(ws), ws.numel(), _stream_handle(stream)))
     return out
+
+
+def clutter_areas(vertices, normals, triangles, origins, support_radius: float,
+                  object_vertices: int, *, stream=None):
+    """Eq. clutter inputs per oriented point: float64 [O] tensors (A_all, A_object), the surface
+    area inside the support volume and its part on triangles whose first vertex index is below
+    ``object_vertices`` (clutter = (A_all - A_object) / A_all)."""
+    lib = load_library()
+    v = _need(vertices, torch.float32, "vertices", (3,))
+    n = _need(normals, torch.float32, "normals", (3,))
+    t = _need(triangles, torch.int32, "triangles", (3,))
+    o = _need(origins, torch.int32, "origins")
+    if n.shape != v.shape:
+        raise ValueError("normals must have the same shape as vertices")
+    a_all = torch.empty(o.numel(), dtype=torch.float64, device=v.device)
+    a_obj = torch.empty(o.numel(), dtype=torch.float64, device=v.device)
+    nb = lib.rici_clutter_workspace_size(t.shape[0])
+    if nb < 0:
+        raise ValueError("invalid sizes")
+    ws = workspace(v.device, nb)
+    with torch.cuda.device(v.device):
+        _check(lib.rici_clutter(_ptr(v), _ptr(n), v.shape[0], _ptr(t), t.shape[0], _ptr(o),
+                                o.numel(), float(support_radius), int(object_vertices),
+                                _ptr(a_all), _ptr(a_obj), _ptr(ws), ws.numel(),
+                                _stream_handle(stream)))
+    return a_all, a_obj
 
 
 def crss_search(needles, haystack, true_match=None, *, mode: int = SEARCH_DEFAULT,

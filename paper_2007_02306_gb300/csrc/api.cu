@@ -254,6 +254,50 @@ int rici_generate_ex(const float *vertices, const float *normals, int64_t num_ve
   return RICI_OK;
 }
 
+int64_t rici_clutter_workspace_size(int64_t num_triangles) {
+  if (num_triangles < 0) return -1;
+  return generate_workspace_bytes(num_triangles);
+}
+
+int rici_clutter(const float *vertices, const float *normals, int64_t num_vertices,
+                 const int32_t *triangles, int64_t num_triangles, const int32_t *origins,
+                 int64_t num_origins, float support_radius, int64_t object_vertices,
+                 double *out_area_all, double *out_area_object, void *workspace,
+                 int64_t workspace_bytes, void *stream) {
+  t_last_error.clear();
+  // the generation checks, with the resolution of a valid call and a stand-in output pointer
+  int rc = check_generate_args(vertices, normals, num_vertices, triangles, num_triangles,
+                               origins, num_origins, support_radius, 1,
+                               reinterpret_cast<const uint16_t *>(out_area_all));
+  if (rc) return rc;
+  if (num_origins > 0 && !out_area_object)
+    return fail(RICI_ERR_INVALID_ARGUMENT, "null out_area_object");
+  if (object_vertices < 0) return fail(RICI_ERR_INVALID_ARGUMENT, "negative object_vertices");
+  if (num_origins == 0) return RICI_OK;
+  DeviceState *d = nullptr;
+  if ((rc = device_state(&d))) return rc;
+  void *ws = nullptr;
+  if ((rc = resolve_workspace(d, workspace, workspace_bytes,
+                              generate_workspace_bytes(num_triangles), &ws)))
+    return rc;
+  ClutterArgs a;
+  a.vertices = vertices;
+  a.normals = normals;
+  a.num_vertices = num_vertices;
+  a.triangles = triangles;
+  a.num_triangles = num_triangles;
+  a.origins = origins;
+  a.num_origins = num_origins;
+  a.support_radius = support_radius;
+  a.object_vertices = object_vertices;
+  a.out_area_all = out_area_all;
+  a.out_area_object = out_area_object;
+  a.status = d->status;
+  cudaError_t e = launch_clutter(a, ws, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "rici_clutter launch");
+  return RICI_OK;
+}
+
 int rici_generate(const float *vertices, const float *normals, int64_t num_vertices,
                   const int32_t *triangles, int64_t num_triangles, const int32_t *origins,
                   int64_t num_origins, float support_radius, int32_t resolution,

@@ -30,6 +30,25 @@ int64_t generate_workspace_bytes(int64_t num_triangles);
 // Enqueue generation on `stream` using `ws` (>= generate_workspace_bytes, 256-aligned).
 cudaError_t launch_generate(const GenerateArgs &a, void *ws, cudaStream_t stream);
 
+// Clutter measure (Eq. clutter): per oriented point, the surface area inside its support volume
+// and the part of it on the object's triangles (first vertex index < object_vertices), FP64.
+struct ClutterArgs {
+  const float *vertices;
+  const float *normals;
+  int64_t num_vertices;
+  const int32_t *triangles;
+  int64_t num_triangles;
+  const int32_t *origins;
+  int64_t num_origins;
+  float support_radius;
+  int64_t object_vertices;
+  double *out_area_all;
+  double *out_area_object;
+  int *status;  // device status word
+};
+// Enqueue the clutter measure on `stream` using `ws` (>= generate_workspace_bytes).
+cudaError_t launch_clutter(const ClutterArgs &a, void *ws, cudaStream_t stream);
+
 // One scene of a multi-scene generation launch (entry of the device scene table).
 struct GenScene {
   const float *V;

@@ -555,6 +555,73 @@ __device__ __forceinline__ void add_intervals(int *row, int N, int lo, int hi, i
   }
 }
 
+// Candidate ranges of the grid cells around an oriented point, for every thread of the block:
+// the (2 nhalf + 1)^3 cells around the spin vertex's cell (cell edge > reach / nhalf).  A
+// triangle binned in a cell (by its bounding-sphere centre, radius <= r_big) can reach the
+// support volume only if the cell's box lies within `reach` of the spin vertex and the box's
+// bounding sphere lies within r_big of the support cylinder (axis along the normal); other
+// cells are skipped, and cells that hash to an already listed bucket are listed once.  On
+// return entry i <= nneigh (the last one is the scene's big list) holds the candidate range
+// [buckets[i], bdup[i]) (empty for skipped entries).  Ends with a block barrier.
+__device__ __forceinline__ void neighbour_ranges(const KArgs &a, int64_t bucket_off,
+                                                 uint32_t nbuckets, float Sx, float Sy, float Sz,
+                                                 float nxf, float nyf, float nzf, int *buckets,
+                                                 int *bdup, int tid, int nthreads) {
+  const int nw_ = 2 * a.nhalf + 1, nneigh = nw_ * nw_ * nw_;
+  float ux = 0.0f, uy = 0.0f, uz = 1.0f;  // axis direction (identity rule for a zero normal)
+  {
+    const float n2 = nxf * nxf + nyf * nyf + nzf * nzf;
+    if (n2 > 1e-30f) {
+      const float inv = rsqrtf(n2);
+      ux = nxf * inv;
+      uy = nyf * inv;
+      uz = nzf * inv;
+    }
+  }
+  for (int cidx = tid; cidx < nneigh; cidx += nthreads) {
+    const int ix = cell_coord(Sx, a.inv_cell) + cidx % nw_ - a.nhalf;
+    const int iy = cell_coord(Sy, a.inv_cell) + (cidx / nw_) % nw_ - a.nhalf;
+    const int iz = cell_coord(Sz, a.inv_cell) + cidx / (nw_ * nw_) - a.nhalf;
+    const float c = a.cell;
+    const float gx = fmaxf(fmaxf((float)ix * c - Sx, Sx - (float)(ix + 1) * c), 0.0f);
+    const float gy = fmaxf(fmaxf((float)iy * c - Sy, Sy - (float)(iy + 1) * c), 0.0f);
+    const float gz = fmaxf(fmaxf((float)iz * c - Sz, Sz - (float)(iz + 1) * c), 0.0f);
+    // box centre relative to the spin vertex, its axial and radial distances to the axis
+    const float hb = 0.8660254f * c * 1.001f + 1e-3f * c;  // half diagonal (+ cell rounding)
+    const float cx = ((float)ix + 0.5f) * c - Sx, cy = ((float)iy + 0.5f) * c - Sy,
+                cz = ((float)iz + 0.5f) * c - Sz;
+    const float ax = fabsf(cx * ux + cy * uy + cz * uz);
+    const float rad2 = cx * cx + cy * cy + cz * cz - ax * ax;
+    const float marg = hb + a.r_big + 1e-3f * a.reach + 1e-5f * (fabsf(cx) + fabsf(cy) + fabsf(cz));
+    const float rl = a.alpha_cull + marg;
+    const bool near = gx * gx + gy * gy + gz * gz <= a.reach * a.reach &&
+                      ax <= a.beta_cull + marg && rad2 <= rl * rl;
+    buckets[cidx] = near ? (int)(bucket_off + cell_hash(ix, iy, iz, nbuckets - 1)) : -1;
+  }
+  if (tid == 0) buckets[nneigh] = (int)(bucket_off + nbuckets);  // the scene's big list
+  __syncthreads();
+  for (int cidx = tid; cidx < nneigh; cidx += nthreads) {
+    const int b = buckets[cidx];
+    bool dup = b < 0;
+    for (int k = 0; k < cidx && !dup; ++k) dup = buckets[k] == b;
+    bdup[cidx] = dup ? 1 : 0;
+  }
+  if (tid == 0) bdup[nneigh] = 0;
+  __syncthreads();
+  // candidate range of every listed bucket, fetched once per block
+  for (int cidx = tid; cidx <= nneigh; cidx += nthreads) {
+    int beg = 0, end = 0;
+    if (!bdup[cidx]) {
+      const int b = buckets[cidx];
+      beg = a.starts[b];
+      end = a.starts[b + 1];
+    }
+    buckets[cidx] = beg;
+    bdup[cidx] = end;
+  }
+  __syncthreads();
+}
+
 template <int NW>
 __global__ void __launch_bounds__(NW * 32, NW == 4 ? 7 : 3) k_generate(KArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -621,64 +688,9 @@ __global__ void __launch_bounds__(NW * 32, NW == 4 ? 7 : 3) k_generate(KArgs a) 
     s.fr[2] = Sz;
     frame_fp64(nxf, nyf, nzf, s.fr + 3);
   }
-  // neighbourhood: the (2 nhalf + 1)^3 cells around the spin vertex's cell (cell edge > reach /
-  // nhalf).  A triangle binned in a cell (by its bounding-sphere centre, radius <= r_big) can
-  // reach the support volume only if the cell's box lies within `reach` of the spin vertex and
-  // the box's bounding sphere lies within r_big of the support cylinder (axis along the normal);
-  // other cells are skipped, and cells that hash to an already listed bucket are listed once.
-  const int nw_ = 2 * a.nhalf + 1, nneigh = nw_ * nw_ * nw_;
-  float ux = 0.0f, uy = 0.0f, uz = 1.0f;  // axis direction (identity rule for a zero normal)
-  {
-    const float n2 = nxf * nxf + nyf * nyf + nzf * nzf;
-    if (n2 > 1e-30f) {
-      const float inv = rsqrtf(n2);
-      ux = nxf * inv;
-      uy = nyf * inv;
-      uz = nzf * inv;
-    }
-  }
-  for (int cidx = tid; cidx < nneigh; cidx += NW * 32) {
-    const int ix = cell_coord(Sx, a.inv_cell) + cidx % nw_ - a.nhalf;
-    const int iy = cell_coord(Sy, a.inv_cell) + (cidx / nw_) % nw_ - a.nhalf;
-    const int iz = cell_coord(Sz, a.inv_cell) + cidx / (nw_ * nw_) - a.nhalf;
-    const float c = a.cell;
-    const float gx = fmaxf(fmaxf((float)ix * c - Sx, Sx - (float)(ix + 1) * c), 0.0f);
-    const float gy = fmaxf(fmaxf((float)iy * c - Sy, Sy - (float)(iy + 1) * c), 0.0f);
-    const float gz = fmaxf(fmaxf((float)iz * c - Sz, Sz - (float)(iz + 1) * c), 0.0f);
-    // box centre relative to the spin vertex, its axial and radial distances to the axis
-    const float hb = 0.8660254f * c * 1.001f + 1e-3f * c;  // half diagonal (+ cell rounding)
-    const float cx = ((float)ix + 0.5f) * c - Sx, cy = ((float)iy + 0.5f) * c - Sy,
-                cz = ((float)iz + 0.5f) * c - Sz;
-    const float ax = fabsf(cx * ux + cy * uy + cz * uz);
-    const float rad2 = cx * cx + cy * cy + cz * cz - ax * ax;
-    const float marg = hb + a.r_big + 1e-3f * a.reach + 1e-5f * (fabsf(cx) + fabsf(cy) + fabsf(cz));
-    const float rl = a.alpha_cull + marg;
-    const bool near = gx * gx + gy * gy + gz * gz <= a.reach * a.reach &&
-                      ax <= a.beta_cull + marg && rad2 <= rl * rl;
-    s.buckets[cidx] = near ? (int)(bucket_off + cell_hash(ix, iy, iz, nbuckets - 1)) : -1;
-  }
-  if (tid == 0) s.buckets[nneigh] = (int)(bucket_off + nbuckets);  // the scene's big list
-  __syncthreads();
-  for (int cidx = tid; cidx < nneigh; cidx += NW * 32) {
-    const int b = s.buckets[cidx];
-    bool dup = b < 0;
-    for (int k = 0; k < cidx && !dup; ++k) dup = s.buckets[k] == b;
-    s.bdup[cidx] = dup ? 1 : 0;
-  }
-  if (tid == 0) s.bdup[nneigh] = 0;
-  __syncthreads();
-  // candidate range of every listed bucket, fetched once per block
-  for (int cidx = tid; cidx <= nneigh; cidx += NW * 32) {
-    int beg = 0, end = 0;
-    if (!s.bdup[cidx]) {
-      const int b = s.buckets[cidx];
-      beg = a.starts[b];
-      end = a.starts[b + 1];
-    }
-    s.buckets[cidx] = beg;
-    s.bdup[cidx] = end;
-  }
-  __syncthreads();
+  const int nneigh = (2 * a.nhalf + 1) * (2 * a.nhalf + 1) * (2 * a.nhalf + 1);
+  neighbour_ranges(a, bucket_off, nbuckets, Sx, Sy, Sz, nxf, nyf, nzf, s.buckets, s.bdup, tid,
+                   NW * 32);
 
   const float fax = __double2float_rn(s.fr[3]), fay = __double2float_rn(s.fr[4]);
   const float fbx = __double2float_rn(s.fr[5]), fbz = __double2float_rn(s.fr[6]);
@@ -985,6 +997,262 @@ cudaError_t launch_k_generate(const KArgs &k, int64_t total_origins, cudaStream_
   return cudaGetLastError();
 }
 
+// ------------------------------------------------------------------ clutter measure
+// Eq. clutter (Section 4.1): clutter = (A_all - A_object) / A_all with A_all the surface area
+// inside the support volume of an oriented point and A_object the part on the object of
+// interest.  The support volume is the image's cylinder: Tx^2 + Ty^2 <= R^2, |Tz| <= R/2 in the
+// frame of Eqs. relativeLocation..secondRotation (a rotation, so frame areas are scene areas).
+
+// Signed area of the triangle (0, p, q) that lies inside the disk |x| <= R (R2 = R^2), in the
+// (Tx, Ty) plane.  The segment p-q is inside the disk for t in [t1, t2] (roots of
+// |p + t (q - p)|^2 = R^2) and outside elsewhere; clipped to [0, 1] this gives three pieces: an
+// outer piece adds the circular sector it subtends, the inner one the triangle with the origin.
+__device__ double disk_wedge(double px, double py, double qx, double qy, double R2) {
+  const double dx = qx - px, dy = qy - py;
+  const double A = dx * dx + dy * dy;
+  double ta = 1.0, tb = 1.0;  // no crossing: the whole segment is outside
+  if (A > 0.0) {
+    const double B = px * dx + py * dy, C = px * px + py * py - R2;
+    const double disc = B * B - A * C;
+    if (disc > 0.0) {
+      const double sq = sqrt(disc);
+      ta = fmin(fmax((-B - sq) / A, 0.0), 1.0);
+      tb = fmin(fmax((-B + sq) / A, 0.0), 1.0);
+    }
+  }
+  const double ax = px + ta * dx, ay = py + ta * dy, bx = px + tb * dx, by = py + tb * dy;
+  // an outer piece never spans opposite directions (the segment between them would cross the
+  // disk), so a zero cross product means an empty sector; this also keeps a zero-length piece
+  // at the origin, whose dot product may be -0, from reading as an angle of pi
+  const double c0 = px * ay - py * ax, c1 = bx * qy - by * qx;
+  const double s0 = c0 == 0.0 ? 0.0 : atan2(c0, px * ax + py * ay);  // sector p .. P(ta)
+  const double s1 = c1 == 0.0 ? 0.0 : atan2(c1, bx * qx + by * qy);  // sector P(tb) .. q
+  return 0.5 * R2 * (s0 + s1) + 0.5 * (ax * by - ay * bx);
+}
+
+// Area of the part of one projected triangle inside the support volume: clip it to the slab
+// |Tz| <= R/2, then area(projection onto (Tx, Ty) within the disk) / |cos|, cos the z component
+// of the unit normal.  Planes with |cos| < 1e-7 count as parallel to the axis: the polygon is cut
+// by the two lines where the plane, at its mean distance p from the axis, meets the cylinder
+// (|h| <= sqrt(R^2 - p^2), h the horizontal in-plane coordinate).
+__device__ double support_area64(const double T[3][3], double R) {
+  const double ux = T[1][0] - T[0][0], uy = T[1][1] - T[0][1], uz = T[1][2] - T[0][2];
+  const double vx = T[2][0] - T[0][0], vy = T[2][1] - T[0][1], vz = T[2][2] - T[0][2];
+  const double nx = uy * vz - uz * vy, ny = uz * vx - ux * vz, nz = ux * vy - uy * vx;
+  const double nn = sqrt(nx * nx + ny * ny + nz * nz);
+  if (nn == 0.0) return 0.0;
+  const double H = 0.5 * R;
+  // slab clip (z <= H, then -z <= H), at most 5 vertices
+  double P[5][3], Q[5][3];
+  int m = 0;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const int j = i == 2 ? 0 : i + 1;
+    const double di = H - T[i][2], dj = H - T[j][2];
+    if (di >= 0.0) {
+      P[m][0] = T[i][0]; P[m][1] = T[i][1]; P[m][2] = T[i][2];
+      ++m;
+    }
+    if ((di >= 0.0) != (dj >= 0.0)) {
+      const double f = di / (di - dj);
+      P[m][0] = T[i][0] + f * (T[j][0] - T[i][0]);
+      P[m][1] = T[i][1] + f * (T[j][1] - T[i][1]);
+      P[m][2] = T[i][2] + f * (T[j][2] - T[i][2]);
+      ++m;
+    }
+  }
+  if (m < 3) return 0.0;
+  int k = 0;
+  for (int i = 0; i < m; ++i) {
+    const int j = i + 1 == m ? 0 : i + 1;
+    const double di = H + P[i][2], dj = H + P[j][2];
+    if (di >= 0.0) {
+      Q[k][0] = P[i][0]; Q[k][1] = P[i][1]; Q[k][2] = P[i][2];
+      ++k;
+    }
+    if ((di >= 0.0) != (dj >= 0.0)) {
+      const double f = di / (di - dj);
+      Q[k][0] = P[i][0] + f * (P[j][0] - P[i][0]);
+      Q[k][1] = P[i][1] + f * (P[j][1] - P[i][1]);
+      Q[k][2] = P[i][2] + f * (P[j][2] - P[i][2]);
+      ++k;
+    }
+  }
+  if (k < 3) return 0.0;
+  const double cz = fabs(nz) / nn;
+  if (cz >= 1e-7) {
+    double a = 0.0;
+    for (int i = 0; i < k; ++i) {
+      const int j = i + 1 == k ? 0 : i + 1;
+      a += disk_wedge(Q[i][0], Q[i][1], Q[j][0], Q[j][1], R * R);
+    }
+    return fabs(a) / cz;
+  }
+  // plane parallel to the axis: in-plane coordinates (h, z), h along (-ny, nx) / |n_xy|
+  const double hxy = sqrt(nx * nx + ny * ny);
+  const double ex = -ny / hxy, ey = nx / hxy;
+  double p = 0.0;
+  for (int i = 0; i < k; ++i) p += (Q[i][0] * nx + Q[i][1] * ny) / hxy;
+  p /= (double)k;
+  if (fabs(p) >= R) return 0.0;
+  const double c = sqrt(R * R - p * p);
+  // area of the polygon's part with |h| <= c: shoelace over the polygon clipped to the band
+  double G[7][2], E[7][2];
+  for (int i = 0; i < k; ++i) {
+    G[i][0] = Q[i][0] * ex + Q[i][1] * ey;
+    G[i][1] = Q[i][2];
+  }
+  int g = k;
+#pragma unroll
+  for (int side = 0; side < 2; ++side) {
+    const double sg = side == 0 ? 1.0 : -1.0;
+    int e = 0;
+    for (int i = 0; i < g; ++i) {
+      const int j = i + 1 == g ? 0 : i + 1;
+      const double di = c - sg * G[i][0], dj = c - sg * G[j][0];
+      if (di >= 0.0) {
+        E[e][0] = G[i][0]; E[e][1] = G[i][1];
+        ++e;
+      }
+      if ((di >= 0.0) != (dj >= 0.0)) {
+        const double f = di / (di - dj);
+        E[e][0] = G[i][0] + f * (G[j][0] - G[i][0]);
+        E[e][1] = G[i][1] + f * (G[j][1] - G[i][1]);
+        ++e;
+      }
+    }
+    for (int i = 0; i < e; ++i) {
+      G[i][0] = E[i][0];
+      G[i][1] = E[i][1];
+    }
+    g = e;
+  }
+  if (g < 3) return 0.0;
+  double a = 0.0;
+  for (int i = 0; i < g; ++i) {
+    const int j = i + 1 == g ? 0 : i + 1;
+    a += G[i][0] * G[j][1] - G[j][0] * G[i][1];
+  }
+  return 0.5 * fabs(a);
+}
+
+constexpr int kClutterWarps = 4;
+constexpr int kClutterMaxCells = 7 * 7 * 7 + 1;  // neighbourhoods of nhalf <= 3, + the big list
+
+// One block per oriented point: the candidates of the neighbouring cells pass the same
+// sphere-against-cylinder pretest as generation (limits of the full cylinder), queue per warp,
+// and are evaluated 32 at a time in FP64, one per lane.  A triangle belongs to the object when
+// its first vertex index is below object_vertices.
+__global__ void __launch_bounds__(kClutterWarps * 32) k_clutter(KArgs a, int64_t object_vertices,
+                                                               double *__restrict__ out_all,
+                                                               double *__restrict__ out_obj) {
+  __shared__ int buckets[kClutterMaxCells], bdup[kClutterMaxCells];
+  __shared__ double fr[7];
+  __shared__ int wq[kClutterWarps][64];
+  __shared__ double part[kClutterWarps][2];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t og = a.origin_base + blockIdx.x;
+  const GenScene &sc = a.tab[scene_of_origin(a.tab, a.num_scenes, og)];
+  const int vid = sc.origins[og - sc.origin_off];
+  if (vid < 0 || vid >= sc.nv) {
+    if (tid == 0) {
+      set_status(a.status, RICI_ERR_INDEX_OUT_OF_RANGE);
+      out_all[og] = out_obj[og] = nan("");
+    }
+    return;
+  }
+  const float Sx = sc.V[3 * (int64_t)vid], Sy = sc.V[3 * (int64_t)vid + 1],
+              Sz = sc.V[3 * (int64_t)vid + 2];
+  const float nxf = sc.Nrm[3 * (int64_t)vid], nyf = sc.Nrm[3 * (int64_t)vid + 1],
+              nzf = sc.Nrm[3 * (int64_t)vid + 2];
+  if (!(isfinite(Sx) && isfinite(Sy) && isfinite(Sz) && isfinite(nxf) && isfinite(nyf) &&
+        isfinite(nzf))) {
+    if (tid == 0) {
+      set_status(a.status, RICI_ERR_NONFINITE_INPUT);
+      out_all[og] = out_obj[og] = nan("");
+    }
+    return;
+  }
+  if (tid == 0) {
+    fr[0] = Sx;
+    fr[1] = Sy;
+    fr[2] = Sz;
+    frame_fp64(nxf, nyf, nzf, fr + 3);
+  }
+  neighbour_ranges(a, sc.bucket_off, sc.nbuckets, Sx, Sy, Sz, nxf, nyf, nzf, buckets, bdup, tid,
+                   kClutterWarps * 32);
+  const float fax = __double2float_rn(fr[3]), fay = __double2float_rn(fr[4]);
+  const float fbx = __double2float_rn(fr[5]), fbz = __double2float_rn(fr[6]);
+  const float wx = fbx * fax, wy = fbx * fay, wz = fbz;  // central axis in world coordinates
+  const double R = a.R;
+  double acc_all = 0.0, acc_obj = 0.0;
+  int qn = 0;  // warp-uniform queue length
+  auto process = [&](int cnt) {
+    if (lane < cnt) {
+      const int64_t r = wq[warp][lane];
+      const float4 r1 = a.rec[4 * r + 1], r2 = a.rec[4 * r + 2], r3 = a.rec[4 * r + 3];
+      double T[3][3];
+      project64(r1.x, r1.y, r1.z, fr, T[0]);
+      project64(r1.w, r2.x, r2.y, fr, T[1]);
+      project64(r2.z, r2.w, r3.x, fr, T[2]);
+      const double ar = support_area64(T, R);
+      acc_all += ar;
+      if (__float_as_int(r3.y) < object_vertices) acc_obj += ar;
+    }
+    __syncwarp();
+  };
+  const int nneigh = (2 * a.nhalf + 1) * (2 * a.nhalf + 1) * (2 * a.nhalf + 1);
+  for (int nb = 0; nb <= nneigh; ++nb) {
+    const int64_t beg = buckets[nb], end = bdup[nb];
+    for (int64_t base = beg + warp * 32; base < end; base += kClutterWarps * 32) {
+      const int64_t t = base + lane;
+      bool pass = false;
+      if (t < end) {
+        const float4 c = a.rec[4 * t];
+        const float dx = c.x - Sx, dy = c.y - Sy, dz = c.z - Sz;
+        const float z = fmaf(wx, dx, fmaf(wy, dy, wz * dz));
+        const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        const float mg = 1e-3f * a.R + 1e-5f * (fabsf(dx) + fabsf(dy) + fabsf(dz));
+        const float al = a.alpha_cull + c.w + mg;
+        pass = fabsf(z) <= a.beta_cull + c.w + mg && d2 - z * z <= al * al;
+      }
+      const unsigned bal = __ballot_sync(0xffffffffu, pass);
+      if (pass) wq[warp][qn + __popc(bal & ((1u << lane) - 1u))] = (int)t;
+      qn += __popc(bal);
+      __syncwarp();
+      if (qn >= 32) {
+        process(32);
+        const int rest = qn - 32;
+        const int moved = lane < rest ? wq[warp][32 + lane] : 0;
+        __syncwarp();
+        if (lane < rest) wq[warp][lane] = moved;
+        qn = rest;
+        __syncwarp();
+      }
+    }
+  }
+  if (qn > 0) process(qn);
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) {
+    acc_all += __shfl_down_sync(0xffffffffu, acc_all, d);
+    acc_obj += __shfl_down_sync(0xffffffffu, acc_obj, d);
+  }
+  if (lane == 0) {
+    part[warp][0] = acc_all;
+    part[warp][1] = acc_obj;
+  }
+  __syncthreads();
+  if (tid == 0) {
+    double sa = 0.0, so = 0.0;
+    for (int w = 0; w < kClutterWarps; ++w) {
+      sa += part[w][0];
+      so += part[w][1];
+    }
+    out_all[og] = sa;
+    out_obj[og] = so;
+  }
+}
+
 }  // namespace
 
 uint32_t generate_bucket_count(int64_t nt) { return bucket_count(nt); }
@@ -1014,13 +1282,14 @@ int64_t generate_workspace_bytes(int64_t num_triangles) {
   return generate_batch_workspace_bytes(1, num_triangles, (int64_t)bucket_count(num_triangles) + 1);
 }
 
-cudaError_t launch_generate_batch(const GenScene *scenes, const GenerateBatch &g, void *ws,
-                                  cudaStream_t st) {
-  const int N = g.N;
-  const int64_t nt = g.total_tris, TB = g.total_buckets;
-  if (g.total_origins == 0) return cudaSuccess;
+// Bins every triangle of the scenes into the hashed grid for support volumes of radius amax and
+// half-height bmax around each oriented point, and fills the grid fields of k (table, records,
+// bucket starts, cell size, reach, pretest limits, neighbourhood width).
+static cudaError_t bin_triangles(const GenScene *scenes, int num_scenes, int64_t nt, int64_t TB,
+                                 double R, double amax, double bmax, void *ws, int *status,
+                                 cudaStream_t st, KArgs &k) {
   Carver c(ws);
-  GenScene *tab = c.take<GenScene>(g.num_scenes);
+  GenScene *tab = c.take<GenScene>(num_scenes);
   int *counts = c.take<int>(TB);
   int *starts = c.take<int>(TB + 1);
   int *partials = c.take<int>(TB / kScanItems + 2);
@@ -1029,18 +1298,15 @@ cudaError_t launch_generate_batch(const GenScene *scenes, const GenerateBatch &g
   float4 *rec = c.take<float4>(4 * nt);
 
   cudaError_t e;
-  for (int s0 = 0; s0 < g.num_scenes; s0 += kFillChunk) {
+  for (int s0 = 0; s0 < num_scenes; s0 += kFillChunk) {
     GenFill f;
-    f.n = g.num_scenes - s0 < kFillChunk ? g.num_scenes - s0 : kFillChunk;
+    f.n = num_scenes - s0 < kFillChunk ? num_scenes - s0 : kFillChunk;
     for (int i = 0; i < f.n; ++i) f.e[i] = scenes[s0 + i];
     k_fill_gen_table<<<1, 256, 0, st>>>(tab + s0, f);
     count_launches(1);
   }
 
-  // support cylinder: alpha <= alpha_{N-1}, |beta| <= beta_{N-1}; enclosing sphere radius
-  const double R = g.R;
-  const double amax = R * (2.0 * N - 1.0) / (2.0 * N);
-  const double bmax = R * (N - 1.0) / (2.0 * N);
+  // enclosing sphere radius of the support cylinder
   const double rho = sqrt(amax * amax + bmax * bmax) * (1.0 + 1.0 / 1024.0) + 1e-3 * R;
   const Tuning tu = current_tuning();
   GridParams gp;
@@ -1057,7 +1323,7 @@ cudaError_t launch_generate_batch(const GenScene *scenes, const GenerateBatch &g
   const int64_t want = (nt + tpb - 1) / tpb;
   const int grid = (int)(want < 152 * 32 ? (want > 0 ? want : 1) : 152 * 32);
   if (nt > 0) {
-    k_tri_bin<<<grid, tpb, 0, st>>>(tab, g.num_scenes, nt, gp, counts, tb, ts, g.status);
+    k_tri_bin<<<grid, tpb, 0, st>>>(tab, num_scenes, nt, gp, counts, tb, ts, status);
     count_launches(1);
   }
   const int nb = (int)((TB + kScanItems - 1) / kScanItems);
@@ -1066,29 +1332,76 @@ cudaError_t launch_generate_batch(const GenScene *scenes, const GenerateBatch &g
   k_scan_final<<<nb, 256, 0, st>>>(counts, TB, partials, starts);
   count_launches(3);
   if (nt > 0) {
-    k_tri_scatter<<<grid, tpb, 0, st>>>(tab, g.num_scenes, nt, tb, ts, starts, rec);
+    k_tri_scatter<<<grid, tpb, 0, st>>>(tab, num_scenes, nt, tb, ts, starts, rec);
     count_launches(1);
   }
 
-  KArgs k;
   k.tab = tab;
-  k.num_scenes = g.num_scenes;
+  k.num_scenes = num_scenes;
   k.rec = rec;
   k.starts = starts;
   k.inv_cell = gp.inv_cell;
   k.cell = (float)cell;
   k.reach = (float)(reach + 1e-3 * cell);  // slack for the rounding of cell coordinates
-  k.R = g.R;
-  k.N = N;
+  k.R = (float)R;
   k.alpha_cull = (float)(amax * (1.0 + 1.0 / 1024.0) + 1e-3 * R);
   k.beta_cull = (float)(bmax * (1.0 + 1.0 / 1024.0) + 1e-3 * R);
-  k.mode = g.mode;
   k.nhalf = tu.gen_cells_per_reach;
   k.r_big = gp.r_big;
+  k.status = status;
+  return cudaSuccess;
+}
+
+cudaError_t launch_generate_batch(const GenScene *scenes, const GenerateBatch &g, void *ws,
+                                  cudaStream_t st) {
+  const int N = g.N;
+  if (g.total_origins == 0) return cudaSuccess;
+  // support cylinder: alpha <= alpha_{N-1}, |beta| <= beta_{N-1}
+  const double R = g.R;
+  const double amax = R * (2.0 * N - 1.0) / (2.0 * N);
+  const double bmax = R * (N - 1.0) / (2.0 * N);
+  KArgs k;
+  cudaError_t e = bin_triangles(scenes, g.num_scenes, g.total_tris, g.total_buckets, R, amax,
+                                bmax, ws, g.status, st, k);
+  if (e != cudaSuccess) return e;
+  k.R = g.R;
+  k.N = N;
+  k.mode = g.mode;
   k.counters = reinterpret_cast<unsigned long long *>(g.counters);
-  k.status = g.status;
+  const Tuning tu = current_tuning();
   return tu.gen_warps == 8 ? launch_k_generate<8>(k, g.total_origins, st)
                            : launch_k_generate<4>(k, g.total_origins, st);
+}
+
+cudaError_t launch_clutter(const ClutterArgs &a, void *ws, cudaStream_t st) {
+  if (a.num_origins == 0) return cudaSuccess;
+  GenScene sc = {};
+  sc.V = a.vertices;
+  sc.Nrm = a.normals;
+  sc.tris = a.triangles;
+  sc.origins = a.origins;
+  sc.nv = a.num_vertices;
+  sc.nt = a.num_triangles;
+  sc.no = a.num_origins;
+  sc.nbuckets = bucket_count(a.num_triangles);
+  // the whole support cylinder: alpha <= R, |beta| <= R/2
+  const double R = a.support_radius;
+  KArgs k;
+  cudaError_t e = bin_triangles(&sc, 1, a.num_triangles, (int64_t)sc.nbuckets + 1, R, R, 0.5 * R,
+                                ws, a.status, st, k);
+  if (e != cudaSuccess) return e;
+  k.N = 0;
+  k.mode = 0;
+  k.counters = nullptr;
+  for (int64_t o0 = 0; o0 < a.num_origins; o0 += 0x7fffffff) {
+    const int64_t cnt = a.num_origins - o0 < 0x7fffffff ? a.num_origins - o0 : 0x7fffffff;
+    KArgs kk = k;
+    kk.origin_base = o0;
+    k_clutter<<<(unsigned)cnt, kClutterWarps * 32, 0, st>>>(kk, a.object_vertices, a.out_area_all,
+                                                             a.out_area_object);
+    count_launches(1);
+  }
+  return cudaGetLastError();
 }
 
 cudaError_t launch_generate(const GenerateArgs &a, void *ws, cudaStream_t st) {

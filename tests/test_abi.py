@@ -124,3 +124,21 @@ def test_projection_and_tuning_reject_bad_arguments_on_host(lib):
     assert lib.rici_project_fp32(dummy, 0, None, None, None, None) == 0
     assert lib.rici_get_tuning(None) == 1
     assert lib.rici_measure_dp4a_rate(None, None) == 1
+
+
+def test_clutter_rejects_bad_arguments_on_host(lib):
+    dummy = ctypes.c_void_p(16)
+    # bad support radius, negative object vertex count, null outputs
+    assert lib.rici_clutter(dummy, dummy, 3, dummy, 1, dummy, 1, 0.0, 0, dummy, dummy, None, 0,
+                            None) == 1
+    assert lib.rici_clutter(dummy, dummy, 3, dummy, 1, dummy, 1, 0.3, -1, dummy, dummy, None, 0,
+                            None) == 1
+    assert lib.rici_clutter(dummy, dummy, 3, dummy, 1, dummy, 1, 0.3, 0, None, dummy, None, 0,
+                            None) == 1
+    assert lib.rici_clutter(dummy, dummy, 3, dummy, 1, dummy, 1, 0.3, 0, dummy, None, None, 0,
+                            None) == 1
+    # no oriented points: a valid no-op; the workspace is the generation grid's
+    assert lib.rici_clutter(dummy, dummy, 3, dummy, 1, dummy, 0, 0.3, 0, None, None, None, 0,
+                            None) == 0
+    assert lib.rici_clutter_workspace_size(100) == lib.rici_generate_workspace_size(3, 100, 1, 64)
+    assert lib.rici_clutter_workspace_size(-1) == -1
