@@ -291,8 +291,26 @@ def clutterbox_experiment(p, torch, dev, stream, runs=4, n=10, seed=51, tri_lo=2
         e1.record(stream)
         torch.cuda.synchronize()
         ts.append(e0.elapsed_time(e1))
+    # Eq. clutter around every reference vertex of every level (clutter-versus-rank heatmap)
+    areas = clutterbox.clutter_prepared(prep, R_SUP)
+    torch.cuda.synchronize()
+    tc = []
+    for _ in range(steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        areas = clutterbox.clutter_prepared(prep, R_SUP)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        tc.append(e0.elapsed_time(e1))
     st = p.sync_status()
-    h = clutterbox.histograms(prep, res)
+    h = clutterbox.histograms(prep, res, areas)
+    lv5 = min(4, n - 1)  # the paper's heatmaps: scenes with 4 added objects
+    heat = np.sum([r["heatmap"][lv5] for r in h], axis=0)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        r0_by_clutter = [float(x) if np.isfinite(x) else None
+                         for x in heat[:, 0] / heat.sum(axis=1)]
+    clutter_points = sum(sz[0] * len(sz) for sz in prep["sizes"])
     images = sum(sum(sz) for sz in prep["sizes"])
     comparisons = sum(sz[0] * sum(sz) for sz in prep["sizes"])
     t = statistics.mean(ts)
@@ -301,10 +319,16 @@ def clutterbox_experiment(p, torch, dev, stream, runs=4, n=10, seed=51, tri_lo=2
            "images_per_s": images / (t / 1e3),
            "rank0_fraction_by_level": [float(x) for x in
                                        np.mean([r["rank0_fraction"] for r in h], axis=0)],
+           "clutter_ms": statistics.mean(tc), "clutter_points": clutter_points,
+           "clutter_points_per_s": clutter_points / (statistics.mean(tc) / 1e3),
+           "heatmap_level": lv5 + 1,
+           "heatmap_rank_edges": [int(x) for x in clutterbox.RANK_EDGES[:-1]],
+           "heatmap_counts": heat.tolist(),
+           "rank0_fraction_by_clutter_decile": r0_by_clutter,
            "status": st,
            "recipe": f"synth.scenes.clutterbox(seed={seed}..{seed + runs - 1}, n={n}, box side 3, "
                      f"objects of {tri_lo}-{tri_hi} triangles), N = {N_RES}, R = {R_SUP}"}
-    del prep, res
+    del prep, res, areas
     torch.cuda.empty_cache()
     return out
 

@@ -10,7 +10,10 @@ of those ranks per level is the experiment's output (step 6d), summarised by the
 results at rank 0 (Section 4.2).
 
 All levels of all runs are imaged by one batched generation call and searched by one batched
-search call; everything on the way runs in the library's kernels.  Input meshes come from
+search call; everything on the way runs in the library's kernels.  Optionally the clutter of
+Eq. clutter is measured around every reference vertex of every level (``rici_clutter``: the
+share of the surface area inside its support volume that does not belong to the reference
+object), which gives the clutter-versus-rank heatmap of Section 4.2.  Input meshes come from
 ``synth.scenes.clutterbox`` or any objects with the same fields.
 """
 from __future__ import annotations
@@ -58,29 +61,64 @@ def run_prepared(prep, support_radius: float = 0.3, resolution: int = 64,
     return B.crss_search_batch(search, resolution, mode=mode, stream=stream)
 
 
-def histograms(prep, results):
-    """Per run: ranks, rank histograms (bin i = results at rank i, |CD| bins) and the fraction
-    of results at rank 0, one entry per level."""
+def clutter_prepared(prep, support_radius: float = 0.3, stream=None):
+    """Eq. clutter around every reference vertex of every level: per (run, level) the device
+    tensors (A_all, A_object), the object being the reference object (level 1's vertices)."""
     out, k = [], 0
     for sizes in prep["sizes"]:
-        ranks, hists, frac = [], [], []
+        ref = torch.arange(sizes[0], dtype=torch.int32, device=prep["gen"][k]["vertices"].device)
+        for j in range(len(sizes)):
+            g = prep["gen"][k + j]
+            out.append(B.clutter_areas(g["vertices"], g["normals"], g["triangles"], ref,
+                                       support_radius, sizes[0], stream=stream))
+        k += len(sizes)
+    return out
+
+
+RANK_EDGES = np.array([0, 1, 2, 5, 10, 20, 50, 100, 1000, np.iinfo(np.int64).max])
+
+
+def histograms(prep, results, areas=None, clutter_bins: int = 10):
+    """Per run: ranks, rank histograms (bin i = results at rank i, |CD| bins) and the fraction
+    of results at rank 0, one entry per level.  With ``areas`` (from ``clutter_prepared``) also
+    the clutter of every reference vertex, (A_all - A_object) / A_all, and a heatmap per level:
+    counts of results by clutter (``clutter_bins`` equal bins of [0, 1]) and rank (bins with the
+    edges of RANK_EDGES: rank 0, 1, 2-4, 5-9, ...)."""
+    out, k = [], 0
+    for sizes in prep["sizes"]:
+        ranks, hists, frac, clut, heat = [], [], [], [], []
         for j, v in enumerate(sizes):
             r = results[k + j]["rank"].cpu().numpy()
             h = np.bincount(r, minlength=v).astype(np.int64)
             ranks.append(r)
             hists.append(h)
             frac.append(float(h[0]) / r.size if r.size else float("nan"))
-        out.append({"ranks": ranks, "histograms": hists, "rank0_fraction": frac})
+            if areas is not None:
+                a_all = areas[k + j][0].cpu().numpy()
+                a_obj = areas[k + j][1].cpu().numpy()
+                c = np.where(a_all > 0, (a_all - a_obj) / np.where(a_all > 0, a_all, 1.0), 0.0)
+                clut.append(c)
+                ci = np.minimum((c * clutter_bins).astype(np.int64), clutter_bins - 1)
+                ri = np.searchsorted(RANK_EDGES, r, side="right") - 1
+                hm = np.zeros((clutter_bins, RANK_EDGES.size - 1), np.int64)
+                np.add.at(hm, (ci, ri), 1)
+                heat.append(hm)
+        entry = {"ranks": ranks, "histograms": hists, "rank0_fraction": frac}
+        if areas is not None:
+            entry["clutter"] = clut
+            entry["heatmap"] = heat
+        out.append(entry)
         k += len(sizes)
     return out
 
 
 def run(runs, support_radius: float = 0.3, resolution: int = 64, mode: int = B.SEARCH_TENSOR,
-        device="cuda"):
+        device="cuda", clutter: bool = False):
     """The whole experiment for a list of runs (see ``prepare`` and ``histograms``)."""
     prep = prepare(runs, device)
     res = run_prepared(prep, support_radius, resolution, mode)
+    areas = clutter_prepared(prep, support_radius) if clutter else None
     st = B.sync_status()
     if st:
         raise B.RiciError(f"device status {st} in the clutterbox run")
-    return histograms(prep, res)
+    return histograms(prep, res, areas)

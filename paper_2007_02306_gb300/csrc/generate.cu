@@ -1042,6 +1042,12 @@ __device__ double support_area64(const double T[3][3], double R) {
   const double nn = sqrt(nx * nx + ny * ny + nz * nz);
   if (nn == 0.0) return 0.0;
   const double H = 0.5 * R;
+  // the volume is convex: a triangle whose vertices all lie in it lies in it whole
+  bool whole = true;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+    whole = whole && T[i][0] * T[i][0] + T[i][1] * T[i][1] <= R * R && fabs(T[i][2]) <= H;
+  if (whole) return 0.5 * nn;
   // slab clip (z <= H, then -z <= H), at most 5 vertices
   double P[5][3], Q[5][3];
   int m = 0;

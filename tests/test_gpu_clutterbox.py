@@ -28,7 +28,7 @@ def test_clutterbox_runs_match_the_oracle(rici, oracle_mod, mode):
     runs = [synth.scenes.clutterbox(seed=s, n=3, box_side=3.0, tri_lo=80, tri_hi=700)
             for s in (11, 12)]
     R, N = 0.3, 32
-    got = clutterbox.run(runs, R, N, mode=mode)
+    got = clutterbox.run(runs, R, N, mode=mode, clutter=True)
     for levels, g in zip(runs, got):
         ref = levels[0]
         o_ref = np.arange(ref.num_vertices, dtype=np.int32)
@@ -42,5 +42,13 @@ def test_clutterbox_runs_match_the_oracle(rici, oracle_mod, mode):
             h = np.bincount(r, minlength=lv.num_vertices)
             assert np.array_equal(g["histograms"][k], h), k
             assert g["rank0_fraction"][k] == pytest.approx(h[0] / r.size)
+            # Eq. clutter around the reference vertices (object = the reference object)
+            a_all, a_obj = oracle_mod.clutter_areas(lv.vertices, lv.normals, lv.triangles, o_ref,
+                                                    np.float32(R), ref.num_vertices)
+            c = (a_all - a_obj) / a_all
+            assert np.abs(g["clutter"][k] - c).max() <= 1e-9, k
+            assert g["heatmap"][k].sum() == r.size
+            if k == 0:  # the reference alone: no clutter anywhere
+                assert np.abs(g["clutter"][k]).max() <= 1e-12
         # level 1 searches the reference descriptors against themselves
         assert g["rank0_fraction"][0] == 1.0
