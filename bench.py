@@ -637,6 +637,26 @@ def main():
     cbox = None
     if args.clutterbox_compare and rank == 0:
         cbox = clutterbox_experiment(p, torch, dev, stream)
+        # Eq. clutter around every needle's vertex of the step's scene (object = the target)
+        for _ in range(2):
+            p.clutter_areas(vert, norm, tri, on, R_SUP, Vt)
+        torch.cuda.synchronize()
+        cm = []
+        for _ in range(args.steps):
+            c0 = torch.cuda.Event(enable_timing=True)
+            c1 = torch.cuda.Event(enable_timing=True)
+            c0.record(stream)
+            ca, co = p.clutter_areas(vert, norm, tri, on, R_SUP, Vt)
+            c1.record(stream)
+            torch.cuda.synchronize()
+            cm.append(c0.elapsed_time(c1))
+        cf = ((ca - co) / ca).cpu().numpy()
+        cbox["clutter_scene_measure"] = {
+            "points": Vt, "triangles": T, "ms": statistics.mean(cm),
+            "points_per_s": Vt / (statistics.mean(cm) / 1e3),
+            "clutter_mean": float(cf.mean()), "clutter_quartiles": [
+                float(x) for x in np.quantile(cf, [0.25, 0.5, 0.75])],
+            "status": p.sync_status()}
 
     batched = batched_small = None
     if args.batched_compare and rank == 0:
