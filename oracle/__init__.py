@@ -63,6 +63,10 @@ def _load():
             lib.oracle_rici_fp32.restype = ctypes.c_int
             lib.oracle_clutter_areas.argtypes = [P, P, i64, P, i64, P, i64, f32, i64, P, P, i32]
             lib.oracle_clutter_areas.restype = ctypes.c_int
+            lib.oracle_spin_samples.argtypes = [P, i64, P, i64, i32, P]
+            lib.oracle_spin_samples.restype = ctypes.c_int
+            lib.oracle_spin_images.argtypes = [P, P, i64, P, i64, P, i64, f32, i32, i32, P, i32]
+            lib.oracle_spin_images.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -201,3 +205,34 @@ def clutter(vertices, normals, triangles, origins, support_radius: float, object
                                  object_vertices)
     with np.errstate(invalid="ignore", divide="ignore"):
         return np.where(a_all > 0, (a_all - a_obj) / np.where(a_all > 0, a_all, 1.0), np.nan)
+
+
+def spin_samples(vertices, triangles, m: int):
+    """The m^2 point samples of every triangle used by ``spin_images``: float32 [T, m^2, 3]."""
+    lib = _load()
+    v = np.ascontiguousarray(vertices, dtype=np.float32).reshape(-1, 3)
+    t = np.ascontiguousarray(triangles, dtype=np.int32).reshape(-1, 3)
+    out = np.zeros((t.shape[0], m * m, 3), np.float32)
+    rc = lib.oracle_spin_samples(_ptr(v), v.shape[0], _ptr(t), t.shape[0], int(m), _ptr(out))
+    if rc != 0:
+        raise ValueError(f"oracle_spin_samples failed with status {rc}")
+    return out
+
+
+def spin_images(vertices, normals, triangles, origins, support_radius: float, resolution: int,
+                m: int = 3, num_threads: int = 0):
+    """Spin images (Section 2.1) of the oriented points from m^2 samples per triangle, bilinear
+    weights around the bin centres, float32 [O, N, N] (row = beta bin, column = alpha bin)."""
+    lib = _load()
+    v = np.ascontiguousarray(vertices, dtype=np.float32).reshape(-1, 3)
+    n = np.ascontiguousarray(normals, dtype=np.float32).reshape(-1, 3)
+    t = np.ascontiguousarray(triangles, dtype=np.int32).reshape(-1, 3)
+    o = np.ascontiguousarray(origins, dtype=np.int32).reshape(-1)
+    N = int(resolution)
+    out = np.zeros((o.shape[0], N, N), np.float32)
+    rc = lib.oracle_spin_images(_ptr(v), _ptr(n), v.shape[0], _ptr(t), t.shape[0], _ptr(o),
+                                o.shape[0], float(support_radius), N, int(m), _ptr(out),
+                                int(num_threads))
+    if rc != 0:
+        raise ValueError(f"oracle_spin_images failed with status {rc}")
+    return out

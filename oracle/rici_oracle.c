@@ -33,6 +33,8 @@
  *  - oracle_clutter_areas: per oriented point, the surface area inside its support volume and
  *    the part of it that belongs to the object of interest (Eq. clutter), brute force over
  *    every triangle (see the comment above that function).
+ *  - oracle_spin_samples / oracle_spin_images: spin images (Section 2.1) from m^2 point samples
+ *    per triangle, single precision in a fixed order (see the comment above those functions).
  *
  * Readings where the paper is silent or garbled (each listed with its reason in the design
  * notes):
@@ -659,4 +661,136 @@ int oracle_clutter_areas(const float *vertices, const float *normals, int64_t nu
         area_object[o] = obj;
     }
     return ORACLE_OK;
+}
+
+/* ------------------------------------------------------------------------------------------
+ * Spin images (Section 2.1: the descriptor the RICI is compared with), generated from point
+ * samples of the mesh with the projection of Section 3.1.1, in single precision.
+ *
+ * Samples: m^2 points per triangle (A, B, C in its own vertex order), the centroids of the m^2
+ * congruent triangles obtained by dividing every side into m parts, so the samples are spread
+ * uniformly over the triangle's area.  With barycentric weights (a, b) for B and C:
+ *   upward sub-triangles   i + j <= m - 1:  a = (3i + 1) / (3m),  b = (3j + 1) / (3m)
+ *   downward sub-triangles i + j <= m - 2:  a = (3i + 2) / (3m),  b = (3j + 2) / (3m)
+ *   P = fmaf(b, C - A, fmaf(a, B - A, A)) per coordinate (float).
+ * Readings: the square plane is R wide and R high with its left side on the central axis and
+ * the spin vertex at half height (Section 2.1), divided into N x N bins centred at
+ * (alpha_c, beta_r) of readings (1)-(2); a sample with alpha^2 < R^2 and -R/2 <= beta < R/2 is
+ * in the support volume and adds bilinear weights (Section 2.1) to the four bins around it:
+ *   u = alpha N/R - 1/2, v = (beta + R/2) N/R - 1/2, c = floor(u), r = floor(v),
+ *   fu = u - c, fv = v - r: (1-fu)(1-fv) to (r, c), fu (1-fv) to (r, c+1), (1-fu) fv to
+ *   (r+1, c), fu fv to (r+1, c+1); weight that falls on a bin outside [0, N) is dropped.
+ * The support-angle filter is not applied (Section 4.2 found it does not help).  Every float
+ * operation is written out in the order the GPU uses (projection as oracle_project_fp32); the
+ * weights are summed in FP64 and the image is stored in float32.
+ * ---------------------------------------------------------------------------------------- */
+
+/* Barycentric weights (a, b) of sample k of m^2 (upward sub-triangles first). */
+static void spin_sample_weights(int m, int k, float *a, float *b) {
+    const int up = m * (m + 1) / 2;
+    const float den = (float)(3 * m);
+    int idx = k < up ? k : k - up;
+    const int off = k < up ? 1 : 2;
+    const int rows = k < up ? m : m - 1;
+    int i = 0;
+    while (idx >= rows - i) {
+        idx -= rows - i;
+        i++;
+    }
+    const int j = idx;
+    *a = (float)(3 * i + off) / den;
+    *b = (float)(3 * j + off) / den;
+}
+
+/* Sample positions of every triangle: out[t][k][3], m^2 samples per triangle. */
+int oracle_spin_samples(const float *vertices, int64_t num_vertices, const int32_t *triangles,
+                        int64_t num_triangles, int32_t m, float *out) {
+    if (m < 1 || m > 16 || num_triangles < 0) return ORACLE_BAD_ARGUMENT;
+    for (int64_t t = 0; t < 3 * num_triangles; t++)
+        if (triangles[t] < 0 || triangles[t] >= num_vertices) return ORACLE_BAD_INDEX;
+    for (int64_t t = 0; t < num_triangles; t++) {
+        const float *A = vertices + 3 * (int64_t)triangles[3 * t];
+        const float *B = vertices + 3 * (int64_t)triangles[3 * t + 1];
+        const float *C = vertices + 3 * (int64_t)triangles[3 * t + 2];
+        for (int k = 0; k < m * m; k++) {
+            float a, b;
+            spin_sample_weights(m, k, &a, &b);
+            float *P = out + (t * (int64_t)m * m + k) * 3;
+            for (int d = 0; d < 3; d++) P[d] = fmaf(b, C[d] - A[d], fmaf(a, B[d] - A[d], A[d]));
+        }
+    }
+    return ORACLE_OK;
+}
+
+int oracle_spin_images(const float *vertices, const float *normals, int64_t num_vertices,
+                       const int32_t *triangles, int64_t num_triangles, const int32_t *origins,
+                       int64_t num_origins, float support_radius, int32_t resolution, int32_t m,
+                       float *out_images, int32_t num_threads) {
+    const int32_t N = resolution;
+    if (N < 1 || N > 1024 || m < 1 || m > 16 || !(support_radius > 0.0f) || num_vertices < 0 ||
+        num_triangles < 0 || num_origins < 0)
+        return ORACLE_BAD_ARGUMENT;
+    for (int64_t t = 0; t < 3 * num_triangles; t++)
+        if (triangles[t] < 0 || triangles[t] >= num_vertices) return ORACLE_BAD_INDEX;
+    for (int64_t o = 0; o < num_origins; o++)
+        if (origins[o] < 0 || origins[o] >= num_vertices) return ORACLE_BAD_INDEX;
+    const float R = support_radius;
+    const float R2 = R * R, H = 0.5f * R, s = (float)N / R;
+    int status = ORACLE_OK;
+#ifdef _OPENMP
+    if (num_threads > 0) omp_set_num_threads(num_threads);
+#pragma omp parallel
+#endif
+    {
+        double *img = (double *)malloc(sizeof(double) * (size_t)N * (size_t)N);
+        if (!img) {
+#ifdef _OPENMP
+#pragma omp atomic write
+#endif
+            status = ORACLE_NO_MEMORY;
+        } else {
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 1)
+#endif
+            for (int64_t o = 0; o < num_origins; o++) {
+                memset(img, 0, sizeof(double) * (size_t)N * (size_t)N);
+                const int32_t sv = origins[o];
+                const float S[3] = {vertices[3 * sv], vertices[3 * sv + 1], vertices[3 * sv + 2]};
+                double Nax, Nay, Nbx, Nbz;
+                frame_coefficients(normals[3 * sv], normals[3 * sv + 1], normals[3 * sv + 2],
+                                   &Nax, &Nay, &Nbx, &Nbz);
+                const float ax = (float)Nax, ay = (float)Nay, bx = (float)Nbx, bz = (float)Nbz;
+                for (int64_t t = 0; t < num_triangles; t++) {
+                    const float *A = vertices + 3 * (int64_t)triangles[3 * t];
+                    const float *B = vertices + 3 * (int64_t)triangles[3 * t + 1];
+                    const float *C = vertices + 3 * (int64_t)triangles[3 * t + 2];
+                    for (int k = 0; k < m * m; k++) {
+                        float a, b, P[3], T[3];
+                        spin_sample_weights(m, k, &a, &b);
+                        for (int d = 0; d < 3; d++)
+                            P[d] = fmaf(b, C[d] - A[d], fmaf(a, B[d] - A[d], A[d]));
+                        project_point_fp32(P, S, ax, ay, bx, bz, T);
+                        const float a2 = fmaf(T[0], T[0], T[1] * T[1]);
+                        if (!(a2 < R2) || !(T[2] >= -H) || !(T[2] < H)) continue;
+                        const float u = fmaf(sqrtf(a2), s, -0.5f);
+                        const float v = fmaf(T[2] + H, s, -0.5f);
+                        const float cu = floorf(u), rv = floorf(v);
+                        const float fu = u - cu, fv = v - rv;
+                        const int c = (int)cu, r = (int)rv;
+                        const float w[4] = {(1.0f - fu) * (1.0f - fv), fu * (1.0f - fv),
+                                            (1.0f - fu) * fv, fu * fv};
+                        for (int q = 0; q < 4; q++) {
+                            const int rr = r + (q >> 1), cc = c + (q & 1);
+                            if (rr >= 0 && rr < N && cc >= 0 && cc < N)
+                                img[(int64_t)rr * N + cc] += (double)w[q];
+                        }
+                    }
+                }
+                float *dst = out_images + o * (int64_t)N * N;
+                for (int64_t k = 0; k < (int64_t)N * N; k++) dst[k] = (float)img[k];
+            }
+            free(img);
+        }
+    }
+    return status;
 }
