@@ -88,6 +88,8 @@ def parse():
                     help="also time the sparse-needle CUDA-core search on the same images")
     ap.add_argument("--precision-compare", type=int, default=1,
                     help="also time the three search forms on a precision-form image set sample")
+    ap.add_argument("--spin-compare", type=int, default=1,
+                    help="also time spin-image generation (Section 2.1) for the haystack points")
     ap.add_argument("--clutterbox-compare", type=int, default=1,
                     help="also time a synthetic clutterbox experiment (Section 4.1) on the GPU path")
     ap.add_argument("--batched-compare", type=int, default=1,
@@ -634,6 +636,28 @@ def main():
     if args.precision_compare and rank == 0:
         precision = precision_form_comparison(p, torch, dev, stream)
 
+    spin = None
+    if args.spin_compare:
+        # spin images of every haystack point from 9 samples per triangle (the paper used 10)
+        si = torch.empty((V, N_RES, N_RES), dtype=torch.float32, device=dev)
+        for _ in range(2):
+            p.spin_images(vert, norm, tri, oh, R_SUP, N_RES, 3, out=si)
+        torch.cuda.synchronize()
+        sm = []
+        for _ in range(args.steps):
+            flush.zero_()
+            s0 = torch.cuda.Event(enable_timing=True)
+            s1 = torch.cuda.Event(enable_timing=True)
+            s0.record(stream)
+            p.spin_images(vert, norm, tri, oh, R_SUP, N_RES, 3, out=si)
+            s1.record(stream)
+            torch.cuda.synchronize()
+            sm.append(s0.elapsed_time(s1))
+        spin = {"images": V, "samples_per_triangle": 9, "ms": statistics.mean(sm),
+                "images_per_s": V / (statistics.mean(sm) / 1e3),
+                "rici_haystack_generation_ms": statistics.mean(t_hy), "status": p.sync_status()}
+        del si
+
     cbox = None
     if args.clutterbox_compare and rank == 0:
         cbox = clutterbox_experiment(p, torch, dev, stream)
@@ -805,6 +829,7 @@ def main():
             "search_sparse_needle": sp,
             "precision_form_sample": precision,
             "clutterbox": cbox,
+            "spin_images": spin,
             "batched_run": batched,
             "batched_run_small_scenes": batched_small,
             "tuning": step_tuning,

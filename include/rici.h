@@ -231,6 +231,29 @@ RICI_API int rici_clutter(const float *vertices, const float *normals, int64_t n
                           int64_t workspace_bytes, void *stream);
 
 /*
+ * rici_spin_images — spin images (Section 2.1, the descriptor the RICI is compared with) from
+ * point samples of the mesh, with the projection of Section 3.1.1.
+ *
+ *   vertices, normals, triangles, origins, support_radius, resolution  as for rici_generate.
+ *   samples_side  m in [1, 16]: m^2 samples per triangle, the centroids of the m^2 congruent
+ *              triangles of a division of every side into m parts (uniform over its area).
+ *   out_images [num_origins][N][N] float32 (caller-owned device memory): the plane is R wide
+ *              and R high with the spin vertex at half height; bin (r, c) is centred at
+ *              alpha_c = (c + 1/2) R/N, beta_r = (r + 1/2 - N/2) R/N; each sample with
+ *              alpha^2 < R^2 and -R/2 <= beta < R/2 adds bilinear weights to the four bins
+ *              around it (weight on a bin outside the image is dropped).  No support-angle
+ *              filter.  Weights are formed in FP32 in a fixed order and summed in FP64.
+ * Workspace: rici_clutter_workspace_size bytes (the same grid), or NULL.
+ * Errors: as rici_generate (a zero image for an oriented point with a bad index or a
+ * non-finite coordinate).
+ */
+RICI_API int rici_spin_images(const float *vertices, const float *normals, int64_t num_vertices,
+                              const int32_t *triangles, int64_t num_triangles,
+                              const int32_t *origins, int64_t num_origins, float support_radius,
+                              int32_t resolution, int32_t samples_side, float *out_images,
+                              void *workspace, int64_t workspace_bytes, void *stream);
+
+/*
  * rici_generate_noalloc — rici_generate for callers that must not allocate device memory.
  * (An addition of this library; the paper has no counterpart.)
  *

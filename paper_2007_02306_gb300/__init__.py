@@ -9,5 +9,6 @@ from .binding import (  # noqa: F401
     SEARCH_TENSOR, RiciError,
     autotune_generate_batch, autotune_search_batch, clutter_areas, crss_search, crss_search_batch,
     get_tuning,
-    load_library, rici_generate, rici_generate_batch, set_tuning, sync_status, version,
+    load_library, rici_generate, rici_generate_batch, set_tuning, spin_images, sync_status,
+    version,
 )

@@ -109,6 +109,8 @@ def load_library(path: str | None = None):
         lib.rici_clutter_workspace_size.restype = i64
         lib.rici_clutter.argtypes = [P, P, i64, P, i64, P, i64, f32, i64, P, P, P, i64, P]
         lib.rici_clutter.restype = ctypes.c_int
+        lib.rici_spin_images.argtypes = [P, P, i64, P, i64, P, i64, f32, i32, i32, P, P, i64, P]
+        lib.rici_spin_images.restype = ctypes.c_int
         lib.rici_project_fp32.argtypes = [P, i64, P, P, P, P]
         lib.rici_project_fp32.restype = ctypes.c_int
         lib.rici_set_tuning.argtypes = [P]
@@ -226,6 +228,35 @@ def clutter_areas(vertices, normals, triangles, origins, support_radius: float,
                                 _ptr(a_all), _ptr(a_obj), _ptr(ws), ws.numel(),
                                 _stream_handle(stream)))
     return a_all, a_obj
+
+
+def spin_images(vertices, normals, triangles, origins, support_radius: float, resolution: int,
+                samples_side: int = 3, *, out=None, stream=None):
+    """float32 [O, N, N] spin images (Section 2.1) of the oriented points from samples_side^2
+    point samples per triangle (see include/rici.h for the sampling and binning)."""
+    lib = load_library()
+    v = _need(vertices, torch.float32, "vertices", (3,))
+    n = _need(normals, torch.float32, "normals", (3,))
+    t = _need(triangles, torch.int32, "triangles", (3,))
+    o = _need(origins, torch.int32, "origins")
+    if n.shape != v.shape:
+        raise ValueError("normals must have the same shape as vertices")
+    N = int(resolution)
+    if out is None:
+        out = torch.empty((o.numel(), N, N), dtype=torch.float32, device=v.device)
+    else:
+        _need(out, torch.float32, "out", (N, N))
+        if out.shape[0] != o.numel():
+            raise ValueError("out must have one image per origin")
+    nb = lib.rici_clutter_workspace_size(t.shape[0])
+    if nb < 0:
+        raise ValueError("invalid sizes")
+    ws = workspace(v.device, nb)
+    with torch.cuda.device(v.device):
+        _check(lib.rici_spin_images(_ptr(v), _ptr(n), v.shape[0], _ptr(t), t.shape[0], _ptr(o),
+                                    o.numel(), float(support_radius), N, int(samples_side),
+                                    _ptr(out), _ptr(ws), ws.numel(), _stream_handle(stream)))
+    return out
 
 
 def crss_search(needles, haystack, true_match=None, *, mode: int = SEARCH_DEFAULT,

@@ -298,6 +298,43 @@ int rici_clutter(const float *vertices, const float *normals, int64_t num_vertic
   return RICI_OK;
 }
 
+int rici_spin_images(const float *vertices, const float *normals, int64_t num_vertices,
+                     const int32_t *triangles, int64_t num_triangles, const int32_t *origins,
+                     int64_t num_origins, float support_radius, int32_t resolution,
+                     int32_t samples_side, float *out_images, void *workspace,
+                     int64_t workspace_bytes, void *stream) {
+  t_last_error.clear();
+  int rc = check_generate_args(vertices, normals, num_vertices, triangles, num_triangles,
+                               origins, num_origins, support_radius, resolution,
+                               reinterpret_cast<const uint16_t *>(out_images));
+  if (rc) return rc;
+  if (samples_side < 1 || samples_side > 16)
+    return fail(RICI_ERR_INVALID_ARGUMENT, "samples_side must be in [1, 16]");
+  if (num_origins == 0) return RICI_OK;
+  DeviceState *d = nullptr;
+  if ((rc = device_state(&d))) return rc;
+  void *ws = nullptr;
+  if ((rc = resolve_workspace(d, workspace, workspace_bytes,
+                              generate_workspace_bytes(num_triangles), &ws)))
+    return rc;
+  SpinArgs a;
+  a.vertices = vertices;
+  a.normals = normals;
+  a.num_vertices = num_vertices;
+  a.triangles = triangles;
+  a.num_triangles = num_triangles;
+  a.origins = origins;
+  a.num_origins = num_origins;
+  a.support_radius = support_radius;
+  a.resolution = resolution;
+  a.samples_side = samples_side;
+  a.out_images = out_images;
+  a.status = d->status;
+  cudaError_t e = launch_spin(a, ws, static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(e, "rici_spin_images launch");
+  return RICI_OK;
+}
+
 int rici_generate(const float *vertices, const float *normals, int64_t num_vertices,
                   const int32_t *triangles, int64_t num_triangles, const int32_t *origins,
                   int64_t num_origins, float support_radius, int32_t resolution,

@@ -49,6 +49,24 @@ struct ClutterArgs {
 // Enqueue the clutter measure on `stream` using `ws` (>= generate_workspace_bytes).
 cudaError_t launch_clutter(const ClutterArgs &a, void *ws, cudaStream_t stream);
 
+// Spin images (Section 2.1) from samples_side^2 point samples per triangle, float32 [O][N][N].
+struct SpinArgs {
+  const float *vertices;
+  const float *normals;
+  int64_t num_vertices;
+  const int32_t *triangles;
+  int64_t num_triangles;
+  const int32_t *origins;
+  int64_t num_origins;
+  float support_radius;
+  int32_t resolution;
+  int32_t samples_side;
+  float *out_images;
+  int *status;  // device status word
+};
+// Enqueue spin-image generation on `stream` using `ws` (>= generate_workspace_bytes).
+cudaError_t launch_spin(const SpinArgs &a, void *ws, cudaStream_t stream);
+
 // One scene of a multi-scene generation launch (entry of the device scene table).
 struct GenScene {
   const float *V;

@@ -1259,6 +1259,146 @@ __global__ void __launch_bounds__(kClutterWarps * 32) k_clutter(KArgs a, int64_t
   }
 }
 
+// ------------------------------------------------------------------ spin images
+// Spin images (Section 2.1) from point samples of the mesh, with the FP32 projection stage of
+// the generation kernel (Eqs. relativeLocation..secondRotation, frame rounded from FP64).
+// Samples: m^2 per triangle at the centroids of the m^2 congruent sub-triangles of a division of
+// every side into m parts, P = A + a (B - A) + b (C - A) with barycentric (a, b) = ((3i+1)/3m,
+// (3j+1)/3m) for the upward sub-triangles (i + j <= m - 1) and ((3i+2)/3m, (3j+2)/3m) for the
+// downward ones (i + j <= m - 2).  The plane is R wide and R high with the spin vertex at half
+// height, N x N bins centred at alpha_c = (c + 1/2) R/N and beta_r = (r + 1/2 - N/2) R/N; a
+// sample with alpha^2 < R^2 and -R/2 <= beta < R/2 adds bilinear weights to the four bins around
+// it (weight on a bin outside the image is dropped).  Weights are formed in FP32 with explicit
+// roundings and summed in FP64 in shared memory; the image is stored as float32.
+constexpr int kSpinWarps = 4;
+constexpr int kSpinMaxSide = 16;  // samples per triangle <= 256
+
+__global__ void __launch_bounds__(kSpinWarps * 32) k_spin(KArgs a, int m, float *__restrict__ out) {
+  extern __shared__ __align__(16) unsigned char spin_smem[];
+  __shared__ int buckets[kClutterMaxCells], bdup[kClutterMaxCells];
+  __shared__ double fr[7];
+  __shared__ float smp_a[kSpinMaxSide * kSpinMaxSide], smp_b[kSpinMaxSide * kSpinMaxSide];
+  __shared__ int wq[kSpinWarps][64];
+  const int N = a.N;
+  double *img = reinterpret_cast<double *>(spin_smem);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t og = a.origin_base + blockIdx.x;
+  const GenScene &sc = a.tab[scene_of_origin(a.tab, a.num_scenes, og)];
+  float *dst = out + og * (int64_t)N * N;
+  const int vid = sc.origins[og - sc.origin_off];
+  bool bad = vid < 0 || vid >= sc.nv;
+  float Sx = 0.0f, Sy = 0.0f, Sz = 0.0f, nxf = 0.0f, nyf = 0.0f, nzf = 1.0f;
+  if (!bad) {
+    Sx = sc.V[3 * (int64_t)vid];
+    Sy = sc.V[3 * (int64_t)vid + 1];
+    Sz = sc.V[3 * (int64_t)vid + 2];
+    nxf = sc.Nrm[3 * (int64_t)vid];
+    nyf = sc.Nrm[3 * (int64_t)vid + 1];
+    nzf = sc.Nrm[3 * (int64_t)vid + 2];
+  }
+  const bool nonfinite = !bad && !(isfinite(Sx) && isfinite(Sy) && isfinite(Sz) &&
+                                   isfinite(nxf) && isfinite(nyf) && isfinite(nzf));
+  if (bad || nonfinite) {
+    if (tid == 0)
+      set_status(a.status, bad ? RICI_ERR_INDEX_OUT_OF_RANGE : RICI_ERR_NONFINITE_INPUT);
+    for (int i = tid; i < N * N; i += kSpinWarps * 32) dst[i] = 0.0f;
+    return;
+  }
+  for (int i = tid; i < N * N; i += kSpinWarps * 32) img[i] = 0.0;
+  if (tid == 0) {
+    fr[0] = Sx;
+    fr[1] = Sy;
+    fr[2] = Sz;
+    frame_fp64(nxf, nyf, nzf, fr + 3);
+    // sample table: upward sub-triangles row by row, then the downward ones
+    const float den = (float)(3 * m);
+    int k = 0;
+    for (int i = 0; i < m; ++i)
+      for (int j = 0; i + j <= m - 1; ++j, ++k) {
+        smp_a[k] = __fdiv_rn((float)(3 * i + 1), den);
+        smp_b[k] = __fdiv_rn((float)(3 * j + 1), den);
+      }
+    for (int i = 0; i + 1 < m; ++i)
+      for (int j = 0; i + j <= m - 2; ++j, ++k) {
+        smp_a[k] = __fdiv_rn((float)(3 * i + 2), den);
+        smp_b[k] = __fdiv_rn((float)(3 * j + 2), den);
+      }
+  }
+  neighbour_ranges(a, sc.bucket_off, sc.nbuckets, Sx, Sy, Sz, nxf, nyf, nzf, buckets, bdup, tid,
+                   kSpinWarps * 32);
+  const float fax = __double2float_rn(fr[3]), fay = __double2float_rn(fr[4]);
+  const float fbx = __double2float_rn(fr[5]), fbz = __double2float_rn(fr[6]);
+  const float wx = fbx * fax, wy = fbx * fay, wz = fbz;  // central axis in world coordinates
+  const float R = a.R, R2 = __fmul_rn(R, R), H = __fmul_rn(0.5f, R);
+  const float scale = __fdiv_rn((float)N, R);
+  const int ns = m * m;
+  int qn = 0;
+  auto process = [&](int cnt) {
+    if (lane < cnt) {
+      const int64_t r = wq[warp][lane];
+      const float4 r1 = a.rec[4 * r + 1], r2 = a.rec[4 * r + 2], r3 = a.rec[4 * r + 3];
+      const float A[3] = {r1.x, r1.y, r1.z}, B[3] = {r1.w, r2.x, r2.y}, C[3] = {r2.z, r2.w, r3.x};
+      const float ba[3] = {__fsub_rn(B[0], A[0]), __fsub_rn(B[1], A[1]), __fsub_rn(B[2], A[2])};
+      const float ca[3] = {__fsub_rn(C[0], A[0]), __fsub_rn(C[1], A[1]), __fsub_rn(C[2], A[2])};
+      for (int k = 0; k < ns; ++k) {
+        const float sa = smp_a[k], sb = smp_b[k];
+        const float px = __fmaf_rn(sb, ca[0], __fmaf_rn(sa, ba[0], A[0]));
+        const float py = __fmaf_rn(sb, ca[1], __fmaf_rn(sa, ba[1], A[1]));
+        const float pz = __fmaf_rn(sb, ca[2], __fmaf_rn(sa, ba[2], A[2]));
+        float tx, ty, tz;
+        project_fp32(px, py, pz, Sx, Sy, Sz, fax, fay, fbx, fbz, tx, ty, tz);
+        const float a2 = __fmaf_rn(tx, tx, __fmul_rn(ty, ty));
+        if (!(a2 < R2) || !(tz >= -H) || !(tz < H)) continue;
+        const float u = __fmaf_rn(__fsqrt_rn(a2), scale, -0.5f);
+        const float v = __fmaf_rn(__fadd_rn(tz, H), scale, -0.5f);
+        const float cu = floorf(u), rv = floorf(v);
+        const float fu = __fsub_rn(u, cu), fv = __fsub_rn(v, rv);
+        const float gu = __fsub_rn(1.0f, fu), gv = __fsub_rn(1.0f, fv);
+        const int c = (int)cu, rr = (int)rv;
+        const bool c0 = c >= 0, c1 = c + 1 < N, r0 = rr >= 0, r1_ = rr + 1 < N;
+        if (r0 && c0) atomicAdd(img + rr * N + c, (double)__fmul_rn(gu, gv));
+        if (r0 && c1) atomicAdd(img + rr * N + c + 1, (double)__fmul_rn(fu, gv));
+        if (r1_ && c0) atomicAdd(img + (rr + 1) * N + c, (double)__fmul_rn(gu, fv));
+        if (r1_ && c1) atomicAdd(img + (rr + 1) * N + c + 1, (double)__fmul_rn(fu, fv));
+      }
+    }
+    __syncwarp();
+  };
+  const int nneigh = (2 * a.nhalf + 1) * (2 * a.nhalf + 1) * (2 * a.nhalf + 1);
+  for (int nb = 0; nb <= nneigh; ++nb) {
+    const int64_t beg = buckets[nb], end = bdup[nb];
+    for (int64_t base = beg + warp * 32; base < end; base += kSpinWarps * 32) {
+      const int64_t t = base + lane;
+      bool pass = false;
+      if (t < end) {
+        const float4 c = a.rec[4 * t];
+        const float dx = c.x - Sx, dy = c.y - Sy, dz = c.z - Sz;
+        const float z = fmaf(wx, dx, fmaf(wy, dy, wz * dz));
+        const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        const float mg = 1e-3f * a.R + 1e-5f * (fabsf(dx) + fabsf(dy) + fabsf(dz));
+        const float al = a.alpha_cull + c.w + mg;
+        pass = fabsf(z) <= a.beta_cull + c.w + mg && d2 - z * z <= al * al;
+      }
+      const unsigned bal = __ballot_sync(0xffffffffu, pass);
+      if (pass) wq[warp][qn + __popc(bal & ((1u << lane) - 1u))] = (int)t;
+      qn += __popc(bal);
+      __syncwarp();
+      if (qn >= 32) {
+        process(32);
+        const int rest = qn - 32;
+        const int moved = lane < rest ? wq[warp][32 + lane] : 0;
+        __syncwarp();
+        if (lane < rest) wq[warp][lane] = moved;
+        qn = rest;
+        __syncwarp();
+      }
+    }
+  }
+  if (qn > 0) process(qn);
+  __syncthreads();
+  for (int i = tid; i < N * N; i += kSpinWarps * 32) dst[i] = (float)img[i];
+}
+
 }  // namespace
 
 uint32_t generate_bucket_count(int64_t nt) { return bucket_count(nt); }
@@ -1405,6 +1545,40 @@ cudaError_t launch_clutter(const ClutterArgs &a, void *ws, cudaStream_t st) {
     kk.origin_base = o0;
     k_clutter<<<(unsigned)cnt, kClutterWarps * 32, 0, st>>>(kk, a.object_vertices, a.out_area_all,
                                                              a.out_area_object);
+    count_launches(1);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_spin(const SpinArgs &a, void *ws, cudaStream_t st) {
+  if (a.num_origins == 0) return cudaSuccess;
+  GenScene sc = {};
+  sc.V = a.vertices;
+  sc.Nrm = a.normals;
+  sc.tris = a.triangles;
+  sc.origins = a.origins;
+  sc.nv = a.num_vertices;
+  sc.nt = a.num_triangles;
+  sc.no = a.num_origins;
+  sc.nbuckets = bucket_count(a.num_triangles);
+  // the support cylinder of the plane: alpha <= R, |beta| <= R/2
+  const double R = a.support_radius;
+  KArgs k;
+  cudaError_t e = bin_triangles(&sc, 1, a.num_triangles, (int64_t)sc.nbuckets + 1, R, R, 0.5 * R,
+                                ws, a.status, st, k);
+  if (e != cudaSuccess) return e;
+  k.N = a.resolution;
+  k.mode = 0;
+  k.counters = nullptr;
+  const size_t smem = sizeof(double) * (size_t)a.resolution * a.resolution;
+  if ((e = cudaFuncSetAttribute(k_spin, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem)) != cudaSuccess)
+    return e;
+  for (int64_t o0 = 0; o0 < a.num_origins; o0 += 0x7fffffff) {
+    const int64_t cnt = a.num_origins - o0 < 0x7fffffff ? a.num_origins - o0 : 0x7fffffff;
+    KArgs kk = k;
+    kk.origin_base = o0;
+    k_spin<<<(unsigned)cnt, kSpinWarps * 32, smem, st>>>(kk, a.samples_side, a.out_images);
     count_launches(1);
   }
   return cudaGetLastError();

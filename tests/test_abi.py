@@ -142,3 +142,17 @@ def test_clutter_rejects_bad_arguments_on_host(lib):
                             None) == 0
     assert lib.rici_clutter_workspace_size(100) == lib.rici_generate_workspace_size(3, 100, 1, 64)
     assert lib.rici_clutter_workspace_size(-1) == -1
+
+
+def test_spin_images_reject_bad_arguments_on_host(lib):
+    dummy = ctypes.c_void_p(16)
+    # samples per side outside [1, 16], bad resolution, null output
+    for m in (0, 17):
+        assert lib.rici_spin_images(dummy, dummy, 3, dummy, 1, dummy, 1, 0.3, 64, m, dummy, None,
+                                    0, None) == 1
+    assert lib.rici_spin_images(dummy, dummy, 3, dummy, 1, dummy, 1, 0.3, 0, 3, dummy, None, 0,
+                                None) == 1
+    assert lib.rici_spin_images(dummy, dummy, 3, dummy, 1, dummy, 1, 0.3, 64, 3, None, None, 0,
+                                None) == 1
+    assert lib.rici_spin_images(dummy, dummy, 3, dummy, 1, dummy, 0, 0.3, 64, 3, None, None, 0,
+                                None) == 0
