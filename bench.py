@@ -64,7 +64,7 @@ DP4A_PER_SM_CLK = 64
 # of each origin plus a small read of triangle records, so it is the same for every launch
 # tuning).  Set to None when a kernel changes until it is captured again.
 TRAFFIC_DENSE_FULL = 1.89e9 + 5.30e6
-TRAFFIC_GEN_FULL = 62.83e6 + 900.85e6
+TRAFFIC_GEN_FULL = 63.63e6 + 901.22e6
 
 
 def parse():
