@@ -1149,12 +1149,14 @@ constexpr int kClutterMaxCells = 7 * 7 * 7 + 1;  // neighbourhoods of nhalf <= 3
 // sphere-against-cylinder pretest as generation (limits of the full cylinder), queue per warp,
 // and are evaluated 32 at a time in FP64, one per lane.  A triangle belongs to the object when
 // its first vertex index is below object_vertices.
-__global__ void __launch_bounds__(kClutterWarps * 32) k_clutter(KArgs a, int64_t object_vertices,
-                                                               double *__restrict__ out_all,
-                                                               double *__restrict__ out_obj) {
+__global__ void __launch_bounds__(kClutterWarps * 32, 5)
+    k_clutter(KArgs a, int64_t object_vertices, double *__restrict__ out_all,
+              double *__restrict__ out_obj) {
   __shared__ int buckets[kClutterMaxCells], bdup[kClutterMaxCells];
   __shared__ double fr[7];
   __shared__ int wq[kClutterWarps][64];
+  __shared__ double cq[kClutterWarps][64][9];  // projected triangles waiting to be clipped
+  __shared__ unsigned char cq_obj[kClutterWarps][64];
   __shared__ double part[kClutterWarps][2];
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t og = a.origin_base + blockIdx.x;
@@ -1192,20 +1194,69 @@ __global__ void __launch_bounds__(kClutterWarps * 32) k_clutter(KArgs a, int64_t
   const float wx = fbx * fax, wy = fbx * fay, wz = fbz;  // central axis in world coordinates
   const double R = a.R;
   double acc_all = 0.0, acc_obj = 0.0;
-  int qn = 0;  // warp-uniform queue length
+  int qn = 0;  // warp-uniform candidate queue length
+  int cn = 0;  // warp-uniform clip queue length
+  // triangles that cross the volume's boundary, 32 at a time, so that a warp's lanes all take
+  // the clipping path together
+  auto clip_batch = [&](int cnt) {
+    if (lane < cnt) {
+      double T[3][3];
+#pragma unroll
+      for (int i = 0; i < 9; ++i) T[i / 3][i % 3] = cq[warp][lane][i];
+      const double ar = support_area64(T, R);
+      acc_all += ar;
+      if (cq_obj[warp][lane]) acc_obj += ar;
+    }
+    __syncwarp();
+  };
+  // projected survivors: a triangle with its three vertices in the (convex) volume adds its
+  // whole area at once; the others queue for clipping
   auto process = [&](int cnt) {
+    bool clip = false, obj = false;
+    double T[3][3];
     if (lane < cnt) {
       const int64_t r = wq[warp][lane];
       const float4 r1 = a.rec[4 * r + 1], r2 = a.rec[4 * r + 2], r3 = a.rec[4 * r + 3];
-      double T[3][3];
       project64(r1.x, r1.y, r1.z, fr, T[0]);
       project64(r1.w, r2.x, r2.y, fr, T[1]);
       project64(r2.z, r2.w, r3.x, fr, T[2]);
-      const double ar = support_area64(T, R);
-      acc_all += ar;
-      if (__float_as_int(r3.y) < object_vertices) acc_obj += ar;
+      obj = __float_as_int(r3.y) < object_vertices;
+      bool whole = true;
+#pragma unroll
+      for (int i = 0; i < 3; ++i)
+        whole = whole && T[i][0] * T[i][0] + T[i][1] * T[i][1] <= R * R &&
+                fabs(T[i][2]) <= 0.5 * R;
+      if (whole) {
+        const double ux = T[1][0] - T[0][0], uy = T[1][1] - T[0][1], uz = T[1][2] - T[0][2];
+        const double vx = T[2][0] - T[0][0], vy = T[2][1] - T[0][1], vz = T[2][2] - T[0][2];
+        const double nx = uy * vz - uz * vy, ny = uz * vx - ux * vz, nz = ux * vy - uy * vx;
+        const double ar = 0.5 * sqrt(nx * nx + ny * ny + nz * nz);
+        acc_all += ar;
+        if (obj) acc_obj += ar;
+      } else {
+        clip = true;
+      }
     }
+    const unsigned bal = __ballot_sync(0xffffffffu, clip);
+    if (clip) {
+      const int pos = cn + __popc(bal & ((1u << lane) - 1u));
+#pragma unroll
+      for (int i = 0; i < 9; ++i) cq[warp][pos][i] = T[i / 3][i % 3];
+      cq_obj[warp][pos] = obj ? 1 : 0;
+    }
+    cn += __popc(bal);
     __syncwarp();
+    if (cn >= 32) {
+      clip_batch(32);
+      const int rest = cn - 32;  // entries 32.. move down to 0.. (sources and targets disjoint)
+      if (lane < rest) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) cq[warp][lane][i] = cq[warp][32 + lane][i];
+        cq_obj[warp][lane] = cq_obj[warp][32 + lane];
+      }
+      cn = rest;
+      __syncwarp();
+    }
   };
   const int nneigh = (2 * a.nhalf + 1) * (2 * a.nhalf + 1) * (2 * a.nhalf + 1);
   for (int nb = 0; nb <= nneigh; ++nb) {
@@ -1238,6 +1289,7 @@ __global__ void __launch_bounds__(kClutterWarps * 32) k_clutter(KArgs a, int64_t
     }
   }
   if (qn > 0) process(qn);
+  if (cn > 0) clip_batch(cn);
 #pragma unroll
   for (int d = 16; d > 0; d >>= 1) {
     acc_all += __shfl_down_sync(0xffffffffu, acc_all, d);
