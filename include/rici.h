@@ -204,6 +204,42 @@ RICI_API int crss_search_batch(const RiciSearchScene *scenes, int32_t num_scenes
                                int64_t workspace_bytes, void *stream);
 
 /*
+ * rici_batch_run — the whole path for many scenes in one call: for every scene the needle
+ * images (its target mesh alone), the haystack images (the whole scene) and the search of its
+ * needles against its own haystack.  All needle and haystack images of all scenes come from one
+ * rici_generate_batch launch sequence and the searches from one crss_search_batch sequence, in
+ * stream order, so the call can be recorded into one CUDA graph and replayed.
+ */
+typedef struct RiciBatchScene {
+  const float *vertices;   /* [num_vertices][3] the scene */
+  const float *normals;    /* [num_vertices][3] */
+  int64_t num_vertices;
+  const int32_t *triangles; /* [num_triangles][3] */
+  int64_t num_triangles;
+  int64_t target_triangles; /* the target mesh is triangles [0, target_triangles) */
+  const int32_t *needle_origins;   /* [num_needles] vertex indices (imaged with the target) */
+  int64_t num_needles;
+  const int32_t *haystack_origins; /* [num_haystack] vertex indices (imaged with the scene) */
+  int64_t num_haystack;
+  const int64_t *true_match; /* [num_needles] haystack index of needle i's match, or NULL: i */
+  uint16_t *needle_images;   /* [num_needles][N][N] caller-owned */
+  uint16_t *haystack_images; /* [num_haystack][N][N] caller-owned */
+  int32_t *out_rank;          /* [num_needles] */
+  int64_t *out_true_distance; /* [num_needles] or NULL */
+  int32_t *out_top1;          /* [num_needles] or NULL */
+} RiciBatchScene;
+
+/* Workspace for rici_batch_run: the larger of its generation and search workspaces (the two
+ * stages run one after the other on the stream and share it); -1 on invalid sizes. */
+RICI_API int64_t rici_batch_run_workspace_size(const RiciBatchScene *scenes, int32_t num_scenes,
+                                               int32_t resolution, int32_t mode);
+/* Results identical to rici_generate for each scene's needles and haystack followed by
+ * crss_search per scene; mode as for crss_search_batch. */
+RICI_API int rici_batch_run(const RiciBatchScene *scenes, int32_t num_scenes,
+                            float support_radius, int32_t resolution, int32_t mode,
+                            void *workspace, int64_t workspace_bytes, void *stream);
+
+/*
  * rici_clutter — the clutter measure of Eq. clutter (Section 4.1) per oriented point:
  * clutter = (A_all - A_object) / A_all, with A_all the surface area of the mesh inside the
  * oriented point's support volume and A_object the part of it on the object of interest.

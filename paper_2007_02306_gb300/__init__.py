@@ -7,7 +7,8 @@ with ``paper_2007_02306_gb300.build.build()``.
 from .binding import (  # noqa: F401
     GEN_DEFAULT, GEN_FP64, SEARCH_CUDA_CORE, SEARCH_DEFAULT, SEARCH_EXACT_SLOW, SEARCH_SPARSE,
     SEARCH_TENSOR, RiciError,
-    autotune_generate_batch, autotune_search_batch, clutter_areas, crss_search, crss_search_batch,
+    autotune_generate_batch, autotune_search_batch, batch_run, clutter_areas, crss_search,
+    crss_search_batch,
     get_tuning,
     load_library, rici_generate, rici_generate_batch, set_tuning, spin_images, sync_status,
     version,

@@ -53,6 +53,17 @@ class _SearchScene(ctypes.Structure):
                 ("out_true_distance", ctypes.c_void_p), ("out_top1", ctypes.c_void_p)]
 
 
+class _BatchScene(ctypes.Structure):
+    _fields_ = [("vertices", ctypes.c_void_p), ("normals", ctypes.c_void_p),
+                ("num_vertices", ctypes.c_int64), ("triangles", ctypes.c_void_p),
+                ("num_triangles", ctypes.c_int64), ("target_triangles", ctypes.c_int64),
+                ("needle_origins", ctypes.c_void_p), ("num_needles", ctypes.c_int64),
+                ("haystack_origins", ctypes.c_void_p), ("num_haystack", ctypes.c_int64),
+                ("true_match", ctypes.c_void_p), ("needle_images", ctypes.c_void_p),
+                ("haystack_images", ctypes.c_void_p), ("out_rank", ctypes.c_void_p),
+                ("out_true_distance", ctypes.c_void_p), ("out_top1", ctypes.c_void_p)]
+
+
 class RiciError(RuntimeError):
     def __init__(self, code: int, message: str):
         super().__init__(f"librici error {code}: {message}")
@@ -97,6 +108,10 @@ def load_library(path: str | None = None):
         lib.crss_search_batch_workspace_size.restype = i64
         lib.crss_search_batch.argtypes = [P, i32, i32, i32, P, i64, P]
         lib.crss_search_batch.restype = ctypes.c_int
+        lib.rici_batch_run_workspace_size.argtypes = [P, i32, i32, i32]
+        lib.rici_batch_run_workspace_size.restype = i64
+        lib.rici_batch_run.argtypes = [P, i32, f32, i32, i32, P, i64, P]
+        lib.rici_batch_run.restype = ctypes.c_int
         lib.rici_sync_status.argtypes = [P, ctypes.POINTER(i32)]
         lib.rici_sync_status.restype = ctypes.c_int
         lib.rici_release_workspace.argtypes = []
@@ -352,6 +367,76 @@ def generate_batch_workspace_bytes(scenes, resolution: int) -> int:
                            _ptr0(sc["triangles"]), sc["triangles"].shape[0], _ptr0(sc["origins"]),
                            sc["origins"].numel(), 1)
     return int(lib.rici_generate_batch_workspace_size(arr, len(scenes), int(resolution)))
+
+
+def batch_run(scenes, support_radius: float, resolution: int, *, mode: int = SEARCH_TENSOR,
+              workspace_tensor=None, outputs=None, stream=None):
+    """The whole path for several scenes in one call (rici_batch_run).
+
+    scenes: list of dicts with CUDA tensors "vertices" [V,3] f32, "normals" [V,3] f32,
+    "triangles" [T,3] i32 (the target mesh first), "needle_origins" [Q] i32, "haystack_origins"
+    [H] i32, optional "true_match" [Q] i64, and the int "target_triangles".  outputs: optional
+    list of dicts of preallocated "needle_images", "haystack_images", "rank", "true_distance",
+    "top1" (needed to replay a captured graph).  Returns the list of output dicts.
+    """
+    lib = load_library()
+    N = int(resolution)
+    arr = (_BatchScene * max(1, len(scenes)))()
+    res = []
+    for k, sc in enumerate(scenes):
+        v = _need(sc["vertices"], torch.float32, "vertices", (3,))
+        n = _need(sc["normals"], torch.float32, "normals", (3,))
+        t = _need(sc["triangles"], torch.int32, "triangles", (3,))
+        on = _need(sc["needle_origins"], torch.int32, "needle_origins")
+        oh = _need(sc["haystack_origins"], torch.int32, "haystack_origins")
+        m = sc.get("true_match")
+        if m is not None:
+            _need(m, torch.int64, "true_match")
+        Q, H = on.numel(), oh.numel()
+        if outputs is not None:
+            r = outputs[k]
+        else:
+            r = {"needle_images": torch.empty((Q, N, N), dtype=torch.uint16, device=v.device),
+                 "haystack_images": torch.empty((H, N, N), dtype=torch.uint16, device=v.device),
+                 "rank": torch.empty(Q, dtype=torch.int32, device=v.device),
+                 "true_distance": torch.empty(Q, dtype=torch.int64, device=v.device),
+                 "top1": torch.empty(Q, dtype=torch.int32, device=v.device)}
+        res.append(r)
+        arr[k] = _BatchScene(_ptr0(v), _ptr0(n), v.shape[0], _ptr0(t), t.shape[0],
+                             int(sc["target_triangles"]), _ptr0(on), Q, _ptr0(oh), H, _ptr0(m),
+                             _ptr0(r["needle_images"]), _ptr0(r["haystack_images"]),
+                             _ptr0(r["rank"]), _ptr0(r["true_distance"]), _ptr0(r["top1"]))
+    nb = lib.rici_batch_run_workspace_size(arr, len(scenes), N, int(mode))
+    if nb < 0:
+        _check(1)
+    dev = scenes[0]["vertices"].device if scenes else torch.device("cuda")
+    ws = workspace_tensor if workspace_tensor is not None else workspace(dev, nb)
+    if ws.numel() < nb:
+        raise ValueError(f"workspace_tensor needs {nb} bytes")
+    with torch.cuda.device(dev):
+        _check(lib.rici_batch_run(arr, len(scenes), float(support_radius), N, int(mode), _ptr(ws),
+                                  ws.numel(), _stream_handle(stream)))
+    return res
+
+
+def batch_run_workspace_bytes(scenes, resolution: int, outputs, mode: int = SEARCH_TENSOR) -> int:
+    """Workspace bytes ``batch_run`` needs for these scenes and preallocated ``outputs`` (to
+    size a caller workspace for graph capture)."""
+    lib = load_library()
+    N = int(resolution)
+    arr = (_BatchScene * max(1, len(scenes)))()
+    for k, (sc, r) in enumerate(zip(scenes, outputs)):
+        arr[k] = _BatchScene(_ptr0(sc["vertices"]), _ptr0(sc["normals"]), int(sc["vertices"].shape[0]),
+                             _ptr0(sc["triangles"]), int(sc["triangles"].shape[0]),
+                             int(sc["target_triangles"]), _ptr0(sc["needle_origins"]),
+                             int(sc["needle_origins"].numel()), _ptr0(sc["haystack_origins"]),
+                             int(sc["haystack_origins"].numel()), _ptr0(sc.get("true_match")),
+                             _ptr0(r["needle_images"]), _ptr0(r["haystack_images"]),
+                             _ptr0(r["rank"]), _ptr0(r.get("true_distance")), _ptr0(r.get("top1")))
+    nb = lib.rici_batch_run_workspace_size(arr, len(scenes), N, int(mode))
+    if nb < 0:
+        _check(1)
+    return nb
 
 
 def crss_search_batch(scenes, resolution: int, *, mode: int = SEARCH_TENSOR, workspace_tensor=None,

@@ -573,6 +573,76 @@ int crss_search_batch(const RiciSearchScene *scenes, int32_t num_scenes, int32_t
   return RICI_OK;
 }
 
+namespace {
+// The generation and search scene lists of a batched run: needle scenes (target alone) first,
+// then haystack scenes.
+int split_batch_run(const RiciBatchScene *scenes, int32_t num_scenes,
+                    std::vector<RiciGenerateScene> *gen, std::vector<RiciSearchScene> *srch) {
+  if (num_scenes < 0 || (num_scenes > 0 && !scenes))
+    return fail(RICI_ERR_INVALID_ARGUMENT, "bad scene array");
+  if (num_scenes > (1 << 29)) return fail(RICI_ERR_OUT_TOO_LARGE, "too many scenes");
+  gen->resize(2 * (size_t)num_scenes);
+  srch->resize((size_t)num_scenes);
+  for (int32_t i = 0; i < num_scenes; ++i) {
+    const RiciBatchScene &sc = scenes[i];
+    if (sc.target_triangles < 0 || sc.target_triangles > sc.num_triangles)
+      return fail(RICI_ERR_INVALID_ARGUMENT, "scene %d: target_triangles outside [0, %lld]", i,
+                  (long long)sc.num_triangles);
+    RiciGenerateScene &n = (*gen)[i];
+    n.vertices = sc.vertices;
+    n.normals = sc.normals;
+    n.num_vertices = sc.num_vertices;
+    n.triangles = sc.triangles;
+    n.num_triangles = sc.target_triangles;
+    n.origins = sc.needle_origins;
+    n.num_origins = sc.num_needles;
+    n.out_images = sc.needle_images;
+    RiciGenerateScene &h = (*gen)[num_scenes + i];
+    h = n;
+    h.num_triangles = sc.num_triangles;
+    h.origins = sc.haystack_origins;
+    h.num_origins = sc.num_haystack;
+    h.out_images = sc.haystack_images;
+    RiciSearchScene &q = (*srch)[i];
+    q.needles = sc.needle_images;
+    q.num_needles = sc.num_needles;
+    q.haystack = sc.haystack_images;
+    q.num_haystack = sc.num_haystack;
+    q.true_match = sc.true_match;
+    q.out_rank = sc.out_rank;
+    q.out_true_distance = sc.out_true_distance;
+    q.out_top1 = sc.out_top1;
+  }
+  return RICI_OK;
+}
+}  // namespace
+
+int64_t rici_batch_run_workspace_size(const RiciBatchScene *scenes, int32_t num_scenes,
+                                      int32_t resolution, int32_t mode) {
+  std::vector<RiciGenerateScene> gen;
+  std::vector<RiciSearchScene> srch;
+  if (split_batch_run(scenes, num_scenes, &gen, &srch)) return -1;
+  const int64_t g = rici_generate_batch_workspace_size(gen.data(), 2 * num_scenes, resolution);
+  const int64_t q = crss_search_batch_workspace_size(srch.data(), num_scenes, resolution, mode);
+  if (g < 0 || q < 0) return -1;
+  return g > q ? g : q;
+}
+
+int rici_batch_run(const RiciBatchScene *scenes, int32_t num_scenes, float support_radius,
+                   int32_t resolution, int32_t mode, void *workspace, int64_t workspace_bytes,
+                   void *stream) {
+  t_last_error.clear();
+  std::vector<RiciGenerateScene> gen;
+  std::vector<RiciSearchScene> srch;
+  int rc = split_batch_run(scenes, num_scenes, &gen, &srch);
+  if (rc) return rc;
+  if ((rc = rici_generate_batch(gen.data(), 2 * num_scenes, support_radius, resolution,
+                                workspace, workspace_bytes, stream)))
+    return rc;
+  return crss_search_batch(srch.data(), num_scenes, resolution, mode, workspace, workspace_bytes,
+                           stream);
+}
+
 int rici_sync_status(void *stream, int32_t *device_status) {
   DeviceState *d = nullptr;
   int rc;

@@ -156,3 +156,21 @@ def test_spin_images_reject_bad_arguments_on_host(lib):
                                 None) == 1
     assert lib.rici_spin_images(dummy, dummy, 3, dummy, 1, dummy, 0, 0.3, 64, 3, None, None, 0,
                                 None) == 0
+
+
+def test_batch_run_rejects_bad_scenes_on_host(lib):
+    from paper_2007_02306_gb300 import binding
+
+    arr = (binding._BatchScene * 1)()
+    arr[0] = binding._BatchScene(16, 16, 3, 16, 1, 2, 16, 1, 16, 1, None, 16, 16, 16, None, None)
+    # target_triangles larger than the scene's triangle count
+    assert lib.rici_batch_run(arr, 1, 0.3, 64, 3, None, 0, None) == 1
+    assert lib.rici_batch_run_workspace_size(arr, 1, 64, 3) == -1
+    # null scene array with scenes, negative scene count
+    assert lib.rici_batch_run(None, 1, 0.3, 64, 3, None, 0, None) == 1
+    assert lib.rici_batch_run(arr, -1, 0.3, 64, 3, None, 0, None) == 1
+    # bad resolution and support radius reach the generation checks
+    arr[0] = binding._BatchScene(16, 16, 3, 16, 1, 1, 16, 1, 16, 1, None, 16, 16, 16, None, None)
+    assert lib.rici_batch_run(arr, 1, 0.3, 0, 3, None, 0, None) == 1
+    assert lib.rici_batch_run(arr, 1, -1.0, 64, 3, None, 0, None) == 1
+    assert lib.rici_batch_run(arr, 0, 0.3, 64, 3, None, 0, None) == 0

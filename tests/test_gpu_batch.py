@@ -139,3 +139,57 @@ def test_batch_run_replays_from_a_cuda_graph(rici, batch):
                 assert torch.equal(r0[k], r1[k]), k
         for a, b2 in zip(imgs, gen_outs):
             assert torch.equal(a.view(torch.int16), b2.view(torch.int16))
+
+
+def run_single_call(rici, b, ws=None, outputs=None):
+    scenes = [{"vertices": x["V"], "normals": x["Nrm"], "triangles": x["T"],
+               "target_triangles": x["scene"].target_triangles, "needle_origins": x["on"],
+               "haystack_origins": x["oh"], "true_match": x["match"]} for x in b]
+    return rici.batch_run(scenes, R, N, workspace_tensor=ws, outputs=outputs), scenes
+
+
+def test_single_call_batch_run_equals_the_two_batched_calls(rici, batch):
+    imgs, res = run_batch(rici, batch)
+    one, _ = run_single_call(rici, batch)
+    assert rici.sync_status() == 0
+    for i in range(len(batch)):
+        assert np.array_equal(host_u16(one[i]["needle_images"]), host_u16(imgs[2 * i]))
+        assert np.array_equal(host_u16(one[i]["haystack_images"]), host_u16(imgs[2 * i + 1]))
+        for k in ("rank", "true_distance", "top1"):
+            assert torch_equal(one[i][k], res[i][k]), (i, k)
+
+
+def torch_equal(a, b):
+    import torch
+
+    return bool(torch.equal(a, b))
+
+
+def test_single_call_batch_run_replays_from_a_cuda_graph(rici, batch):
+    import torch
+
+    ref, scenes = run_single_call(rici, batch)
+    torch.cuda.synchronize()
+    ref = [{k: v.clone() for k, v in r.items()} for r in ref]
+    outs = [{k: torch.empty_like(v) for k, v in r.items()} for r in ref]
+    nb = rici.binding.batch_run_workspace_bytes(scenes, N, outs)
+    ws = torch.empty(nb + 256, dtype=torch.uint8, device="cuda")
+    ws = ws[(-ws.data_ptr()) % 256:]
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        run_single_call(rici, batch, ws, outs)  # warm-up on the capture stream
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        run_single_call(rici, batch, ws, outs)
+    for o in outs:
+        for v in o.values():
+            v.fill_(7)
+    g.replay()
+    torch.cuda.synchronize()
+    assert rici.sync_status() == 0
+    for r0, r1 in zip(ref, outs):
+        for k in r0:
+            assert torch.equal(r0[k], r1[k]), k
