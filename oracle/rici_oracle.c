@@ -681,8 +681,10 @@ int oracle_clutter_areas(const float *vertices, const float *normals, int64_t nu
  *   fu = u - c, fv = v - r: (1-fu)(1-fv) to (r, c), fu (1-fv) to (r, c+1), (1-fu) fv to
  *   (r+1, c), fu fv to (r+1, c+1); weight that falls on a bin outside [0, N) is dropped.
  * The support-angle filter is not applied (Section 4.2 found it does not help).  Every float
- * operation is written out in the order the GPU uses (projection as oracle_project_fp32); the
- * weights are summed in FP64 and the image is stored in float32.
+ * operation is written out in the order the GPU uses (projection as oracle_project_fp32).
+ * Reading: each weight is accumulated as an integer number of units of 2^-24 (w * 2^24 rounded
+ * to the nearest integer), so a bin's sum is exact and does not depend on the order of the
+ * samples; the image stores float32(sum * 2^-24).
  * ---------------------------------------------------------------------------------------- */
 
 /* Barycentric weights (a, b) of sample k of m^2 (upward sub-triangles first). */
@@ -742,7 +744,7 @@ int oracle_spin_images(const float *vertices, const float *normals, int64_t num_
 #pragma omp parallel
 #endif
     {
-        double *img = (double *)malloc(sizeof(double) * (size_t)N * (size_t)N);
+        uint64_t *img = (uint64_t *)malloc(sizeof(uint64_t) * (size_t)N * (size_t)N);
         if (!img) {
 #ifdef _OPENMP
 #pragma omp atomic write
@@ -753,7 +755,7 @@ int oracle_spin_images(const float *vertices, const float *normals, int64_t num_
 #pragma omp for schedule(dynamic, 1)
 #endif
             for (int64_t o = 0; o < num_origins; o++) {
-                memset(img, 0, sizeof(double) * (size_t)N * (size_t)N);
+                memset(img, 0, sizeof(uint64_t) * (size_t)N * (size_t)N);
                 const int32_t sv = origins[o];
                 const float S[3] = {vertices[3 * sv], vertices[3 * sv + 1], vertices[3 * sv + 2]};
                 double Nax, Nay, Nbx, Nbz;
@@ -782,12 +784,13 @@ int oracle_spin_images(const float *vertices, const float *normals, int64_t num_
                         for (int q = 0; q < 4; q++) {
                             const int rr = r + (q >> 1), cc = c + (q & 1);
                             if (rr >= 0 && rr < N && cc >= 0 && cc < N)
-                                img[(int64_t)rr * N + cc] += (double)w[q];
+                                img[(int64_t)rr * N + cc] += (uint64_t)rintf(w[q] * 16777216.0f);
                         }
                     }
                 }
                 float *dst = out_images + o * (int64_t)N * N;
-                for (int64_t k = 0; k < (int64_t)N * N; k++) dst[k] = (float)img[k];
+                for (int64_t k = 0; k < (int64_t)N * N; k++)
+                    dst[k] = (float)((double)img[k] * (1.0 / 16777216.0));
             }
             free(img);
         }

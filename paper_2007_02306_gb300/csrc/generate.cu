@@ -1321,7 +1321,9 @@ __global__ void __launch_bounds__(kClutterWarps * 32, 5)
 // height, N x N bins centred at alpha_c = (c + 1/2) R/N and beta_r = (r + 1/2 - N/2) R/N; a
 // sample with alpha^2 < R^2 and -R/2 <= beta < R/2 adds bilinear weights to the four bins around
 // it (weight on a bin outside the image is dropped).  Weights are formed in FP32 with explicit
-// roundings and summed in FP64 in shared memory; the image is stored as float32.
+// roundings and summed exactly as integers in units of 2^-24 (w * 2^24 rounded to the nearest
+// integer) in shared memory, so the sums do not depend on the order of the samples; the image
+// stores float32(sum * 2^-24).
 constexpr int kSpinWarps = 4;
 constexpr int kSpinMaxSide = 16;  // samples per triangle <= 256
 
@@ -1332,7 +1334,7 @@ __global__ void __launch_bounds__(kSpinWarps * 32) k_spin(KArgs a, int m, float 
   __shared__ float smp_a[kSpinMaxSide * kSpinMaxSide], smp_b[kSpinMaxSide * kSpinMaxSide];
   __shared__ int wq[kSpinWarps][64];
   const int N = a.N;
-  double *img = reinterpret_cast<double *>(spin_smem);
+  unsigned long long *img = reinterpret_cast<unsigned long long *>(spin_smem);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t og = a.origin_base + blockIdx.x;
   const GenScene &sc = a.tab[scene_of_origin(a.tab, a.num_scenes, og)];
@@ -1356,7 +1358,7 @@ __global__ void __launch_bounds__(kSpinWarps * 32) k_spin(KArgs a, int m, float 
     for (int i = tid; i < N * N; i += kSpinWarps * 32) dst[i] = 0.0f;
     return;
   }
-  for (int i = tid; i < N * N; i += kSpinWarps * 32) img[i] = 0.0;
+  for (int i = tid; i < N * N; i += kSpinWarps * 32) img[i] = 0ull;
   if (tid == 0) {
     fr[0] = Sx;
     fr[1] = Sy;
@@ -1408,10 +1410,16 @@ __global__ void __launch_bounds__(kSpinWarps * 32) k_spin(KArgs a, int m, float 
         const float gu = __fsub_rn(1.0f, fu), gv = __fsub_rn(1.0f, fv);
         const int c = (int)cu, rr = (int)rv;
         const bool c0 = c >= 0, c1 = c + 1 < N, r0 = rr >= 0, r1_ = rr + 1 < N;
-        if (r0 && c0) atomicAdd(img + rr * N + c, (double)__fmul_rn(gu, gv));
-        if (r0 && c1) atomicAdd(img + rr * N + c + 1, (double)__fmul_rn(fu, gv));
-        if (r1_ && c0) atomicAdd(img + (rr + 1) * N + c, (double)__fmul_rn(gu, fv));
-        if (r1_ && c1) atomicAdd(img + (rr + 1) * N + c + 1, (double)__fmul_rn(fu, fv));
+        constexpr float kUnit = 16777216.0f;  // 2^24 units per sample
+        if (r0 && c0)
+          atomicAdd(img + rr * N + c, __float2ull_rn(__fmul_rn(__fmul_rn(gu, gv), kUnit)));
+        if (r0 && c1)
+          atomicAdd(img + rr * N + c + 1, __float2ull_rn(__fmul_rn(__fmul_rn(fu, gv), kUnit)));
+        if (r1_ && c0)
+          atomicAdd(img + (rr + 1) * N + c, __float2ull_rn(__fmul_rn(__fmul_rn(gu, fv), kUnit)));
+        if (r1_ && c1)
+          atomicAdd(img + (rr + 1) * N + c + 1,
+                    __float2ull_rn(__fmul_rn(__fmul_rn(fu, fv), kUnit)));
       }
     }
     __syncwarp();
@@ -1448,7 +1456,8 @@ __global__ void __launch_bounds__(kSpinWarps * 32) k_spin(KArgs a, int m, float 
   }
   if (qn > 0) process(qn);
   __syncthreads();
-  for (int i = tid; i < N * N; i += kSpinWarps * 32) dst[i] = (float)img[i];
+  for (int i = tid; i < N * N; i += kSpinWarps * 32)
+    dst[i] = __double2float_rn(__dmul_rn(__ull2double_rn(img[i]), 1.0 / 16777216.0));
 }
 
 }  // namespace
@@ -1622,7 +1631,7 @@ cudaError_t launch_spin(const SpinArgs &a, void *ws, cudaStream_t st) {
   k.N = a.resolution;
   k.mode = 0;
   k.counters = nullptr;
-  const size_t smem = sizeof(double) * (size_t)a.resolution * a.resolution;
+  const size_t smem = sizeof(unsigned long long) * (size_t)a.resolution * a.resolution;
   if ((e = cudaFuncSetAttribute(k_spin, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)smem)) != cudaSuccess)
     return e;
