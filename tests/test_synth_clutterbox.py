@@ -42,3 +42,32 @@ def test_seeded_and_rejects_a_box_too_small_for_a_unit_sphere():
     assert all(np.array_equal(x.vertices, y.vertices) for x, y in zip(a, b))
     with pytest.raises(ValueError):
         synth.scenes.clutterbox(seed=5, n=3, box_side=1.5)
+
+
+def test_histograms_and_heatmaps_on_the_host():
+    """The driver's host-side binning: rank histograms, rank-0 fractions, clutter fractions and
+    the clutter-versus-rank heatmap (no GPU: device results are stood in for by CPU tensors)."""
+    import torch
+
+    from paper_2007_02306_gb300 import clutterbox
+
+    prep = {"sizes": [[4, 200]]}  # one run: level 1 (4 reference vertices), level 2 (200 images)
+    results = [{"rank": torch.tensor([0, 0, 0, 0], dtype=torch.int32)},
+               {"rank": torch.tensor([0, 3, 0, 120], dtype=torch.int32)}]
+    a_all = torch.tensor([1.0, 2.0, 4.0, 1.0], dtype=torch.float64)
+    areas = [(a_all, a_all.clone()),
+             (a_all, torch.tensor([1.0, 1.0, 0.4, 0.05], dtype=torch.float64))]
+    h = clutterbox.histograms(prep, results, areas, clutter_bins=10)[0]
+    assert h["rank0_fraction"] == [1.0, 0.5]
+    hist = h["histograms"][1]
+    assert hist.size == 200 and hist.sum() == 4
+    assert hist[0] == 2 and hist[3] == 1 and hist[120] == 1
+    np.testing.assert_allclose(h["clutter"][0], 0.0)
+    np.testing.assert_allclose(h["clutter"][1], [0.0, 0.5, 0.9, 0.95])
+    heat = h["heatmap"][1]
+    assert heat.shape == (10, len(clutterbox.RANK_EDGES) - 1)
+    assert heat.sum() == 4
+    assert heat[0, 0] == 1      # clutter 0, rank 0
+    assert heat[5, 2] == 1      # clutter 0.5, rank 3 (bin 2-4)
+    assert heat[9, 0] == 1      # clutter 0.9, rank 0
+    assert heat[9, 7] == 1      # clutter 0.95, rank 120 (bin 100-999)
