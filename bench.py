@@ -63,7 +63,7 @@ DP4A_PER_SM_CLK = 64
 # size: k_dense (the search) and k_generate (the haystack images; its traffic is the 8 KB image
 # of each origin plus a small read of triangle records, so it is the same for every launch
 # tuning).  Set to None when a kernel changes until it is captured again.
-TRAFFIC_DENSE_FULL = 1.89e9 + 5.30e6
+TRAFFIC_DENSE_FULL = 1.90e9 + 5.01e6
 TRAFFIC_GEN_FULL = 63.63e6 + 901.22e6
 
 

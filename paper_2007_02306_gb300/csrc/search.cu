@@ -298,10 +298,12 @@ __global__ void __launch_bounds__(kDenseThreads, (N * kImg <= 64 ? 4 : 2) * 256 
     const int64_t j0 = ht * kTile + (int64_t)warp * (32 * kImg) + lane;
     int acc[kImg][kTQ];  // partial distance minus the needle's true distance (exit once > 0)
     unsigned alive[kImg];
+    unsigned inrange = 0;  // images of this thread inside the haystack (their rows are loaded)
 #pragma unroll
     for (int k = 0; k < kImg; ++k) {
       const int64_t j = j0 + 32 * k;
       const bool valid = j < H && !hwide[j];
+      if (j < H) inrange |= 1u << k;
       alive[k] = 0;
 #pragma unroll
       for (int q = 0; q < kTQ; ++q) {
@@ -333,7 +335,9 @@ __global__ void __launch_bounds__(kDenseThreads, (N * kImg <= 64 ? 4 : 2) * 256 
       const unsigned wuse = __reduce_or_sync(0xffffffffu, uor);  // needles any lane still needs
 #pragma unroll
       for (int k = 0; k < kImg; ++k) {
-        if (use[k]) {
+        // every row of an image inside the haystack is loaded, even once its pairs have all
+        // exited: a uniform load is cheaper than the divergent branch that would skip it
+        if ((inrange >> k) & 1u) {
           const int *src = hgrp + k * kGroupWords + r * (WPR * 32);
 #pragma unroll
           for (int v = 0; v < WPR / CW; ++v) {
