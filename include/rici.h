@@ -278,8 +278,11 @@ RICI_API int rici_clutter(const float *vertices, const float *normals, int64_t n
  *              alpha_c = (c + 1/2) R/N, beta_r = (r + 1/2 - N/2) R/N; each sample with
  *              alpha^2 < R^2 and -R/2 <= beta < R/2 adds bilinear weights to the four bins
  *              around it (weight on a bin outside the image is dropped).  No support-angle
- *              filter.  Weights are formed in FP32 in a fixed order and summed exactly as
- *              integers in units of 2^-24 (independent of the order of the samples).
+ *              filter.  The definition sums the weights as real numbers; this call forms
+ *              positions, projection and weights in FP32 in a fixed order and sums each weight
+ *              exactly as an integer number of units of 2^-24 (rounding error <= 2^-25 per
+ *              weight; the sums do not depend on the order of the samples), so each bin differs
+ *              from the FP64 definition by at most the rounding of those FP32 steps.
  * Workspace: rici_clutter_workspace_size bytes (the same grid), or NULL.
  * Errors: as rici_generate (a zero image for an oriented point with a bad index or a
  * non-finite coordinate).

@@ -65,8 +65,12 @@ def _load():
             lib.oracle_clutter_areas.restype = ctypes.c_int
             lib.oracle_spin_samples.argtypes = [P, i64, P, i64, i32, P]
             lib.oracle_spin_samples.restype = ctypes.c_int
-            lib.oracle_spin_images.argtypes = [P, P, i64, P, i64, P, i64, f32, i32, i32, P, i32]
-            lib.oracle_spin_images.restype = ctypes.c_int
+            lib.oracle_spin_images_fp32.argtypes = [P, P, i64, P, i64, P, i64, f32, i32, i32, P,
+                                                    i32]
+            lib.oracle_spin_images_fp32.restype = ctypes.c_int
+            lib.oracle_spin_images_fp64.argtypes = [P, P, i64, P, i64, P, i64, f32, i32, i32, P,
+                                                    P, i32]
+            lib.oracle_spin_images_fp64.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -219,20 +223,46 @@ def spin_samples(vertices, triangles, m: int):
     return out
 
 
-def spin_images(vertices, normals, triangles, origins, support_radius: float, resolution: int,
-                m: int = 3, num_threads: int = 0):
-    """Spin images (Section 2.1) of the oriented points from m^2 samples per triangle, bilinear
-    weights around the bin centres, float32 [O, N, N] (row = beta bin, column = alpha bin)."""
-    lib = _load()
+def _spin_args(vertices, normals, triangles, origins):
     v = np.ascontiguousarray(vertices, dtype=np.float32).reshape(-1, 3)
     n = np.ascontiguousarray(normals, dtype=np.float32).reshape(-1, 3)
     t = np.ascontiguousarray(triangles, dtype=np.int32).reshape(-1, 3)
     o = np.ascontiguousarray(origins, dtype=np.int32).reshape(-1)
+    return v, n, t, o
+
+
+def spin_images(vertices, normals, triangles, origins, support_radius: float, resolution: int,
+                m: int = 3, num_threads: int = 0, return_bound: bool = False):
+    """Spin images (Section 2.1) of the oriented points from m^2 samples per triangle: sample
+    positions, projection and bilinear weights around the bin centres in FP64, summed in FP64
+    and rounded once to float32 [O, N, N] (row = beta bin, column = alpha bin).
+
+    With ``return_bound`` also a float64 [O, N, N] bound on how far a single-precision
+    evaluation of the same definition may lie from each bin (derivation in rici_oracle.c)."""
+    lib = _load()
+    v, n, t, o = _spin_args(vertices, normals, triangles, origins)
     N = int(resolution)
     out = np.zeros((o.shape[0], N, N), np.float32)
-    rc = lib.oracle_spin_images(_ptr(v), _ptr(n), v.shape[0], _ptr(t), t.shape[0], _ptr(o),
-                                o.shape[0], float(support_radius), N, int(m), _ptr(out),
-                                int(num_threads))
+    bound = np.zeros((o.shape[0], N, N), np.float64) if return_bound else None
+    rc = lib.oracle_spin_images_fp64(_ptr(v), _ptr(n), v.shape[0], _ptr(t), t.shape[0], _ptr(o),
+                                     o.shape[0], float(support_radius), N, int(m), _ptr(out),
+                                     _ptr(bound), int(num_threads))
     if rc != 0:
-        raise ValueError(f"oracle_spin_images failed with status {rc}")
+        raise ValueError(f"oracle_spin_images_fp64 failed with status {rc}")
+    return (out, bound) if return_bound else out
+
+
+def spin_images_fp32(vertices, normals, triangles, origins, support_radius: float,
+                     resolution: int, m: int = 3, num_threads: int = 0):
+    """Single-precision same-operation-order mode of ``spin_images``: every operation in FP32 in
+    one fixed order, weights summed exactly as integers in units of 2^-24, float32 [O, N, N]."""
+    lib = _load()
+    v, n, t, o = _spin_args(vertices, normals, triangles, origins)
+    N = int(resolution)
+    out = np.zeros((o.shape[0], N, N), np.float32)
+    rc = lib.oracle_spin_images_fp32(_ptr(v), _ptr(n), v.shape[0], _ptr(t), t.shape[0], _ptr(o),
+                                     o.shape[0], float(support_radius), N, int(m), _ptr(out),
+                                     int(num_threads))
+    if rc != 0:
+        raise ValueError(f"oracle_spin_images_fp32 failed with status {rc}")
     return out

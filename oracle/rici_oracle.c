@@ -33,8 +33,11 @@
  *  - oracle_clutter_areas: per oriented point, the surface area inside its support volume and
  *    the part of it that belongs to the object of interest (Eq. clutter), brute force over
  *    every triangle (see the comment above that function).
- *  - oracle_spin_samples / oracle_spin_images: spin images (Section 2.1) from m^2 point samples
- *    per triangle, single precision in a fixed order (see the comment above those functions).
+ *  - oracle_spin_images_fp64: spin images (Section 2.1) from m^2 point samples per triangle,
+ *    FP64 positions, projection and bilinear weights summed in FP64, with a per-bin bound on
+ *    the deviation of a single-precision evaluation; oracle_spin_samples /
+ *    oracle_spin_images_fp32: the samples and a single-precision same-order mode with weights
+ *    summed as integers in units of 2^-24 (see the comments above those functions).
  *
  * Readings where the paper is silent or garbled (each listed with its reason in the design
  * notes):
@@ -665,7 +668,9 @@ int oracle_clutter_areas(const float *vertices, const float *normals, int64_t nu
 
 /* ------------------------------------------------------------------------------------------
  * Spin images (Section 2.1: the descriptor the RICI is compared with), generated from point
- * samples of the mesh with the projection of Section 3.1.1, in single precision.
+ * samples of the mesh with the projection of Section 3.1.1.  oracle_spin_images_fp64 (further
+ * below) is the definition; oracle_spin_images_fp32 is a single-precision same-operation-order
+ * mode, a second check of a GPU evaluation's arithmetic, itself pinned to the FP64 definition.
  *
  * Samples: m^2 points per triangle (A, B, C in its own vertex order), the centroids of the m^2
  * congruent triangles obtained by dividing every side into m parts, so the samples are spread
@@ -680,11 +685,12 @@ int oracle_clutter_areas(const float *vertices, const float *normals, int64_t nu
  *   u = alpha N/R - 1/2, v = (beta + R/2) N/R - 1/2, c = floor(u), r = floor(v),
  *   fu = u - c, fv = v - r: (1-fu)(1-fv) to (r, c), fu (1-fv) to (r, c+1), (1-fu) fv to
  *   (r+1, c), fu fv to (r+1, c+1); weight that falls on a bin outside [0, N) is dropped.
- * The support-angle filter is not applied (Section 4.2 found it does not help).  Every float
- * operation is written out in the order the GPU uses (projection as oracle_project_fp32).
- * Reading: each weight is accumulated as an integer number of units of 2^-24 (w * 2^24 rounded
- * to the nearest integer), so a bin's sum is exact and does not depend on the order of the
- * samples; the image stores float32(sum * 2^-24).
+ * The support-angle filter is not applied (Section 4.2 found it does not help).
+ * FP32 mode: every float operation is written out in one fixed order (projection as
+ * oracle_project_fp32), and each weight is accumulated as an integer number of units of 2^-24
+ * (w * 2^24 rounded to the nearest integer), so a bin's sum is exact and does not depend on the
+ * order of the samples; the image stores float32(sum * 2^-24).  This quantisation belongs to
+ * the single-precision mode only, not to the definition.
  * ---------------------------------------------------------------------------------------- */
 
 /* Barycentric weights (a, b) of sample k of m^2 (upward sub-triangles first). */
@@ -724,10 +730,11 @@ int oracle_spin_samples(const float *vertices, int64_t num_vertices, const int32
     return ORACLE_OK;
 }
 
-int oracle_spin_images(const float *vertices, const float *normals, int64_t num_vertices,
-                       const int32_t *triangles, int64_t num_triangles, const int32_t *origins,
-                       int64_t num_origins, float support_radius, int32_t resolution, int32_t m,
-                       float *out_images, int32_t num_threads) {
+int oracle_spin_images_fp32(const float *vertices, const float *normals, int64_t num_vertices,
+                            const int32_t *triangles, int64_t num_triangles,
+                            const int32_t *origins, int64_t num_origins, float support_radius,
+                            int32_t resolution, int32_t m, float *out_images,
+                            int32_t num_threads) {
     const int32_t N = resolution;
     if (N < 1 || N > 1024 || m < 1 || m > 16 || !(support_radius > 0.0f) || num_vertices < 0 ||
         num_triangles < 0 || num_origins < 0)
@@ -794,6 +801,187 @@ int oracle_spin_images(const float *vertices, const float *normals, int64_t num_
             }
             free(img);
         }
+    }
+    return status;
+}
+
+/* ------------------------------------------------------------------------------------------
+ * Spin images in FP64: the definition of Section 2.1 with the sample pattern above, evaluated
+ * in double precision throughout and summed as real numbers.
+ *
+ *   samples   P = A + a (B - A) + b (C - A) with the barycentric weights a = (3i + off)/(3m),
+ *             b = (3j + off)/(3m) of oracle_spin_samples, in double;
+ *   frame     Eq. rotationCoefficients in double (frame_coefficients);
+ *   projection Eqs. relativeLocation, firstRotation, secondRotation in double (project_point's
+ *             arithmetic on the double sample);
+ *   volume    alpha^2 < R^2 and -R/2 <= beta < R/2;
+ *   weights   bilinear around the bin centres (readings (1)-(2)): u = alpha N/R - 1/2,
+ *             v = (beta + R/2) N/R - 1/2, (1-fu)(1-fv), fu(1-fv), (1-fu)fv, fu fv on the bins
+ *             (r, c), (r, c+1), (r+1, c), (r+1, c+1), c = floor(u), r = floor(v); weight on a bin
+ *             outside the image is dropped;
+ *   image     the double sum of the weights, rounded once to float.
+ *
+ * out_bound (optional, [O][N][N] double) receives, per bin, a bound on how far an evaluation of
+ * the same definition in single precision may lie from this image: each sample position, the
+ * projection, alpha = sqrt(Tx^2 + Ty^2), u and v formed in FP32 (one rounding per operation,
+ * fused multiply-adds where the single-precision form uses them, the frame coefficients rounded
+ * from FP64 to FP32), each weight rounded to a multiple of 2^-24, and the bin sums rounded to
+ * float.  For one sample, with unit roundoff u32 = 2^-24:
+ *   dP_d  <= u32 (|P_d| + |A_d + a (B_d - A_d)| + 2 a |B_d - A_d| + 2 b |C_d - A_d|)
+ *            (a and b rounded, B - A and C - A rounded, two fused multiply-adds);
+ *   dT    <= 10 u32 (|d_x| + |d_y| + |d_z|) + sum_d dP_d with d = P - S (the projection bound of
+ *            the FP32 mode, pinned by the tests, plus the position error carried through the
+ *            rotation, whose rows have unit length);
+ *   dA2   <= 2 (|Tx| + |Ty|) dT + 2 dT^2 + 2 u32 alpha^2  (alpha^2 = Tx^2 + Ty^2);
+ *   dAl   <= min(sqrt(dA2), dA2 / alpha) + u32 alpha;
+ *   du    <= s dAl + 2 u32 s alpha + u32 |u|,  s = N/R;
+ *   dv    <= s (dT + u32 |beta + R/2|) + u32 s |beta + R/2| + u32 |v|;
+ *   dw    <= du + dv + du dv + 3 u32 + 2^-25  (|d w / d fu| <= 1 and |d w / d fv| <= 1; two
+ *            roundings in 1 - f and one in the product; the 2^-24 quantisation).
+ * Twice dw is added to every bin the sample can reach in either evaluation (floor(u - du) ..
+ * floor(u + du) + 1, and the same for v).  A sample that may fall on the other side of the
+ * volume boundary in single precision (|alpha^2 - R^2| <= 2 (dA2 + u32 R^2), or beta within
+ * 2 dT of -R/2 or R/2) adds 1 (the largest weight) to each bin it can reach instead.  Finally
+ * 2^-23 |image| covers the two roundings of a bin sum to float.
+ * ---------------------------------------------------------------------------------------- */
+static void spin_sample_index(int m, int k, int *i_out, int *j_out, int *off_out) {
+    const int up = m * (m + 1) / 2;
+    int idx = k < up ? k : k - up;
+    const int rows = k < up ? m : m - 1;
+    int i = 0;
+    while (idx >= rows - i) {
+        idx -= rows - i;
+        i++;
+    }
+    *i_out = i;
+    *j_out = idx;
+    *off_out = k < up ? 1 : 2;
+}
+
+int oracle_spin_images_fp64(const float *vertices, const float *normals, int64_t num_vertices,
+                            const int32_t *triangles, int64_t num_triangles,
+                            const int32_t *origins, int64_t num_origins, float support_radius,
+                            int32_t resolution, int32_t m, float *out_images, double *out_bound,
+                            int32_t num_threads) {
+    const int32_t N = resolution;
+    if (N < 1 || N > 1024 || m < 1 || m > 16 || !(support_radius > 0.0f) || num_vertices < 0 ||
+        num_triangles < 0 || num_origins < 0)
+        return ORACLE_BAD_ARGUMENT;
+    for (int64_t t = 0; t < 3 * num_triangles; t++)
+        if (triangles[t] < 0 || triangles[t] >= num_vertices) return ORACLE_BAD_INDEX;
+    for (int64_t o = 0; o < num_origins; o++)
+        if (origins[o] < 0 || origins[o] >= num_vertices) return ORACLE_BAD_INDEX;
+    const double R = (double)support_radius;
+    const double R2 = R * R, H = 0.5 * R, s = (double)N / R;
+    const double u32 = 1.0 / 16777216.0;
+    const int64_t NN = (int64_t)N * N;
+    int status = ORACLE_OK;
+#ifdef _OPENMP
+    if (num_threads > 0) omp_set_num_threads(num_threads);
+#pragma omp parallel
+#endif
+    {
+        double *img = (double *)malloc(sizeof(double) * (size_t)NN);
+        double *bnd = (double *)malloc(sizeof(double) * (size_t)NN);
+        if (!img || !bnd) {
+#ifdef _OPENMP
+#pragma omp atomic write
+#endif
+            status = ORACLE_NO_MEMORY;
+        } else {
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 1)
+#endif
+            for (int64_t o = 0; o < num_origins; o++) {
+                memset(img, 0, sizeof(double) * (size_t)NN);
+                memset(bnd, 0, sizeof(double) * (size_t)NN);
+                const int32_t sv = origins[o];
+                const double S[3] = {vertices[3 * sv], vertices[3 * sv + 1], vertices[3 * sv + 2]};
+                double Nax, Nay, Nbx, Nbz;
+                frame_coefficients(normals[3 * sv], normals[3 * sv + 1], normals[3 * sv + 2],
+                                   &Nax, &Nay, &Nbx, &Nbz);
+                for (int64_t t = 0; t < num_triangles; t++) {
+                    const float *A = vertices + 3 * (int64_t)triangles[3 * t];
+                    const float *B = vertices + 3 * (int64_t)triangles[3 * t + 1];
+                    const float *C = vertices + 3 * (int64_t)triangles[3 * t + 2];
+                    for (int k = 0; k < m * m; k++) {
+                        int si, sj, off;
+                        spin_sample_index(m, k, &si, &sj, &off);
+                        const double a = (double)(3 * si + off) / (double)(3 * m);
+                        const double b = (double)(3 * sj + off) / (double)(3 * m);
+                        double P[3], dP = 0.0, dsum = 0.0;
+                        for (int d = 0; d < 3; d++) {
+                            const double ba = (double)B[d] - (double)A[d];
+                            const double ca = (double)C[d] - (double)A[d];
+                            const double inner = (double)A[d] + a * ba;
+                            P[d] = inner + b * ca;
+                            dP += u32 * (fabs(P[d]) + fabs(inner) + 2.0 * a * fabs(ba) +
+                                         2.0 * b * fabs(ca));
+                            dsum += fabs(P[d] - S[d]);
+                        }
+                        /* Eqs. relativeLocation, firstRotation, secondRotation */
+                        const double px = P[0] - S[0], py = P[1] - S[1], pz = P[2] - S[2];
+                        const double qx = Nax * px + Nay * py;
+                        const double qy = (-Nay) * px + Nax * py;
+                        const double Tx = Nbz * qx - Nbx * pz;
+                        const double Ty = qy;
+                        const double Tz = Nbx * qx + Nbz * pz;
+                        const double alpha2 = Tx * Tx + Ty * Ty;
+                        const int inside = alpha2 < R2 && Tz >= -H && Tz < H;
+                        /* single-precision deviation of this sample (comment above) */
+                        const double dT = 10.0 * u32 * dsum + dP;
+                        const double dA2 = 2.0 * (fabs(Tx) + fabs(Ty)) * dT + 2.0 * dT * dT +
+                                           2.0 * u32 * alpha2;
+                        const double alpha = sqrt(alpha2);
+                        double dAl = sqrt(dA2);
+                        if (alpha > 0.0 && dA2 / alpha < dAl) dAl = dA2 / alpha;
+                        dAl += u32 * alpha;
+                        const double u = alpha * s - 0.5;
+                        const double v = (Tz + H) * s - 0.5;
+                        const double du = s * dAl + 2.0 * u32 * s * alpha + u32 * fabs(u);
+                        const double dv = s * (dT + u32 * fabs(Tz + H)) +
+                                          u32 * s * fabs(Tz + H) + u32 * fabs(v);
+                        const double dw = du + dv + du * dv + 3.0 * u32 + 0.5 * u32;
+                        const int flip = fabs(alpha2 - R2) <= 2.0 * (dA2 + u32 * R2) ||
+                                         fabs(Tz + H) <= 2.0 * dT || fabs(Tz - H) <= 2.0 * dT;
+                        if (inside) {
+                            const double cu = floor(u), rv = floor(v);
+                            const double fu = u - cu, fv = v - rv;
+                            const int c = (int)cu, r = (int)rv;
+                            const double w[4] = {(1.0 - fu) * (1.0 - fv), fu * (1.0 - fv),
+                                                 (1.0 - fu) * fv, fu * fv};
+                            for (int q = 0; q < 4; q++) {
+                                const int rr = r + (q >> 1), cc = c + (q & 1);
+                                if (rr >= 0 && rr < N && cc >= 0 && cc < N)
+                                    img[(int64_t)rr * N + cc] += w[q];
+                            }
+                        }
+                        if (out_bound && (inside || flip)) {
+                            /* bins the sample can reach in either evaluation */
+                            const double add = flip ? 1.0 : 2.0 * dw;
+                            int c_lo = (int)floor(u - du), c_hi = (int)floor(u + du) + 1;
+                            int r_lo = (int)floor(v - dv), r_hi = (int)floor(v + dv) + 1;
+                            if (c_lo < 0) c_lo = 0;
+                            if (r_lo < 0) r_lo = 0;
+                            if (c_hi > N - 1) c_hi = N - 1;
+                            if (r_hi > N - 1) r_hi = N - 1;
+                            for (int rr = r_lo; rr <= r_hi; rr++)
+                                for (int cc = c_lo; cc <= c_hi; cc++)
+                                    bnd[(int64_t)rr * N + cc] += add;
+                        }
+                    }
+                }
+                float *dst = out_images + o * NN;
+                for (int64_t q = 0; q < NN; q++) dst[q] = (float)img[q];
+                if (out_bound) {
+                    double *db = out_bound + o * NN;
+                    for (int64_t q = 0; q < NN; q++)
+                        db[q] = bnd[q] + fabs(img[q]) * (2.0 * u32) + 1e-30;
+                }
+            }
+        }
+        free(img);
+        free(bnd);
     }
     return status;
 }
