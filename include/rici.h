@@ -255,6 +255,8 @@ RICI_API int rici_batch_run(const RiciBatchScene *scenes, int32_t num_scenes,
  *              part inside the volume (FP64 closed form: slab clip, then the projection's area
  *              within the disk over the cosine of the plane's tilt; planes within 1e-7 of
  *              parallel to the axis are cut by the two lines where they meet the cylinder).
+ *   out_clutter  [num_origins] float64 device array, or NULL: Eq. clutter itself,
+ *              (A_all - A_object) / A_all in FP64 (NaN where A_all = 0).
  * Workspace: rici_clutter_workspace_size bytes, or NULL to use the library's own.
  * Errors: as rici_generate (NaN outputs for an oriented point with a bad index or a
  * non-finite coordinate).
@@ -263,8 +265,8 @@ RICI_API int64_t rici_clutter_workspace_size(int64_t num_triangles);
 RICI_API int rici_clutter(const float *vertices, const float *normals, int64_t num_vertices,
                           const int32_t *triangles, int64_t num_triangles, const int32_t *origins,
                           int64_t num_origins, float support_radius, int64_t object_vertices,
-                          double *out_area_all, double *out_area_object, void *workspace,
-                          int64_t workspace_bytes, void *stream);
+                          double *out_area_all, double *out_area_object, double *out_clutter,
+                          void *workspace, int64_t workspace_bytes, void *stream);
 
 /*
  * rici_spin_images — spin images (Section 2.1, the descriptor the RICI is compared with) from

@@ -25,8 +25,9 @@
  *  - oracle_project_fp32 / oracle_rici_fp32: the same steps in single precision in one fixed
  *    operation order (see the comment above those functions), with a count of the items whose
  *    counts differ from the FP64 definition;
- *  - oracle_crss: the clutter-resistant distance of Listing 1 / Eq. distanceFunctionExpression,
- *    in int64.
+ *  - oracle_crss: the clutter-resistant distance of Eq. distanceFunctionExpression in int64:
+ *    both images' difference images (Eq. D), then the squared differences summed where the
+ *    needle's difference is non-zero.
  *  - oracle_crss_search: per needle, the distance to its true match, the rank of that match
  *    (number of haystack images strictly closer, the tie rule of Section 4.2) and the top-1
  *    haystack index (smallest index among the minimal distances).
@@ -59,7 +60,7 @@
  *      vertex v (global indices), and E0 is the crossed edge with the smaller (u,v) key, so
  *      an edge shared by two triangles yields the same point in both;
  *  (8) counts saturate at 65535 (uint16 images);
- *  (9) Listing 1's loops run r in [0,N) and c in [1,N).
+ *  (9) the sums of Eq. distanceFunctionExpression run over r in [0,N) and c in [1,N).
  */
 #include <math.h>
 #include <stdint.h>
@@ -236,17 +237,42 @@ int oracle_rici_fp64(const float *vertices, const float *normals, int64_t num_ve
     return status;
 }
 
-/* Listing 1 / Eq. distanceFunctionExpression. */
-int64_t oracle_crss(const uint16_t *needle, const uint16_t *haystack, int32_t N) {
-    int64_t score = 0;
-    for (int32_t r = 0; r < N; r++) {
-        for (int32_t c = 1; c < N; c++) {
-            int64_t nd = (int64_t)needle[r * N + c] - (int64_t)needle[r * N + c - 1];
-            int64_t hd = (int64_t)haystack[r * N + c] - (int64_t)haystack[r * N + c - 1];
-            if (nd != 0) score += (nd - hd) * (nd - hd);
-        }
+/* Eq. D: the horizontal difference image of one image, D(x, r, c) = x(r, c) - x(r, c-1) for
+ * c in [1, N) (reading (9): the bounds of Eq. distanceFunctionExpression), stored at r*N + c;
+ * entry c = 0 is left unused. */
+static void difference_image(const uint16_t *x, int32_t N, int32_t *D) {
+    for (int64_t p = 0; p < (int64_t)N * N; p++) {
+        const int32_t c = (int32_t)(p % N);
+        D[p] = c == 0 ? 0 : (int32_t)x[p] - (int32_t)x[p - 1];
     }
-    return score;
+}
+
+/* Eq. distanceFunctionExpression: CRD(n, h) is the sum, over the positions where the needle's
+ * difference image is non-zero, of the squared difference of the two difference images
+ * (positions with D(n) = 0 contribute nothing; the sum is exact in int64). */
+static int64_t crd_of_differences(const int32_t *Dn, const int32_t *Dh, int32_t N) {
+    int64_t total = 0;
+    for (int64_t p = 0; p < (int64_t)N * N; p++) {
+        if ((p % N) == 0 || Dn[p] == 0) continue;
+        const int64_t e = (int64_t)Dn[p] - (int64_t)Dh[p];
+        total += e * e;
+    }
+    return total;
+}
+
+/* Eq. distanceFunctionExpression for one pair of images. */
+int64_t oracle_crss(const uint16_t *needle, const uint16_t *haystack, int32_t N) {
+    int32_t *Dn = (int32_t *)malloc(sizeof(int32_t) * (size_t)N * (size_t)N);
+    int32_t *Dh = (int32_t *)malloc(sizeof(int32_t) * (size_t)N * (size_t)N);
+    int64_t d = -1;
+    if (Dn && Dh) {
+        difference_image(needle, N, Dn);
+        difference_image(haystack, N, Dh);
+        d = crd_of_differences(Dn, Dh, N);
+    }
+    free(Dn);
+    free(Dh);
+    return d;
 }
 
 /*
@@ -266,29 +292,49 @@ int oracle_crss_search(const uint16_t *needles, int64_t num_needles, const uint1
         if (m < 0 || m >= num_haystack) return ORACLE_BAD_INDEX;
     }
     const int64_t img = (int64_t)N * N;
+    int status = ORACLE_OK;
 #ifdef _OPENMP
     if (num_threads > 0) omp_set_num_threads(num_threads);
-#pragma omp parallel for schedule(dynamic, 1)
+#pragma omp parallel
 #endif
-    for (int64_t i = 0; i < num_needles; i++) {
-        const uint16_t *n = needles + i * img;
-        int64_t m = true_match ? true_match[i] : i;
-        int64_t dt = oracle_crss(n, haystack + m * img, N);
-        int64_t rank = 0, best = INT64_MAX, best_j = -1;
-        for (int64_t j = 0; j < num_haystack; j++) {
-            int64_t d = oracle_crss(n, haystack + j * img, N);
-            if (out_distances) out_distances[i * num_haystack + j] = d;
-            if (d < dt) rank++;
-            if (d < best) {
-                best = d;
-                best_j = j;
+    {
+        /* per thread: the needle's difference image and one haystack image's */
+        int32_t *Dn = (int32_t *)malloc(sizeof(int32_t) * (size_t)img);
+        int32_t *Dh = (int32_t *)malloc(sizeof(int32_t) * (size_t)img);
+        if (!Dn || !Dh) {
+#ifdef _OPENMP
+#pragma omp atomic write
+#endif
+            status = ORACLE_NO_MEMORY;
+        } else {
+#ifdef _OPENMP
+#pragma omp for schedule(dynamic, 1)
+#endif
+            for (int64_t i = 0; i < num_needles; i++) {
+                difference_image(needles + i * img, N, Dn);
+                const int64_t m = true_match ? true_match[i] : i;
+                difference_image(haystack + m * img, N, Dh);
+                const int64_t dt = crd_of_differences(Dn, Dh, N);
+                int64_t rank = 0, best = INT64_MAX, best_j = -1;
+                for (int64_t j = 0; j < num_haystack; j++) {
+                    difference_image(haystack + j * img, N, Dh);
+                    const int64_t d = crd_of_differences(Dn, Dh, N);
+                    if (out_distances) out_distances[i * num_haystack + j] = d;
+                    if (d < dt) rank++;
+                    if (d < best) {
+                        best = d;
+                        best_j = j;
+                    }
+                }
+                if (out_rank) out_rank[i] = (int32_t)rank;
+                if (out_true_distance) out_true_distance[i] = dt;
+                if (out_top1) out_top1[i] = (int32_t)best_j;
             }
         }
-        if (out_rank) out_rank[i] = (int32_t)rank;
-        if (out_true_distance) out_true_distance[i] = dt;
-        if (out_top1) out_top1[i] = (int32_t)best_j;
+        free(Dn);
+        free(Dh);
     }
-    return ORACLE_OK;
+    return status;
 }
 
 /*

@@ -122,7 +122,7 @@ def load_library(path: str | None = None):
         lib.rici_kernel_launches.restype = i64
         lib.rici_clutter_workspace_size.argtypes = [i64]
         lib.rici_clutter_workspace_size.restype = i64
-        lib.rici_clutter.argtypes = [P, P, i64, P, i64, P, i64, f32, i64, P, P, P, i64, P]
+        lib.rici_clutter.argtypes = [P, P, i64, P, i64, P, i64, f32, i64, P, P, P, P, i64, P]
         lib.rici_clutter.restype = ctypes.c_int
         lib.rici_spin_images.argtypes = [P, P, i64, P, i64, P, i64, f32, i32, i32, P, P, i64, P]
         lib.rici_spin_images.restype = ctypes.c_int
@@ -220,10 +220,11 @@ def rici_generate(vertices, normals, triangles, origins, support_radius: float, 
 
 
 def clutter_areas(vertices, normals, triangles, origins, support_radius: float,
-                  object_vertices: int, *, stream=None):
+                  object_vertices: int, *, with_clutter: bool = False, stream=None):
     """Eq. clutter inputs per oriented point: float64 [O] tensors (A_all, A_object), the surface
     area inside the support volume and its part on triangles whose first vertex index is below
-    ``object_vertices`` (clutter = (A_all - A_object) / A_all)."""
+    ``object_vertices``; with ``with_clutter`` also Eq. clutter itself, (A_all - A_object) /
+    A_all computed by the library (NaN where A_all = 0)."""
     lib = load_library()
     v = _need(vertices, torch.float32, "vertices", (3,))
     n = _need(normals, torch.float32, "normals", (3,))
@@ -233,6 +234,7 @@ def clutter_areas(vertices, normals, triangles, origins, support_radius: float,
         raise ValueError("normals must have the same shape as vertices")
     a_all = torch.empty(o.numel(), dtype=torch.float64, device=v.device)
     a_obj = torch.empty(o.numel(), dtype=torch.float64, device=v.device)
+    clu = torch.empty(o.numel(), dtype=torch.float64, device=v.device) if with_clutter else None
     nb = lib.rici_clutter_workspace_size(t.shape[0])
     if nb < 0:
         raise ValueError("invalid sizes")
@@ -240,9 +242,9 @@ def clutter_areas(vertices, normals, triangles, origins, support_radius: float,
     with torch.cuda.device(v.device):
         _check(lib.rici_clutter(_ptr(v), _ptr(n), v.shape[0], _ptr(t), t.shape[0], _ptr(o),
                                 o.numel(), float(support_radius), int(object_vertices),
-                                _ptr(a_all), _ptr(a_obj), _ptr(ws), ws.numel(),
+                                _ptr(a_all), _ptr(a_obj), _ptr(clu), _ptr(ws), ws.numel(),
                                 _stream_handle(stream)))
-    return a_all, a_obj
+    return (a_all, a_obj, clu) if with_clutter else (a_all, a_obj)
 
 
 def spin_images(vertices, normals, triangles, origins, support_radius: float, resolution: int,

@@ -63,14 +63,16 @@ def run_prepared(prep, support_radius: float = 0.3, resolution: int = 64,
 
 def clutter_prepared(prep, support_radius: float = 0.3, stream=None):
     """Eq. clutter around every reference vertex of every level: per (run, level) the device
-    tensors (A_all, A_object), the object being the reference object (level 1's vertices)."""
+    tensors (A_all, A_object, clutter), the object being the reference object (level 1's
+    vertices); the library computes clutter = (A_all - A_object) / A_all."""
     out, k = [], 0
     for sizes in prep["sizes"]:
         ref = torch.arange(sizes[0], dtype=torch.int32, device=prep["gen"][k]["vertices"].device)
         for j in range(len(sizes)):
             g = prep["gen"][k + j]
             out.append(B.clutter_areas(g["vertices"], g["normals"], g["triangles"], ref,
-                                       support_radius, sizes[0], stream=stream))
+                                       support_radius, sizes[0], with_clutter=True,
+                                       stream=stream))
         k += len(sizes)
     return out
 
@@ -81,7 +83,8 @@ RANK_EDGES = np.array([0, 1, 2, 5, 10, 20, 50, 100, 1000, np.iinfo(np.int64).max
 def histograms(prep, results, areas=None, clutter_bins: int = 10):
     """Per run: ranks, rank histograms (bin i = results at rank i, |CD| bins) and the fraction
     of results at rank 0, one entry per level.  With ``areas`` (from ``clutter_prepared``) also
-    the clutter of every reference vertex, (A_all - A_object) / A_all, and a heatmap per level:
+    the clutter of every reference vertex (Eq. clutter, from the library; 0 where the volume
+    holds no surface) and a heatmap per level:
     counts of results by clutter (``clutter_bins`` equal bins of [0, 1]) and rank (bins with the
     edges of RANK_EDGES: rank 0, 1, 2-4, 5-9, ...)."""
     out, k = [], 0
@@ -94,9 +97,7 @@ def histograms(prep, results, areas=None, clutter_bins: int = 10):
             hists.append(h)
             frac.append(float(h[0]) / r.size if r.size else float("nan"))
             if areas is not None:
-                a_all = areas[k + j][0].cpu().numpy()
-                a_obj = areas[k + j][1].cpu().numpy()
-                c = np.where(a_all > 0, (a_all - a_obj) / np.where(a_all > 0, a_all, 1.0), 0.0)
+                c = np.nan_to_num(areas[k + j][2].cpu().numpy(), nan=0.0)
                 clut.append(c)
                 ci = np.minimum((c * clutter_bins).astype(np.int64), clutter_bins - 1)
                 ri = np.searchsorted(RANK_EDGES, r, side="right") - 1
@@ -120,5 +121,5 @@ def run(runs, support_radius: float = 0.3, resolution: int = 64, mode: int = B.S
     areas = clutter_prepared(prep, support_radius) if clutter else None
     st = B.sync_status()
     if st:
-        raise B.RiciError(f"device status {st} in the clutterbox run")
+        raise B.RiciError(st, "device status in the clutterbox run")
     return histograms(prep, res, areas)

@@ -115,6 +115,14 @@ int check_generate_args(const float *V, const float *Nrm, int64_t nv, const int3
 
 void count_launches(int64_t n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
 
+int begin_generate_call(const float *V, const float *Nrm, int64_t nv, const int32_t *T, int64_t nt,
+                        const int32_t *O, int64_t no, float R, int32_t N, const uint16_t *out) {
+  t_last_error.clear();
+  return check_generate_args(V, Nrm, nv, T, nt, O, no, R, N, out);
+}
+
+int report_error(int code, const char *message) { return fail(code, "%s", message); }
+
 cudaError_t status_word_address(int **address) {
   return cudaGetSymbolAddress((void **)address, g_status);
 }
@@ -262,7 +270,8 @@ int64_t rici_clutter_workspace_size(int64_t num_triangles) {
 int rici_clutter(const float *vertices, const float *normals, int64_t num_vertices,
                  const int32_t *triangles, int64_t num_triangles, const int32_t *origins,
                  int64_t num_origins, float support_radius, int64_t object_vertices,
-                 double *out_area_all, double *out_area_object, void *workspace,
+                 double *out_area_all, double *out_area_object, double *out_clutter,
+                 void *workspace,
                  int64_t workspace_bytes, void *stream) {
   t_last_error.clear();
   // the generation checks, with the resolution of a valid call and a stand-in output pointer
@@ -292,6 +301,7 @@ int rici_clutter(const float *vertices, const float *normals, int64_t num_vertic
   a.object_vertices = object_vertices;
   a.out_area_all = out_area_all;
   a.out_area_object = out_area_object;
+  a.out_clutter = out_clutter;
   a.status = d->status;
   cudaError_t e = launch_clutter(a, ws, static_cast<cudaStream_t>(stream));
   if (e != cudaSuccess) return cuda_fail(e, "rici_clutter launch");

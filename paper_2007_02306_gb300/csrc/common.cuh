@@ -26,7 +26,6 @@ struct GenerateArgs {
 };
 
 // Byte size of the generation workspace.
-int64_t generate_workspace_bytes(int64_t num_triangles);
 // Enqueue generation on `stream` using `ws` (>= generate_workspace_bytes, 256-aligned).
 cudaError_t launch_generate(const GenerateArgs &a, void *ws, cudaStream_t stream);
 
@@ -44,6 +43,7 @@ struct ClutterArgs {
   int64_t object_vertices;
   double *out_area_all;
   double *out_area_object;
+  double *out_clutter;  // NULL, or (A_all - A_object) / A_all per oriented point
   int *status;  // device status word
 };
 // Enqueue the clutter measure on `stream` using `ws` (>= generate_workspace_bytes).
@@ -90,9 +90,6 @@ struct GenerateBatch {
   int *status;
 };
 
-// Hashed buckets used for a scene of nt triangles (a power of two).
-uint32_t generate_bucket_count(int64_t nt);
-int64_t generate_batch_workspace_bytes(int num_scenes, int64_t total_tris, int64_t total_buckets);
 // scenes: host array with every offset filled; the table is written to the workspace by kernels
 // (no host memory is referenced after the call returns).
 cudaError_t launch_generate_batch(const GenScene *scenes, const GenerateBatch &b, void *ws,
@@ -175,9 +172,10 @@ cudaError_t launch_tc_encode_and_rank(const SearchScene *tab, int num_scenes, co
 struct Carver {
   char *base;
   int64_t off = 0;
+  constexpr Carver() : base(nullptr) {}  // sizing only: take() returns null pointers
   explicit Carver(void *b) : base(static_cast<char *>(b)) {}
   template <class T>
-  T *take(int64_t count) {
+  constexpr T *take(int64_t count) {
     off = (off + 255) & ~int64_t(255);
     T *p = base ? reinterpret_cast<T *>(base + off) : nullptr;
     off += count * int64_t(sizeof(T));
@@ -185,10 +183,47 @@ struct Carver {
   }
 };
 
+// Items per block of the generation's bucket scan.
+constexpr int kGenScanItems = 2048;
+
+// Hashed buckets used for a scene of nt triangles (a power of two in [2^10, 2^22]).
+__host__ __device__ constexpr uint32_t generate_bucket_count(int64_t nt) {
+  uint32_t b = 1024;
+  while (b < (uint64_t)nt && b < (1u << 22)) b <<= 1;
+  return b;
+}
+
+// Generation workspace of a batch (the layout that bin_triangles carves, plus alignment slack).
+constexpr int64_t generate_batch_workspace_bytes(int num_scenes, int64_t total_tris,
+                                                 int64_t total_buckets) {
+  Carver c;
+  c.take<GenScene>(num_scenes);
+  c.take<int>(total_buckets);                      // counts
+  c.take<int>(total_buckets + 1);                  // starts
+  c.take<int>(total_buckets / kGenScanItems + 2);  // scan partials
+  c.take<uint32_t>(total_tris);                    // bucket of each triangle
+  c.take<int>(total_tris);                         // slot within its bucket
+  c.take<float4>(4 * total_tris);                  // records
+  return c.off + 256;
+}
+
+// Workspace of a single-scene generation (also used by the clutter measure and spin images).
+constexpr int64_t generate_workspace_bytes(int64_t num_triangles) {
+  return generate_batch_workspace_bytes(1, num_triangles,
+                                        (int64_t)generate_bucket_count(num_triangles) + 1);
+}
+
 __device__ __forceinline__ void set_status(int *status, int bits) { atomicOr(status, bits); }
 
 // Number of kernels this library has enqueued in the process (for launch accounting).
 void count_launches(int64_t n);
+
+// Clears the calling thread's last-error text and checks the arguments of a generation call
+// (as rici_generate does); returns RICI_OK or the error code, with its text recorded.
+int begin_generate_call(const float *V, const float *Nrm, int64_t nv, const int32_t *T, int64_t nt,
+                        const int32_t *O, int64_t no, float R, int32_t N, const uint16_t *out);
+// Records `message` as the calling thread's last-error text and returns `code`.
+int report_error(int code, const char *message);
 
 // Device address of the status word on the current device.
 cudaError_t status_word_address(int **address);

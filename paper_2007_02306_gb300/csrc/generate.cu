@@ -35,16 +35,12 @@ constexpr float kSafety = 2.0f;                // multiplies every derived error
 constexpr uint32_t kSkip = 0xFFFFFFFEu;
 constexpr float kCellClamp = 1048576.0f;  // |cell coordinate| limit (2^20)
 constexpr int kSlot = 21;  // words per staged triangle (odd stride: conflict-free lookups)
-constexpr int kScanItems = 2048;
+constexpr int kScanItems = kGenScanItems;
 // shared words per warp: candidate queue, FP64 queue (triangle records, then their layers as
 // bytes), staged triangles
 constexpr int kPerWarp = 64 + 64 + 16 + 32 * kSlot;
 
-__host__ __device__ inline uint32_t bucket_count(int64_t nt) {
-  uint32_t b = 1024;
-  while (b < (uint64_t)nt && b < (1u << 22)) b <<= 1;
-  return b;
-}
+__host__ __device__ constexpr uint32_t bucket_count(int64_t nt) { return generate_bucket_count(nt); }
 
 __device__ __forceinline__ int cell_coord(float x, float inv_cell) {
   float f = floorf(x * inv_cell);
@@ -1151,7 +1147,7 @@ constexpr int kClutterMaxCells = 7 * 7 * 7 + 1;  // neighbourhoods of nhalf <= 3
 // its first vertex index is below object_vertices.
 __global__ void __launch_bounds__(kClutterWarps * 32, 5)
     k_clutter(KArgs a, int64_t object_vertices, double *__restrict__ out_all,
-              double *__restrict__ out_obj) {
+              double *__restrict__ out_obj, double *__restrict__ out_clutter) {
   __shared__ int buckets[kClutterMaxCells], bdup[kClutterMaxCells];
   __shared__ double fr[7];
   __shared__ int wq[kClutterWarps][64];
@@ -1166,6 +1162,7 @@ __global__ void __launch_bounds__(kClutterWarps * 32, 5)
     if (tid == 0) {
       set_status(a.status, RICI_ERR_INDEX_OUT_OF_RANGE);
       out_all[og] = out_obj[og] = nan("");
+      if (out_clutter) out_clutter[og] = nan("");
     }
     return;
   }
@@ -1178,6 +1175,7 @@ __global__ void __launch_bounds__(kClutterWarps * 32, 5)
     if (tid == 0) {
       set_status(a.status, RICI_ERR_NONFINITE_INPUT);
       out_all[og] = out_obj[og] = nan("");
+      if (out_clutter) out_clutter[og] = nan("");
     }
     return;
   }
@@ -1308,6 +1306,8 @@ __global__ void __launch_bounds__(kClutterWarps * 32, 5)
     }
     out_all[og] = sa;
     out_obj[og] = so;
+    // Eq. clutter: the share of the area inside the support volume not on the object
+    if (out_clutter) out_clutter[og] = sa > 0.0 ? __ddiv_rn(__dsub_rn(sa, so), sa) : nan("");
   }
 }
 
@@ -1462,8 +1462,6 @@ __global__ void __launch_bounds__(kSpinWarps * 32) k_spin(KArgs a, int m, float 
 
 }  // namespace
 
-uint32_t generate_bucket_count(int64_t nt) { return bucket_count(nt); }
-
 cudaError_t launch_project_fp32(const float *pts, int64_t n, const float *sv, const float *sn,
                                 float *out, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
@@ -1471,22 +1469,6 @@ cudaError_t launch_project_fp32(const float *pts, int64_t n, const float *sv, co
   k_project_fp32<<<(unsigned)(want < 152 * 16 ? want : 152 * 16), 256, 0, st>>>(pts, n, sv, sn, out);
   count_launches(1);
   return cudaGetLastError();
-}
-
-int64_t generate_batch_workspace_bytes(int num_scenes, int64_t total_tris, int64_t total_buckets) {
-  Carver c(nullptr);
-  c.take<GenScene>(num_scenes);
-  c.take<int>(total_buckets);          // counts
-  c.take<int>(total_buckets + 1);      // starts
-  c.take<int>(total_buckets / kScanItems + 2);  // scan partials
-  c.take<uint32_t>(total_tris);        // bucket of each triangle
-  c.take<int>(total_tris);             // slot within its bucket
-  c.take<float4>(4 * total_tris);      // records
-  return c.off + 256;
-}
-
-int64_t generate_workspace_bytes(int64_t num_triangles) {
-  return generate_batch_workspace_bytes(1, num_triangles, (int64_t)bucket_count(num_triangles) + 1);
 }
 
 // Bins every triangle of the scenes into the hashed grid for support volumes of radius amax and
@@ -1605,7 +1587,7 @@ cudaError_t launch_clutter(const ClutterArgs &a, void *ws, cudaStream_t st) {
     KArgs kk = k;
     kk.origin_base = o0;
     k_clutter<<<(unsigned)cnt, kClutterWarps * 32, 0, st>>>(kk, a.object_vertices, a.out_area_all,
-                                                             a.out_area_object);
+                                                             a.out_area_object, a.out_clutter);
     count_launches(1);
   }
   return cudaGetLastError();

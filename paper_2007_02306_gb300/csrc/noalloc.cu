@@ -26,6 +26,9 @@ namespace {
 constexpr int64_t kNoAllocMaxTriangles = 262144;
 constexpr size_t kNoAllocScratchBytes = (size_t)21 << 20;  // 21 MiB
 
+static_assert(generate_workspace_bytes(kNoAllocMaxTriangles) <= (int64_t)kNoAllocScratchBytes,
+              "the scratch array must hold the workspace of the largest accepted mesh");
+
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocScratchBytes];
 
 constexpr int kMaxDevices = 64;
@@ -62,24 +65,21 @@ extern "C" int rici_generate_noalloc(const float *vertices, const float *normals
                                      int64_t num_triangles, const int32_t *origins,
                                      int64_t num_origins, float support_radius,
                                      int32_t resolution, uint16_t *out_images, void *stream) {
-  if (num_vertices < 0 || num_triangles < 0 || num_origins < 0) return RICI_ERR_INVALID_ARGUMENT;
-  if (resolution < 1 || resolution > RICI_MAX_RESOLUTION) return RICI_ERR_INVALID_ARGUMENT;
-  if (!(support_radius > 0.0f) || !(support_radius < 3.4e38f)) return RICI_ERR_INVALID_ARGUMENT;
-  if (num_triangles > 0 && (!triangles || !vertices)) return RICI_ERR_INVALID_ARGUMENT;
-  if (num_origins > 0 && (!origins || !vertices || !normals || !out_images))
-    return RICI_ERR_INVALID_ARGUMENT;
-  if (num_origins > 0 && num_vertices == 0) return RICI_ERR_INVALID_ARGUMENT;
-  if (num_vertices > (int64_t(1) << 31) - 2) return RICI_ERR_OUT_TOO_LARGE;
-  // the scratch array has room for at most kNoAllocMaxTriangles triangles
-  if (num_triangles > kNoAllocMaxTriangles ||
-      generate_workspace_bytes(num_triangles) > (int64_t)kNoAllocScratchBytes)
-    return RICI_ERR_OUT_TOO_LARGE;
+  int rc = begin_generate_call(vertices, normals, num_vertices, triangles, num_triangles, origins,
+                               num_origins, support_radius, resolution, out_images);
+  if (rc) return rc;
+  // the scratch array has room for the workspace of at most kNoAllocMaxTriangles triangles
+  if (num_triangles > kNoAllocMaxTriangles)
+    return report_error(RICI_ERR_OUT_TOO_LARGE,
+                        "rici_generate_noalloc accepts at most 262144 triangles");
   if (num_origins == 0) return RICI_OK;
   int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return RICI_ERR_CUDA;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
+    return report_error(RICI_ERR_CUDA, "rici_generate_noalloc: no usable current device");
   void *scratch = nullptr;
   int *status = nullptr;
-  if (noalloc_setup(dev, &scratch, &status) != cudaSuccess) return RICI_ERR_CUDA;
+  if (noalloc_setup(dev, &scratch, &status) != cudaSuccess)
+    return report_error(RICI_ERR_CUDA, "rici_generate_noalloc: device address lookup failed");
   GenerateArgs a;
   a.vertices = vertices;
   a.normals = normals;
@@ -95,6 +95,6 @@ extern "C" int rici_generate_noalloc(const float *vertices, const float *normals
   a.counters = nullptr;
   a.status = status;
   if (launch_generate(a, scratch, static_cast<cudaStream_t>(stream)) != cudaSuccess)
-    return RICI_ERR_CUDA;
+    return report_error(RICI_ERR_CUDA, "rici_generate_noalloc: launch failed");
   return RICI_OK;
 }

@@ -129,17 +129,17 @@ def test_projection_and_tuning_reject_bad_arguments_on_host(lib):
 def test_clutter_rejects_bad_arguments_on_host(lib):
     dummy = ctypes.c_void_p(16)
     # bad support radius, negative object vertex count, null outputs
-    assert lib.rici_clutter(dummy, dummy, 3, dummy, 1, dummy, 1, 0.0, 0, dummy, dummy, None, 0,
-                            None) == 1
-    assert lib.rici_clutter(dummy, dummy, 3, dummy, 1, dummy, 1, 0.3, -1, dummy, dummy, None, 0,
-                            None) == 1
-    assert lib.rici_clutter(dummy, dummy, 3, dummy, 1, dummy, 1, 0.3, 0, None, dummy, None, 0,
-                            None) == 1
-    assert lib.rici_clutter(dummy, dummy, 3, dummy, 1, dummy, 1, 0.3, 0, dummy, None, None, 0,
-                            None) == 1
+    assert lib.rici_clutter(dummy, dummy, 3, dummy, 1, dummy, 1, 0.0, 0, dummy, dummy, None, None,
+                            0, None) == 1
+    assert lib.rici_clutter(dummy, dummy, 3, dummy, 1, dummy, 1, 0.3, -1, dummy, dummy, None, None,
+                            0, None) == 1
+    assert lib.rici_clutter(dummy, dummy, 3, dummy, 1, dummy, 1, 0.3, 0, None, dummy, None, None,
+                            0, None) == 1
+    assert lib.rici_clutter(dummy, dummy, 3, dummy, 1, dummy, 1, 0.3, 0, dummy, None, None, None,
+                            0, None) == 1
     # no oriented points: a valid no-op; the workspace is the generation grid's
-    assert lib.rici_clutter(dummy, dummy, 3, dummy, 1, dummy, 0, 0.3, 0, None, None, None, 0,
-                            None) == 0
+    assert lib.rici_clutter(dummy, dummy, 3, dummy, 1, dummy, 0, 0.3, 0, None, None, None, None,
+                            0, None) == 0
     assert lib.rici_clutter_workspace_size(100) == lib.rici_generate_workspace_size(3, 100, 1, 64)
     assert lib.rici_clutter_workspace_size(-1) == -1
 
@@ -174,3 +174,21 @@ def test_batch_run_rejects_bad_scenes_on_host(lib):
     assert lib.rici_batch_run(arr, 1, 0.3, 0, 3, None, 0, None) == 1
     assert lib.rici_batch_run(arr, 1, -1.0, 64, 3, None, 0, None) == 1
     assert lib.rici_batch_run(arr, 0, 0.3, 64, 3, None, 0, None) == 0
+
+
+def test_noalloc_rejects_on_host_with_error_text(lib):
+    dummy = ctypes.c_void_p(16)
+    lib.rici_last_error_string.restype = ctypes.c_char_p
+    # one triangle beyond the largest accepted mesh
+    assert lib.rici_generate_noalloc(dummy, dummy, 3, dummy, 262145, dummy, 1, ctypes.c_float(0.3),
+                                     64, dummy, None) == 8
+    assert b"262144" in lib.rici_last_error_string()
+    # the checks of rici_generate: radius, resolution, null output
+    for R, N, out in ((float("inf"), 64, dummy), (0.3, 0, dummy), (0.3, 64, None)):
+        assert lib.rici_generate_noalloc(dummy, dummy, 3, dummy, 1, dummy, 1, ctypes.c_float(R),
+                                         N, out, None) == 1
+        assert lib.rici_last_error_string() != b""
+    # a finite radius near FLT_MAX is valid: no origins makes the call a no-op
+    assert lib.rici_generate_noalloc(dummy, dummy, 3, dummy, 1, dummy, 0,
+                                     ctypes.c_float(3.4028e38), 64, None, None) == 0
+    assert lib.rici_last_error_string() == b""

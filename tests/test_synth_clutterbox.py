@@ -54,9 +54,11 @@ def test_histograms_and_heatmaps_on_the_host():
     prep = {"sizes": [[4, 200]]}  # one run: level 1 (4 reference vertices), level 2 (200 images)
     results = [{"rank": torch.tensor([0, 0, 0, 0], dtype=torch.int32)},
                {"rank": torch.tensor([0, 3, 0, 120], dtype=torch.int32)}]
+    # stand-ins for the library's (A_all, A_object, clutter) tensors
     a_all = torch.tensor([1.0, 2.0, 4.0, 1.0], dtype=torch.float64)
-    areas = [(a_all, a_all.clone()),
-             (a_all, torch.tensor([1.0, 1.0, 0.4, 0.05], dtype=torch.float64))]
+    a_obj = torch.tensor([1.0, 1.0, 0.4, 0.05], dtype=torch.float64)
+    areas = [(a_all, a_all.clone(), torch.zeros(4, dtype=torch.float64)),
+             (a_all, a_obj, (a_all - a_obj) / a_all)]
     h = clutterbox.histograms(prep, results, areas, clutter_bins=10)[0]
     assert h["rank0_fraction"] == [1.0, 0.5]
     hist = h["histograms"][1]
