@@ -95,13 +95,14 @@ def rici_fp64(vertices, normals, triangles, origins, support_radius: float, reso
         raise ValueError("normals must match vertices")
     N = int(resolution)
     out = np.zeros((o.size, N, N), dtype=np.uint16)
-    cnt = np.zeros(2, dtype=np.int64)
+    cnt = np.zeros(4, dtype=np.int64)
     rc = lib.oracle_rici_fp64(_ptr(v), _ptr(n), v.shape[0], _ptr(t), t.shape[0], _ptr(o), o.size,
                               float(support_radius), N, _ptr(out), int(num_threads), _ptr(cnt))
     if rc != 0:
         raise ValueError(f"oracle_rici_fp64 failed with status {rc}")
     if return_counters:
-        return out, {"pairs_crossing": int(cnt[0]), "layer_crossings": int(cnt[1])}
+        return out, {"pairs_crossing": int(cnt[0]), "layer_crossings": int(cnt[1]),
+                     "pairs_contributing": int(cnt[2]), "crossings_contributing": int(cnt[3])}
     return out
 
 
@@ -141,7 +142,7 @@ def rici_fp32(vertices, normals, triangles, origins, support_radius: float, reso
         raise ValueError("normals must match vertices")
     N = int(resolution)
     out = np.zeros((o.size, N, N), dtype=np.uint16)
-    cnt = np.zeros(2, dtype=np.int64)
+    cnt = np.zeros(4, dtype=np.int64)
     rc = lib.oracle_rici_fp32(_ptr(v), _ptr(n), v.shape[0], _ptr(t), t.shape[0], _ptr(o), o.size,
                               float(support_radius), N, _ptr(out), int(num_threads), _ptr(cnt))
     if rc != 0:

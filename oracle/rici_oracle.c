@@ -123,7 +123,8 @@ static int key_less(int32_t a0, int32_t a1, int32_t b0, int32_t b1) {
 
 /* Counts of one triangle in one layer, added to the row (steps 2-6 of Section 3.1.2). */
 static void count_layer(const double T[3][3], const int32_t gid[3], double beta,
-                        const double *alpha2, int32_t N, int64_t *row, int64_t *crossings) {
+                        const double *alpha2, int32_t N, int64_t *row, int64_t *crossings,
+                        int64_t *contributing) {
     int s0 = T[0][2] >= beta, s1 = T[1][2] >= beta, s2 = T[2][2] >= beta;
     if (s0 == s1 && s1 == s2) return;
     int lone = (s0 != s1 && s0 != s2) ? 0 : ((s1 != s0 && s1 != s2) ? 1 : 2);
@@ -147,6 +148,13 @@ static void count_layer(const double T[3][3], const int32_t gid[3], double beta,
     double d1 = E1[0] * Dx + E1[1] * Dy; /* sign: is C before E1 along D? */
     double cr = E0[0] * Dy - E0[1] * Dx; /* |C| * |D| (signed) */
     double dd = Dx * Dx + Dy * Dy;       /* |D|^2 */
+    /* With both ends outside the largest circle (e >= alpha2[c] for every c) there is no
+     * single crossing at any radius, and the double-crossing test alpha2[c] * dd > cr * cr can
+     * only hold for some c if it holds for the largest alpha2 (rounded products are monotone):
+     * such a segment, farther than alpha_{N-1} from the axis, adds nothing to the row. */
+    const double amax = alpha2[N - 1];
+    if (e0 >= amax && e1 >= amax && !(d0 < 0.0 && d1 > 0.0 && amax * dd > cr * cr)) return;
+    (*contributing)++;
     for (int32_t c = 0; c < N; c++) {
         int in0 = e0 >= alpha2[c];
         int in1 = e1 >= alpha2[c];
@@ -184,15 +192,20 @@ int oracle_rici_fp64(const float *vertices, const float *normals, int64_t num_ve
         alpha2[i] = a * a;
         beta[i] = (R * (double)(2 * i + 1 - N)) / (double)(2 * N);
     }
-    int64_t total_crossings = 0, total_pairs = 0;
+    int64_t total_crossings = 0, total_pairs = 0, total_contributing = 0;
+    int64_t total_contributing_pairs = 0;
     int status = ORACLE_OK;
 #ifdef _OPENMP
     if (num_threads > 0) omp_set_num_threads(num_threads);
-#pragma omp parallel reduction(+ : total_crossings, total_pairs)
+#pragma omp parallel reduction(+ : total_crossings, total_pairs, total_contributing, \
+                                   total_contributing_pairs)
 #endif
     {
         int64_t *img = (int64_t *)malloc(sizeof(int64_t) * (size_t)N * (size_t)N);
-        if (!img) {
+        /* every vertex projected once per oriented point (the same values a projection per
+         * triangle corner gives) */
+        double *TV = (double *)malloc(sizeof(double) * 3 * (size_t)(num_vertices > 0 ? num_vertices : 1));
+        if (!img || !TV) {
 #ifdef _OPENMP
 #pragma omp atomic write
 #endif
@@ -208,31 +221,52 @@ int oracle_rici_fp64(const float *vertices, const float *normals, int64_t num_ve
                 double Nax, Nay, Nbx, Nbz;
                 frame_coefficients(normals[3 * sv], normals[3 * sv + 1], normals[3 * sv + 2], &Nax,
                                    &Nay, &Nbx, &Nbz);
+                for (int64_t v = 0; v < num_vertices; v++)
+                    project_point(vertices + 3 * v, S, Nax, Nay, Nbx, Nbz, TV + 3 * v);
                 for (int64_t t = 0; t < num_triangles; t++) {
                     double T[3][3];
                     int32_t gid[3];
                     for (int k = 0; k < 3; k++) {
                         gid[k] = triangles[3 * t + k];
-                        project_point(vertices + 3 * (int64_t)gid[k], S, Nax, Nay, Nbx, Nbz, T[k]);
+                        for (int d = 0; d < 3; d++) T[k][d] = TV[3 * (int64_t)gid[k] + d];
                     }
-                    int64_t before = total_crossings;
-                    for (int32_t r = 0; r < N; r++)
+                    /* step 1's side rule for every layer at once: with all three heights
+                     * below beta_0, or all at or above beta_{N-1}, no layer is crossed */
+                    double zlo = T[0][2], zhi = T[0][2];
+                    for (int k = 1; k < 3; k++) {
+                        if (T[k][2] < zlo) zlo = T[k][2];
+                        if (T[k][2] > zhi) zhi = T[k][2];
+                    }
+                    if (zhi < beta[0] || zlo >= beta[N - 1]) continue;
+                    int64_t before = total_crossings, before_c = total_contributing;
+                    /* only layers with zlo < beta_r <= zhi can be crossed; count_layer applies
+                     * the side rule to each of them */
+                    for (int32_t r = 0; r < N; r++) {
+                        if (beta[r] <= zlo) continue;
+                        if (beta[r] > zhi) break;
                         count_layer(T, gid, beta[r], alpha2, N, img + (int64_t)r * N,
-                                    &total_crossings);
+                                    &total_crossings, &total_contributing);
+                    }
                     if (total_crossings != before) total_pairs++;
+                    if (total_contributing != before_c) total_contributing_pairs++;
                 }
                 uint16_t *out = out_images + o * (int64_t)N * N;
                 for (int64_t b = 0; b < (int64_t)N * N; b++)
                     out[b] = (uint16_t)(img[b] > 65535 ? 65535 : img[b]);
             }
-            free(img);
         }
+        free(img);
+        free(TV);
     }
     free(alpha2);
     free(beta);
     if (counters) {
         counters[0] = total_pairs;     /* (origin, triangle) pairs crossing at least one layer */
         counters[1] = total_crossings; /* (origin, triangle, layer) crossings */
+        /* the same, for crossings whose segment reaches within alpha_{N-1} of the axis (the
+         * ones that can add to a bin; the others are rejected by the largest circle) */
+        counters[2] = total_contributing_pairs;
+        counters[3] = total_contributing;
     }
     return status;
 }
@@ -486,9 +520,9 @@ int oracle_rici_fp32(const float *vertices, const float *normals, int64_t num_ve
                     for (int32_t r = 0; r < N; r++) {
                         memset(r32, 0, sizeof(int64_t) * (size_t)N);
                         memset(r64, 0, sizeof(int64_t) * (size_t)N);
-                        int64_t dummy = 0;
+                        int64_t dummy = 0, dummy_c = 0;
                         crossings32 += count_layer_fp32(T32, gid, bf[r], a2f, N, r32);
-                        count_layer(T64, gid, bd[r], a2d, N, r64, &dummy);
+                        count_layer(T64, gid, bd[r], a2d, N, r64, &dummy, &dummy_c);
                         if (memcmp(r32, r64, sizeof(int64_t) * (size_t)N) != 0) differing++;
                         for (int32_t c = 0; c < N; c++) img[(int64_t)r * N + c] += r32[c];
                     }
