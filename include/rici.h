@@ -70,6 +70,11 @@ extern "C" {
                                    heaviest first, early exit after every word; single-scene
                                    calls with N in {8,16,32,64,128} (other calls take the int64
                                    kernel); fastest when needles are sparse */
+#define RICI_SEARCH_INT8_TC 5  /* exact int8 tensor-core GEMM of the expanded distance (warp-level
+                                   mma.sync s8 -> s32, N in 8..128, powers of two): operands a, m
+                                   and the haystack deltas b with b^2 split into two 7-bit limbs;
+                                   pairs with |delta| > 127 on either side run in exact int64 on
+                                   CUDA cores; single- and multi-scene calls */
 /* Test hook, OR-ed into RICI_SEARCH_TENSOR: one CTA of the tensor-core kernel withholds its
  * first tile load, so its bounded waits run out (about 2 s), RICI_ERR_TIMEOUT is raised in the
  * status word and the kernel returns; outputs of that call are unspecified. */
@@ -394,6 +399,14 @@ RICI_API int rici_project_fp32(const float *points, int64_t num_points, const fl
  * A measurement helper for roofline peaks: the paper has no counterpart.  Returns RICI_OK, or
  * RICI_ERR_INVALID_ARGUMENT for a null pointer, or RICI_ERR_CUDA. */
 RICI_API int rici_measure_dp4a_rate(void *stream, double *dp4a_per_second);
+
+/* Measures, on the current device and the given stream, how many int8 multiply-adds per second
+ * the whole GPU performs through warp-level mma.sync m16n8k32 s8 x s8 -> s32 (the instruction of
+ * RICI_SEARCH_INT8_TC), running independent accumulator chains on every SM; the result goes to
+ * *int8_macs_per_second.  Synchronises the stream; allocates and frees a small device buffer.
+ * A measurement helper for roofline peaks: the paper has no counterpart.  Returns RICI_OK,
+ * RICI_ERR_INVALID_ARGUMENT for a null pointer, or RICI_ERR_CUDA. */
+RICI_API int rici_measure_mma_s8_rate(void *stream, double *int8_macs_per_second);
 
 /* Library version string. */
 RICI_API const char *rici_version(void);

@@ -22,6 +22,7 @@ SEARCH_CUDA_CORE = 1
 SEARCH_EXACT_SLOW = 2
 SEARCH_TENSOR = 3
 SEARCH_SPARSE = 4
+SEARCH_INT8_TC = 5
 SEARCH_TEST_WITHHOLD_LOAD = 0x100  # test hook (see include/rici.h)
 
 ERR_INVALID_ARGUMENT = 1
@@ -138,6 +139,8 @@ def load_library(path: str | None = None):
         lib.rici_autotune_search_batch.restype = ctypes.c_int
         lib.rici_measure_dp4a_rate.argtypes = [P, ctypes.POINTER(ctypes.c_double)]
         lib.rici_measure_dp4a_rate.restype = ctypes.c_int
+        lib.rici_measure_mma_s8_rate.argtypes = [P, ctypes.POINTER(ctypes.c_double)]
+        lib.rici_measure_mma_s8_rate.restype = ctypes.c_int
         lib.rici_version.argtypes = []
         lib.rici_version.restype = ctypes.c_char_p
         _lib = lib
@@ -518,6 +521,15 @@ def measure_dp4a_rate(stream=None) -> float:
     lib = load_library()
     out = ctypes.c_double(0.0)
     _check(lib.rici_measure_dp4a_rate(_stream_handle(stream), ctypes.byref(out)))
+    return float(out.value)
+
+
+def measure_mma_s8_rate(stream=None) -> float:
+    """Whole-device int8 multiply-adds per second through mma.sync s8 (the int8 tensor-core
+    search's instruction)."""
+    lib = load_library()
+    out = ctypes.c_double(0.0)
+    _check(lib.rici_measure_mma_s8_rate(_stream_handle(stream), ctypes.byref(out)))
     return float(out.value)
 
 

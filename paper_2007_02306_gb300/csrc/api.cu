@@ -374,7 +374,7 @@ int crss_search_ex(const uint16_t *needles, int64_t num_needles, const uint16_t 
   const int base_mode = mode & 0xff;
   if ((base_mode != RICI_SEARCH_DEFAULT && base_mode != RICI_SEARCH_CUDA_CORE &&
        base_mode != RICI_SEARCH_EXACT_SLOW && base_mode != RICI_SEARCH_TENSOR &&
-       base_mode != RICI_SEARCH_SPARSE) ||
+       base_mode != RICI_SEARCH_SPARSE && base_mode != RICI_SEARCH_INT8_TC) ||
       (mode & ~(0xff | RICI_SEARCH_TEST_WITHHOLD_LOAD)) ||
       ((mode & RICI_SEARCH_TEST_WITHHOLD_LOAD) && base_mode != RICI_SEARCH_TENSOR))
     return fail(RICI_ERR_INVALID_ARGUMENT, "unknown search mode %d", mode);
@@ -509,7 +509,8 @@ static int build_search_batch(const RiciSearchScene *scenes, int32_t ns, int32_t
   if (N < 2 || N > RICI_MAX_RESOLUTION)
     return fail(RICI_ERR_INVALID_ARGUMENT, "resolution must be in [2, %d]", RICI_MAX_RESOLUTION);
   if (mode != RICI_SEARCH_DEFAULT && mode != RICI_SEARCH_CUDA_CORE &&
-      mode != RICI_SEARCH_EXACT_SLOW && mode != RICI_SEARCH_TENSOR && mode != RICI_SEARCH_SPARSE)
+      mode != RICI_SEARCH_EXACT_SLOW && mode != RICI_SEARCH_TENSOR && mode != RICI_SEARCH_SPARSE &&
+      mode != RICI_SEARCH_INT8_TC)
     return fail(RICI_ERR_INVALID_ARGUMENT, "unknown search mode %d", mode);
   out->resize(ns);
   int64_t q = 0, h = 0, hmax = 0, tiles = 0;
@@ -704,6 +705,14 @@ int rici_measure_dp4a_rate(void *stream, double *dp4a_per_second) {
   if (!dp4a_per_second) return fail(RICI_ERR_INVALID_ARGUMENT, "null output pointer");
   cudaError_t e = measure_dp4a_rate(static_cast<cudaStream_t>(stream), dp4a_per_second);
   if (e != cudaSuccess) return cuda_fail(e, "dp4a rate");
+  return RICI_OK;
+}
+
+int rici_measure_mma_s8_rate(void *stream, double *int8_macs_per_second) {
+  t_last_error.clear();
+  if (!int8_macs_per_second) return fail(RICI_ERR_INVALID_ARGUMENT, "null output pointer");
+  cudaError_t e = measure_mma_s8_rate(static_cast<cudaStream_t>(stream), int8_macs_per_second);
+  if (e != cudaSuccess) return cuda_fail(e, "mma.sync s8 rate");
   return RICI_OK;
 }
 

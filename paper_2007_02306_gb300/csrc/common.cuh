@@ -150,6 +150,40 @@ struct SearchBatch {
 
 // Tensor-core tiles of a scene (128 needles x 256 haystack images).
 void search_tiles(int64_t Q, int64_t H, int32_t *tiles_m, int32_t *tiles_n);
+
+// A tile of one scene: needle rows [qbeg + 128 m, ...), haystack columns [hbeg + 256 n, ...),
+// valid for scene-local rows < Q and columns < H.
+struct TcTile {
+  int64_t m, n;          // tile coordinates within the scene
+  int64_t qbeg, hbeg;    // scene offsets in the launch-wide needle / haystack arrays
+  int64_t Q, H;
+};
+
+// Needle tiles are swept in groups of group_m over the scene's haystack tiles (L2 reuse).
+__device__ __forceinline__ TcTile search_tile_of(const SearchScene *tab, int ns, int64_t t,
+                                                int group_m) {
+  int lo = 0, hi = ns - 1;
+  while (lo < hi) {  // last scene whose first tile is <= t (empty scenes own no tile)
+    const int mid = (lo + hi + 1) >> 1;
+    if (tab[mid].tile_off <= t) lo = mid; else hi = mid - 1;
+  }
+  const SearchScene &sc = tab[lo];
+  const int64_t tl = t - sc.tile_off;
+  const int tiles_m = sc.tiles_m, tiles_n = sc.tiles_n;
+  const int64_t per_group = (int64_t)group_m * tiles_n;
+  const int64_t g = tl / per_group;
+  const int64_t r = tl - g * per_group;
+  const int64_t gm = min((int64_t)group_m, (int64_t)tiles_m - g * group_m);
+  TcTile tt;
+  tt.n = r / gm;
+  tt.m = g * group_m + r % gm;
+  tt.qbeg = sc.qoff;
+  tt.hbeg = sc.hoff;
+  tt.Q = sc.Q;
+  tt.H = sc.H;
+  return tt;
+}
+
 int64_t search_batch_workspace_bytes(int num_scenes, int64_t Qtot, int64_t Htot, int N, int mode);
 // scenes: host array with every offset filled (copied into the workspace by kernels).
 cudaError_t launch_search_batch(const SearchScene *scenes, const SearchBatch &b, void *ws,
@@ -167,6 +201,18 @@ cudaError_t launch_tc_encode_and_rank(const SearchScene *tab, int num_scenes, co
                                       const int *nflags, const int64_t *dtrue, int *rank,
                                       unsigned long long *best, int *status, int test_withhold,
                                       cudaStream_t st);
+
+// Integer tensor-core search (i8_search.cu): int8 operand encoding + mma.sync s8 GEMM with the
+// rank / top-1 epilogue for int8-narrow x int8-narrow pairs of every scene (the tiles of the
+// fp16 form).  Fills nwide/hwide (|delta| > 127) and the wide lists/counts.
+bool i8_supported(int N);
+int64_t i8_workspace_bytes(int64_t Q, int64_t H, int N);
+cudaError_t launch_i8_encode_and_rank(const SearchScene *tab, int num_scenes, const int *qscene,
+                                      const int *hscene, int64_t Qtot, int64_t Htot,
+                                      int64_t tiles_total, int N, void *ws, int *nwide, int *hwide,
+                                      int *wn_list, int *wh_list, int *counts,
+                                      const int *nflags, const int64_t *dtrue, int *rank,
+                                      unsigned long long *best, cudaStream_t st);
 
 // Carve 256-byte aligned sub-buffers out of one workspace allocation.
 struct Carver {
@@ -234,5 +280,7 @@ cudaError_t launch_project_fp32(const float *pts, int64_t n, const float *sv, co
 
 // Measured whole-device dp4a issue rate (instructions per second), for roofline peaks.
 cudaError_t measure_dp4a_rate(cudaStream_t st, double *per_second);
+// Measured whole-device mma.sync s8 rate (int8 multiply-adds per second), for roofline peaks.
+cudaError_t measure_mma_s8_rate(cudaStream_t st, double *macs_per_second);
 
 }  // namespace rici

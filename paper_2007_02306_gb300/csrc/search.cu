@@ -65,16 +65,21 @@ __device__ __forceinline__ int64_t word_major_offset(int64_t i, int N, int k) {
 // One warp per image.  interleave: 0 image-major deltas; 1 the layout of interleaved_offset (the
 // haystack of the dense kernel); 2 the layout of word_major_offset (the haystack of k_sparse).
 // row_sq (optional): per row, the sum of the squared (clamped) deltas, [n][N].
+// list (optional): encode images list[0 .. *list_count) of imgs as images 0, 1, ... (a compacted
+// subset, count read on the device; n is then an upper bound).
 __global__ void k_encode(const uint16_t *__restrict__ imgs, int64_t n, int N,
                          int8_t *__restrict__ delta, int8_t *__restrict__ mask,
                          int *__restrict__ wide_flag, int *__restrict__ wide_list,
-                         int *__restrict__ wide_count, int interleave, int *__restrict__ row_sq) {
+                         int *__restrict__ wide_count, int interleave, int *__restrict__ row_sq,
+                         const int *__restrict__ list = nullptr,
+                         const int *__restrict__ list_count = nullptr) {
   const int lane = threadIdx.x & 31;
   const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int K = N * N;
+  if (list) n = *list_count < n ? *list_count : n;
   for (int64_t i = w; i < n; i += nw) {
-    const uint16_t *img = imgs + i * K;
+    const uint16_t *img = imgs + (list ? (int64_t)list[i] : i) * K;
     int wide = 0;
     for (int k = lane; k < K; k += 32) {
       int r = k / N, c = k - r * N;
@@ -215,7 +220,9 @@ __global__ void __launch_bounds__(kDenseThreads, (N * kImg <= 64 ? 4 : 2) * 256 
     const int *__restrict__ hwide, int64_t H, const int64_t *__restrict__ dtrue,
     const int *__restrict__ nflags, int *__restrict__ rank, unsigned long long *__restrict__ best,
     unsigned long long *__restrict__ counters, int64_t tile0, int64_t tiles_q, int64_t tiles_h,
-    int64_t band_h) {
+    int64_t band_h, const int *__restrict__ hcount, const int *__restrict__ hmap) {
+  // hcount (optional): the haystack holds *hcount images (H is then an upper bound); hmap
+  // (optional): haystack image j is image hmap[j] of the caller's haystack (a compacted subset)
   constexpr int WPR = N / 4;  // 32-bit words per row
   constexpr int K = N * N;
   extern __shared__ int2 am_raw[];  // [kTQ][K/4] (needle delta word, mask word)
@@ -236,6 +243,10 @@ __global__ void __launch_bounds__(kDenseThreads, (N * kImg <= 64 ? 4 : 2) * 256 
   const int64_t h0 = band * band_h;
   const int64_t h1 = tiles_h - h0 < band_h ? tiles_h : h0 + band_h;
   const int64_t q0 = qt * kTQ;
+  if (hcount) {
+    H = *hcount < H ? *hcount : H;
+    if (h0 * (int64_t)(kDenseThreads * kImg) >= H) return;  // uniform over the block
+  }
 
   for (int x = tid; x < kTQ * (K / 4); x += kDenseThreads) {
     int q = x / (K / 4), wd = x - q * (K / 4);
@@ -402,7 +413,9 @@ __global__ void __launch_bounds__(kDenseThreads, (N * kImg <= 64 ? 4 : 2) * 256 
       for (int k = 0; k < kImg; ++k) {
         const bool fin = (alive[k] >> q) & 1u;
         c += fin && acc[k][q] < 0;
-        const unsigned long long bk = fin ? pack_best(acc[k][q] + thr_s[q], j0 + 32 * k) : kNoBest;
+        const int64_t jj = j0 + 32 * k;
+        const unsigned long long bk =
+            fin ? pack_best(acc[k][q] + thr_s[q], hmap ? (int64_t)hmap[jj] : jj) : kNoBest;
         b = bk < b ? bk : b;
       }
 #pragma unroll
@@ -611,7 +624,9 @@ __global__ void __launch_bounds__(kWideThreads) k_wide(
     const int *__restrict__ wide_n_count, const int *__restrict__ wide_h_list,
     const int *__restrict__ wide_h_count, const int64_t *__restrict__ dtrue,
     const int *__restrict__ nflags, int *__restrict__ rank, unsigned long long *__restrict__ best,
-    int *__restrict__ top1_flag, unsigned long long *__restrict__ counters) {
+    int *__restrict__ top1_flag, unsigned long long *__restrict__ counters,
+    const int *__restrict__ keep_h) {
+  // keep_h (optional, pass 1): only entries hj of the wide haystack list with keep_h[hj] != 0
   extern __shared__ int2 nz[];  // (flat position, needle delta) of non-zero needle deltas
   __shared__ int nnz_s;
   const int tid = threadIdx.x, lane = tid & 31;
@@ -652,7 +667,7 @@ __global__ void __launch_bounds__(kWideThreads) k_wide(
     const int64_t hj = ch * kWideThreads + tid;
     int64_t jl = -1;  // scene-local haystack index
     if (pass == 1) {
-      if (hj < nh) {
+      if (hj < nh && (!keep_h || keep_h[hj])) {
         const int64_t jg = wide_h_list[hj];
         if (hscene[jg] == si) jl = jg - sc.hoff;
       }
@@ -777,7 +792,8 @@ template <int N>
 cudaError_t launch_dense(const int8_t *nd, const int8_t *nm, const int *nrs, const int *nw, int64_t Q,
                          const int8_t *hd, const int *hw, int64_t H, const int64_t *dt,
                          const int *nf, int *rank, unsigned long long *best,
-                         unsigned long long *counters, cudaStream_t st) {
+                         unsigned long long *counters, cudaStream_t st,
+                         const int *hcount = nullptr, const int *hmap = nullptr) {
   // 4 needles x 4 haystack images per thread (N <= 64; 120 registers, two blocks of 256 threads
   // per SM) is the fastest measured shape: each broadcast needle word serves four images, and
   // the per-row bookkeeping is shared by 16 (needle, image) pairs
@@ -800,7 +816,8 @@ cudaError_t launch_dense(const int8_t *nd, const int8_t *nm, const int *nrs, con
   for (int64_t t0 = 0; t0 < total; t0 += kMaxGrid) {
     const int64_t n = total - t0 < kMaxGrid ? total - t0 : kMaxGrid;
     kern<<<(unsigned)n, kDenseThreads, smem, st>>>(nd, nm, nrs, nw, Q, hd, hw, H, dt, nf, rank,
-                                                   best, counters, t0, tq, th, band_h);
+                                                   best, counters, t0, tq, th, band_h, hcount,
+                                                   hmap);
     count_launches(1);
   }
   return cudaGetLastError();
@@ -842,16 +859,18 @@ int64_t search_batch_workspace_bytes(int num_scenes, int64_t Q, int64_t H, int N
   mode &= 0xff;
   const bool tensor =
       (mode == RICI_SEARCH_TENSOR || mode == RICI_SEARCH_DEFAULT) && tc_supported(N);
-  const bool packed = !tensor && mode != RICI_SEARCH_EXACT_SLOW && dense_supported(N);
+  const bool i8 = mode == RICI_SEARCH_INT8_TC && i8_supported(N);
+  const bool packed = !tensor && !i8 && mode != RICI_SEARCH_EXACT_SLOW && dense_supported(N);
   const bool sparse = packed && mode == RICI_SEARCH_SPARSE;
+  const bool mid = tensor && num_scenes == 1 && dense_supported(N);
   Carver c(nullptr);
   c.take<SearchScene>(num_scenes);
   c.take<int>(Q);                        // scene of each needle
   c.take<int>(H);                        // scene of each haystack image
-  c.take<int8_t>(packed ? Q * K : 0);    // needle deltas (packed CUDA-core forms only)
-  c.take<int8_t>(packed ? Q * K : 0);    // needle masks
-  c.take<int>(packed && !sparse ? Q * N : 0);  // needle row sums of squared deltas (dense)
-  c.take<int8_t>(packed ? (H + 31) / 32 * 32 * K : 0);  // haystack deltas (groups of 32)
+  c.take<int8_t>(packed || mid ? Q * K : 0);  // needle deltas (CUDA-core forms)
+  c.take<int8_t>(packed || mid ? Q * K : 0);  // needle masks
+  c.take<int>((packed && !sparse) || mid ? Q * N : 0);  // needle row sums of squared deltas
+  c.take<int8_t>(packed || mid ? (H + 31) / 32 * 32 * K : 0);  // haystack deltas (groups of 32)
   c.take<int>(Q);                        // needle wide flags
   c.take<int>(H);                        // haystack wide flags
   c.take<int>(Q);                        // wide needle list
@@ -865,6 +884,10 @@ int64_t search_batch_workspace_bytes(int num_scenes, int64_t Q, int64_t H, int N
   c.take<int4>(sparse ? Q * (K / 4) : 0);  // sparse needle entries (one slab per needle)
   c.take<int>(sparse ? Q : 0);           // sparse entries per needle
   c.take<char>(tensor ? tc_workspace_bytes(Q, H, N) : 0);
+  c.take<char>(i8 ? i8_workspace_bytes(Q, H, N) : 0);
+  c.take<int>(mid ? Q : 0);      // int8 class flags of the needles (dense middle pass)
+  c.take<int>(mid ? H : 0);      // int8 class flags of the compacted haystack images
+  c.take<int>(mid ? Q + H : 0);  // lists written by its encodes
   return c.off + 256;
 }
 
@@ -882,18 +905,23 @@ cudaError_t launch_search_batch(const SearchScene *scenes, const SearchBatch &b,
   const int mode = b.mode & 0xff;
   const bool tensor =
       (mode == RICI_SEARCH_TENSOR || mode == RICI_SEARCH_DEFAULT) && tc_supported(N);
-  const bool packed = !tensor && mode != RICI_SEARCH_EXACT_SLOW && dense_supported(N) &&
+  const bool i8 = mode == RICI_SEARCH_INT8_TC && i8_supported(N);
+  const bool packed = !tensor && !i8 && mode != RICI_SEARCH_EXACT_SLOW && dense_supported(N) &&
                       b.num_scenes == 1;
   const bool sparse = packed && mode == RICI_SEARCH_SPARSE;
   const bool dense = packed && !sparse;
+  // single-scene tensor-core calls: pairs of a narrow needle with a haystack image outside the
+  // fp16 class but inside int8 (32 < |delta| <= 127) run on the dense CUDA-core kernel over a
+  // compacted haystack instead of the int64 kernel
+  const bool mid = tensor && b.num_scenes == 1 && dense_supported(N);
   Carver c(ws);
   SearchScene *tab = c.take<SearchScene>(b.num_scenes);
   int *qscene = c.take<int>(Q);
   int *hscene = c.take<int>(H);
-  int8_t *nd = c.take<int8_t>(packed ? Q * K : 0);
-  int8_t *nm = c.take<int8_t>(packed ? Q * K : 0);
-  int *nrs = c.take<int>(dense ? Q * N : 0);
-  int8_t *hd = c.take<int8_t>(packed ? (H + 31) / 32 * 32 * K : 0);
+  int8_t *nd = c.take<int8_t>(packed || mid ? Q * K : 0);
+  int8_t *nm = c.take<int8_t>(packed || mid ? Q * K : 0);
+  int *nrs = c.take<int>(dense || mid ? Q * N : 0);
+  int8_t *hd = c.take<int8_t>(packed || mid ? (H + 31) / 32 * 32 * K : 0);
   int *nwide = c.take<int>(Q);
   int *hwide = c.take<int>(H);
   int *wn_list = c.take<int>(Q);
@@ -907,6 +935,10 @@ cudaError_t launch_search_batch(const SearchScene *scenes, const SearchBatch &b,
   int4 *sent = c.take<int4>(sparse ? Q * (K / 4) : 0);
   int *scount = c.take<int>(sparse ? Q : 0);
   char *tc_ws = tensor ? c.take<char>(tc_workspace_bytes(Q, H, N)) : nullptr;
+  char *i8_ws = i8 ? c.take<char>(i8_workspace_bytes(Q, H, N)) : nullptr;
+  int *mid_nflag = c.take<int>(mid ? Q : 0);
+  int *mid_hflag = c.take<int>(mid ? H : 0);
+  int *mid_list = c.take<int>(mid ? Q + H : 0);
 
   cudaError_t e;
   for (int s0 = 0; s0 < b.num_scenes; s0 += kFillChunk) {
@@ -933,16 +965,49 @@ cudaError_t launch_search_batch(const SearchScene *scenes, const SearchBatch &b,
   if ((e = cudaFuncSetAttribute(k_wide, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)wide_smem)) != cudaSuccess)
     return e;
-  auto wide = [&](int pass) {
+  auto wide = [&](int pass, const int *keep_h = nullptr) {
     k_wide<<<152 * 8, kWideThreads, wide_smem, st>>>(tab, qscene, hscene, Q, b.Hmax, N, pass,
                                                    nwide, wn_list, counts + 0, wh_list,
-                                                   counts + 1, dt, nflags, rank, best, t1flag, cnt);
+                                                   counts + 1, dt, nflags, rank, best, t1flag, cnt,
+                                                   keep_h);
     count_launches(1);
+  };
+  auto run_dense = [&](const int *nexcl, const int *hexcl, const int *hcount, const int *hmap) {
+    switch (N) {
+      case 8: return launch_dense<8>(nd, nm, nrs, nexcl, Q, hd, hexcl, H, dt, nflags, rank, best, cnt, st, hcount, hmap);
+      case 16: return launch_dense<16>(nd, nm, nrs, nexcl, Q, hd, hexcl, H, dt, nflags, rank, best, cnt, st, hcount, hmap);
+      case 32: return launch_dense<32>(nd, nm, nrs, nexcl, Q, hd, hexcl, H, dt, nflags, rank, best, cnt, st, hcount, hmap);
+      case 64: return launch_dense<64>(nd, nm, nrs, nexcl, Q, hd, hexcl, H, dt, nflags, rank, best, cnt, st, hcount, hmap);
+      default: return launch_dense<128>(nd, nm, nrs, nexcl, Q, hd, hexcl, H, dt, nflags, rank, best, cnt, st, hcount, hmap);
+    }
   };
   if (tensor) {
     if ((e = launch_tc_encode_and_rank(tab, b.num_scenes, qscene, hscene, Q, H, b.tiles_total, N,
                                        tc_ws, nwide, hwide, wn_list, wh_list, counts, nflags, dt,
                                        rank, best, b.status, withhold, st)) != cudaSuccess)
+      return e;
+    wide(0);  // needles outside the fp16 class against the whole haystack (int64)
+    if (mid) {
+      // dense encodes: every needle (the fp16-class ones are int8-class too), and the haystack
+      // images outside the fp16 class, compacted in list order (list and count from the
+      // tensor-core encode); then narrow needles x those images on CUDA cores, and the int64
+      // kernel only for the compacted images outside the int8 class
+      const SearchScene &s0 = scenes[0];
+      k_encode<<<blocks_for(Q), 32 * wpb, 0, st>>>(s0.needles, Q, N, nd, nm, mid_nflag, mid_list,
+                                                   counts + 2, 0, nrs);
+      k_encode<<<blocks_for(H), 32 * wpb, 0, st>>>(s0.haystack, H, N, hd, nullptr, mid_hflag,
+                                                   mid_list + Q, counts + 3, 1, nullptr, wh_list,
+                                                   counts + 1);
+      count_launches(2);
+      if ((e = run_dense(nwide, mid_hflag, counts + 1, wh_list)) != cudaSuccess) return e;
+      wide(1, mid_hflag);
+    } else {
+      wide(1);
+    }
+  } else if (i8) {
+    if ((e = launch_i8_encode_and_rank(tab, b.num_scenes, qscene, hscene, Q, H, b.tiles_total, N,
+                                       i8_ws, nwide, hwide, wn_list, wh_list, counts, nflags, dt,
+                                       rank, best, st)) != cudaSuccess)
       return e;
     wide(0);
     wide(1);
@@ -954,14 +1019,7 @@ cudaError_t launch_search_batch(const SearchScene *scenes, const SearchBatch &b,
     k_encode<<<blocks_for(H), 32 * wpb, 0, st>>>(s0.haystack, H, N, hd, nullptr, hwide, wh_list,
                                                  counts + 1, 1, nullptr);
     count_launches(2);
-    switch (N) {
-      case 8: e = launch_dense<8>(nd, nm, nrs, nwide, Q, hd, hwide, H, dt, nflags, rank, best, cnt, st); break;
-      case 16: e = launch_dense<16>(nd, nm, nrs, nwide, Q, hd, hwide, H, dt, nflags, rank, best, cnt, st); break;
-      case 32: e = launch_dense<32>(nd, nm, nrs, nwide, Q, hd, hwide, H, dt, nflags, rank, best, cnt, st); break;
-      case 64: e = launch_dense<64>(nd, nm, nrs, nwide, Q, hd, hwide, H, dt, nflags, rank, best, cnt, st); break;
-      default: e = launch_dense<128>(nd, nm, nrs, nwide, Q, hd, hwide, H, dt, nflags, rank, best, cnt, st); break;
-    }
-    if (e != cudaSuccess) return e;
+    if ((e = run_dense(nwide, hwide, nullptr, nullptr)) != cudaSuccess) return e;
     wide(0);
     wide(1);
   } else if (sparse) {

@@ -241,36 +241,9 @@ struct TcArgs {
   int group_m;              // needle tiles per group of the tile order
 };
 
-// A tile of one scene: needle rows [qbeg + 128 m, ...), haystack columns [hbeg + 256 n, ...),
-// valid for scene-local rows < Q and columns < H.
-struct TcTile {
-  int64_t m, n;          // tile coordinates within the scene
-  int64_t qbeg, hbeg;    // scene offsets in the launch-wide needle / haystack arrays
-  int64_t Q, H;
-};
-
-// Needle tiles are swept in groups of group_m over the scene's haystack tiles (L2 reuse).
+// Tiles and their order: search_tile_of (common.cuh).
 __device__ __forceinline__ TcTile tile_of(const SearchScene *tab, int ns, int64_t t, int group_m) {
-  int lo = 0, hi = ns - 1;
-  while (lo < hi) {  // last scene whose first tile is <= t (empty scenes own no tile)
-    const int mid = (lo + hi + 1) >> 1;
-    if (tab[mid].tile_off <= t) lo = mid; else hi = mid - 1;
-  }
-  const SearchScene &sc = tab[lo];
-  const int64_t tl = t - sc.tile_off;
-  const int tiles_m = sc.tiles_m, tiles_n = sc.tiles_n;
-  const int64_t per_group = (int64_t)group_m * tiles_n;
-  const int64_t g = tl / per_group;
-  const int64_t r = tl - g * per_group;
-  const int64_t gm = min((int64_t)group_m, (int64_t)tiles_m - g * group_m);
-  TcTile tt;
-  tt.n = r / gm;
-  tt.m = g * group_m + r % gm;
-  tt.qbeg = sc.qoff;
-  tt.hbeg = sc.hoff;
-  tt.Q = sc.Q;
-  tt.H = sc.H;
-  return tt;
+  return search_tile_of(tab, ns, t, group_m);
 }
 
 __global__ void __launch_bounds__(kTcThreads, 1)

@@ -150,3 +150,75 @@ def needle_haystack_set_torch(seed: int, num_needles: int, num_haystack: int, N:
     for s in range(0, num_haystack, chunk):
         plateaus(hay16[s:s + min(chunk, num_haystack - s)], clutter_fraction, 0.1, 2)
     return needles16.view(torch.uint16), hay16.view(torch.uint16), match
+
+
+def plateau_list(rng: np.random.Generator, n_images: int, N: int, image_fraction: float,
+                 row_fraction: float, heights=None, kmax: int = 300):
+    """A seeded list of plateaus: (image, row, c1, c2, height) arrays, one entry per selected row
+    of each selected image (every selected image gets at least one row), adding ``height`` to
+    columns [c1, c2) of that row.  heights: None draws heavy-tailed signed heights
+    (``heavy_tail_heights``), an int gives a fixed height.  Within one list every (image, row)
+    pair appears at most once, so the entries can be applied in any order."""
+    imgs = np.nonzero(rng.random(n_images) < image_fraction)[0]
+    rows = rng.random((imgs.size, N)) < row_fraction
+    none = np.nonzero(~rows.any(axis=1))[0]
+    rows[none, rng.integers(0, N, none.size)] = True
+    ii, rr = np.nonzero(rows)
+    img = imgs[ii].astype(np.int64)
+    c1 = rng.integers(0, N - 1, img.size)
+    c2 = c1 + 1 + np.floor(rng.random(img.size) * (N - c1)).astype(np.int64)
+    if heights is None:
+        h = heavy_tail_heights(rng, img.size, kmax)
+    else:
+        h = np.full(img.size, int(heights), np.int64)
+    return {"image": img, "row": rr.astype(np.int64), "c1": c1, "c2": c2, "height": h}
+
+
+def apply_plateaus(images: np.ndarray, plist, chunk: int = 1 << 18) -> np.ndarray:
+    """Apply a ``plateau_list`` to uint16 [n, N, N] images in place (results clipped to the
+    uint16 range)."""
+    N = images.shape[2]
+    cols = np.arange(N)[None, :]
+    for s in range(0, plist["image"].size, chunk):
+        sl = slice(s, s + chunk)
+        i, r = plist["image"][sl], plist["row"][sl]
+        add = ((cols >= plist["c1"][sl, None]) & (cols < plist["c2"][sl, None])) * \
+            plist["height"][sl, None]
+        images[i, r] = np.clip(images[i, r].astype(np.int64) + add, 0, 65535).astype(np.uint16)
+    return images
+
+
+def apply_plateaus_torch(images16, plist, chunk: int = 1 << 18):
+    """``apply_plateaus`` for a torch uint16 tensor (any device), in place."""
+    import torch
+
+    dev = images16.device
+    ims = images16.view(torch.int16)
+    N = ims.shape[2]
+    cols = torch.arange(N, device=dev)[None, :]
+    for s in range(0, plist["image"].size, chunk):
+        sl = slice(s, s + chunk)
+        t = {k: torch.from_numpy(np.ascontiguousarray(v[sl])).to(dev) for k, v in plist.items()}
+        add = ((cols >= t["c1"][:, None]) & (cols < t["c2"][:, None])).to(torch.int64) * \
+            t["height"][:, None]
+        cur = ims[t["image"], t["row"]].to(torch.int64) & 0xFFFF
+        v = (cur + add).clamp(0, 65535)
+        ims[t["image"], t["row"]] = torch.where(v > 32767, v - 65536, v).to(torch.int16)
+    return images16
+
+
+def precision_form_recipe(seed: int, num_images: int, num_needles: int, N: int,
+                          tail_image_fraction: float = 0.02, tail_row_fraction: float = 0.03,
+                          clutter_fraction: float = 0.3, clutter_row_fraction: float = 0.1,
+                          clutter_height: int = 2, kmax: int = 300):
+    """Everything but the base images of the precision-form set: heavy-tailed plateaus (2 % of
+    the images, 3 % of their rows, P(|v| = k) ~ k^-2 up to 300), the needle indices (distinct,
+    taken after the tails and before clutter) and clutter plateaus (+2 in 10 % of the rows of
+    30 % of the haystack images).  The base images are RICI images of seeded scenes
+    (``synth.scenes.precision_form_scenes``), computed by whichever side uses the recipe."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    tails = plateau_list(rng, num_images, N, tail_image_fraction, tail_row_fraction, None, kmax)
+    needles = rng.choice(num_images, size=num_needles, replace=False).astype(np.int64)
+    clutter = plateau_list(rng, num_images, N, clutter_fraction, clutter_row_fraction,
+                           clutter_height)
+    return tails, needles, clutter

@@ -168,3 +168,10 @@ def clutterbox(seed: int, n: int = 10, box_side: float = 3.0, tri_lo: int = 2000
     half = box_side / 2.0 - 1.0
     placed = [_place(rng, objects[i], half) for i in order]
     return [assemble(placed[:k]) for k in range(1, n + 1)]
+
+
+def precision_form_scenes(seed: int = 31, n_scenes: int = 6473):
+    """The base meshes of the precision-form image set: n_scenes single displaced icospheres
+    (subdivision 2, 162 vertices each, as ``tiny_scene``), each with its own seed; their RICI
+    images in scene order, first 2^20 kept, make the haystack pool."""
+    return [tiny_scene(seed * 100_000 + k) for k in range(n_scenes)]

@@ -4,8 +4,10 @@ Scenes follow the batched workload's recipe (a target plus 1-15 clutter meshes o
 here 24 scenes of 10k-300k triangles so the test stays short).  Per scene: needle images of a
 seeded sample of target vertices with the target alone, haystack images of every scene vertex,
 and a tensor-core search of the needles against their own scene.  The batched results must equal
-one rici_generate / crss_search call per scene bit for bit, sampled images and ranks must equal
-the oracle, and the whole batched run recorded into a CUDA graph must replay to the same results.
+one rici_generate / crss_search call per scene bit for bit, sampled images (and every image and
+rank of the two smallest scenes, from the oracle's own images) must equal the oracle, every exact
+search form must agree, and the whole batched run recorded into a CUDA graph must replay to the
+same results.
 """
 import numpy as np
 import pytest
@@ -87,15 +89,39 @@ def test_batch_equals_per_scene_calls_and_oracle(rici, oracle_mod, batch):
         assert np.array_equal(host_u16(imgs[2 * i + 1]), host_u16(hy))
         for k in ("rank", "true_distance", "top1"):
             assert np.array_equal(res[i][k].cpu().numpy(), one[k].cpu().numpy()), (i, k)
-        if i % 6 == 0:  # oracle: sampled haystack images and needle ranks of some scenes
+        if i % 6 == 0:  # oracle: sampled haystack images of some scenes
             pick = rng.choice(s.num_vertices, 3, replace=False)
             ref = oracle_mod.rici_fp64(s.vertices, s.normals, s.triangles, pick, R, N)
             assert np.array_equal(host_u16(imgs[2 * i + 1])[pick], ref)
-            qs = np.array([0, len(x["needle_origins"]) - 1])
-            ro = oracle_mod.crss_search(host_u16(imgs[2 * i])[qs], host_u16(imgs[2 * i + 1]),
-                                        x["needle_origins"][qs].astype(np.int64))
-            for k in ("rank", "true_distance", "top1"):
-                assert np.array_equal(res[i][k].cpu().numpy()[qs], ro[k]), (i, k)
+    # oracle: the two smallest scenes in full, images and ranks computed from the oracle's own
+    # images (needles with the target alone, haystack with the whole scene)
+    small = sorted(range(len(batch)), key=lambda i: batch[i]["scene"].num_triangles)[:2]
+    for i in small:
+        x, s = batch[i], batch[i]["scene"]
+        tgt = s.target_only()
+        ond = oracle_mod.rici_fp64(tgt.vertices, tgt.normals, tgt.triangles, x["needle_origins"],
+                                   R, N)
+        ohy = oracle_mod.rici_fp64(s.vertices, s.normals, s.triangles,
+                                   np.arange(s.num_vertices), R, N)
+        assert np.array_equal(host_u16(imgs[2 * i]), ond)
+        assert np.array_equal(host_u16(imgs[2 * i + 1]), ohy)
+        ro = oracle_mod.crss_search(ond, ohy, x["needle_origins"].astype(np.int64))
+        for k in ("rank", "true_distance", "top1"):
+            assert np.array_equal(res[i][k].cpu().numpy(), ro[k]), (i, k)
+
+
+@pytest.mark.parametrize("mode", [1, 4, 5])
+def test_batch_search_forms_agree(rici, batch, mode):
+    """Every exact form of the multi-scene search gives the tensor-core form's ranks, true
+    distances and top-1 on the batch's images (each needle against its own scene only)."""
+    imgs, res = run_batch(rici, batch)
+    srch = [{"needles": imgs[2 * i], "haystack": imgs[2 * i + 1], "true_match": x["match"]}
+            for i, x in enumerate(batch)]
+    other = rici.crss_search_batch(srch, N, mode=mode)
+    assert rici.sync_status() == 0
+    for i in range(len(batch)):
+        for k in ("rank", "true_distance", "top1"):
+            assert np.array_equal(other[i][k].cpu().numpy(), res[i][k].cpu().numpy()), (i, k)
 
 
 def test_batch_run_replays_from_a_cuda_graph(rici, batch):

@@ -53,7 +53,7 @@ def dataset(seed, Q, H, N, **kw):
     return synth.images.needle_haystack_set(rng, Q, H, N, **kw)
 
 
-@pytest.mark.parametrize("mode", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("mode", [0, 1, 2, 3, 4, 5])
 def test_small_set_all_outputs(rici, oracle_mod, mode):
     nd, hay, m = dataset(1, 64, 700, 64)
     ref = oracle_mod.crss_search(nd, hay, m, return_distances=True)
@@ -62,14 +62,14 @@ def test_small_set_all_outputs(rici, oracle_mod, mode):
 
 
 @pytest.mark.parametrize("N", [8, 16, 32, 128, 12, 2])
-@pytest.mark.parametrize("mode", [1, 3, 4])
+@pytest.mark.parametrize("mode", [1, 3, 4, 5])
 def test_resolutions(rici, oracle_mod, N, mode):
     nd, hay, m = dataset(2, 40, 300, N)
     ref = oracle_mod.crss_search(nd, hay, m)
     check(run(rici, nd, hay, m, mode=mode), ref)
 
 
-@pytest.mark.parametrize("mode", [1, 3, 4])
+@pytest.mark.parametrize("mode", [1, 3, 4, 5])
 def test_heavy_tails_and_extremes(rici, oracle_mod, mode):
     rng = np.random.default_rng(3)
     nd, hay, m = synth.images.needle_haystack_set(rng, 60, 900, 64, tail_image_fraction=0.3,
@@ -105,14 +105,35 @@ def test_tensor_accumulator_exact_at_the_narrow_limit(rici, oracle_mod):
     check(run(rici, nd, hay, m, mode=3, dist=True), ref, dist=True)
 
 
-@pytest.mark.parametrize("Q,H", [(1, 1), (129, 257), (300, 1000)])
-def test_tensor_ragged_tiles(rici, oracle_mod, Q, H):
+def test_int8_accumulators_exact_at_the_int8_limit(rici, oracle_mod):
+    """Largest sums the int8 operands allow: deltas +-127 everywhere (|G1| = 4032 * 127^2,
+    the squared-delta limbs at q = 126, r = 1), in every combination of signs."""
+    N = 64
+    col = np.arange(N)
+    up = np.tile((127 * col).astype(np.uint16), (N, 1))           # deltas +127 everywhere
+    down = np.tile((127 * (N - 1 - col)).astype(np.uint16), (N, 1))  # deltas -127 everywhere
+    zig = np.tile(np.where(col % 2 == 0, 0, 127).astype(np.uint16), (N, 1))  # +127/-127
+    rng = np.random.default_rng(13)
+    rnd = np.cumsum(rng.choice([-127, 127, -126, 11, -12], size=(6, N, N)), axis=2)
+    rnd = (rnd - rnd.min(axis=2, keepdims=True)).astype(np.uint16)
+    ims = np.concatenate([np.stack([up, down, zig, np.zeros((N, N), np.uint16)]), rnd])
+    nd = ims.copy()
+    hay = np.concatenate([ims[::-1], ims])
+    m = np.arange(len(nd)) + len(ims)
+    ref = oracle_mod.crss_search(nd, hay, m, return_distances=True)
+    assert ref["distances"].max() == 64 * 63 * 254 ** 2  # +127 against -127 at every position
+    check(run(rici, nd, hay, m, mode=5, dist=True), ref, dist=True)
+
+
+@pytest.mark.parametrize("mode", [3, 5])
+@pytest.mark.parametrize("Q,H", [(1, 1), (65, 129), (129, 257), (300, 1000)])
+def test_tensor_ragged_tiles(rici, oracle_mod, Q, H, mode):
     nd, hay, m = dataset(11, Q, H, 64)
-    check(run(rici, nd, hay, m, mode=3), oracle_mod.crss_search(nd, hay, m))
+    check(run(rici, nd, hay, m, mode=mode), oracle_mod.crss_search(nd, hay, m))
 
 
 @pytest.mark.parametrize("N", [64, 32, 16])
-@pytest.mark.parametrize("mode", [1, 4])
+@pytest.mark.parametrize("mode", [1, 4, 5])
 def test_dense_bands_and_ragged_tiles(rici, oracle_mod, N, mode):
     """CUDA-core forms (dense and sparse-needle) over many haystack tiles: bands of several tiles, a ragged last tile whose
     tail ends inside a thread's image groups, and a partial last needle tile; needles sampled
@@ -151,7 +172,7 @@ def test_dense_bands_and_ragged_tiles(rici, oracle_mod, N, mode):
         assert np.array_equal(got[k][pick], ref[k]), k
 
 
-@pytest.mark.parametrize("mode", [1, 4])
+@pytest.mark.parametrize("mode", [1, 4, 5])
 def test_degenerate_needles(rici, oracle_mod, mode):
     """Needles with no non-zero delta (constant rows: distance 0 to everything), one non-zero
     delta, a non-zero delta only in the last column, and one full row of +-127 deltas."""
@@ -168,7 +189,7 @@ def test_degenerate_needles(rici, oracle_mod, mode):
     check(run(rici, nd, hay, m, mode=mode, dist=True), ref, dist=True)
 
 
-@pytest.mark.parametrize("mode", [0, 1, 4])
+@pytest.mark.parametrize("mode", [0, 1, 4, 5])
 def test_ties_keep_best_rank(rici, oracle_mod, mode):
     nd, hay, m = dataset(4, 50, 500, 32)
     for k in range(0, 50, 3):  # duplicates of true matches elsewhere in the haystack
@@ -219,7 +240,7 @@ def test_single_haystack_and_single_needle(rici, oracle_mod):
     check(run(rici, nd, hay, m), oracle_mod.crss_search(nd, hay, m))
 
 
-@pytest.mark.parametrize("mode", [1, 3, 4])
+@pytest.mark.parametrize("mode", [1, 3, 4, 5])
 def test_clutter_scale_search_sampled_needles(rici, oracle_mod, mode):
     """Full benchmark size: 10,242 needles x 114,892 haystack images, N = 64."""
     Q, H = 10242, 114892
