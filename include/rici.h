@@ -63,8 +63,12 @@ extern "C" {
 #define RICI_SEARCH_CUDA_CORE 1 /* Listing 1 per pair on CUDA cores, early exit */
 #define RICI_SEARCH_EXACT_SLOW 2 /* generic int64 per-pair kernel for every pair (test reference) */
 #define RICI_SEARCH_TENSOR 3    /* exact fp16 tcgen05 GEMM of the expanded distance (N in 8..128,
-                                   powers of two); pairs with |delta| > 32 on either side run in
-                                   exact int64 on CUDA cores */
+                                   powers of two) for needles with every |delta| <= 127 and
+                                   haystack images with every |delta| <= 45 and
+                                   sum b^2 + 254 sum |b| < 2^24 (all partial sums exact in FP32);
+                                   single-scene calls run the other int8-class pairs on the dense
+                                   CUDA-core kernel, and pairs with |delta| > 127 (multi-scene
+                                   calls: any pair outside the fp16 class) in exact int64 */
 #define RICI_SEARCH_SPARSE 4    /* Listing 1 over each needle's non-zero delta words only (the
                                    positions where a != 0, Section 3.2), on CUDA cores: words
                                    heaviest first, early exit after every word; single-scene
@@ -362,7 +366,7 @@ RICI_API int rici_set_tuning(const RiciTuning *tuning);
 RICI_API int rici_get_tuning(RiciTuning *tuning);
 
 /* Autotuner of the batched run.  Runs rici_generate_batch on the given scenes under each candidate
- * generation setting (gen_cells_per_reach in {2,3} x gen_big_radius in {1/8, 1/4, 1/2} x
+ * generation setting (gen_cells_per_reach in {2,3} x gen_big_radius in {1/8, 1/4, 1/2, 1} x
  * gen_warps in {4,8}; the other fields as in force), one untimed warm-up and `repeats` (1..100)
  * runs timed with CUDA events on `stream`, and writes the fastest setting to *best and its mean
  * time in milliseconds to *best_ms (may be NULL).  The scenes' output images are written by every

@@ -745,7 +745,7 @@ int rici_autotune_generate_batch(const RiciGenerateScene *scenes, int32_t num_sc
   std::vector<Tuning> cands;
   const Tuning base = current_tuning();
   const int cells[] = {2, 3};
-  const float big[] = {0.125f, 0.25f, 0.5f};
+  const float big[] = {0.125f, 0.25f, 0.5f, 1.0f};
   const int warps[] = {4, 8};
   for (int c : cells)
     for (float b : big)

@@ -6,11 +6,13 @@
 // with a, b the column deltas (delta of column 0 := 0) and m_ik = [a_ik != 0] (m a = a).
 // S is one GEMM with K = 2 N^2:  needle row [m_i | a_i]  x  haystack row [b_j^2 | -2 b_j].
 //
-// Exactness: for images whose deltas all satisfy |delta| <= 32 ("narrow"), every operand is an
-// integer exactly representable in fp16 (b^2 <= 1024, |2b| <= 64), every product is an exact
-// integer and every partial sum is an integer of magnitude <= 4032 * (1024 + 2048) < 2^24, so
-// the FP32 accumulation in TMEM is exact in any order.  Pairs with a wide side go to the exact
-// int64 CUDA-core kernel.  The rank test S_ij < d(i,match_i) - A_i, and the top-1 key
+// Exactness (the fp16 class): a needle is in the class when every |a| <= 127, a haystack image
+// when every |b| <= 45 and S2_j + 254 S1_j < 2^24, with S2_j = sum_k b_jk^2 and
+// S1_j = sum_k |b_jk|.  Every operand is then an integer exactly representable in fp16 (m, a;
+// b^2 <= 2025 < 2^11, |2b| <= 90), every product is an exact integer, and every partial sum of
+// any subset of the products m_ik b_jk^2 - 2 a_ik b_jk is an integer of magnitude at most
+// S2_j + 2 * 127 * S1_j < 2^24, so the FP32 accumulation in TMEM is exact in any order.  Pairs
+// with a side outside the class go to the CUDA-core kernels (dense int8 or exact int64).  The rank test S_ij < d(i,match_i) - A_i, and the top-1 key
 // (A_i + S_ij, j), are evaluated in the GEMM epilogue; S is never written to memory.
 //
 // Kernel structure (one CTA per SM, persistent over 128 x 256 output tiles):
@@ -36,7 +38,9 @@ constexpr int kStages = 4;
 constexpr int kTcThreads = 192;   // 6 warps
 constexpr uint32_t kStageA = kBM * kBK * 2;  // 16 KB
 constexpr uint32_t kStageB = kBN * kBK * 2;  // 32 KB
-constexpr int kNarrow = 32;       // |delta| limit of the exact fp16 operands
+constexpr int kNarrowA = 127;     // |delta| limit of fp16-class needles (int8)
+constexpr int kNarrowB = 45;      // |delta| limit of fp16-class haystack images (b^2 < 2^11)
+constexpr int64_t kExactSum = 1ll << 24;  // bound on every partial sum (exact FP32 integers)
 constexpr unsigned long long kNoBestTc = ~0ull;
 constexpr unsigned long long kWaitBudgetNs = 2000000000ull;
 constexpr unsigned long long kDrainBudgetNs = 200000000ull;
@@ -171,8 +175,8 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t (&v)[32]) {
 // ---------------------------------------------------------------- operand encoding (S2)
 
 // One warp per image (launch-wide index).  Needle rows: [m | a]; haystack rows: [b^2 | -2b]
-// (fp16, K = 2 N^2).  Also: narrow flag (all |delta| <= kNarrow), list of wide images, and for
-// needles A_i.
+// (fp16, K = 2 N^2).  Also: the class flag (wide = outside the fp16 class, see the exactness
+// note above), the list of wide images, and for needles A_i.
 __global__ void k_tc_encode(const SearchScene *__restrict__ tab, const int *__restrict__ scene_of,
                             int64_t n, int N, int needle_side, __half *__restrict__ op,
                             int *__restrict__ wide_flag, int *__restrict__ wide_list,
@@ -187,7 +191,8 @@ __global__ void k_tc_encode(const SearchScene *__restrict__ tab, const int *__re
     const uint16_t *img = needle_side ? sc.needles + (i - sc.qoff) * K0
                                       : sc.haystack + (i - sc.hoff) * K0;
     __half *row = op + i * (int64_t)(2 * K0);
-    int wide = 0, a2 = 0;
+    const int lim = needle_side ? kNarrowA : kNarrowB;
+    int wide = 0, a2 = 0, s1 = 0;  // needles: a2 = sum a^2; haystack: a2 = S2_j, s1 = S1_j
     for (int k0 = lane * 8; k0 < K0; k0 += 32 * 8) {
       __align__(16) __half lo[8], hi[8];
 #pragma unroll
@@ -195,14 +200,15 @@ __global__ void k_tc_encode(const SearchScene *__restrict__ tab, const int *__re
         const int k = k0 + e;
         const int r = k / N, c = k - r * N;
         const int d = c == 0 ? 0 : (int)img[r * N + c] - (int)img[r * N + c - 1];
-        const bool nar = d >= -kNarrow && d <= kNarrow;
+        const bool nar = d >= -lim && d <= lim;
         wide |= !nar;
         const int dc = nar ? d : 0;
+        a2 += dc * dc;
         if (needle_side) {
           lo[e] = __int2half_rn(dc != 0 ? 1 : 0);
           hi[e] = __int2half_rn(dc);
-          a2 += dc * dc;
         } else {
+          s1 += dc < 0 ? -dc : dc;
           lo[e] = __int2half_rn(dc * dc);
           hi[e] = __int2half_rn(-2 * dc);
         }
@@ -212,8 +218,12 @@ __global__ void k_tc_encode(const SearchScene *__restrict__ tab, const int *__re
     }
     wide = __any_sync(0xffffffffu, wide);
 #pragma unroll
-    for (int d = 16; d > 0; d >>= 1) a2 += __shfl_down_sync(0xffffffffu, a2, d);
+    for (int d = 16; d > 0; d >>= 1) {
+      a2 += __shfl_down_sync(0xffffffffu, a2, d);
+      s1 += __shfl_down_sync(0xffffffffu, s1, d);
+    }
     if (lane == 0) {
+      if (!needle_side && (int64_t)a2 + 2ll * kNarrowA * s1 >= kExactSum) wide = 1;
       wide_flag[i] = wide;
       if (wide) wide_list[atomicAdd(wide_count, 1)] = (int)i;
       if (asum) asum[i] = a2;
@@ -371,7 +381,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       if (row_ok) {
         asum = a.asum[i];
         thr_i = a.dtrue[i] - asum;
-        // narrow S values are integers with |S| < 2^24; clamping keeps S < thr exact in fp32
+        // fp16-class S values are integers with |S| < 2^24; clamping keeps S < thr exact
         thr = (float)(thr_i > (1ll << 25) ? (1ll << 25) : (thr_i < -(1ll << 25) ? -(1ll << 25) : thr_i));
       }
       int cnt = 0;

@@ -105,6 +105,31 @@ def test_tensor_accumulator_exact_at_the_narrow_limit(rici, oracle_mod):
     check(run(rici, nd, hay, m, mode=3, dist=True), ref, dist=True)
 
 
+def test_tensor_class_exact_at_its_partial_sum_bound(rici, oracle_mod):
+    """The fp16 class's bound: a haystack image with n deltas of +45 against a needle with
+    deltas of -127 at the same positions gives partial sums up to n (45^2 + 2 * 127 * 45), just
+    below 2^24 for n = 1,246 (in the class) and above it for n = 1,247 (the dense kernel)."""
+    N = 64
+
+    def image(n, step, base):
+        img = np.zeros((N, N), np.int64)
+        flat = np.zeros(N * (N - 1), np.int64)
+        flat[:n] = step
+        img[:, 1:] = flat.reshape(N, N - 1)
+        return (base + np.cumsum(img, axis=1)).astype(np.uint16)
+
+    h_in, h_out = image(1246, 45, 0), image(1247, 45, 0)
+    n_in, n_out = image(1246, -127, 127 * 63), image(1247, -127, 127 * 63)
+    rng = np.random.default_rng(14)
+    noise = synth.images.rici_like_images(rng, 6, N)
+    hay = np.stack([h_in, h_in.copy(), h_out, h_out.copy(), np.zeros((N, N), np.uint16), *noise])
+    nd = np.stack([n_in, n_out, n_in, n_out, noise[0]])
+    m = np.array([0, 2, 1, 3, 5], np.int64)
+    ref = oracle_mod.crss_search(nd, hay, m, return_distances=True)
+    assert ref["distances"][0, 0] == 1246 * (127 ** 2 + 45 ** 2 + 2 * 127 * 45)
+    check(run(rici, nd, hay, m, mode=3, dist=True), ref, dist=True)
+
+
 def test_int8_accumulators_exact_at_the_int8_limit(rici, oracle_mod):
     """Largest sums the int8 operands allow: deltas +-127 everywhere (|G1| = 4032 * 127^2,
     the squared-delta limbs at q = 126, r = 1), in every combination of signs."""

@@ -57,7 +57,7 @@ def images(rici, scenes):
 
 
 GEN_CANDIDATES = [{"gen_cells_per_reach": c, "gen_big_radius": b, "gen_warps": w, "tc_group_m": 8}
-                  for c in (2, 3) for b in (0.125, 0.25, 0.5) for w in (4, 8)]
+                  for c in (2, 3) for b in (0.125, 0.25, 0.5, 1.0) for w in (4, 8)]
 
 
 def test_every_generation_tuning_gives_the_same_images(rici, scenes, oracle_mod):
