@@ -1,20 +1,26 @@
 #!/usr/bin/env python
-"""Benchmark of the RICI hot path on one clutter scene (one JSON line on stdout).
+"""Benchmark of the RICI hot path on the large scene (one JSON line on stdout).
 
-Workload: a displaced-icosphere target (20,480 triangles) plus 9 clutter meshes of
-5k-50k triangles in a box of side 2 (229,756 triangles, 114,892 vertices, seed 2).
-One step is the whole hot path over that scene:
-  1. RICI 64x64 images (R = 0.3) of the target's 10,242 vertices with the target alone
-     (the needles),
-  2. RICI images of all 114,892 scene vertices (the haystack),
-  3. CUDA-core clutter-resistant search of every needle against every haystack image
-     (1.18e9 comparisons): rank of its true match, true distance, top-1.
-value = (needle + haystack images) / step time, whole job.  Inputs are resident in HBM and
-L2 is flushed (512 MB write) before every timed step.  e2e repeats the step through the
-same public API starting from pinned host buffers, with the host<->device copies timed.
+Workload (the largest single-GPU configuration): 41 seeded displaced meshes (a subdivision-7
+icosphere target, subdivision-6 icospheres and tori) with 5,019,510 triangles and 2,509,797
+vertices, centres in [-1,1]^3 (box of side 4, every bounding sphere inside).  One step is the
+whole hot path over that scene:
+  1. RICI 64x64 images of every vertex at support radii 0.15, 0.3 and 0.6 (7,529,391 images),
+  2. RICI images (R = 0.3) of 100,000 seeded target vertices with the target alone (needles),
+  3. clutter-resistant search of every needle against all 2,509,797 R = 0.3 images
+     (2.5e11 comparisons): rank of its true match (the same vertex), true distance, top-1.
+value = images generated per second of the whole step (7,629,391 images / step time); the
+breakdown gives every part and comparisons/s.  Inputs are resident in HBM (all images are
+larger than L2) and L2 is flushed by a 512 MB write before every timed step.  e2e repeats the
+step through the same public API from pinned host buffers with the copies timed.
 
---impl reference times the CPU oracle (FP64 brute force / int64 Listing 1) on bounded
-samples of the same workload and extrapolates to the full step.
+Beside the step (outside its timed region): the other exact search forms on a needle sample of
+the same images (int8 tensor cores, CUDA-core dense, sparse-needle), and the comparison
+workloads: the clutter scene, the precision-form image set at full size, the batched run of
+256 scenes at full size, a synthetic clutterbox experiment, the clutter measure and spin images.
+
+--impl reference times the CPU oracle (FP64 brute force / int64 distances) on bounded samples
+of the same workload and extrapolates to the full step.
 """
 from __future__ import annotations
 
@@ -36,68 +42,73 @@ if ROOT not in sys.path:
 
 METRIC = "RICI images/s; CRSS comparisons/s (int8-TC vs CUDA-core), ranks exact vs oracle"
 N_RES = 64
-R_SUP = 0.3
-SEED = 2
-WORKLOAD = ("clutter scene: displaced icosphere target (subdivision 5, 20,480 triangles) + 9 "
-            "clutter meshes (5k-50k triangles, displaced icospheres/tori), box side 2; RICI 64x64 "
-            "uint16 at R=0.3 for the 10,242 target vertices (target alone) and all 114,892 scene "
-            "vertices; CUDA-core CRSS search of every needle against every haystack image, ranks")
+RADII = (0.15, 0.3, 0.6)
+R_SEARCH = 0.3
+SEED = 5
+NEEDLES = 100_000
+WORKLOAD = ("large scene: 41 displaced meshes (icosphere target of subdivision 7, icospheres of "
+            "subdivision 6 and tori), 5,019,510 triangles, 2,509,797 vertices, box side 4; RICI "
+            "64x64 uint16 of every vertex at R = 0.15, 0.3, 0.6, then 100,000 seeded target "
+            "vertices imaged with the target alone (R = 0.3) searched against all 2,509,797 "
+            "R = 0.3 images (tensor-core CRSS): rank, true distance, top-1")
 
-# FP32-pipe operations of the definition per unit of generation work: the projection of one
-# vertex (Eqs. relativeLocation, firstRotation, secondRotation: 3 subtractions and 6 multiply-adds
-# with their roundings, counted as 15 operations) for each vertex of an (origin, triangle) pair
-# that crosses a layer, and per (origin, triangle, layer) crossing the slicing of two edges, the
-# segment quantities |E0|^2, |E1|^2, E0.D, E1.D, E0 x D, |D|^2 and the interval boundaries of
-# Section 3.1.2 (counted as 40 operations)
+# FP32 operations of the definition (Section 3.1.2), counted from its formulas:
+#  F_PROJ per projected vertex: P' = P - S (3 subtractions), P''x, P''y, Tx, Tz (2 products and
+#    a sum each: 12) = 15;
+#  F_LAYER per (triangle, layer) crossing: per crossed edge lambda = (beta - z_u) / (z_v - z_u)
+#    (2 subtractions, 1 division) and E = T_u + lambda (T_v - T_u) in x and y (2 x 3) = 9, two
+#    edges = 18; |E0|^2, |E1|^2, E0.D, E1.D, E0 x D, |D|^2 (3 each = 18) and D (2) = 20; = 38;
+#  F_COL per crossing: the interval boundaries, min/max of |E|^2 (1), h^2 = (E0 x D)^2 / |D|^2
+#    (2), the two sign tests d0 < 0 < d1 (2) and the comparisons that place the single and double
+#    intervals against the bin radii (3) = 8.
+# Work is counted only where it can change an image: pairs and crossings whose segment comes
+# within the largest circle (the oracle's contributing counters); culled work is not counted.
 F_PROJ = 15
-F_LAYER = 40
+F_LAYER = 38
+F_COL = 8
 # int8 multiply-adds per masked squared difference in the expanded form m(a-b)^2 =
-# a^2 - 2ab + (mb)^2 with sum a^2 per row precomputed: one for a*b and one for (mb)*(mb); dp4a
-# performs four of them per instruction.
+# a^2 - 2ab + (mb)^2 with sum a^2 per row precomputed: one for a*b and one for (mb)*(mb)
 MACS_PER_TERM = 2
-# dp4a instructions per SM per clock: half the 128 FP32 lanes (a microbenchmark of independent
-# dp4a chains measured 61.3 per SM per clock at 2070 MHz; FFMA measured 117.3)
 DP4A_PER_SM_CLK = 64
-# DRAM bytes (read + write) per launch from one-pass ncu captures (dram__bytes_read and
-# dram__bytes_write; commands in profiles/) of the current kernels at the full clutter-scene
-# size: k_dense (the search) and k_generate (the haystack images; its traffic is the 8 KB image
-# of each origin plus a small read of triangle records, so it is the same for every launch
-# tuning).  Set to None when a kernel changes until it is captured again.
-TRAFFIC_DENSE_FULL = 1.90e9 + 5.01e6
-TRAFFIC_GEN_FULL = 63.63e6 + 901.22e6
+# DRAM bytes (read + write) per full-size launch from one-pass ncu captures (commands in
+# profiles/); None where the kernel changed since it was captured
+TRAFFIC = {"k_generate_R0.6": None, "k_tc_rank": None, "k_dense_clutter": 1.90e9 + 5.01e6}
 
 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--search-mode", type=int, default=1)
+    ap.add_argument("--search-mode", type=int, default=3,
+                    help="search form of the step (3 tensor cores, 1 CUDA cores, 4 sparse, "
+                         "5 int8 tensor cores)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-autotune", action="store_true",
-                    help="keep the default launch tuning instead of autotuning the generation")
-    ap.add_argument("--cpu-origins", type=int, default=96)
-    ap.add_argument("--cpu-needle-origins", type=int, default=48)
-    ap.add_argument("--cpu-needles", type=int, default=12)
-    ap.add_argument("--cpu-haystack", type=int, default=24000)
-    ap.add_argument("--tc-compare", type=int, default=1,
-                    help="also time the tensor-core search on the same images (breakdown)")
-    ap.add_argument("--sparse-compare", type=int, default=1,
-                    help="also time the sparse-needle CUDA-core search on the same images")
+                    help="keep the default launch tuning instead of autotuning each radius")
+    ap.add_argument("--forms-needles", type=int, default=10_000,
+                    help="needle sample for the other search forms on the step's images")
+    ap.add_argument("--cpu-origins", type=int, default=256,
+                    help="oracle sample: oriented points per radius (scene brute force)")
+    ap.add_argument("--cpu-needle-origins", type=int, default=64)
+    ap.add_argument("--cpu-needles", type=int, default=32)
+    ap.add_argument("--cpu-haystack", type=int, default=100_000)
+    ap.add_argument("--clutter-compare", type=int, default=1,
+                    help="the clutter scene (10 meshes, 229,756 triangles): generation and search")
     ap.add_argument("--precision-compare", type=int, default=1,
-                    help="also time the three search forms on a precision-form image set sample")
-    ap.add_argument("--spin-compare", type=int, default=1,
-                    help="also time spin-image generation (Section 2.1) for the haystack points")
-    ap.add_argument("--clutterbox-compare", type=int, default=1,
-                    help="also time a synthetic clutterbox experiment (Section 4.1) on the GPU path")
+                    help="the precision-form set at full size (2^20 RICI images, 65,536 needles)")
     ap.add_argument("--batched-compare", type=int, default=1,
-                    help="also time the batched multi-scene run (CUDA graph) against per-scene calls")
-    ap.add_argument("--haystack-limit", type=int, default=0,
-                    help="image only the first H scene vertices (small profiling case)")
+                    help="the batched run at full size (256 scenes, 1,024 needles each)")
+    ap.add_argument("--clutterbox-compare", type=int, default=1,
+                    help="a synthetic clutterbox experiment (Section 4.1) with the clutter measure")
+    ap.add_argument("--spin-compare", type=int, default=1,
+                    help="spin images (Section 2.1) of the clutter scene")
+    ap.add_argument("--origin-limit", type=int, default=0,
+                    help="image only the first V scene vertices (small profiling case)")
     ap.add_argument("--needle-limit", type=int, default=0,
-                    help="use only the first Q target vertices as needles (small profiling case)")
+                    help="use only the first Q needles (small profiling case)")
     return ap.parse_args()
 
 
@@ -195,81 +206,316 @@ class ClockSampler:
                 "reasons": sorted(reasons)}
 
 
+class Timer:
+    """CUDA events on the launching stream around named parts of a step."""
+
+    def __init__(self, torch, stream):
+        self.torch, self.stream, self.marks = torch, stream, []
+
+    def mark(self, name):
+        e = self.torch.cuda.Event(enable_timing=True)
+        e.record(self.stream)
+        self.marks.append((name, e))
+
+    def parts(self):
+        self.torch.cuda.synchronize()
+        return {self.marks[k + 1][0]: self.marks[k][1].elapsed_time(self.marks[k + 1][1])
+                for k in range(len(self.marks) - 1)}
+
+
+def timed_ms(torch, stream, fn, reps=1, flush=None):
+    """Mean CUDA-event time of fn over reps runs (after one warm-up run)."""
+    out = fn()
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(reps):
+        if flush is not None:
+            flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        out = fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return statistics.mean(ts), out
+
+
+def release(p, torch):
+    p.binding.release_workspaces()
+    torch.cuda.empty_cache()
+
+
 def build_workload():
     import synth
 
-    return synth.clutter_scene(seed=SEED)
+    return synth.large_scene(seed=SEED)
+
+
+def needle_origins(scene, limit=0):
+    rng = np.random.default_rng(SEED)
+    q = min(NEEDLES, scene.target_vertices)
+    on = np.sort(rng.choice(scene.target_vertices, q, replace=False)).astype(np.int32)
+    return on[:limit] if limit else on
 
 
 def cpu_baseline(scene, args, steps: int = 1):
-    """Oracle on bounded samples of the step; returns per-step extrapolated seconds and info."""
+    """Oracle on bounded samples of the step; per-step extrapolated seconds, threads, sample text
+    and the oracle's per-origin work counters at each radius."""
     import oracle
     import synth
 
     oracle.build()
     rng = np.random.default_rng(123)
     V, Vt = scene.num_vertices, scene.target_vertices
+    Q = len(needle_origins(scene, args.needle_limit))
+    if args.origin_limit:
+        V = min(V, args.origin_limit)
     tgt = scene.target_only()
-    og = rng.choice(V, args.cpu_origins, replace=False)
+    og = {R: rng.choice(scene.num_vertices, args.cpu_origins, replace=False) for R in RADII}
     on = rng.choice(Vt, args.cpu_needle_origins, replace=False)
     ims_rng = np.random.default_rng(7)
     nd = synth.images.rici_like_images(ims_rng, args.cpu_needles, N_RES)
     hay = synth.images.rici_like_images(ims_rng, args.cpu_haystack, N_RES)
     threads = oracle.max_threads()
-    est = []
+    est, work = [], {}
     for _ in range(steps):
+        total = 0.0
+        for R in RADII:
+            t0 = time.perf_counter()
+            _, c = oracle.rici_fp64(scene.vertices, scene.normals, scene.triangles, og[R], R, N_RES,
+                                    return_counters=True)
+            total += (time.perf_counter() - t0) / len(og[R]) * V
+            work[R] = {k: v / len(og[R]) for k, v in c.items()}
         t0 = time.perf_counter()
-        oracle.rici_fp64(scene.vertices, scene.normals, scene.triangles, og, R_SUP, N_RES)
-        t1 = time.perf_counter()
-        oracle.rici_fp64(tgt.vertices, tgt.normals, tgt.triangles, on, R_SUP, N_RES)
-        t2 = time.perf_counter()
+        oracle.rici_fp64(tgt.vertices, tgt.normals, tgt.triangles, on, R_SEARCH, N_RES)
+        total += (time.perf_counter() - t0) / len(on) * Q
+        t0 = time.perf_counter()
         oracle.crss_search(nd, hay, np.zeros(len(nd), np.int64))
-        t3 = time.perf_counter()
-        per_o = (t1 - t0) / len(og)
-        per_n = (t2 - t1) / len(on)
-        per_pair = (t3 - t2) / (len(nd) * len(hay))
-        est.append(per_o * V + per_n * Vt + per_pair * Vt * V)
-    sample = (f"{len(og)} scene-vertex images + {len(on)} target-alone images (FP64 brute force "
-              f"over all triangles) and {len(nd)} needles x {len(hay)} haystack images (int64 "
-              f"Listing 1) per step, extrapolated to {Vt + V} images and {Vt * V} comparisons")
-    return est, threads, sample
+        total += (time.perf_counter() - t0) / (len(nd) * len(hay)) * Q * V
+        est.append(total)
+    sample = (f"{args.cpu_origins} scene-vertex images per radius at R = 0.15 / 0.3 / 0.6 and "
+              f"{len(on)} target-alone images (FP64 brute force over all {scene.num_triangles} "
+              f"triangles), {len(nd)} needles x {len(hay)} haystack images (int64 distances) per "
+              f"step, extrapolated to {3 * V + Q} images and {Q * V} comparisons")
+    return est, threads, sample, work
 
 
-def precision_form_comparison(p, torch, dev, stream, Q=16384, H=262144, seed=31, steps=3):
-    """The three exact search forms on a sample of the precision-form image set (heavy-tailed
-    RICI-like rows, needles copied before clutter is added to 30 % of the haystack)."""
+def generation_work(work, F=None):
+    """Definition FP32 operations per oriented point from the oracle's contributing counters."""
+    return (F_PROJ * 3 * work["pairs_contributing"] +
+            (F_LAYER + F_COL) * work["crossings_contributing"])
+
+
+def search_forms(p, torch, stream, nd, hay, match, q, ref):
+    """The other exact forms on the first q needles of the step's search (same images)."""
+    out = {"needles": q, "haystack": int(hay.shape[0]), "comparisons": q * int(hay.shape[0])}
+    ndq, mq = nd[:q], match[:q]
+    for name, mode in (("tensor_core", p.SEARCH_TENSOR), ("int8_tensor_core", p.SEARCH_INT8_TC),
+                       ("cuda_core_dense", p.SEARCH_CUDA_CORE), ("sparse_needle", p.SEARCH_SPARSE)):
+        cnt = torch.zeros(4, dtype=torch.int64, device=nd.device)
+        p.crss_search(ndq, hay, mq, mode=mode, counters=cnt)  # warm-up, with the work counters
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        r = p.crss_search(ndq, hay, mq, mode=mode)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        same = all(bool(torch.equal(r[k], ref[k][:q])) for k in ("rank", "true_distance", "top1"))
+        out[name] = {"ms": ms, "comparisons_per_s": q * int(hay.shape[0]) / (ms / 1e3),
+                     "same_as_step": same, "counters": [int(x) for x in cnt.cpu()],
+                     "status": p.sync_status()}
+        del r
+    return out
+
+
+def clutter_scene_comparison(p, torch, dev, stream, flush, steps=3):
+    """The clutter scene (target icosphere of subdivision 5 + 9 clutter meshes, 229,756
+    triangles): needle and haystack images and the CUDA-core search, as one step; the same search
+    in the tensor-core form; the dense kernel's roofline (dp4a issue)."""
     import synth
 
-    nd, hay, m = synth.images.needle_haystack_set_torch(seed, Q, H, N_RES, dev)
-    flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
-    out = {"recipe": f"synth.images.needle_haystack_set_torch(seed={seed}), {Q} needles x {H} "
-                     f"haystack images, N = {N_RES}", "comparisons": Q * H}
+    s = synth.clutter_scene(seed=2)
+    d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)  # noqa: E731
+    v, n, t = d(s.vertices), d(s.normals), d(s.triangles)
+    on = d(np.arange(s.target_vertices, dtype=np.int32))
+    oh = d(np.arange(s.num_vertices, dtype=np.int32))
+    m = torch.arange(s.target_vertices, dtype=torch.int64, device=dev)
+    Vt, V = s.target_vertices, s.num_vertices
+    nd = p.rici_generate(v, n, t[: s.target_triangles], on, R_SEARCH, N_RES)
+    hy = p.rici_generate(v, n, t, oh, R_SEARCH, N_RES)
+    res = {}
+    for _ in range(2):
+        p.crss_search(nd, hy, m, mode=p.SEARCH_CUDA_CORE)
+    torch.cuda.synchronize()
+    parts = []
+    for _ in range(steps):
+        flush.zero_()
+        tm = Timer(torch, stream)
+        tm.mark("start")
+        p.rici_generate(v, n, t[: s.target_triangles], on, R_SEARCH, N_RES, out=nd)
+        tm.mark("needles")
+        p.rici_generate(v, n, t, oh, R_SEARCH, N_RES, out=hy)
+        tm.mark("haystack")
+        r = p.crss_search(nd, hy, m, mode=p.SEARCH_CUDA_CORE)
+        tm.mark("search")
+        parts.append(tm.parts())
+    ms = {k: statistics.mean(x[k] for x in parts) for k in parts[0]}
+    cnt = torch.zeros(4, dtype=torch.int64, device=dev)
+    p.crss_search(nd, hy, m, mode=p.SEARCH_CUDA_CORE, counters=cnt)
+    cnt = [int(x) for x in cnt.cpu()]
+    tc_ms, rt = timed_ms(torch, stream, lambda: p.crss_search(nd, hy, m, mode=p.SEARCH_TENSOR),
+                         reps=steps, flush=flush)
+    same = all(bool(torch.equal(rt[k], r[k])) for k in ("rank", "true_distance", "top1"))
+    pairs = V * Vt
+    res = {"recipe": "synth.clutter_scene(seed=2): 10 meshes, 229,756 triangles, N = 64, R = 0.3",
+           "needles": Vt, "haystack": V, "comparisons": pairs, "step_ms": sum(ms.values()),
+           "needle_generation_ms": ms["needles"], "haystack_generation_ms": ms["haystack"],
+           "images_per_s": (V + Vt) / (sum(ms.values()) / 1e3),
+           "cuda_core_search_ms": ms["search"],
+           "cuda_core_comparisons_per_s": pairs / (ms["search"] / 1e3),
+           "pair_rows": cnt[0], "lane_utilisation": cnt[0] / cnt[3] if cnt[3] else None,
+           "tensor_core_search_ms": tc_ms,
+           "tensor_core_comparisons_per_s": pairs / (tc_ms / 1e3),
+           "tensor_core_same_ranks": same, "status": p.sync_status()}
+    del nd, hy, r, rt
+    return res
+
+
+def precision_form_comparison(p, torch, dev, stream, flush, i8_needles=16384):
+    """The precision-form set at full size: 2^20 RICI images (N = 64, R = 0.3) of 6,473 seeded
+    subdivision-2 icospheres with heavy-tailed plateaus, 65,536 needles taken before clutter
+    plateaus; every exact form of the search (the int8 tensor-core form on a needle sample)."""
+    import synth
+
+    H, Q = 1 << 20, 65536
+    scenes = synth.scenes.precision_form_scenes(31, 6473)
+    tails, match, clutter = synth.images.precision_form_recipe(31, H, Q, N_RES)
+    d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)  # noqa: E731
+    total = sum(sc.num_vertices for sc in scenes)
+    base = torch.empty((total, N_RES, N_RES), dtype=torch.uint16, device=dev)
+    gen, k = [], 0
+    for sc in scenes:
+        gen.append({"vertices": d(sc.vertices), "normals": d(sc.normals),
+                    "triangles": d(sc.triangles),
+                    "origins": d(np.arange(sc.num_vertices, dtype=np.int32)),
+                    "out": base[k:k + sc.num_vertices]})
+        k += sc.num_vertices
+    gen_ms, _ = timed_ms(torch, stream, lambda: p.rici_generate_batch(gen, R_SEARCH, N_RES))
+    hay = base[:H]
+    synth.images.apply_plateaus_torch(hay, tails)
+    nd = hay.view(torch.int16)[d(match)].view(torch.uint16)
+    synth.images.apply_plateaus_torch(hay, clutter)
+    m = d(match)
+    out = {"recipe": "6,473 seeded subdivision-2 icospheres (synth.scenes.precision_form_scenes(31)"
+                     "), RICI 64x64 at R = 0.3, first 2^20 images; synth.images."
+                     "precision_form_recipe(31): heavy-tailed plateaus, 65,536 needles, clutter",
+           "generation_ms": gen_ms, "generation_images_per_s": total / (gen_ms / 1e3),
+           "scenes": len(scenes), "needles": Q, "haystack": H, "comparisons": Q * H}
     ref = None
-    for name, mode in (("tensor_core", p.SEARCH_TENSOR), ("cuda_core", p.SEARCH_CUDA_CORE),
-                       ("sparse_needle", p.SEARCH_SPARSE)):
-        r = p.crss_search(nd, hay, m, mode=mode)
-        torch.cuda.synchronize()
-        ts = []
-        for _ in range(steps):
-            flush.zero_()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            r = p.crss_search(nd, hay, m, mode=mode)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            ts.append(e0.elapsed_time(e1))
-        same = None if ref is None else all(bool(torch.equal(r[k], ref[k]))
-                                            for k in ("rank", "true_distance", "top1"))
+    for name, mode, q in (("tensor_core", p.SEARCH_TENSOR, Q), ("cuda_core_dense", p.SEARCH_CUDA_CORE, Q),
+                          ("sparse_needle", p.SEARCH_SPARSE, Q),
+                          ("int8_tensor_core", p.SEARCH_INT8_TC, i8_needles)):
+        ms, r = timed_ms(torch, stream, lambda: p.crss_search(nd[:q], hay, m[:q], mode=mode),
+                         flush=flush)
         if ref is None:
             ref = r
-        t = statistics.mean(ts)
-        out[name] = {"ms": t, "comparisons_per_s": Q * H / (t / 1e3),
-                     "same_ranks_as_tensor_core": same}
+        same = all(bool(torch.equal(r[k2], ref[k2][:q])) for k2 in ("rank", "true_distance", "top1"))
+        out[name] = {"needles": q, "ms": ms, "comparisons_per_s": q * H / (ms / 1e3),
+                     "same_as_tensor_core": same}
+        del r
     out["status"] = p.sync_status()
-    del nd, hay, m, ref, r, flush
-    torch.cuda.empty_cache()
+    del gen, base, hay, nd, m, ref
+    release(p, torch)
     return out
+
+
+def batched_full(p, torch, dev, stream, n_scenes=256, needles=1024, seed=44,
+                 chunk_images=6_000_000):
+    """The batched run at its stated size: 256 scenes of a target plus 1-15 clutter meshes
+    (2k-200k triangles each, 10k-2M per scene) from a pooled collection, needle images of up to
+    1,024 seeded target vertices per scene (target alone), haystack images of every scene vertex,
+    tensor-core search per scene.  The scenes do not fit on the device at once (about 0.45 TB of
+    images), so they run in chunks of at most chunk_images haystack images, each chunk one
+    rici_batch_run call; against one rici_generate / rici_generate / crss_search sequence per
+    scene over the same chunks."""
+    import synth
+
+    t0 = time.time()
+    scenes = synth.scenes.scene_batch_pooled(seed, n_scenes)
+    build_s = time.time() - t0
+    rng = np.random.default_rng(3)
+    d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)  # noqa: E731
+    chunks, cur, cur_n = [], [], 0
+    for s in scenes:
+        if cur and cur_n + s.num_vertices > chunk_images:
+            chunks.append(cur)
+            cur, cur_n = [], 0
+        cur.append(s)
+        cur_n += s.num_vertices
+    if cur:
+        chunks.append(cur)
+
+    def prepare(chunk):
+        xs = []
+        for s in chunk:
+            q = min(needles, s.target_vertices)
+            on = np.sort(rng.choice(s.target_vertices, q, replace=False)).astype(np.int32)
+            xs.append({"vertices": d(s.vertices), "normals": d(s.normals),
+                       "triangles": d(s.triangles), "target_triangles": s.target_triangles,
+                       "needle_origins": d(on),
+                       "haystack_origins": d(np.arange(s.num_vertices, dtype=np.int32)),
+                       "true_match": d(on.astype(np.int64))})
+        return xs
+
+    t_b = t_p = 0.0
+    images = pairs = 0
+    same = True
+    first = True
+    for chunk in chunks:
+        xs = prepare(chunk)
+        if first:  # warm-up on the first chunk
+            p.batch_run(xs, R_SEARCH, N_RES)
+            torch.cuda.synchronize()
+            release(p, torch)
+            first = False
+        ms_b, rb = timed_ms(torch, stream, lambda: p.batch_run(xs, R_SEARCH, N_RES), reps=1)
+        rb = [{k: r[k].clone() for k in ("rank", "true_distance", "top1")} for r in rb]
+        release(p, torch)
+
+        def plain():
+            out = []
+            for x in xs:
+                ni = p.rici_generate(x["vertices"], x["normals"],
+                                     x["triangles"][: x["target_triangles"]], x["needle_origins"],
+                                     R_SEARCH, N_RES)
+                hi = p.rici_generate(x["vertices"], x["normals"], x["triangles"],
+                                     x["haystack_origins"], R_SEARCH, N_RES)
+                out.append(p.crss_search(ni, hi, x["true_match"], mode=p.SEARCH_TENSOR))
+                del ni, hi
+            return out
+
+        ms_p, rp = timed_ms(torch, stream, plain, reps=1)
+        for a, b in zip(rb, rp):
+            same &= all(bool(torch.equal(a[k], b[k])) for k in ("rank", "true_distance", "top1"))
+        t_b += ms_b
+        t_p += ms_p
+        images += sum(int(x["needle_origins"].numel() + x["haystack_origins"].numel()) for x in xs)
+        pairs += sum(int(x["needle_origins"].numel()) * int(x["haystack_origins"].numel())
+                     for x in xs)
+        del xs, rb, rp
+        release(p, torch)
+    return {"recipe": f"synth.scenes.scene_batch_pooled(seed={seed}, {n_scenes} scenes, pool of "
+                      f"96 meshes), up to {needles} needles per scene (target alone) vs every "
+                      "scene vertex, N = 64, R = 0.3, tensor-core search",
+            "scenes": n_scenes, "triangles": int(sum(s.num_triangles for s in scenes)),
+            "chunks": len(chunks), "images": images, "comparisons": pairs,
+            "batched_ms": t_b, "per_scene_calls_ms": t_p, "speedup": t_p / t_b,
+            "batched_images_per_s": images / (t_b / 1e3),
+            "batched_comparisons_per_s": pairs / (t_b / 1e3),
+            "same_results": same, "scene_build_s": build_s, "status": p.sync_status()}
 
 
 def clutterbox_experiment(p, torch, dev, stream, runs=4, n=10, seed=51, tri_lo=2000,
@@ -282,26 +528,26 @@ def clutterbox_experiment(p, torch, dev, stream, runs=4, n=10, seed=51, tri_lo=2
     levels = [synth.scenes.clutterbox(seed + r, n=n, box_side=3.0, tri_lo=tri_lo, tri_hi=tri_hi)
               for r in range(runs)]
     prep = clutterbox.prepare(levels, dev)
-    clutterbox.run_prepared(prep, R_SUP, N_RES)
+    clutterbox.run_prepared(prep, R_SEARCH, N_RES)
     torch.cuda.synchronize()
     ts = []
     for _ in range(steps):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        res = clutterbox.run_prepared(prep, R_SUP, N_RES)
+        res = clutterbox.run_prepared(prep, R_SEARCH, N_RES)
         e1.record(stream)
         torch.cuda.synchronize()
         ts.append(e0.elapsed_time(e1))
     # Eq. clutter around every reference vertex of every level (clutter-versus-rank heatmap)
-    areas = clutterbox.clutter_prepared(prep, R_SUP)
+    areas = clutterbox.clutter_prepared(prep, R_SEARCH)
     torch.cuda.synchronize()
     tc = []
     for _ in range(steps):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        areas = clutterbox.clutter_prepared(prep, R_SUP)
+        areas = clutterbox.clutter_prepared(prep, R_SEARCH)
         e1.record(stream)
         torch.cuda.synchronize()
         tc.append(e0.elapsed_time(e1))
@@ -329,118 +575,29 @@ def clutterbox_experiment(p, torch, dev, stream, runs=4, n=10, seed=51, tri_lo=2
            "rank0_fraction_by_clutter_decile": r0_by_clutter,
            "status": st,
            "recipe": f"synth.scenes.clutterbox(seed={seed}..{seed + runs - 1}, n={n}, box side 3, "
-                     f"objects of {tri_lo}-{tri_hi} triangles), N = {N_RES}, R = {R_SUP}"}
+                     f"objects of {tri_lo}-{tri_hi} triangles), N = {N_RES}, R = {R_SEARCH}"}
     del prep, res, areas
     torch.cuda.empty_cache()
     return out
 
 
-def batched_comparison(p, torch, dev, stream, args, n_scenes=24, needles=256, seed=41,
-                       tri_lo=2000, tri_hi=60_000, total_lo=10_000, total_hi=300_000):
-    """Batched run of many uneven scenes (one set of launches, replayed from a CUDA graph)
-    against one plain generate/generate/search call sequence per scene."""
+def spin_comparison(p, torch, dev, stream, flush, steps=3):
+    """Spin images (Section 2.1, 9 samples per triangle) of every vertex of the clutter scene,
+    beside the RICI images of the same points."""
     import synth
 
-    scenes = synth.scene_batch(seed=seed, n_scenes=n_scenes, tri_lo=tri_lo, tri_hi=tri_hi,
-                               total_lo=total_lo, total_hi=total_hi)
-    rng = np.random.default_rng(2)
+    s = synth.clutter_scene(seed=2)
     d = lambda a: torch.from_numpy(np.ascontiguousarray(a)).to(dev)  # noqa: E731
-    xs = []
-    for s in scenes:
-        q = min(needles, s.target_vertices)
-        on = np.sort(rng.choice(s.target_vertices, q, replace=False)).astype(np.int32)
-        xs.append({"V": d(s.vertices), "Nrm": d(s.normals), "T": d(s.triangles),
-                   "Tt": d(s.triangles[: s.target_triangles]), "on": d(on),
-                   "oh": d(np.arange(s.num_vertices, dtype=np.int32)), "m": d(on.astype(np.int64))})
-    gen = []
-    for x in xs:
-        gen.append({"vertices": x["V"], "normals": x["Nrm"], "triangles": x["Tt"], "origins": x["on"]})
-        gen.append({"vertices": x["V"], "normals": x["Nrm"], "triangles": x["T"], "origins": x["oh"]})
-    outs = [torch.empty((g["origins"].numel(), N_RES, N_RES), dtype=torch.uint16, device=dev)
-            for g in gen]
-    for g, o in zip(gen, outs):
-        g["out"] = o
-    srch = [{"needles": outs[2 * i], "haystack": outs[2 * i + 1], "true_match": x["m"]}
-            for i, x in enumerate(xs)]
-    res = [{"rank": torch.empty(x["on"].numel(), dtype=torch.int32, device=dev),
-            "true_distance": torch.empty(x["on"].numel(), dtype=torch.int64, device=dev),
-            "top1": torch.empty(x["on"].numel(), dtype=torch.int32, device=dev)} for x in xs]
-    wg = torch.empty(p.binding.generate_batch_workspace_bytes(gen, N_RES) + 512, dtype=torch.uint8,
-                     device=dev)
-    wsr = torch.empty(p.binding.search_batch_workspace_bytes(srch, N_RES) + 512, dtype=torch.uint8,
-                      device=dev)
-    wg = wg[(-wg.data_ptr()) % 256:]
-    wsr = wsr[(-wsr.data_ptr()) % 256:]
-
-    def run_batched():
-        p.rici_generate_batch(gen, R_SUP, N_RES, workspace_tensor=wg)
-        p.crss_search_batch(srch, N_RES, workspace_tensor=wsr, outputs=res)
-
-    def run_plain():
-        for x, g0, g1 in zip(xs, gen[0::2], gen[1::2]):
-            p.rici_generate(x["V"], x["Nrm"], x["Tt"], x["on"], R_SUP, N_RES, out=g0["out"])
-            p.rici_generate(x["V"], x["Nrm"], x["T"], x["oh"], R_SUP, N_RES, out=g1["out"])
-            p.crss_search(g0["out"], g1["out"], x["m"], mode=p.SEARCH_TENSOR)
-
-    def capture():
-        cs = torch.cuda.Stream(device=dev)
-        cs.wait_stream(stream)
-        with torch.cuda.stream(cs):
-            run_batched()
-        stream.wait_stream(cs)
-        torch.cuda.synchronize()
-        g = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(g):
-            run_batched()
-        return g
-
-    # a graph replays the launch shapes in force when it was captured: one with the default
-    # tuning, one with the autotuned tuning (measured on the first scenes, fresh cache)
-    from paper_2007_02306_gb300 import autotune
-
-    prev_tuning = p.get_tuning()
-    p.set_tuning(None)
-    graph_default = capture()
-    t_tune = time.time()
-    with tempfile.TemporaryDirectory() as td:
-        tuning = autotune.tune_batch(gen, srch, R_SUP, N_RES, gpu_name=torch.cuda.get_device_name(dev),
-                                     sample=4, path=os.path.join(td, "tuning.json"))
-    t_tune = time.time() - t_tune
-    graph = capture()
-    for _ in range(2):
-        graph.replay()
-        run_plain()
-        graph_default.replay()
-    torch.cuda.synchronize()
-    reps = max(3, args.steps)
-    t_b, t_p, t_d = [], [], []
-    for _ in range(reps):
-        e0, e1, e2, e3 = (torch.cuda.Event(enable_timing=True) for _ in range(4))
-        e0.record(stream)
-        graph.replay()
-        e1.record(stream)
-        run_plain()
-        e2.record(stream)
-        graph_default.replay()
-        e3.record(stream)
-        torch.cuda.synchronize()
-        t_b.append(e0.elapsed_time(e1))
-        t_p.append(e1.elapsed_time(e2))
-        t_d.append(e2.elapsed_time(e3))
-    st = p.sync_status()
-    p.set_tuning(prev_tuning)
-    images = sum(g["origins"].numel() for g in gen)
-    pairs = sum(x["on"].numel() * x["oh"].numel() for x in xs)
-    return {"scenes": n_scenes, "triangles": int(sum(s.num_triangles for s in scenes)),
-            "images": int(images), "comparisons": int(pairs),
-            "batched_graph_ms": statistics.mean(t_b), "per_scene_calls_ms": statistics.mean(t_p),
-            "speedup": statistics.mean(t_p) / statistics.mean(t_b),
-            "batched_graph_default_tuning_ms": statistics.mean(t_d),
-            "autotuned": tuning, "autotune_s": t_tune,
-            "batched_images_per_s": images / (statistics.mean(t_b) / 1e3), "status": st,
-            "recipe": f"synth.scene_batch(seed={seed}, {n_scenes} scenes, {total_lo}-{total_hi} "
-                      f"triangles each), {needles} needles per scene (target alone) vs all scene "
-                      "vertices, tensor-core search"}
+    v, n, t = d(s.vertices), d(s.normals), d(s.triangles)
+    oh = d(np.arange(s.num_vertices, dtype=np.int32))
+    si = torch.empty((s.num_vertices, N_RES, N_RES), dtype=torch.float32, device=dev)
+    ms, _ = timed_ms(torch, stream, lambda: p.spin_images(v, n, t, oh, R_SEARCH, N_RES, 3, out=si),
+                     reps=steps, flush=flush)
+    rms, _ = timed_ms(torch, stream, lambda: p.rici_generate(v, n, t, oh, R_SEARCH, N_RES),
+                      reps=steps, flush=flush)
+    return {"images": s.num_vertices, "samples_per_triangle": 9, "ms": ms,
+            "images_per_s": s.num_vertices / (ms / 1e3), "rici_images_ms": rms,
+            "status": p.sync_status()}
 
 
 def run_reference(args):
@@ -449,16 +606,18 @@ def run_reference(args):
         return
     scene = build_workload()
     cpu_baseline(scene, args, steps=max(0, args.warmup))
-    est, threads, sample = cpu_baseline(scene, args, steps=args.steps)
-    images = scene.num_vertices + scene.target_vertices
+    est, threads, sample, _ = cpu_baseline(scene, args, steps=args.steps)
+    images = 3 * scene.num_vertices + len(needle_origins(scene))
     sec = statistics.mean(est)
     value = images / sec
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "images/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-        "ms_per_step": sec * 1e3, "higher_is_better": True, "scaling": "weak",
+        "ms_per_step": sec * 1e3,
+        "ms_per_step_kind": "extrapolated from the timed oracle samples to the whole step",
+        "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64+i64", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "resolution": N_RES, "support_radius": R_SUP,
+        "config": {"workload": WORKLOAD, "resolution": N_RES, "support_radii": list(RADII),
                    "seed": SEED},
         "cpu_baseline": {"value": value, "unit": "images/s", "cores": threads, "kind": "oracle",
                          "sample": sample},
@@ -495,79 +654,84 @@ def main():
     p.load_library()
 
     scene = build_workload()
-    V, T, Vt, Tt = scene.num_vertices, scene.num_triangles, scene.target_vertices, scene.target_triangles
-    if args.needle_limit:
-        Vt = min(Vt, args.needle_limit)
-    if args.haystack_limit:
-        V = max(Vt, min(V, args.haystack_limit))
+    V = scene.num_vertices if not args.origin_limit else min(scene.num_vertices, args.origin_limit)
+    Vt, Tt, T = scene.target_vertices, scene.target_triangles, scene.num_triangles
+    on_np = needle_origins(scene, args.needle_limit)
+    Q = len(on_np)
+    if args.origin_limit or args.needle_limit:
+        args.no_cpu_baseline = True
     h_vert = torch.from_numpy(scene.vertices).pin_memory()
     h_norm = torch.from_numpy(scene.normals).pin_memory()
     h_tri = torch.from_numpy(scene.triangles).pin_memory()
     h_oh = torch.arange(V, dtype=torch.int32).pin_memory()
-    h_on = torch.arange(Vt, dtype=torch.int32).pin_memory()
-    h_match = torch.arange(Vt, dtype=torch.int64).pin_memory()
-
+    h_on = torch.from_numpy(on_np).pin_memory()
+    h_match = torch.from_numpy(on_np.astype(np.int64)).pin_memory()
     vert, norm, tri = h_vert.to(dev), h_norm.to(dev), h_tri.to(dev)
-    if args.needle_limit or args.haystack_limit:
-        args.no_cpu_baseline = True
-    tri_t = tri[:Tt]
     oh, on, match = h_oh.to(dev), h_on.to(dev), h_match.to(dev)
-    needles = torch.empty((Vt, N_RES, N_RES), dtype=torch.uint16, device=dev)
-    hay = torch.empty((V, N_RES, N_RES), dtype=torch.uint16, device=dev)
+    imgs = {R: torch.empty((V, N_RES, N_RES), dtype=torch.uint16, device=dev) for R in RADII}
+    needles = torch.empty((Q, N_RES, N_RES), dtype=torch.uint16, device=dev)
     flush = torch.empty(512 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
 
-    def step():
-        p.rici_generate(vert, norm, tri_t, on, R_SUP, N_RES, out=needles)
-        p.rici_generate(vert, norm, tri, oh, R_SUP, N_RES, out=hay)
-        return p.crss_search(needles, hay, match, mode=args.search_mode)
+    # launch tuning of each radius, measured on three contiguous blocks of oriented points (the
+    # order of the full run, so their cache behaviour is the full run's), fresh every run
+    tunings, tune_s = {}, 0.0
+    t0 = time.time()
+    blk = min(4096, V)
+    sub = torch.cat([oh[:blk], oh[V // 2: V // 2 + blk], oh[V - blk:]]).contiguous()
+    subout = torch.empty((sub.numel(), N_RES, N_RES), dtype=torch.uint16, device=dev)
+    for R in RADII:
+        if args.no_autotune:
+            tunings[R] = p.get_tuning()
+        else:
+            tunings[R], _ = p.autotune_generate_batch(
+                [{"vertices": vert, "normals": norm, "triangles": tri, "origins": sub,
+                  "out": subout}], R, N_RES, repeats=2)
+    tune_s = time.time() - t0
+    del sub, subout
 
-    # launch tuning of the generation kernels, measured on this workload (fresh cache)
-    tune_s = 0.0
-    if not args.no_autotune:
-        from paper_2007_02306_gb300 import autotune
+    def step(vv, nn, tt, ohh, onn, mm, tm=None, gcnt=None, scnt=None):
+        for R in RADII:
+            p.set_tuning(tunings[R])
+            p.rici_generate(vv, nn, tt, ohh, R, N_RES, out=imgs[R],
+                            counters=None if gcnt is None else gcnt[R])
+            if tm:
+                tm.mark(f"generation_R{R}")
+        p.set_tuning(tunings[R_SEARCH])
+        p.rici_generate(vv, nn, tt[:Tt], onn, R_SEARCH, N_RES, out=needles)
+        if tm:
+            tm.mark("needle_generation")
+        r = p.crss_search(needles, imgs[R_SEARCH], mm, mode=args.search_mode, counters=scnt)
+        if tm:
+            tm.mark("search")
+        return r
 
-        t0 = time.time()
-        with tempfile.TemporaryDirectory() as td:
-            autotune.tune_batch(
-                [{"vertices": vert, "normals": norm, "triangles": tri_t, "origins": on, "out": needles},
-                 {"vertices": vert, "normals": norm, "triangles": tri, "origins": oh, "out": hay}],
-                [], R_SUP, N_RES, gpu_name=torch.cuda.get_device_name(dev), sample=2, repeats=2,
-                path=os.path.join(td, "tuning.json"))
-        tune_s = time.time() - t0
-    step_tuning = p.get_tuning()
-
-    for _ in range(args.warmup):
-        step()
+    gcnt = {R: torch.zeros(4, dtype=torch.int64, device=dev) for R in RADII}
+    scnt = torch.zeros(4, dtype=torch.int64, device=dev)
+    for k in range(args.warmup):
+        last = k == args.warmup - 1
+        step(vert, norm, tri, oh, on, match, gcnt=gcnt if last else None,
+             scnt=scnt if last else None)
+    torch.cuda.synchronize()
     st = p.sync_status()
     if st != 0:
         raise RuntimeError(f"device status {st} during warm-up")
-
-    # untimed: work counters for the roofline
-    gcnt = torch.zeros(4, dtype=torch.int64, device=dev)
-    scnt = torch.zeros(4, dtype=torch.int64, device=dev)
-    p.rici_generate(vert, norm, tri, oh, R_SUP, N_RES, out=hay, counters=gcnt)
-    p.crss_search(needles, hay, match, mode=args.search_mode, counters=scnt)
-    torch.cuda.synchronize()
-    gcnt, scnt = gcnt.cpu().tolist(), scnt.cpu().tolist()
+    gcnt = {R: [int(x) for x in c.cpu()] for R, c in gcnt.items()}
+    scnt = [int(x) for x in scnt.cpu()]
 
     clocks = ClockSampler(dev.index if world == 1 else local)
-    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
     launches0 = p.binding.kernel_launches()
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
     clocks.start()
+    parts = []
     for k in range(args.steps):
         flush.zero_()
-        e = ev[k]
-        e[0].record(stream)
-        p.rici_generate(vert, norm, tri_t, on, R_SUP, N_RES, out=needles)
-        e[1].record(stream)
-        p.rici_generate(vert, norm, tri, oh, R_SUP, N_RES, out=hay)
-        e[2].record(stream)
-        res = p.crss_search(needles, hay, match, mode=args.search_mode)
-        e[3].record(stream)
+        tm = Timer(torch, stream)
+        tm.mark("start")
+        res = step(vert, norm, tri, oh, on, match, tm=tm)
+        parts.append(tm)
     torch.cuda.synchronize()
     clk = clocks.stop()
     launches = p.binding.kernel_launches() - launches0
@@ -576,126 +740,29 @@ def main():
     st = p.sync_status()
     if st != 0:
         raise RuntimeError(f"device status {st} in the timed region")
-    t_nd = [ev[k][0].elapsed_time(ev[k][1]) for k in range(args.steps)]
-    t_hy = [ev[k][1].elapsed_time(ev[k][2]) for k in range(args.steps)]
-    t_se = [ev[k][2].elapsed_time(ev[k][3]) for k in range(args.steps)]
-    ms = [a + b + c for a, b, c in zip(t_nd, t_hy, t_se)]
-    ms_step = max_over_ranks(statistics.mean(ms), dev)
-    images = V + Vt
-    pairs = V * Vt
+    parts = [tm.parts() for tm in parts]
+    pms = {k: statistics.mean(x[k] for x in parts) for k in parts[0]}
+    ms_step = max_over_ranks(statistics.mean(sum(x.values()) for x in parts), dev)
+    images = 3 * V + Q
+    pairs = Q * V
     value = job_rate(images, ms_step, world)
+    rk = res["rank"].cpu().numpy()
 
-    # tensor-core form of the same search (exact fp16 tcgen05 GEMM), timed separately
-    tc = None
-    if args.tc_compare:
-        for _ in range(2):
-            p.crss_search(needles, hay, match, mode=p.SEARCH_TENSOR)
-        torch.cuda.synchronize()
-        tc_ms = []
-        for k in range(args.steps):
-            flush.zero_()
-            b0 = torch.cuda.Event(enable_timing=True)
-            b1 = torch.cuda.Event(enable_timing=True)
-            b0.record(stream)
-            rt = p.crss_search(needles, hay, match, mode=p.SEARCH_TENSOR)
-            b1.record(stream)
-            torch.cuda.synchronize()
-            tc_ms.append(b0.elapsed_time(b1))
-        same = all(bool(torch.equal(rt[k2], res[k2])) for k2 in ("rank", "true_distance", "top1"))
-        st = p.sync_status()
-        tc = {"ms": statistics.mean(tc_ms), "comparisons_per_s": pairs / (statistics.mean(tc_ms) / 1e3),
-              "same_ranks_as_cuda_core": same, "status": st}
+    # the other exact forms of the same search on a needle sample of the step's images
+    forms = None
+    if rank == 0 and args.forms_needles:
+        forms = search_forms(p, torch, stream, needles, imgs[R_SEARCH], match,
+                             min(args.forms_needles, Q), res)
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    dp4a_rate = p.binding.measure_dp4a_rate()
+    mma_rate = p.binding.measure_mma_s8_rate()
 
-    # sparse-needle form of the same search (CUDA cores, the needles' non-zero words only)
-    sp = None
-    if args.sparse_compare:
-        for _ in range(2):
-            p.crss_search(needles, hay, match, mode=p.SEARCH_SPARSE)
-        torch.cuda.synchronize()
-        sp_ms = []
-        for k in range(args.steps):
-            flush.zero_()
-            b0 = torch.cuda.Event(enable_timing=True)
-            b1 = torch.cuda.Event(enable_timing=True)
-            b0.record(stream)
-            rs = p.crss_search(needles, hay, match, mode=p.SEARCH_SPARSE)
-            b1.record(stream)
-            torch.cuda.synchronize()
-            sp_ms.append(b0.elapsed_time(b1))
-        same = all(bool(torch.equal(rs[k2], res[k2])) for k2 in ("rank", "true_distance", "top1"))
-        spc = torch.zeros(4, dtype=torch.int64, device=dev)
-        p.crss_search(needles, hay, match, mode=p.SEARCH_SPARSE, counters=spc)
-        spc = [int(x) for x in spc.cpu()]
-        st = p.sync_status()
-        sp = {"ms": statistics.mean(sp_ms),
-              "comparisons_per_s": pairs / (statistics.mean(sp_ms) / 1e3),
-              "same_ranks_as_cuda_core": same, "status": st,
-              "pair_words": spc[0], "lane_slots": spc[3],
-              "lane_utilisation": spc[0] / spc[3] if spc[3] else None}
-    precision = None
-    if args.precision_compare and rank == 0:
-        precision = precision_form_comparison(p, torch, dev, stream)
-
-    spin = None
-    if args.spin_compare:
-        # spin images of every haystack point from 9 samples per triangle (the paper used 10)
-        si = torch.empty((V, N_RES, N_RES), dtype=torch.float32, device=dev)
-        for _ in range(2):
-            p.spin_images(vert, norm, tri, oh, R_SUP, N_RES, 3, out=si)
-        torch.cuda.synchronize()
-        sm = []
-        for _ in range(args.steps):
-            flush.zero_()
-            s0 = torch.cuda.Event(enable_timing=True)
-            s1 = torch.cuda.Event(enable_timing=True)
-            s0.record(stream)
-            p.spin_images(vert, norm, tri, oh, R_SUP, N_RES, 3, out=si)
-            s1.record(stream)
-            torch.cuda.synchronize()
-            sm.append(s0.elapsed_time(s1))
-        spin = {"images": V, "samples_per_triangle": 9, "ms": statistics.mean(sm),
-                "images_per_s": V / (statistics.mean(sm) / 1e3),
-                "rici_haystack_generation_ms": statistics.mean(t_hy), "status": p.sync_status()}
-        del si
-
-    cbox = None
-    if args.clutterbox_compare and rank == 0:
-        cbox = clutterbox_experiment(p, torch, dev, stream)
-        # Eq. clutter around every needle's vertex of the step's scene (object = the target)
-        for _ in range(2):
-            p.clutter_areas(vert, norm, tri, on, R_SUP, Vt)
-        torch.cuda.synchronize()
-        cm = []
-        for _ in range(args.steps):
-            c0 = torch.cuda.Event(enable_timing=True)
-            c1 = torch.cuda.Event(enable_timing=True)
-            c0.record(stream)
-            ca, co = p.clutter_areas(vert, norm, tri, on, R_SUP, Vt)
-            c1.record(stream)
-            torch.cuda.synchronize()
-            cm.append(c0.elapsed_time(c1))
-        cf = ((ca - co) / ca).cpu().numpy()
-        cbox["clutter_scene_measure"] = {
-            "points": Vt, "triangles": T, "ms": statistics.mean(cm),
-            "points_per_s": Vt / (statistics.mean(cm) / 1e3),
-            "clutter_mean": float(cf.mean()), "clutter_quartiles": [
-                float(x) for x in np.quantile(cf, [0.25, 0.5, 0.75])],
-            "status": p.sync_status()}
-
-    batched = batched_small = None
-    if args.batched_compare and rank == 0:
-        batched = batched_comparison(p, torch, dev, stream, args)
-        # many small scenes: where one set of launches per batch matters most
-        batched_small = batched_comparison(p, torch, dev, stream, args, n_scenes=256, needles=64,
-                                           seed=42, tri_lo=500, tri_hi=5000, total_lo=2000,
-                                           total_hi=12_000)
-
-    # e2e: same step from pinned host buffers, host<->device copies inside the timed region
+    # e2e: the same step from pinned host buffers, host<->device copies inside the timed region
     e2e = None
     if not args.no_e2e:
-        h_rank = torch.empty(Vt, dtype=torch.int32).pin_memory()
-        h_top1 = torch.empty(Vt, dtype=torch.int32).pin_memory()
-        h_dt = torch.empty(Vt, dtype=torch.int64).pin_memory()
+        h_rank = torch.empty(Q, dtype=torch.int32).pin_memory()
+        h_top1 = torch.empty(Q, dtype=torch.int32).pin_memory()
+        h_dt = torch.empty(Q, dtype=torch.int64).pin_memory()
         e2e_ms = []
         for k in range(args.steps + 1):
             flush.zero_()
@@ -708,140 +775,173 @@ def main():
             doh = h_oh.to(dev, non_blocking=True)
             don = h_on.to(dev, non_blocking=True)
             dm = h_match.to(dev, non_blocking=True)
-            p.rici_generate(dv, dn, dtri[:Tt], don, R_SUP, N_RES, out=needles)
-            p.rici_generate(dv, dn, dtri, doh, R_SUP, N_RES, out=hay)
-            r = p.crss_search(needles, hay, dm, mode=args.search_mode)
+            r = step(dv, dn, dtri, doh, don, dm)
             h_rank.copy_(r["rank"], non_blocking=True)
             h_top1.copy_(r["top1"], non_blocking=True)
             h_dt.copy_(r["true_distance"], non_blocking=True)
             a1.record(stream)
             torch.cuda.synchronize()
-            if k > 0:  # first pass warms the copy path
+            if k > 0:  # the first pass warms the copy path
                 e2e_ms.append(a0.elapsed_time(a1))
+            del dv, dn, dtri, doh, don, dm, r
         e_ms = max_over_ranks(statistics.mean(e2e_ms), dev)
         h2d = sum(x.numel() * x.element_size() for x in (h_vert, h_norm, h_tri, h_oh, h_on, h_match))
-        d2h = Vt * (4 + 4 + 8)
+        d2h = Q * (4 + 4 + 8)
         e2e = {"value": job_rate(images, e_ms, world), "unit": "images/s",
                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "ms_per_step": e_ms}
+    st = p.sync_status()
+
+    # free the step's buffers before the comparison workloads
+    del imgs, needles, res, vert, norm, tri, oh, on, match
+    p.set_tuning(None)
+    release(p, torch)
+
+    cmp = {}
+    if rank == 0:
+        if args.clutter_compare:
+            cmp["clutter_scene"] = clutter_scene_comparison(p, torch, dev, stream, flush)
+            release(p, torch)
+        if args.precision_compare:
+            cmp["precision_form"] = precision_form_comparison(p, torch, dev, stream, flush)
+        if args.batched_compare:
+            cmp["batched_run"] = batched_full(p, torch, dev, stream)
+            release(p, torch)
+        if args.clutterbox_compare:
+            cmp["clutterbox"] = clutterbox_experiment(p, torch, dev, stream)
+            release(p, torch)
+        if args.spin_compare:
+            cmp["spin_images"] = spin_comparison(p, torch, dev, stream, flush)
+            release(p, torch)
+
+    # oracle on the host cores: the CPU baseline, and the definition's work counts per radius
+    cpu, work = None, None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        est, threads, sample, work = cpu_baseline(scene, args)
+        cpu = {"value": images / est[0], "unit": "images/s", "cores": threads, "kind": "oracle",
+               "sample": sample}
+    elif rank == 0:
+        import oracle
+
+        rng = np.random.default_rng(123)
+        work = {}
+        for R in RADII:
+            og = rng.choice(scene.num_vertices, 8, replace=False)
+            _, c = oracle.rici_fp64(scene.vertices, scene.normals, scene.triangles, og, R, N_RES,
+                                    return_counters=True)
+            work[R] = {k: v / len(og) for k, v in c.items()}
 
     pk, pk_kind = peaks()
     clk_mhz = (clk or {}).get("sm_mhz") or pk.get("sm_max_mhz", 2070.0)
-    sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    alu_peak_gops = sms * 128 * clk_mhz * 1e6 / 1e9  # 32-bit lane operations per second
-    mac_peak_gops = sms * DP4A_PER_SM_CLK * 4 * clk_mhz * 1e6 / 1e9  # int8 MACs via dp4a
-    dp4a_rate = p.binding.measure_dp4a_rate()  # after the timed regions
-
-    gen_ms = statistics.mean(t_hy)
-    se_ms = statistics.mean(t_se)
-    cpu = None
-    cpu_ops = None
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        est, threads, sample = cpu_baseline(scene, args)
-        cpu = {"value": images / est[0], "unit": "images/s", "cores": threads, "kind": "oracle",
-               "sample": sample}
-        import oracle
-
-        rng = np.random.default_rng(5)
-        og = rng.choice(V, 32, replace=False)
-        _, cc = oracle.rici_fp64(scene.vertices, scene.normals, scene.triangles, og, R_SUP, N_RES,
-                                 return_counters=True)
-        cpu_ops = cc
-    # roofline of the dominant kernel (the larger of haystack generation and search)
+    lane_peak = sms * 128 * clk_mhz * 1e6 / 1e9  # FP32 lane operations, G/s
+    dp4a_peak = sms * DP4A_PER_SM_CLK * 4 * clk_mhz * 1e6 / 1e9  # int8 MACs via dp4a, G/s
     rooflines = {}
-    search_terms = scnt[0] * (N_RES - 1)
-    rooflines["search"] = {
-        "bound": "alu", "unit": "G int8-MAC/s",
-        "achieved": MACS_PER_TERM * search_terms / (se_ms / 1e3) / 1e9,
-        "peak": mac_peak_gops,
-        "work": f"{scnt[0]} (pair, row) evaluations x {N_RES - 1} masked squared differences x "
-                f"{MACS_PER_TERM} int8 multiply-adds",
-        "traffic": (TRAFFIC_DENSE_FULL if not (args.haystack_limit or args.needle_limit)
-                    else None),
-        "peak_kind": f"derived: {sms} SMs x {DP4A_PER_SM_CLK} dp4a per clock x 4 MACs x "
-                     f"{clk_mhz:.0f} MHz (median SM clock)",
-        "measured_dp4a_per_sm_per_clk": dp4a_rate / sms / (clk_mhz * 1e6),
-    }
-    if cpu_ops is not None:
-        per_o = (F_PROJ * 3 * cpu_ops["pairs_crossing"] + F_LAYER * cpu_ops["layer_crossings"]) / 32
-        rooflines["generation"] = {
-            "bound": "alu", "unit": "Gop/s",
-            "achieved": per_o * V / (gen_ms / 1e3) / 1e9, "peak": alu_peak_gops,
-            "work": f"{F_PROJ} ops x 3 vertices per crossing (origin, triangle) pair + {F_LAYER} "
-                    "ops per (origin, triangle, layer) crossing, counted by the oracle on 32 "
-                    "sampled origins and scaled to all haystack origins",
-            "traffic": (TRAFFIC_GEN_FULL if not (args.haystack_limit or args.needle_limit)
-                        else None),
-        }
+    if work is not None:
+        for R in RADII:
+            ops = generation_work(work[R]) * V
+            rooflines[f"generation_R{R}"] = {
+                "bound": "alu", "unit": "Gop/s",
+                "achieved": ops / (pms[f"generation_R{R}"] / 1e3) / 1e9, "peak": lane_peak,
+                "work": (f"{F_PROJ} FP32 ops x 3 vertices per contributing (origin, triangle) pair "
+                         f"+ {F_LAYER + F_COL} per contributing (origin, triangle, layer) "
+                         "crossing (segment within the largest circle), counted by the oracle "
+                         f"on sampled origins: {work[R]['pairs_contributing']:.0f} pairs and "
+                         f"{work[R]['crossings_contributing']:.0f} crossings per origin, x {V} "
+                         "origins"),
+                "traffic": TRAFFIC["k_generate_R0.6"] if R == 0.6 else None,
+                "peak_kind": f"derived: {sms} SMs x 128 FP32 lanes x {clk_mhz:.0f} MHz "
+                             "(median SM clock)"}
+    if forms is not None:
+        f = forms
+        n8 = f["int8_tensor_core"]
+        i8_pairs = f["comparisons"] - n8["counters"][1]  # pairs outside the int8 class: int64
+        rooflines["search_int8_tensor_core"] = {
+            "bound": "tensor", "unit": "G int8-MAC/s",
+            "achieved": 3 * N_RES * N_RES * i8_pairs / (n8["ms"] / 1e3) / 1e9,
+            "peak": mma_rate / 1e9,
+            "work": f"{i8_pairs} int8-class pairs x 3 GEMM terms x {N_RES * N_RES} int8 MACs",
+            "traffic": None,
+            "peak_kind": "measured: mma.sync m16n8k32 s8 issue rate of the whole GPU"}
+        dn = f["cuda_core_dense"]
+        rooflines["search_cuda_core_dense"] = {
+            "bound": "alu", "unit": "G int8-MAC/s",
+            "achieved": MACS_PER_TERM * dn["counters"][0] * (N_RES - 1) / (dn["ms"] / 1e3) / 1e9,
+            "peak": dp4a_peak,
+            "work": f"{dn['counters'][0]} (pair, row) evaluations x {N_RES - 1} x "
+                    f"{MACS_PER_TERM} int8 MACs",
+            "traffic": None,
+            "peak_kind": f"derived: {sms} SMs x {DP4A_PER_SM_CLK} dp4a per clock x 4 MACs x "
+                         f"{clk_mhz:.0f} MHz; measured {dp4a_rate / sms / (clk_mhz * 1e6):.1f} "
+                         "dp4a per SM per clock"}
+    if "clutter_scene" in cmp:
+        c = cmp["clutter_scene"]
+        kt = 2 * N_RES * N_RES
+        rooflines["search_tensor_core_clutter_scene"] = {
+            "bound": "tensor", "unit": "TFLOP/s",
+            "achieved": 2.0 * kt * c["comparisons"] / (c["tensor_core_search_ms"] / 1e3) / 1e12,
+            "peak": pk.get("bf16_tflops", 1900.0),
+            "work": f"{c['comparisons']} pairs x 2 x {kt} fp16 multiply-adds (dense, K = 2 N^2; "
+                    "every image of the clutter scene is in the fp16 class)",
+            "traffic": None,
+            "peak_kind": f"{pk_kind} bf16 dense burst (fp16 runs at the bf16 rate)"}
+        rooflines["search_cuda_core_clutter_scene"] = {
+            "bound": "alu", "unit": "G int8-MAC/s",
+            "achieved": MACS_PER_TERM * c["pair_rows"] * (N_RES - 1) /
+            (c["cuda_core_search_ms"] / 1e3) / 1e9,
+            "peak": dp4a_peak,
+            "work": f"{c['pair_rows']} (pair, row) evaluations x {N_RES - 1} x {MACS_PER_TERM} "
+                    "int8 MACs",
+            "traffic": TRAFFIC["k_dense_clutter"],
+            "peak_kind": f"derived: {sms} SMs x {DP4A_PER_SM_CLK} dp4a per clock x 4 MACs x "
+                         f"{clk_mhz:.0f} MHz (median SM clock)"}
     for r in rooflines.values():
         r["frac"] = r["achieved"] / r["peak"]
-        r.setdefault("peak_kind", f"derived: {sms} SMs x 128 lanes x {clk_mhz:.0f} MHz "
-                                  "(median SM clock)")
-    if tc is not None:
-        kt = 2 * N_RES * N_RES
-        rooflines["search_tensor_core"] = {
-            "bound": "tensor", "unit": "TFLOP/s",
-            "achieved": 2.0 * kt * pairs / (tc["ms"] / 1e3) / 1e12,
-            "peak": pk.get("bf16_tflops", 1900.0),
-            "work": f"{pairs} pairs x 2 x {kt} fp16 multiply-adds (dense, K = 2 N^2)",
-            "traffic": None, "peak_kind": f"{pk_kind} bf16 dense burst (fp16 runs at the bf16 rate)",
-        }
-        rooflines["search_tensor_core"]["frac"] = (rooflines["search_tensor_core"]["achieved"] /
-                                                   rooflines["search_tensor_core"]["peak"])
-    if sp is not None:
-        rooflines["search_sparse"] = {
-            "bound": "alu", "unit": "G int8-MAC/s",
-            "achieved": sp["pair_words"] * 4 * MACS_PER_TERM / (sp["ms"] / 1e3) / 1e9,
-            "peak": rooflines["search"]["peak"],
-            "work": f"{sp['pair_words']} (pair, needle word) evaluations x 4 masked squared "
-                    "differences x 2 int8 multiply-adds",
-            "traffic": None, "peak_kind": rooflines["search"]["peak_kind"],
-        }
-        rooflines["search_sparse"]["frac"] = (rooflines["search_sparse"]["achieved"] /
-                                              rooflines["search_sparse"]["peak"])
-    dom = "search" if se_ms >= gen_ms or "generation" not in rooflines else "generation"
-    roof = dict(rooflines[dom])
-    roof["kernel"] = "k_dense (CUDA-core CRSS)" if dom == "search" else "k_generate"
+    gen_parts = {R: pms[f"generation_R{R}"] for R in RADII}
+    dom_R = max(gen_parts, key=gen_parts.get)
+    dominant = (f"generation_R{dom_R}" if gen_parts[dom_R] >= pms["search"] or
+                f"generation_R{dom_R}" not in rooflines else None)
+    roof = dict(rooflines[dominant]) if dominant in rooflines else None
+    if roof is not None:
+        roof["kernel"] = f"k_generate (R = {dom_R})"
 
     line = {
         "metric": METRIC, "value": value, "unit": "images/s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_step,
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+i32",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32+f16+i32",
         "data": "synthetic",
-        "config": {"workload": WORKLOAD, "resolution": N_RES, "support_radius": R_SUP,
-                   "triangles": T, "needles": Vt, "haystack": V, "comparisons": pairs, "seed": SEED,
-                   "search_mode": args.search_mode,
+        "config": {"workload": WORKLOAD, "resolution": N_RES, "support_radii": list(RADII),
+                   "triangles": T, "vertices": V, "needles": Q, "haystack": V, "comparisons": pairs,
+                   "images_per_step": images, "seed": SEED, "search_mode": args.search_mode,
                    "input_sha256": input_digest(scene),
-                   "l2": "flushed by a 512 MB device write before every timed step",
+                   "l2": "inputs larger than L2; also flushed by a 512 MB device write before "
+                         "every timed step",
                    "parallelism": f"replicas x{world}"},
         "breakdown": {
-            "needle_generation_ms": statistics.mean(t_nd),
-            "haystack_generation_ms": gen_ms,
-            "search_ms": se_ms,
-            "generation_images_per_s": images / ((statistics.mean(t_nd) + gen_ms) / 1e3),
-            "search_comparisons_per_s": pairs / (se_ms / 1e3),
-            "generation_counters": {"triangles_processed": gcnt[0], "layer_items": gcnt[1],
-                                    "fp64_band_items": gcnt[2], "cull_candidates": gcnt[3],
-                                    "fp64_band_rate": gcnt[2] / gcnt[1] if gcnt[1] else None},
-            "search_counters": {"pair_rows": scnt[0], "wide_pairs": scnt[1],
-                                "wide_terms": scnt[2], "lane_slots": scnt[3],
-                                "lane_utilisation": scnt[0] / scnt[3] if scnt[3] else None},
-            "search_tensor_core": tc,
-            "search_sparse_needle": sp,
-            "precision_form_sample": precision,
-            "clutterbox": cbox,
-            "spin_images": spin,
-            "batched_run": batched,
-            "batched_run_small_scenes": batched_small,
-            "tuning": step_tuning,
-            "autotune_s": tune_s,
+            **{f"{k}_ms": v for k, v in pms.items()},
+            **{f"generation_R{R}_images_per_s": V / (pms[f'generation_R{R}'] / 1e3) for R in RADII},
+            "search_comparisons_per_s": pairs / (pms["search"] / 1e3),
+            "rank0_fraction": float((rk == 0).mean()),
+            "generation_counters": {
+                str(R): {"pairs_processed": c[0], "layer_items": c[1], "fp64_band_items": c[2],
+                         "cull_candidates": c[3], "fp64_band_rate": c[2] / c[1] if c[1] else None}
+                for R, c in gcnt.items()},
+            "search_counters": {"dense_pair_rows": scnt[0], "int64_pairs": scnt[1],
+                                "int64_terms": scnt[2], "dense_lane_slots": scnt[3]},
+            "oracle_work_per_origin": work,
+            "search_forms_on_step_images": forms,
+            "tuning": {str(R): t for R, t in tunings.items()}, "autotune_s": tune_s,
+            **cmp,
         },
         "roofline": roof,
         "rooflines": rooflines,
-        "peaks": {"kind": pk_kind, "hbm_gbs": pk.get("hbm_gbs")},
+        "peaks": {"kind": pk_kind, "hbm_gbs": pk.get("hbm_gbs"),
+                  "bf16_tflops": pk.get("bf16_tflops"),
+                  "mma_s8_gmacs_measured": mma_rate / 1e9,
+                  "dp4a_g_per_s_measured": dp4a_rate / 1e9},
         "cpu_baseline": cpu,
         "e2e": e2e,
         "clocks": clk,
         "gpu_launches": launches,
+        "status": st,
     }
     if rank == 0:
         print(json.dumps(line), flush=True)

@@ -190,6 +190,12 @@ def workspace(device, nbytes: int) -> torch.Tensor:
     return buf[off:]
 
 
+def release_workspaces() -> None:
+    """Drop the cached scratch buffers of every device (their memory returns to torch's
+    allocator once no call still holds them)."""
+    _workspaces.clear()
+
+
 def rici_generate(vertices, normals, triangles, origins, support_radius: float, resolution: int,
                   *, out=None, mode: int = GEN_DEFAULT, counters=None, stream=None):
     """uint16 [O, N, N] RICI images of the oriented points (vertices[origins], normals[origins])."""

@@ -175,3 +175,49 @@ def precision_form_scenes(seed: int = 31, n_scenes: int = 6473):
     (subdivision 2, 162 vertices each, as ``tiny_scene``), each with its own seed; their RICI
     images in scene order, first 2^20 kept, make the haystack pool."""
     return [tiny_scene(seed * 100_000 + k) for k in range(n_scenes)]
+
+
+def scene_batch_pooled(seed: int, n_scenes: int = 256, pool_size: int = 96, tri_lo: int = 2000,
+                       tri_hi: int = 200_000, clutter_lo: int = 1, clutter_hi: int = 15,
+                       total_lo: int = 10_000, total_hi: int = 2_000_000, half_box: float = 1.0):
+    """The batched workload at scale: n_scenes scenes of a target plus clutter_lo..clutter_hi
+    clutter meshes (2k-200k triangles, log-uniform), totals clipped to [total_lo, total_hi], with
+    every mesh drawn from a seeded pool of ``pool_size`` meshes of the synthetic collection (as
+    the clutterbox draws from a fixed object collection) and placed at its own uniform random
+    orientation and centre in [-half_box, half_box]^3.  Normals are the pool mesh's area-weighted
+    normals (FP64) turned with it.  Building a few hundred scenes of up to 2M triangles from
+    scratch would take minutes; placing pooled meshes takes seconds."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    pool = [_clutter_mesh(rng, tri_lo, tri_hi) for _ in range(pool_size)]
+    pool_n = [M.area_weighted_normals(m.vertices, m.triangles) for m in pool]
+    out = []
+    for _ in range(n_scenes):
+        picks = [int(rng.integers(pool_size))]
+        total = pool[picks[0]].num_triangles
+        for _ in range(int(rng.integers(clutter_lo, clutter_hi + 1))):
+            k = int(rng.integers(pool_size))
+            if total + pool[k].num_triangles > total_hi:
+                break
+            picks.append(k)
+            total += pool[k].num_triangles
+        while total < total_lo:
+            k = int(rng.integers(pool_size))
+            picks.append(k)
+            total += pool[k].num_triangles
+        vs, ns, ts, voff, toff = [], [], [], [], []
+        nv = nt = 0
+        for k in picks:
+            rot = M.random_rotation(rng)
+            centre = rng.uniform(-half_box, half_box, size=3)
+            vs.append(pool[k].vertices @ rot.T + centre[None, :])
+            ns.append(pool_n[k] @ rot.T)
+            ts.append(pool[k].triangles + nv)
+            voff.append(nv)
+            toff.append(nt)
+            nv += pool[k].num_vertices
+            nt += pool[k].num_triangles
+        out.append(Scene(np.ascontiguousarray(np.concatenate(vs).astype(np.float32)),
+                         np.ascontiguousarray(np.concatenate(ns).astype(np.float32)),
+                         np.ascontiguousarray(np.concatenate(ts).astype(np.int32)),
+                         pool[picks[0]].num_vertices, pool[picks[0]].num_triangles, voff, toff))
+    return out
