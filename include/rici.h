@@ -346,9 +346,10 @@ RICI_API int64_t rici_kernel_launches(void);
  * process-wide (every device and stream) and is read when a call launches its kernels.  The
  * paper has no counterpart (it fixes one kernel configuration for its GPU). */
 typedef struct RiciTuning {
-  int32_t gen_cells_per_reach; /* 2 or 3: generation grid cells per triangle reach (the support
-                                  sphere's radius plus the largest binned triangle's); each
-                                  oriented point scans (2 x this + 1)^3 cells. Default 2. */
+  int32_t gen_cells_per_reach; /* 2, 3 or 4: generation grid cells per triangle reach (the
+                                  support sphere's radius plus the largest binned triangle's);
+                                  each oriented point scans (2 x this + 1)^3 cells (the clutter
+                                  measure and spin images use at most 3). Default 2. */
   float gen_big_radius;        /* in [1/16, 1]: triangles whose bounding radius exceeds this
                                   fraction of the support sphere's radius are checked by every
                                   oriented point of their scene instead of being binned.
@@ -366,7 +367,7 @@ RICI_API int rici_set_tuning(const RiciTuning *tuning);
 RICI_API int rici_get_tuning(RiciTuning *tuning);
 
 /* Autotuner of the batched run.  Runs rici_generate_batch on the given scenes under each candidate
- * generation setting (gen_cells_per_reach in {2,3} x gen_big_radius in {1/8, 1/4, 1/2, 1} x
+ * generation setting (gen_cells_per_reach in {2,3,4} x gen_big_radius in {1/8, 1/4, 1/2, 1} x
  * gen_warps in {4,8}; the other fields as in force), one untimed warm-up and `repeats` (1..100)
  * runs timed with CUDA events on `stream`, and writes the fastest setting to *best and its mean
  * time in milliseconds to *best_ms (may be NULL).  The scenes' output images are written by every

@@ -136,7 +136,7 @@ const Tuning kDefaultTuning = {2, 0.25f, 4, 8};
 Tuning g_tuning = kDefaultTuning;
 
 bool tuning_valid(const RiciTuning &t) {
-  return (t.gen_cells_per_reach == 2 || t.gen_cells_per_reach == 3) &&
+  return (t.gen_cells_per_reach >= 2 && t.gen_cells_per_reach <= 4) &&
          t.gen_big_radius >= 0.0625f && t.gen_big_radius <= 1.0f &&
          (t.gen_warps == 4 || t.gen_warps == 8) && t.tc_group_m >= 1 && t.tc_group_m <= 64;
 }
@@ -725,7 +725,7 @@ int rici_set_tuning(const RiciTuning *tuning) {
   }
   if (!tuning_valid(*tuning))
     return fail(RICI_ERR_INVALID_ARGUMENT,
-                "tuning out of range (cells per reach 2|3, big radius [1/16,1], warps 4|8, "
+                "tuning out of range (cells per reach 2..4, big radius [1/16,1], warps 4|8, "
                 "group 1..64)");
   store_tuning(from_public(*tuning));
   return RICI_OK;
@@ -744,7 +744,7 @@ int rici_autotune_generate_batch(const RiciGenerateScene *scenes, int32_t num_sc
   t_last_error.clear();
   std::vector<Tuning> cands;
   const Tuning base = current_tuning();
-  const int cells[] = {2, 3};
+  const int cells[] = {2, 3, 4};
   const float big[] = {0.125f, 0.25f, 0.5f, 1.0f};
   const int warps[] = {4, 8};
   for (int c : cells)

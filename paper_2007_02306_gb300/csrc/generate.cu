@@ -36,6 +36,8 @@ constexpr uint32_t kSkip = 0xFFFFFFFEu;
 constexpr float kCellClamp = 1048576.0f;  // |cell coordinate| limit (2^20)
 constexpr int kSlot = 21;  // words per staged triangle (odd stride: conflict-free lookups)
 constexpr int kScanItems = kGenScanItems;
+constexpr int kGenMaxCellsPerReach = 4;      // generation: up to (2 x 4 + 1)^3 cells per point
+constexpr int kClutterMaxCellsPerReach = 3;  // clutter measure and spin images: up to 7^3
 // shared words per warp: candidate queue, FP64 queue (triangle records, then their layers as
 // bytes), staged triangles
 constexpr int kPerWarp = 64 + 64 + 16 + 32 * kSlot;
@@ -815,21 +817,18 @@ __global__ void __launch_bounds__(NW * 32, NW == 4 ? 7 : 3) k_generate(KArgs a) 
     for (int base = 0; base < total; base += 32) {
       const int it = base + lane;
       const bool act = it < total;
-      // owner of each item of this window: every triangle marks the first window position it
-      // owns (positions are distinct), and a running maximum carries the mark to the positions
-      // that follow (owners' lanes increase with their first item)
-      s.wst[lane] = -1;
-      __syncwarp();
+      // owner of each item of this window: every triangle with items in the window marks the
+      // first window position it owns (positions are distinct; the triangle holding position 0
+      // always marks it), and an item belongs to the triangle of the last mark at or before it
       const int d = first - base;
-      if (nlay > 0 && d < 32 && d + nlay > 0) s.wst[d > 0 ? d : 0] = lane;
+      const bool mark = nlay > 0 && d < 32 && d + nlay > 0;
+      const int pos = d > 0 ? d : 0;
+      if (mark) s.wst[pos] = lane;
+      const unsigned starts = __reduce_or_sync(0xffffffffu, mark ? 1u << pos : 0u);
       __syncwarp();
-      int owner = s.wst[lane];
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, owner, o);
-        if (lane >= o) owner = max(owner, y);
-      }
-      const int ofirst = __shfl_sync(0xffffffffu, first, owner < 0 ? 0 : owner);
+      const int q = 31 - __clz(starts & (0xffffffffu >> (31 - lane)));  // bit 0 is always set
+      const int owner = s.wst[q];
+      const int ofirst = __shfl_sync(0xffffffffu, first, owner);
       int res = 0, r = 0, rec = 0, lo = 0, hi = 0, dlo = 0;
       if (act) {
         const float *ts = s.slots + owner * kSlot;
@@ -1476,7 +1475,7 @@ cudaError_t launch_project_fp32(const float *pts, int64_t n, const float *sv, co
 // bucket starts, cell size, reach, pretest limits, neighbourhood width).
 static cudaError_t bin_triangles(const GenScene *scenes, int num_scenes, int64_t nt, int64_t TB,
                                  double R, double amax, double bmax, void *ws, int *status,
-                                 cudaStream_t st, KArgs &k) {
+                                 cudaStream_t st, KArgs &k, int max_cells_per_reach) {
   Carver c(ws);
   GenScene *tab = c.take<GenScene>(num_scenes);
   int *counts = c.take<int>(TB);
@@ -1503,7 +1502,9 @@ static cudaError_t bin_triangles(const GenScene *scenes, int num_scenes, int64_t
   // a triangle (centre c, radius <= r_big) reaching the support volume has |c - S| <= reach;
   // with cell > reach / nhalf its cell lies within +-nhalf cells of the spin vertex's cell
   const double reach = (rho + gp.r_big) * 1.001;
-  const double cell = reach / tu.gen_cells_per_reach * 1.01;
+  const int cpr = tu.gen_cells_per_reach < max_cells_per_reach ? tu.gen_cells_per_reach
+                                                               : max_cells_per_reach;
+  const double cell = reach / cpr * 1.01;
   gp.inv_cell = (float)(1.0 / cell);
   gp.mask = 0;
 
@@ -1535,7 +1536,7 @@ static cudaError_t bin_triangles(const GenScene *scenes, int num_scenes, int64_t
   k.R = (float)R;
   k.alpha_cull = (float)(amax * (1.0 + 1.0 / 1024.0) + 1e-3 * R);
   k.beta_cull = (float)(bmax * (1.0 + 1.0 / 1024.0) + 1e-3 * R);
-  k.nhalf = tu.gen_cells_per_reach;
+  k.nhalf = cpr;
   k.r_big = gp.r_big;
   k.status = status;
   return cudaSuccess;
@@ -1551,7 +1552,7 @@ cudaError_t launch_generate_batch(const GenScene *scenes, const GenerateBatch &g
   const double bmax = R * (N - 1.0) / (2.0 * N);
   KArgs k;
   cudaError_t e = bin_triangles(scenes, g.num_scenes, g.total_tris, g.total_buckets, R, amax,
-                                bmax, ws, g.status, st, k);
+                                bmax, ws, g.status, st, k, kGenMaxCellsPerReach);
   if (e != cudaSuccess) return e;
   k.R = g.R;
   k.N = N;
@@ -1577,7 +1578,7 @@ cudaError_t launch_clutter(const ClutterArgs &a, void *ws, cudaStream_t st) {
   const double R = a.support_radius;
   KArgs k;
   cudaError_t e = bin_triangles(&sc, 1, a.num_triangles, (int64_t)sc.nbuckets + 1, R, R, 0.5 * R,
-                                ws, a.status, st, k);
+                                ws, a.status, st, k, kClutterMaxCellsPerReach);
   if (e != cudaSuccess) return e;
   k.N = 0;
   k.mode = 0;
@@ -1608,7 +1609,7 @@ cudaError_t launch_spin(const SpinArgs &a, void *ws, cudaStream_t st) {
   const double R = a.support_radius;
   KArgs k;
   cudaError_t e = bin_triangles(&sc, 1, a.num_triangles, (int64_t)sc.nbuckets + 1, R, R, 0.5 * R,
-                                ws, a.status, st, k);
+                                ws, a.status, st, k, kClutterMaxCellsPerReach);
   if (e != cudaSuccess) return e;
   k.N = a.resolution;
   k.mode = 0;

@@ -57,7 +57,7 @@ def images(rici, scenes):
 
 
 GEN_CANDIDATES = [{"gen_cells_per_reach": c, "gen_big_radius": b, "gen_warps": w, "tc_group_m": 8}
-                  for c in (2, 3) for b in (0.125, 0.25, 0.5, 1.0) for w in (4, 8)]
+                  for c in (2, 3, 4) for b in (0.125, 0.25, 0.5, 1.0) for w in (4, 8)]
 
 
 def test_every_generation_tuning_gives_the_same_images(rici, scenes, oracle_mod):
@@ -69,7 +69,7 @@ def test_every_generation_tuning_gives_the_same_images(rici, scenes, oracle_mod)
         for a, b in zip(got, ref):
             assert np.array_equal(a, b), t
     # the most different tuning against the oracle on sampled origins of the largest scene
-    rici.set_tuning({"gen_cells_per_reach": 3, "gen_big_radius": 0.5, "gen_warps": 8,
+    rici.set_tuning({"gen_cells_per_reach": 4, "gen_big_radius": 0.5, "gen_warps": 8,
                      "tc_group_m": 8})
     got = images(rici, scenes)
     rici.set_tuning(None)

@@ -35,7 +35,7 @@ def test_defaults_and_roundtrip(binding):
     assert binding.get_tuning() == DEFAULT
 
 
-@pytest.mark.parametrize("field,value", [("gen_cells_per_reach", 1), ("gen_cells_per_reach", 4),
+@pytest.mark.parametrize("field,value", [("gen_cells_per_reach", 1), ("gen_cells_per_reach", 5),
                                          ("gen_big_radius", 0.01), ("gen_big_radius", 1.5),
                                          ("gen_warps", 6), ("tc_group_m", 0),
                                          ("tc_group_m", 65)])
