@@ -248,6 +248,17 @@ RICI_API int rici_batch_run(const RiciBatchScene *scenes, int32_t num_scenes,
                             float support_radius, int32_t resolution, int32_t mode,
                             void *workspace, int64_t workspace_bytes, void *stream);
 
+/* rici_batch_run with the launch tuning of this call: `tuning` (see RiciTuning below) is in force
+ * for this call only, on the calling thread (concurrent callers with different tunings do not
+ * interfere, and the process-wide setting is neither read nor changed); NULL takes the
+ * process-wide setting.  RICI_ERR_INVALID_ARGUMENT for a tuning out of range.  Results do not
+ * depend on the tuning. */
+typedef struct RiciTuning RiciTuning;
+RICI_API int rici_batch_run_ex(const RiciBatchScene *scenes, int32_t num_scenes,
+                               float support_radius, int32_t resolution, int32_t mode,
+                               const RiciTuning *tuning, void *workspace, int64_t workspace_bytes,
+                               void *stream);
+
 /*
  * rici_clutter — the clutter measure of Eq. clutter (Section 4.1) per oriented point:
  * clutter = (A_all - A_object) / A_all, with A_all the surface area of the mesh inside the
@@ -345,7 +356,7 @@ RICI_API int64_t rici_kernel_launches(void);
  * top-1 are bit-identical for every valid setting; only the speed differs.  The setting is
  * process-wide (every device and stream) and is read when a call launches its kernels.  The
  * paper has no counterpart (it fixes one kernel configuration for its GPU). */
-typedef struct RiciTuning {
+struct RiciTuning {
   int32_t gen_cells_per_reach; /* 2, 3 or 4: generation grid cells per triangle reach (the
                                   support sphere's radius plus the largest binned triangle's);
                                   each oriented point scans (2 x this + 1)^3 cells (the clutter
@@ -357,7 +368,7 @@ typedef struct RiciTuning {
   int32_t gen_warps;           /* 4 or 8 warps per oriented point. Default 4. */
   int32_t tc_group_m;          /* 1..64: needle tiles of 128 that the tensor-core search sweeps
                                   together over the haystack (L2 reuse). Default 8. */
-} RiciTuning;
+};
 
 /* Sets the process-wide tuning; NULL restores the defaults.  RICI_ERR_INVALID_ARGUMENT when a
  * field is out of range (nothing changes then). */

@@ -113,6 +113,8 @@ def load_library(path: str | None = None):
         lib.rici_batch_run_workspace_size.restype = i64
         lib.rici_batch_run.argtypes = [P, i32, f32, i32, i32, P, i64, P]
         lib.rici_batch_run.restype = ctypes.c_int
+        lib.rici_batch_run_ex.argtypes = [P, i32, f32, i32, i32, P, P, i64, P]
+        lib.rici_batch_run_ex.restype = ctypes.c_int
         lib.rici_sync_status.argtypes = [P, ctypes.POINTER(i32)]
         lib.rici_sync_status.restype = ctypes.c_int
         lib.rici_release_workspace.argtypes = []
@@ -381,14 +383,16 @@ def generate_batch_workspace_bytes(scenes, resolution: int) -> int:
 
 
 def batch_run(scenes, support_radius: float, resolution: int, *, mode: int = SEARCH_TENSOR,
-              workspace_tensor=None, outputs=None, stream=None):
+              workspace_tensor=None, outputs=None, tuning=None, stream=None):
     """The whole path for several scenes in one call (rici_batch_run).
 
     scenes: list of dicts with CUDA tensors "vertices" [V,3] f32, "normals" [V,3] f32,
     "triangles" [T,3] i32 (the target mesh first), "needle_origins" [Q] i32, "haystack_origins"
     [H] i32, optional "true_match" [Q] i64, and the int "target_triangles".  outputs: optional
     list of dicts of preallocated "needle_images", "haystack_images", "rank", "true_distance",
-    "top1" (needed to replay a captured graph).  Returns the list of output dicts.
+    "top1" (needed to replay a captured graph).  tuning: a dict of RiciTuning fields in force for
+    this call only (rici_batch_run_ex), or None for the process-wide setting.  Returns the list of
+    output dicts.
     """
     lib = load_library()
     N = int(resolution)
@@ -424,9 +428,13 @@ def batch_run(scenes, support_radius: float, resolution: int, *, mode: int = SEA
     ws = workspace_tensor if workspace_tensor is not None else workspace(dev, nb)
     if ws.numel() < nb:
         raise ValueError(f"workspace_tensor needs {nb} bytes")
+    tun = None
+    if tuning is not None:
+        tun = _Tuning(**{k: tuning[k] for k in TUNING_FIELDS})
     with torch.cuda.device(dev):
-        _check(lib.rici_batch_run(arr, len(scenes), float(support_radius), N, int(mode), _ptr(ws),
-                                  ws.numel(), _stream_handle(stream)))
+        _check(lib.rici_batch_run_ex(arr, len(scenes), float(support_radius), N, int(mode),
+                                     None if tun is None else ctypes.byref(tun), _ptr(ws),
+                                     ws.numel(), _stream_handle(stream)))
     return res
 
 

@@ -134,6 +134,16 @@ namespace {
 std::mutex g_tune_mu;
 const Tuning kDefaultTuning = {2, 0.25f, 4, 8};
 Tuning g_tuning = kDefaultTuning;
+// A tuning in force for the calling thread only (a per-call tuning or an autotuner's candidate);
+// null: the process-wide setting.
+thread_local const Tuning *t_tuning_override = nullptr;
+
+// Puts `t` in force for the calling thread until the guard ends (the previous override returns).
+struct TuningOverride {
+  const Tuning *prev;
+  explicit TuningOverride(const Tuning *t) : prev(t_tuning_override) { t_tuning_override = t; }
+  ~TuningOverride() { t_tuning_override = prev; }
+};
 
 bool tuning_valid(const RiciTuning &t) {
   return (t.gen_cells_per_reach >= 2 && t.gen_cells_per_reach <= 4) &&
@@ -170,6 +180,7 @@ int autotune(const std::vector<Tuning> &cands, int32_t repeats, void *stream, Ru
   if (repeats < 1 || repeats > 100) return fail(RICI_ERR_INVALID_ARGUMENT, "repeats in [1, 100]");
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const Tuning saved = current_tuning();
+  TuningOverride guard(nullptr);  // candidates below are in force for this thread only
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   cudaError_t e;
   if ((e = cudaEventCreate(&e0)) != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
@@ -181,7 +192,7 @@ int autotune(const std::vector<Tuning> &cands, int32_t repeats, void *stream, Ru
   float best_t = 0.0f;
   Tuning best_c = saved;
   for (size_t i = 0; i < cands.size() && rc == RICI_OK; ++i) {
-    store_tuning(cands[i]);
+    t_tuning_override = &cands[i];
     if ((rc = run()) != RICI_OK) break;
     if ((e = cudaEventRecord(e0, st)) != cudaSuccess) { rc = cuda_fail(e, "event"); break; }
     for (int r = 0; r < repeats && rc == RICI_OK; ++r) rc = run();
@@ -196,7 +207,6 @@ int autotune(const std::vector<Tuning> &cands, int32_t repeats, void *stream, Ru
       best_c = cands[i];
     }
   }
-  store_tuning(saved);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   if (rc != RICI_OK) return rc;
@@ -207,6 +217,7 @@ int autotune(const std::vector<Tuning> &cands, int32_t repeats, void *stream, Ru
 }  // namespace
 
 Tuning current_tuning() {
+  if (t_tuning_override) return *t_tuning_override;
   std::lock_guard<std::mutex> lk(g_tune_mu);
   return g_tuning;
 }
@@ -652,6 +663,23 @@ int rici_batch_run(const RiciBatchScene *scenes, int32_t num_scenes, float suppo
     return rc;
   return crss_search_batch(srch.data(), num_scenes, resolution, mode, workspace, workspace_bytes,
                            stream);
+}
+
+int rici_batch_run_ex(const RiciBatchScene *scenes, int32_t num_scenes, float support_radius,
+                      int32_t resolution, int32_t mode, const RiciTuning *tuning,
+                      void *workspace, int64_t workspace_bytes, void *stream) {
+  t_last_error.clear();
+  if (!tuning)
+    return rici_batch_run(scenes, num_scenes, support_radius, resolution, mode, workspace,
+                          workspace_bytes, stream);
+  if (!tuning_valid(*tuning))
+    return fail(RICI_ERR_INVALID_ARGUMENT,
+                "tuning out of range (cells per reach 2..4, big radius [1/16,1], warps 4|8, "
+                "group 1..64)");
+  const Tuning t = from_public(*tuning);
+  TuningOverride guard(&t);
+  return rici_batch_run(scenes, num_scenes, support_radius, resolution, mode, workspace,
+                        workspace_bytes, stream);
 }
 
 int rici_sync_status(void *stream, int32_t *device_status) {

@@ -193,3 +193,25 @@ def test_noalloc_rejects_on_host_with_error_text(lib):
     assert lib.rici_generate_noalloc(dummy, dummy, 3, dummy, 1, dummy, 0,
                                      ctypes.c_float(3.4028e38), 64, None, None) == 0
     assert lib.rici_last_error_string() == b""
+
+
+def test_batch_run_ex_rejects_a_bad_tuning_on_host(lib):
+    class T(ctypes.Structure):
+        _fields_ = [("gen_cells_per_reach", ctypes.c_int32), ("gen_big_radius", ctypes.c_float),
+                    ("gen_warps", ctypes.c_int32), ("tc_group_m", ctypes.c_int32)]
+
+    lib.rici_last_error_string.restype = ctypes.c_char_p
+    bad = T(5, 0.25, 4, 8)
+    assert lib.rici_batch_run_ex(None, 0, ctypes.c_float(0.3), 64, 3, ctypes.byref(bad), None, 0,
+                                 None) == 1
+    assert b"tuning" in lib.rici_last_error_string()
+    # a valid tuning for an empty batch: a no-op that leaves the process-wide tuning alone
+    before = T()
+    assert lib.rici_get_tuning(ctypes.byref(before)) == 0
+    good = T(4, 1.0, 8, 16)
+    assert lib.rici_batch_run_ex(None, 0, ctypes.c_float(0.3), 64, 3, ctypes.byref(good), None, 0,
+                                 None) == 0
+    after = T()
+    assert lib.rici_get_tuning(ctypes.byref(after)) == 0
+    assert (after.gen_cells_per_reach, after.tc_group_m) == (before.gen_cells_per_reach,
+                                                            before.tc_group_m)

@@ -219,3 +219,23 @@ def test_single_call_batch_run_replays_from_a_cuda_graph(rici, batch):
     for r0, r1 in zip(ref, outs):
         for k in r0:
             assert torch.equal(r0[k], r1[k]), k
+
+
+def test_per_call_tuning_gives_the_same_results_and_leaves_the_setting(rici, batch):
+    """rici_batch_run_ex: a tuning in force for one call only (different grid, warps and tile
+    grouping) gives the results of the process-wide setting, and does not change that setting."""
+    scenes = [{"vertices": x["V"], "normals": x["Nrm"], "triangles": x["T"],
+               "target_triangles": x["scene"].target_triangles, "needle_origins": x["on"],
+               "haystack_origins": x["oh"], "true_match": x["match"]} for x in batch[:6]]
+    rici.set_tuning(None)
+    before = rici.get_tuning()
+    ref = rici.batch_run(scenes, R, N)
+    other = {"gen_cells_per_reach": 4, "gen_big_radius": 1.0, "gen_warps": 8, "tc_group_m": 3}
+    got = rici.batch_run(scenes, R, N, tuning=other)
+    assert rici.sync_status() == 0
+    assert rici.get_tuning() == before
+    for a, b in zip(ref, got):
+        for k in ("needle_images", "haystack_images"):
+            assert np.array_equal(host_u16(a[k]), host_u16(b[k])), k
+        for k in ("rank", "true_distance", "top1"):
+            assert np.array_equal(a[k].cpu().numpy(), b[k].cpu().numpy()), k
