@@ -206,8 +206,11 @@ RICI_API int64_t crss_search_batch_workspace_size(const RiciSearchScene *scenes,
                                                   int32_t num_scenes, int32_t resolution,
                                                   int32_t mode);
 /* crss_search for every scene of the batch: each needle is ranked against its own scene's
- * haystack only.  mode RICI_SEARCH_TENSOR (or DEFAULT) runs one persistent tensor-core launch
- * over all scenes; other modes use the exact int64 kernel for multi-scene batches. */
+ * haystack only.  RICI_SEARCH_TENSOR (or DEFAULT) runs one persistent tensor-core launch over all
+ * scenes' tiles (pairs outside the fp16 class in exact int64), RICI_SEARCH_INT8_TC one int8
+ * tensor-core launch over all scenes' tiles; RICI_SEARCH_CUDA_CORE and RICI_SEARCH_SPARSE run
+ * the single-scene form scene after scene on the stream (one workspace sized for the largest
+ * scene, no host synchronisation); RICI_SEARCH_EXACT_SLOW the int64 kernel over all scenes. */
 RICI_API int crss_search_batch(const RiciSearchScene *scenes, int32_t num_scenes,
                                int32_t resolution, int32_t mode, void *workspace,
                                int64_t workspace_bytes, void *stream);

@@ -563,13 +563,34 @@ static int build_search_batch(const RiciSearchScene *scenes, int32_t ns, int32_t
   return RICI_OK;
 }
 
+// The CUDA-core dense and sparse-needle kernels work on one haystack, so a multi-scene batch in
+// those forms runs scene by scene (each scene's launches on the same stream, reusing one
+// workspace sized for the largest scene; no host synchronisation, so the sequence can still be
+// recorded into a CUDA graph).  The tensor-core forms run every scene in one set of launches.
+static bool per_scene_form(int mode, int num_scenes) {
+  return num_scenes > 1 && (mode == RICI_SEARCH_CUDA_CORE || mode == RICI_SEARCH_SPARSE);
+}
+
+static int64_t batch_search_workspace(const std::vector<SearchScene> &tab, const SearchBatch &b,
+                                      int32_t num_scenes, int32_t N) {
+  if (per_scene_form(b.mode, num_scenes)) {
+    int64_t m = 256;
+    for (const SearchScene &s : tab) {
+      if (s.Q == 0) continue;
+      const int64_t w = search_workspace_bytes(s.Q, s.H, N, b.mode);
+      m = w > m ? w : m;
+    }
+    return m;
+  }
+  return search_batch_workspace_bytes(num_scenes > 0 ? num_scenes : 1, b.Qtot, b.Htot, N, b.mode);
+}
+
 int64_t crss_search_batch_workspace_size(const RiciSearchScene *scenes, int32_t num_scenes,
                                          int32_t resolution, int32_t mode) {
   std::vector<SearchScene> tab;
   SearchBatch b{};
   if (build_search_batch(scenes, num_scenes, resolution, mode, &tab, &b)) return -1;
-  return search_batch_workspace_bytes(num_scenes > 0 ? num_scenes : 1, b.Qtot, b.Htot, resolution,
-                                      b.mode);
+  return batch_search_workspace(tab, b, num_scenes, resolution);
 }
 
 int crss_search_batch(const RiciSearchScene *scenes, int32_t num_scenes, int32_t resolution,
@@ -584,13 +605,34 @@ int crss_search_batch(const RiciSearchScene *scenes, int32_t num_scenes, int32_t
   if ((rc = device_state(&d))) return rc;
   void *ws = nullptr;
   if ((rc = resolve_workspace(d, workspace, workspace_bytes,
-                              search_batch_workspace_bytes(num_scenes, b.Qtot, b.Htot, resolution,
-                                                           b.mode),
-                              &ws)))
+                              batch_search_workspace(tab, b, num_scenes, resolution), &ws)))
     return rc;
   b.counters = nullptr;
   b.status = d->status;
-  cudaError_t e = launch_search_batch(tab.data(), b, ws, static_cast<cudaStream_t>(stream), nullptr);
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (per_scene_form(b.mode, num_scenes)) {
+    for (const SearchScene &sc : tab) {
+      if (sc.Q == 0) continue;
+      SearchArgs a;
+      a.needles = sc.needles;
+      a.num_needles = sc.Q;
+      a.haystack = sc.haystack;
+      a.num_haystack = sc.H;
+      a.resolution = resolution;
+      a.true_match = sc.match;
+      a.out_rank = sc.rank;
+      a.out_true_distance = sc.dtrue;
+      a.out_top1 = sc.top1;
+      a.out_distances = nullptr;
+      a.mode = b.mode;
+      a.counters = nullptr;
+      a.status = d->status;
+      cudaError_t e = launch_search(a, ws, st);
+      if (e != cudaSuccess) return cuda_fail(e, "crss_search_batch launch");
+    }
+    return RICI_OK;
+  }
+  cudaError_t e = launch_search_batch(tab.data(), b, ws, st, nullptr);
   if (e != cudaSuccess) return cuda_fail(e, "crss_search_batch launch");
   return RICI_OK;
 }
