@@ -109,6 +109,8 @@ def parse():
                     help="image only the first V scene vertices (small profiling case)")
     ap.add_argument("--needle-limit", type=int, default=0,
                     help="use only the first Q needles (small profiling case)")
+    ap.add_argument("--radii", type=str, default="",
+                    help="comma-separated subset of the support radii (small profiling case)")
     return ap.parse_args()
 
 
@@ -654,11 +656,16 @@ def main():
     p.load_library()
 
     scene = build_workload()
+    global RADII
+    if args.radii:
+        RADII = tuple(float(x) for x in args.radii.split(","))
+        if R_SEARCH not in RADII:
+            raise SystemExit("--radii must include the search radius 0.3")
     V = scene.num_vertices if not args.origin_limit else min(scene.num_vertices, args.origin_limit)
     Vt, Tt, T = scene.target_vertices, scene.target_triangles, scene.num_triangles
     on_np = needle_origins(scene, args.needle_limit)
     Q = len(on_np)
-    if args.origin_limit or args.needle_limit:
+    if args.origin_limit or args.needle_limit or args.radii:
         args.no_cpu_baseline = True
     h_vert = torch.from_numpy(scene.vertices).pin_memory()
     h_norm = torch.from_numpy(scene.normals).pin_memory()
@@ -728,10 +735,12 @@ def main():
     parts = []
     for k in range(args.steps):
         flush.zero_()
+        torch.cuda.nvtx.range_push("timed_step")  # selects the step's launches for ncu
         tm = Timer(torch, stream)
         tm.mark("start")
         res = step(vert, norm, tri, oh, on, match, tm=tm)
         parts.append(tm)
+        torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize()
     clk = clocks.stop()
     launches = p.binding.kernel_launches() - launches0
@@ -743,7 +752,7 @@ def main():
     parts = [tm.parts() for tm in parts]
     pms = {k: statistics.mean(x[k] for x in parts) for k in parts[0]}
     ms_step = max_over_ranks(statistics.mean(sum(x.values()) for x in parts), dev)
-    images = 3 * V + Q
+    images = len(RADII) * V + Q
     pairs = Q * V
     value = job_rate(images, ms_step, world)
     rk = res["rank"].cpu().numpy()
