@@ -155,11 +155,13 @@ __global__ void k_tri_scatter(const GenScene *__restrict__ tab, int ns, int64_t 
     for (int k = 0; k < 3; ++k)
       for (int d = 0; d < 3; ++d) v[3 * k + d] = sc.V[3 * (int64_t)id[k] + d];
     TriSphere s = tri_sphere(v);
-    rec[4 * pos + 0] = make_float4(s.cx, s.cy, s.cz, s.r);
-    rec[4 * pos + 1] = make_float4(v[0], v[1], v[2], v[3]);
-    rec[4 * pos + 2] = make_float4(v[4], v[5], v[6], v[7]);
-    rec[4 * pos + 3] = make_float4(v[8], __int_as_float(id[0]), __int_as_float(id[1]),
-                                   __int_as_float(id[2]));
+    // four columns of nt_total records: the culling pass streams only the first (16 bytes per
+    // triangle), the set-up of survivors reads the other three
+    rec[pos] = make_float4(s.cx, s.cy, s.cz, s.r);
+    rec[nt_total + pos] = make_float4(v[0], v[1], v[2], v[3]);
+    rec[2 * nt_total + pos] = make_float4(v[4], v[5], v[6], v[7]);
+    rec[3 * nt_total + pos] = make_float4(v[8], __int_as_float(id[0]), __int_as_float(id[1]),
+                                          __int_as_float(id[2]));
   }
 }
 
@@ -259,7 +261,8 @@ struct KArgs {
   const GenScene *tab;
   int num_scenes;
   int64_t origin_base;  // first launch-wide origin index of this grid
-  const float4 *rec;
+  const float4 *rec;    // triangle records, 4 columns: rec[k * rs + t]
+  int64_t rs;           // column stride of rec (the launch's triangle count)
   const int *starts;
   float inv_cell;
   float cell;       // grid cell edge (1 / inv_cell)
@@ -397,11 +400,10 @@ __device__ __forceinline__ void project64(float px, float py, float pz, const do
 // Returns false when the triangle does not cross the layer; otherwise the single-crossing
 // columns are [lo, hi) and the double-crossing columns [dlo, lo).
 // (Plain pointer arguments: no structure has to live in local memory.)
-__device__ __forceinline__ bool layer_fp64(const float4 *__restrict__ recs, const double *fr,
-                                        const double *bd, const double *a2d, int N, int rec, int r,
-                                        int &lo, int &hi, int &dlo) {
-  float4 r1 = recs[4 * (int64_t)rec + 1], r2 = recs[4 * (int64_t)rec + 2],
-         r3 = recs[4 * (int64_t)rec + 3];
+__device__ __forceinline__ bool layer_fp64(const float4 *__restrict__ recs, int64_t rs,
+                                        const double *fr, const double *bd, const double *a2d,
+                                        int N, int rec, int r, int &lo, int &hi, int &dlo) {
+  float4 r1 = recs[rs + rec], r2 = recs[2 * rs + rec], r3 = recs[3 * rs + rec];
   double T[3][3];
   project64(r1.x, r1.y, r1.z, fr, T[0]);
   project64(r1.w, r2.x, r2.y, fr, T[1]);
@@ -708,7 +710,7 @@ __global__ void __launch_bounds__(NW * 32, NW == 4 ? 7 : 3) k_generate(KArgs a) 
     if (lane < cnt) {
       int lo = 0, hi = 0, dlo = 0;
       const int r = s.bq_r[lane];
-      if (layer_fp64(a.rec, s.fr, s.bd, s.a2d, N, s.bq_rec[lane], r, lo, hi, dlo))
+      if (layer_fp64(a.rec, a.rs, s.fr, s.bd, s.a2d, N, s.bq_rec[lane], r, lo, hi, dlo))
         add_intervals(s.diff + r * N, N, lo, hi, dlo);
     }
     __syncwarp();
@@ -733,8 +735,7 @@ __global__ void __launch_bounds__(NW * 32, NW == 4 ? 7 : 3) k_generate(KArgs a) 
     float *sl = s.slots + lane * kSlot;
     if (lane < cnt) {
       const int rec = s.wq[lane];
-      float4 r1 = a.rec[4 * (int64_t)rec + 1], r2 = a.rec[4 * (int64_t)rec + 2],
-             r3 = a.rec[4 * (int64_t)rec + 3];
+      float4 r1 = a.rec[a.rs + rec], r2 = a.rec[2 * a.rs + rec], r3 = a.rec[3 * a.rs + rec];
       float P[9] = {r1.x, r1.y, r1.z, r1.w, r2.x, r2.y, r2.z, r2.w, r3.x};
       float tx[3], ty[3], tz[3], M = 0.0f;
 #pragma unroll
@@ -864,7 +865,7 @@ __global__ void __launch_bounds__(NW * 32, NW == 4 ? 7 : 3) k_generate(KArgs a) 
       const int64_t t = base + lane;
       bool pass = false;
       if (t < end) {
-        float4 c = a.rec[4 * t];
+        float4 c = a.rec[t];
         float dx = c.x - Sx, dy = c.y - Sy, dz = c.z - Sz;
         float z = fmaf(wx, dx, fmaf(wy, dy, wz * dz));
         float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
@@ -1213,7 +1214,7 @@ __global__ void __launch_bounds__(kClutterWarps * 32, 5)
     double T[3][3];
     if (lane < cnt) {
       const int64_t r = wq[warp][lane];
-      const float4 r1 = a.rec[4 * r + 1], r2 = a.rec[4 * r + 2], r3 = a.rec[4 * r + 3];
+      const float4 r1 = a.rec[a.rs + r], r2 = a.rec[2 * a.rs + r], r3 = a.rec[3 * a.rs + r];
       project64(r1.x, r1.y, r1.z, fr, T[0]);
       project64(r1.w, r2.x, r2.y, fr, T[1]);
       project64(r2.z, r2.w, r3.x, fr, T[2]);
@@ -1262,7 +1263,7 @@ __global__ void __launch_bounds__(kClutterWarps * 32, 5)
       const int64_t t = base + lane;
       bool pass = false;
       if (t < end) {
-        const float4 c = a.rec[4 * t];
+        const float4 c = a.rec[t];
         const float dx = c.x - Sx, dy = c.y - Sy, dz = c.z - Sz;
         const float z = fmaf(wx, dx, fmaf(wy, dy, wz * dz));
         const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
@@ -1389,7 +1390,7 @@ __global__ void __launch_bounds__(kSpinWarps * 32) k_spin(KArgs a, int m, float 
   auto process = [&](int cnt) {
     if (lane < cnt) {
       const int64_t r = wq[warp][lane];
-      const float4 r1 = a.rec[4 * r + 1], r2 = a.rec[4 * r + 2], r3 = a.rec[4 * r + 3];
+      const float4 r1 = a.rec[a.rs + r], r2 = a.rec[2 * a.rs + r], r3 = a.rec[3 * a.rs + r];
       const float A[3] = {r1.x, r1.y, r1.z}, B[3] = {r1.w, r2.x, r2.y}, C[3] = {r2.z, r2.w, r3.x};
       const float ba[3] = {__fsub_rn(B[0], A[0]), __fsub_rn(B[1], A[1]), __fsub_rn(B[2], A[2])};
       const float ca[3] = {__fsub_rn(C[0], A[0]), __fsub_rn(C[1], A[1]), __fsub_rn(C[2], A[2])};
@@ -1430,7 +1431,7 @@ __global__ void __launch_bounds__(kSpinWarps * 32) k_spin(KArgs a, int m, float 
       const int64_t t = base + lane;
       bool pass = false;
       if (t < end) {
-        const float4 c = a.rec[4 * t];
+        const float4 c = a.rec[t];
         const float dx = c.x - Sx, dy = c.y - Sy, dz = c.z - Sz;
         const float z = fmaf(wx, dx, fmaf(wy, dy, wz * dz));
         const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
@@ -1529,6 +1530,7 @@ static cudaError_t bin_triangles(const GenScene *scenes, int num_scenes, int64_t
   k.tab = tab;
   k.num_scenes = num_scenes;
   k.rec = rec;
+  k.rs = nt;
   k.starts = starts;
   k.inv_cell = gp.inv_cell;
   k.cell = (float)cell;
