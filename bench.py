@@ -355,6 +355,7 @@ def clutter_scene_comparison(p, torch, dev, stream, flush, steps=3):
     parts = []
     for _ in range(steps):
         flush.zero_()
+        torch.cuda.nvtx.range_push("clutter_step")  # selects these launches for ncu
         tm = Timer(torch, stream)
         tm.mark("start")
         p.rici_generate(v, n, t[: s.target_triangles], on, R_SEARCH, N_RES, out=nd)
@@ -363,7 +364,11 @@ def clutter_scene_comparison(p, torch, dev, stream, flush, steps=3):
         tm.mark("haystack")
         r = p.crss_search(nd, hy, m, mode=p.SEARCH_CUDA_CORE)
         tm.mark("search")
+        torch.cuda.nvtx.range_pop()
         parts.append(tm.parts())
+    torch.cuda.nvtx.range_push("clutter_sparse")
+    p.crss_search(nd, hy, m, mode=p.SEARCH_SPARSE)
+    torch.cuda.nvtx.range_pop()
     ms = {k: statistics.mean(x[k] for x in parts) for k in parts[0]}
     cnt = torch.zeros(4, dtype=torch.int64, device=dev)
     p.crss_search(nd, hy, m, mode=p.SEARCH_CUDA_CORE, counters=cnt)
@@ -593,6 +598,9 @@ def spin_comparison(p, torch, dev, stream, flush, steps=3):
     v, n, t = d(s.vertices), d(s.normals), d(s.triangles)
     oh = d(np.arange(s.num_vertices, dtype=np.int32))
     si = torch.empty((s.num_vertices, N_RES, N_RES), dtype=torch.float32, device=dev)
+    torch.cuda.nvtx.range_push("spin_images")
+    p.spin_images(v, n, t, oh, R_SEARCH, N_RES, 3, out=si)
+    torch.cuda.nvtx.range_pop()
     ms, _ = timed_ms(torch, stream, lambda: p.spin_images(v, n, t, oh, R_SEARCH, N_RES, 3, out=si),
                      reps=steps, flush=flush)
     rms, _ = timed_ms(torch, stream, lambda: p.rici_generate(v, n, t, oh, R_SEARCH, N_RES),
