@@ -625,14 +625,15 @@ __global__ void __launch_bounds__(kWideThreads) k_wide(
     const int *__restrict__ wide_h_count, const int64_t *__restrict__ dtrue,
     const int *__restrict__ nflags, int *__restrict__ rank, unsigned long long *__restrict__ best,
     int *__restrict__ top1_flag, unsigned long long *__restrict__ counters,
-    const int *__restrict__ keep_h) {
-  // keep_h (optional, pass 1): only entries hj of the wide haystack list with keep_h[hj] != 0
+    const int *__restrict__ sub_list, const int *__restrict__ sub_count) {
+  // sub_list (optional, pass 1): iterate entries sub_list[0 .. *sub_count) of the wide haystack
+  // list only (the images of that list outside the int8 class)
   extern __shared__ int2 nz[];  // (flat position, needle delta) of non-zero needle deltas
   __shared__ int nnz_s;
   const int tid = threadIdx.x, lane = tid & 31;
   const int64_t K = (int64_t)N * N;
   const int64_t nq = pass == 0 ? *wide_n_count : Qtot;
-  const int64_t nh = pass == 1 ? *wide_h_count : Hmax;
+  const int64_t nh = pass == 1 ? (sub_list ? *sub_count : *wide_h_count) : Hmax;
   const int64_t chunks = (nh + kWideThreads - 1) / kWideThreads;
   const int64_t items = nq * chunks;
   for (int64_t it = blockIdx.x; it < items; it += gridDim.x) {
@@ -667,8 +668,8 @@ __global__ void __launch_bounds__(kWideThreads) k_wide(
     const int64_t hj = ch * kWideThreads + tid;
     int64_t jl = -1;  // scene-local haystack index
     if (pass == 1) {
-      if (hj < nh && (!keep_h || keep_h[hj])) {
-        const int64_t jg = wide_h_list[hj];
+      if (hj < nh) {
+        const int64_t jg = wide_h_list[sub_list ? sub_list[hj] : hj];
         if (hscene[jg] == si) jl = jg - sc.hoff;
       }
     } else if (hj < sc.H) {
@@ -965,11 +966,11 @@ cudaError_t launch_search_batch(const SearchScene *scenes, const SearchBatch &b,
   if ((e = cudaFuncSetAttribute(k_wide, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)wide_smem)) != cudaSuccess)
     return e;
-  auto wide = [&](int pass, const int *keep_h = nullptr) {
+  auto wide = [&](int pass, const int *sub_list = nullptr, const int *sub_count = nullptr) {
     k_wide<<<152 * 8, kWideThreads, wide_smem, st>>>(tab, qscene, hscene, Q, b.Hmax, N, pass,
                                                    nwide, wn_list, counts + 0, wh_list,
                                                    counts + 1, dt, nflags, rank, best, t1flag, cnt,
-                                                   keep_h);
+                                                   sub_list, sub_count);
     count_launches(1);
   };
   auto run_dense = [&](const int *nexcl, const int *hexcl, const int *hcount, const int *hmap) {
@@ -1000,7 +1001,8 @@ cudaError_t launch_search_batch(const SearchScene *scenes, const SearchBatch &b,
                                                    counts + 1);
       count_launches(2);
       if ((e = run_dense(nwide, mid_hflag, counts + 1, wh_list)) != cudaSuccess) return e;
-      wide(1, mid_hflag);
+      // the compacted encode listed its images outside the int8 class (compact indices)
+      wide(1, mid_list + Q, counts + 3);
     } else {
       wide(1);
     }
