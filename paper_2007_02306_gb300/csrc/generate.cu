@@ -861,11 +861,16 @@ __global__ void __launch_bounds__(NW * 32, NW == 4 ? 7 : 3) k_generate(KArgs a) 
   // ---- stream candidates of the listed neighbouring cells and the scene's big list
   for (int nb = 0; nb <= nneigh; ++nb) {
     const int64_t beg = s.buckets[nb], end = s.bdup[nb];
+    // the warp's next 32 bounding spheres of the cell are loaded before the current ones are
+    // tested and queued, so the load's latency overlaps that work (and any batch it triggers)
+    float4 cn = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+    if (beg + warp * 32 + lane < end) cn = a.rec[beg + warp * 32 + lane];
     for (int64_t base = beg + warp * 32; base < end; base += NW * 32) {
       const int64_t t = base + lane;
+      const float4 c = cn;
+      if (t + NW * 32 < end) cn = a.rec[t + NW * 32];
       bool pass = false;
       if (t < end) {
-        float4 c = a.rec[t];
         float dx = c.x - Sx, dy = c.y - Sy, dz = c.z - Sz;
         float z = fmaf(wx, dx, fmaf(wy, dy, wz * dz));
         float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
