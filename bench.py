@@ -314,7 +314,8 @@ def search_forms(p, torch, stream, nd, hay, match, q, ref):
     out = {"needles": q, "haystack": int(hay.shape[0]), "comparisons": q * int(hay.shape[0])}
     ndq, mq = nd[:q], match[:q]
     for name, mode in (("tensor_core", p.SEARCH_TENSOR), ("int8_tensor_core", p.SEARCH_INT8_TC),
-                       ("cuda_core_dense", p.SEARCH_CUDA_CORE), ("sparse_needle", p.SEARCH_SPARSE)):
+                       ("cuda_core_dense", p.SEARCH_CUDA_CORE), ("sparse_needle", p.SEARCH_SPARSE),
+                       ("auto", p.SEARCH_AUTO)):
         cnt = torch.zeros(4, dtype=torch.int64, device=nd.device)
         p.crss_search(ndq, hay, mq, mode=mode, counters=cnt)  # warm-up, with the work counters
         torch.cuda.synchronize()
@@ -423,7 +424,7 @@ def precision_form_comparison(p, torch, dev, stream, flush, i8_needles=16384):
            "scenes": len(scenes), "needles": Q, "haystack": H, "comparisons": Q * H}
     ref = None
     for name, mode, q in (("tensor_core", p.SEARCH_TENSOR, Q), ("cuda_core_dense", p.SEARCH_CUDA_CORE, Q),
-                          ("sparse_needle", p.SEARCH_SPARSE, Q),
+                          ("sparse_needle", p.SEARCH_SPARSE, Q), ("auto", p.SEARCH_AUTO, Q),
                           ("int8_tensor_core", p.SEARCH_INT8_TC, i8_needles)):
         ms, r = timed_ms(torch, stream, lambda: p.crss_search(nd[:q], hay, m[:q], mode=mode),
                          flush=flush)

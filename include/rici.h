@@ -79,6 +79,11 @@ extern "C" {
                                    and the haystack deltas b with b^2 split into two 7-bit limbs;
                                    pairs with |delta| > 127 on either side run in exact int64 on
                                    CUDA cores; single- and multi-scene calls */
+#define RICI_SEARCH_AUTO 6      /* each needle ranked by the fp16 tensor-core form or by the
+                                   sparse-needle form, chosen per needle on the device: the
+                                   sparse form when at most a quarter of its 32-bit delta words
+                                   hold a non-zero delta (N in 8..128, powers of two, single-scene
+                                   calls; multi-scene calls take RICI_SEARCH_TENSOR) */
 /* Test hook, OR-ed into RICI_SEARCH_TENSOR: one CTA of the tensor-core kernel withholds its
  * first tile load, so its bounded waits run out (about 2 s), RICI_ERR_TIMEOUT is raised in the
  * status word and the kernel returns; outputs of that call are unspecified. */

@@ -23,6 +23,7 @@ SEARCH_EXACT_SLOW = 2
 SEARCH_TENSOR = 3
 SEARCH_SPARSE = 4
 SEARCH_INT8_TC = 5
+SEARCH_AUTO = 6
 SEARCH_TEST_WITHHOLD_LOAD = 0x100  # test hook (see include/rici.h)
 
 ERR_INVALID_ARGUMENT = 1

@@ -385,7 +385,8 @@ int crss_search_ex(const uint16_t *needles, int64_t num_needles, const uint16_t 
   const int base_mode = mode & 0xff;
   if ((base_mode != RICI_SEARCH_DEFAULT && base_mode != RICI_SEARCH_CUDA_CORE &&
        base_mode != RICI_SEARCH_EXACT_SLOW && base_mode != RICI_SEARCH_TENSOR &&
-       base_mode != RICI_SEARCH_SPARSE && base_mode != RICI_SEARCH_INT8_TC) ||
+       base_mode != RICI_SEARCH_SPARSE && base_mode != RICI_SEARCH_INT8_TC &&
+       base_mode != RICI_SEARCH_AUTO) ||
       (mode & ~(0xff | RICI_SEARCH_TEST_WITHHOLD_LOAD)) ||
       ((mode & RICI_SEARCH_TEST_WITHHOLD_LOAD) && base_mode != RICI_SEARCH_TENSOR))
     return fail(RICI_ERR_INVALID_ARGUMENT, "unknown search mode %d", mode);
@@ -521,7 +522,7 @@ static int build_search_batch(const RiciSearchScene *scenes, int32_t ns, int32_t
     return fail(RICI_ERR_INVALID_ARGUMENT, "resolution must be in [2, %d]", RICI_MAX_RESOLUTION);
   if (mode != RICI_SEARCH_DEFAULT && mode != RICI_SEARCH_CUDA_CORE &&
       mode != RICI_SEARCH_EXACT_SLOW && mode != RICI_SEARCH_TENSOR && mode != RICI_SEARCH_SPARSE &&
-      mode != RICI_SEARCH_INT8_TC)
+      mode != RICI_SEARCH_INT8_TC && mode != RICI_SEARCH_AUTO)
     return fail(RICI_ERR_INVALID_ARGUMENT, "unknown search mode %d", mode);
   out->resize(ns);
   int64_t q = 0, h = 0, hmax = 0, tiles = 0;

@@ -716,6 +716,42 @@ __global__ void __launch_bounds__(kWideThreads) k_wide(
   }
 }
 
+// Per-needle choice of form (RICI_SEARCH_AUTO): a needle whose non-zero delta words are at most
+// 1/kAutoSparseShare of its words goes to the sparse-needle form, every other int8-class needle
+// to the fp16 tensor cores.  Writes the tensor-core skip flags (sparse_of), the exclusions of the
+// dense middle pass (the sparse needles and those outside int8) and of the sparse kernel (the
+// tensor-core needles and those outside int8).
+constexpr int kAutoSparseShare = 4;
+
+__global__ void k_auto_assign(const int *__restrict__ ecount, const int *__restrict__ n8wide,
+                              int64_t Q, int KW, int *__restrict__ sparse_of,
+                              int *__restrict__ excl_dense, int *__restrict__ excl_sparse) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < Q;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    const int wide = n8wide[i];
+    const int sp = !wide && (int64_t)ecount[i] * kAutoSparseShare <= KW;
+    sparse_of[i] = sp;
+    excl_dense[i] = wide || sp;
+    excl_sparse[i] = wide || !sp;
+  }
+}
+
+// skip_tile[m] = 1 when no needle of tensor-core needle tile m (128 needles) is ranked there.
+__global__ void k_auto_tiles(const int *__restrict__ excl_dense, int64_t Q, int64_t tiles_m,
+                             int *__restrict__ skip_tile) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t m = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; m < tiles_m;
+       m += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    int any = 0;
+    for (int k = lane; k < 128; k += 32) {
+      const int64_t i = m * 128 + k;
+      any |= i < Q && !excl_dense[i];
+    }
+    any = __any_sync(0xffffffffu, any);
+    if (lane == 0) skip_tile[m] = !any;
+  }
+}
+
 // Scene-local outputs: rank, true distance and top-1 (smallest index among minimal distances).
 __global__ void k_finalize(const SearchScene *__restrict__ tab, const int *__restrict__ qscene,
                            int64_t Qtot, const int *__restrict__ rank,
@@ -858,8 +894,10 @@ void search_tiles(int64_t Q, int64_t H, int32_t *tiles_m, int32_t *tiles_n) {
 int64_t search_batch_workspace_bytes(int num_scenes, int64_t Q, int64_t H, int N, int mode) {
   const int64_t K = (int64_t)N * N;
   mode &= 0xff;
-  const bool tensor =
-      (mode == RICI_SEARCH_TENSOR || mode == RICI_SEARCH_DEFAULT) && tc_supported(N);
+  const bool autom = mode == RICI_SEARCH_AUTO && num_scenes == 1 && tc_supported(N) &&
+                     dense_supported(N);
+  const bool tensor = (mode == RICI_SEARCH_TENSOR || mode == RICI_SEARCH_DEFAULT ||
+                       mode == RICI_SEARCH_AUTO) && tc_supported(N);
   const bool i8 = mode == RICI_SEARCH_INT8_TC && i8_supported(N);
   const bool packed = !tensor && !i8 && mode != RICI_SEARCH_EXACT_SLOW && dense_supported(N);
   const bool sparse = packed && mode == RICI_SEARCH_SPARSE;
@@ -876,19 +914,23 @@ int64_t search_batch_workspace_bytes(int num_scenes, int64_t Q, int64_t H, int N
   c.take<int>(H);                        // haystack wide flags
   c.take<int>(Q);                        // wide needle list
   c.take<int>(H);                        // wide haystack list
-  c.take<int>(4);                        // list lengths
+  c.take<int>(8);                        // list lengths
   c.take<int>(Q);                        // per-needle state flags
   c.take<int>(Q);                        // top-1 exact fallback flags
   c.take<unsigned long long>(Q);         // packed best (distance, index)
   c.take<int64_t>(Q);                    // true distances
   c.take<int>(Q);                        // ranks
-  c.take<int4>(sparse ? Q * (K / 4) : 0);  // sparse needle entries (one slab per needle)
-  c.take<int>(sparse ? Q : 0);           // sparse entries per needle
+  c.take<int4>(sparse || autom ? Q * (K / 4) : 0);  // sparse needle entries (a slab per needle)
+  c.take<int>(sparse || autom ? Q : 0);  // sparse entries per needle
   c.take<char>(tensor ? tc_workspace_bytes(Q, H, N) : 0);
   c.take<char>(i8 ? i8_workspace_bytes(Q, H, N) : 0);
   c.take<int>(mid ? Q : 0);      // int8 class flags of the needles (dense middle pass)
   c.take<int>(mid ? H : 0);      // int8 class flags of the compacted haystack images
   c.take<int>(mid ? Q + H : 0);  // lists written by its encodes
+  c.take<int8_t>(autom ? (H + 31) / 32 * 32 * K : 0);  // word-major haystack of the sparse form
+  c.take<int>(autom ? H : 0);     // its int8 class flags
+  c.take<int>(autom ? 3 * Q : 0);  // per-needle choice and the two exclusions
+  c.take<int>(autom ? Q / 128 + 2 : 0);  // tensor-core needle tiles to skip
   return c.off + 256;
 }
 
@@ -904,8 +946,12 @@ cudaError_t launch_search_batch(const SearchScene *scenes, const SearchBatch &b,
   if (Q == 0) return cudaSuccess;
   const int withhold = (b.mode & RICI_SEARCH_TEST_WITHHOLD_LOAD) ? 1 : 0;
   const int mode = b.mode & 0xff;
-  const bool tensor =
-      (mode == RICI_SEARCH_TENSOR || mode == RICI_SEARCH_DEFAULT) && tc_supported(N);
+  // RICI_SEARCH_AUTO (single scene): each needle ranked by the fp16 tensor cores or by the
+  // sparse-needle form, chosen from its share of non-zero delta words (k_auto_assign)
+  const bool autom = mode == RICI_SEARCH_AUTO && b.num_scenes == 1 && tc_supported(N) &&
+                     dense_supported(N);
+  const bool tensor = (mode == RICI_SEARCH_TENSOR || mode == RICI_SEARCH_DEFAULT ||
+                       mode == RICI_SEARCH_AUTO) && tc_supported(N);
   const bool i8 = mode == RICI_SEARCH_INT8_TC && i8_supported(N);
   const bool packed = !tensor && !i8 && mode != RICI_SEARCH_EXACT_SLOW && dense_supported(N) &&
                       b.num_scenes == 1;
@@ -927,19 +973,26 @@ cudaError_t launch_search_batch(const SearchScene *scenes, const SearchBatch &b,
   int *hwide = c.take<int>(H);
   int *wn_list = c.take<int>(Q);
   int *wh_list = c.take<int>(H);
-  int *counts = c.take<int>(4);
+  int *counts = c.take<int>(8);
   int *nflags = c.take<int>(Q);
   int *t1flag = c.take<int>(Q);
   unsigned long long *best = c.take<unsigned long long>(Q);
   int64_t *dt = c.take<int64_t>(Q);
   int *rank = c.take<int>(Q);
-  int4 *sent = c.take<int4>(sparse ? Q * (K / 4) : 0);
-  int *scount = c.take<int>(sparse ? Q : 0);
+  int4 *sent = c.take<int4>(sparse || autom ? Q * (K / 4) : 0);
+  int *scount = c.take<int>(sparse || autom ? Q : 0);
   char *tc_ws = tensor ? c.take<char>(tc_workspace_bytes(Q, H, N)) : nullptr;
   char *i8_ws = i8 ? c.take<char>(i8_workspace_bytes(Q, H, N)) : nullptr;
   int *mid_nflag = c.take<int>(mid ? Q : 0);
   int *mid_hflag = c.take<int>(mid ? H : 0);
   int *mid_list = c.take<int>(mid ? Q + H : 0);
+  int8_t *hword = c.take<int8_t>(autom ? (H + 31) / 32 * 32 * K : 0);
+  int *auto_hflag = c.take<int>(autom ? H : 0);
+  int *auto_n = c.take<int>(autom ? 3 * Q : 0);
+  int *skip_tile = c.take<int>(autom ? Q / 128 + 2 : 0);
+  int *sparse_of = autom ? auto_n : nullptr;
+  int *excl_dense = autom ? auto_n + Q : nullptr;
+  int *excl_sparse = autom ? auto_n + 2 * Q : nullptr;
 
   cudaError_t e;
   for (int s0 = 0; s0 < b.num_scenes; s0 += kFillChunk) {
@@ -949,7 +1002,7 @@ cudaError_t launch_search_batch(const SearchScene *scenes, const SearchBatch &b,
     k_fill_search_table<<<1, 256, 0, st>>>(tab + s0, f);
     count_launches(1);
   }
-  if ((e = cudaMemsetAsync(counts, 0, sizeof(int) * 4, st)) != cudaSuccess) return e;
+  if ((e = cudaMemsetAsync(counts, 0, sizeof(int) * 8, st)) != cudaSuccess) return e;
   if ((e = cudaMemsetAsync(t1flag, 0, sizeof(int) * Q, st)) != cudaSuccess) return e;
   const int wpb = 8;
   auto blocks_for = [&](int64_t items) {
@@ -983,28 +1036,53 @@ cudaError_t launch_search_batch(const SearchScene *scenes, const SearchBatch &b,
     }
   };
   if (tensor) {
+    const SearchScene &s0 = scenes[0];
+    if (mid) {
+      // CUDA-core encode of every needle (the fp16-class ones are int8-class too)
+      k_encode<<<blocks_for(Q), 32 * wpb, 0, st>>>(s0.needles, Q, N, nd, nm, mid_nflag, mid_list,
+                                                   counts + 2, 0, nrs);
+      count_launches(1);
+    }
+    if (autom) {
+      // each needle's form, decided before the tensor-core kernel runs
+      k_sparse_needles<<<blocks_for(Q), 32 * wpb, 0, st>>>(nd, nm, Q, N, sent, scount);
+      k_auto_assign<<<blocks_for(Q / 32 + 1), 256, 0, st>>>(scount, mid_nflag, Q, (int)(K / 4),
+                                                            sparse_of, excl_dense, excl_sparse);
+      k_auto_tiles<<<blocks_for(Q / 128 + 1), 256, 0, st>>>(excl_dense, Q, (Q + 127) / 128,
+                                                            skip_tile);
+      count_launches(3);
+    }
     if ((e = launch_tc_encode_and_rank(tab, b.num_scenes, qscene, hscene, Q, H, b.tiles_total, N,
                                        tc_ws, nwide, hwide, wn_list, wh_list, counts, nflags, dt,
-                                       rank, best, b.status, withhold, st)) != cudaSuccess)
+                                       rank, best, b.status, withhold, st, sparse_of,
+                                       autom ? skip_tile : nullptr)) != cudaSuccess)
       return e;
     wide(0);  // needles outside the fp16 class against the whole haystack (int64)
     if (mid) {
-      // dense encodes: every needle (the fp16-class ones are int8-class too), and the haystack
-      // images outside the fp16 class, compacted in list order (list and count from the
-      // tensor-core encode); then narrow needles x those images on CUDA cores, and the int64
-      // kernel only for the compacted images outside the int8 class
-      const SearchScene &s0 = scenes[0];
-      k_encode<<<blocks_for(Q), 32 * wpb, 0, st>>>(s0.needles, Q, N, nd, nm, mid_nflag, mid_list,
-                                                   counts + 2, 0, nrs);
+      // the haystack images outside the fp16 class, compacted in list order (list and count
+      // from the tensor-core encode); narrow needles x those images on CUDA cores, and the
+      // int64 kernel only for the compacted images outside the int8 class
       k_encode<<<blocks_for(H), 32 * wpb, 0, st>>>(s0.haystack, H, N, hd, nullptr, mid_hflag,
                                                    mid_list + Q, counts + 3, 1, nullptr, wh_list,
                                                    counts + 1);
-      count_launches(2);
-      if ((e = run_dense(nwide, mid_hflag, counts + 1, wh_list)) != cudaSuccess) return e;
+      count_launches(1);
+      if ((e = run_dense(autom ? excl_dense : nwide, mid_hflag, counts + 1, wh_list)) !=
+          cudaSuccess)
+        return e;
       // the compacted encode listed its images outside the int8 class (compact indices)
       wide(1, mid_list + Q, counts + 3);
     } else {
       wide(1);
+    }
+    if (autom) {
+      // the sparse-needle form for its needles against every int8-class image (the encode's list
+      // of images outside int8 goes to wh_list, whose readers above precede it on the stream)
+      k_encode<<<blocks_for(H), 32 * wpb, 0, st>>>(s0.haystack, H, N, hword, nullptr, auto_hflag,
+                                                   wh_list, counts + 4, 2, nullptr);
+      count_launches(1);
+      if ((e = launch_sparse(sent, scount, excl_sparse, Q, hword, auto_hflag, H, N, dt, nflags,
+                             rank, best, cnt, st)) != cudaSuccess)
+        return e;
     }
   } else if (i8) {
     if ((e = launch_i8_encode_and_rank(tab, b.num_scenes, qscene, hscene, Q, H, b.tiles_total, N,

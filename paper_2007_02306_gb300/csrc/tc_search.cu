@@ -249,6 +249,8 @@ struct TcArgs {
   int *status;
   int withhold_first_load;  // test hook: CTA 0 never issues its first stage (its waits time out)
   int group_m;              // needle tiles per group of the tile order
+  const int *skip_needle;   // optional: 1 = this needle is ranked by another form
+  const int *skip_tile;     // optional (single scene): 1 = needle tile m has no needle here
 };
 
 // Tiles and their order: search_tile_of (common.cuh).
@@ -308,6 +310,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       bool ok = true;
       for (int64_t t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
         const TcTile tt = tile_of(a.tab, a.num_scenes, t, a.group_m);
+        if (a.skip_tile && a.skip_tile[tt.m]) continue;  // every role skips the same tiles
         const int ya = (int)(tt.qbeg + tt.m * kBM), yb = (int)(tt.hbeg + tt.n * kBN);
         for (int kb = 0; kb < kblocks; ++kb, ++it) {
           const uint32_t s = it % kStages, round = it / kStages;
@@ -334,8 +337,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     if (lane == 0) {
       uint32_t it = 0, lt = 0;
       bool ok = true;
-      for (int64_t t = blockIdx.x; t < tiles && ok; t += gridDim.x, ++lt) {
+      for (int64_t t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
+        if (a.skip_tile && a.skip_tile[tile_of(a.tab, a.num_scenes, t, a.group_m).m]) continue;
         const uint32_t buf = lt & 1, use = lt >> 1;
+        ++lt;  // local count of processed tiles (selects the accumulator buffer)
         if (!mbar_wait(&tempty[buf], (use & 1) ^ 1, a.status, abort_flag)) break;
         tc_fence_after();
         const uint32_t tacc = tmem + buf * kBN;
@@ -366,16 +371,19 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     const int quarter = warp & 3;
     const int row = quarter * 32 + lane;
     uint32_t lt = 0;
-    for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x, ++lt) {
+    for (int64_t t = blockIdx.x; t < tiles; t += gridDim.x) {
       const TcTile tt = tile_of(a.tab, a.num_scenes, t, a.group_m);
+      if (a.skip_tile && a.skip_tile[tt.m]) continue;
       const uint32_t buf = lt & 1, use = lt >> 1;
+      ++lt;
       // warp-uniform outcome before the .sync.aligned TMEM loads
       const bool ready = __all_sync(0xffffffffu, mbar_wait(&tfull[buf], use & 1, a.status, abort_flag));
       if (!ready) break;
       tc_fence_after();
       const int64_t il = tt.m * kBM + row;  // scene-local needle
       const int64_t i = tt.qbeg + il;         // launch-wide needle
-      const bool row_ok = il < tt.Q && a.nflags[i] == 0 && !a.nwide[i];
+      const bool row_ok = il < tt.Q && a.nflags[i] == 0 && !a.nwide[i] &&
+                          !(a.skip_needle && a.skip_needle[i]);
       float thr = 0.0f;
       int64_t asum = 0, thr_i = 0;
       if (row_ok) {
@@ -476,7 +484,8 @@ cudaError_t launch_tc_encode_and_rank(const SearchScene *tab, int num_scenes, co
                                       int *wn_list, int *wh_list, int *counts,
                                       const int *nflags, const int64_t *dtrue, int *rank,
                                       unsigned long long *best, int *status, int test_withhold,
-                                      cudaStream_t st) {
+                                      cudaStream_t st, const int *skip_needle,
+                                      const int *skip_tile) {
   const int64_t KT = 2ll * N * N;
   Carver c(ws);
   __half *opa = c.take<__half>(Q * KT);
@@ -514,6 +523,8 @@ cudaError_t launch_tc_encode_and_rank(const SearchScene *tab, int num_scenes, co
   a.status = status;
   a.withhold_first_load = test_withhold;
   a.group_m = current_tuning().tc_group_m;
+  a.skip_needle = skip_needle;
+  a.skip_tile = skip_tile;
   const size_t smem = 1024 + kStages * (kStageA + kStageB) + 256;
   if ((e = cudaFuncSetAttribute(k_tc_rank, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)smem)) != cudaSuccess)

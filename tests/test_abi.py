@@ -86,7 +86,7 @@ def test_search_rejects_bad_arguments_on_host(lib):
     assert lib.crss_search(dummy, 1, dummy, 0, 64, None, dummy, None, None, None, 0, None, 0, None) == 1
     assert lib.crss_search(dummy, 1, dummy, 1, 1, None, dummy, None, None, None, 0, None, 0, None) == 1
     assert lib.crss_search(dummy, 1, dummy, 1, 64, None, dummy, None, None, None, 9, None, 0, None) == 1
-    assert lib.crss_search(dummy, 1, dummy, 1, 64, None, dummy, None, None, None, 6, None, 0, None) == 1
+    assert lib.crss_search(dummy, 1, dummy, 1, 64, None, dummy, None, None, None, 7, None, 0, None) == 1
     # the withheld-load hook is a tensor-core test bit: rejected with the sparse-needle form
     assert lib.crss_search(dummy, 1, dummy, 1, 64, None, dummy, None, None, None, 0x104, None, 0,
                            None) == 1

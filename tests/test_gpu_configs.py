@@ -78,7 +78,7 @@ def test_clutter_scene_every_image_equals_the_oracle(clutter):
     assert bad.size == 0, f"{bad.size} haystack images differ, first {bad[:8]}"
 
 
-@pytest.mark.parametrize("mode", [1, 3, 4, 5])
+@pytest.mark.parametrize("mode", [1, 3, 4, 5, 6])
 def test_clutter_scene_search_on_real_images(rici, oracle_mod, clutter, mode):
     Vt = clutter["scene"].target_vertices
     match = np.arange(Vt, dtype=np.int64)
@@ -135,12 +135,12 @@ def test_precision_form_from_rici_images(rici, oracle_mod):
     assert np.abs(d).max() > 127  # the tails reach the int64 path of every form
     m = dev(match)
     res = {}
-    for mode in (3, 1, 4, 5):
+    for mode in (3, 1, 4, 5, 6):
         r = rici.crss_search(nd, hay, m, mode=mode)
         assert rici.sync_status() == 0
         res[mode] = {k: r[k].cpu().numpy() for k in KEYS}
         del r
-    for mode in (1, 4, 5):
+    for mode in (1, 4, 5, 6):
         for k in KEYS:
             assert np.array_equal(res[mode][k], res[3][k]), (mode, k)
     rng = np.random.default_rng(128)

@@ -53,7 +53,7 @@ def dataset(seed, Q, H, N, **kw):
     return synth.images.needle_haystack_set(rng, Q, H, N, **kw)
 
 
-@pytest.mark.parametrize("mode", [0, 1, 2, 3, 4, 5])
+@pytest.mark.parametrize("mode", [0, 1, 2, 3, 4, 5, 6])
 def test_small_set_all_outputs(rici, oracle_mod, mode):
     nd, hay, m = dataset(1, 64, 700, 64)
     ref = oracle_mod.crss_search(nd, hay, m, return_distances=True)
@@ -62,14 +62,14 @@ def test_small_set_all_outputs(rici, oracle_mod, mode):
 
 
 @pytest.mark.parametrize("N", [8, 16, 32, 128, 12, 2])
-@pytest.mark.parametrize("mode", [1, 3, 4, 5])
+@pytest.mark.parametrize("mode", [1, 3, 4, 5, 6])
 def test_resolutions(rici, oracle_mod, N, mode):
     nd, hay, m = dataset(2, 40, 300, N)
     ref = oracle_mod.crss_search(nd, hay, m)
     check(run(rici, nd, hay, m, mode=mode), ref)
 
 
-@pytest.mark.parametrize("mode", [1, 3, 4, 5])
+@pytest.mark.parametrize("mode", [1, 3, 4, 5, 6])
 def test_heavy_tails_and_extremes(rici, oracle_mod, mode):
     rng = np.random.default_rng(3)
     nd, hay, m = synth.images.needle_haystack_set(rng, 60, 900, 64, tail_image_fraction=0.3,
@@ -150,7 +150,7 @@ def test_int8_accumulators_exact_at_the_int8_limit(rici, oracle_mod):
     check(run(rici, nd, hay, m, mode=5, dist=True), ref, dist=True)
 
 
-@pytest.mark.parametrize("mode", [3, 5])
+@pytest.mark.parametrize("mode", [3, 5, 6])
 @pytest.mark.parametrize("Q,H", [(1, 1), (65, 129), (129, 257), (300, 1000)])
 def test_tensor_ragged_tiles(rici, oracle_mod, Q, H, mode):
     nd, hay, m = dataset(11, Q, H, 64)
@@ -197,7 +197,7 @@ def test_dense_bands_and_ragged_tiles(rici, oracle_mod, N, mode):
         assert np.array_equal(got[k][pick], ref[k]), k
 
 
-@pytest.mark.parametrize("mode", [1, 4, 5])
+@pytest.mark.parametrize("mode", [1, 4, 5, 6])
 def test_degenerate_needles(rici, oracle_mod, mode):
     """Needles with no non-zero delta (constant rows: distance 0 to everything), one non-zero
     delta, a non-zero delta only in the last column, and one full row of +-127 deltas."""
@@ -214,7 +214,7 @@ def test_degenerate_needles(rici, oracle_mod, mode):
     check(run(rici, nd, hay, m, mode=mode, dist=True), ref, dist=True)
 
 
-@pytest.mark.parametrize("mode", [0, 1, 4, 5])
+@pytest.mark.parametrize("mode", [0, 1, 4, 5, 6])
 def test_ties_keep_best_rank(rici, oracle_mod, mode):
     nd, hay, m = dataset(4, 50, 500, 32)
     for k in range(0, 50, 3):  # duplicates of true matches elsewhere in the haystack
@@ -265,7 +265,7 @@ def test_single_haystack_and_single_needle(rici, oracle_mod):
     check(run(rici, nd, hay, m), oracle_mod.crss_search(nd, hay, m))
 
 
-@pytest.mark.parametrize("mode", [1, 3, 4, 5])
+@pytest.mark.parametrize("mode", [1, 3, 4, 5, 6])
 def test_clutter_scale_search_sampled_needles(rici, oracle_mod, mode):
     """Full benchmark size: 10,242 needles x 114,892 haystack images, N = 64."""
     Q, H = 10242, 114892
@@ -277,3 +277,26 @@ def test_clutter_scale_search_sampled_needles(rici, oracle_mod, mode):
     assert np.array_equal(got["true_distance"][s], ref["true_distance"])
     assert np.array_equal(got["rank"][s], ref["rank"])
     assert np.array_equal(got["top1"][s], ref["top1"])
+
+
+def test_auto_form_with_mixed_needles(rici, oracle_mod):
+    """RICI_SEARCH_AUTO on needles of both kinds: sparse needles (about 3 changes per row) go to
+    the sparse-needle form, dense ones (about 40 per row) to the tensor cores.  The needle order
+    puts a first tensor-core tile (128 needles) entirely on the sparse side, so that tile is
+    skipped, and mixes the kinds in the other tiles; heavy-tailed haystack plateaus reach the
+    dense middle pass and the int64 pass.  Every output equals the oracle's."""
+    N, Hn = 64, 3000
+    rng = np.random.default_rng(21)
+    sparse = synth.images.rici_like_images(rng, 200, N, changes_per_row=3.0)
+    dense = synth.images.rici_like_images(rng, 120, N, changes_per_row=40.0, small=6)
+    order = np.concatenate([np.arange(130), 200 + np.arange(60), 130 + np.arange(70),
+                            200 + np.arange(60, 120)])
+    pool = np.concatenate([sparse, dense])
+    hay = synth.images.rici_like_images(rng, Hn, N, changes_per_row=10.0)
+    match = rng.choice(Hn, len(order), replace=False).astype(np.int64)
+    hay[match] = pool[order]
+    nd = pool[order].copy()
+    synth.images.add_plateaus(rng, hay, 0.05, 0.05)  # tails: some images leave fp16 and int8
+    ref = oracle_mod.crss_search(nd, hay, match)
+    check(run(rici, nd, hay, match, mode=6), ref)
+    check(run(rici, nd, hay, match, mode=3), ref)
