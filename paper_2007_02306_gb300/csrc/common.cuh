@@ -201,7 +201,8 @@ cudaError_t launch_tc_encode_and_rank(const SearchScene *tab, int num_scenes, co
                                       const int *nflags, const int64_t *dtrue, int *rank,
                                       unsigned long long *best, int *status, int test_withhold,
                                       cudaStream_t st, const int *skip_needle = nullptr,
-                                      const int *skip_tile = nullptr);
+                                      const int *skip_tile = nullptr,
+                                      const int *any_tile = nullptr);
 
 // Integer tensor-core search (i8_search.cu): int8 operand encoding + mma.sync s8 GEMM with the
 // rank / top-1 epilogue for int8-narrow x int8-narrow pairs of every scene (the tiles of the

@@ -248,6 +248,15 @@ __global__ void __launch_bounds__(kDenseThreads, (N * kImg <= 64 ? 4 : 2) * 256 
     if (h0 * (int64_t)(kDenseThreads * kImg) >= H) return;  // uniform over the block
   }
 
+  bool act = false;
+  if (tid < kTQ) {
+    const int64_t q = q0 + tid;
+    act = q < Q && nflags[q] == 0 && !nwide[q];
+    int64_t t = act ? dtrue[q] : -1;
+    thr_s[tid] = t > 0x7fffffffll ? 0x7fffffff : (int)t;
+    act_s[tid] = act;
+  }
+  if (!__syncthreads_or(act)) return;  // no needle of this tile is ranked here
   for (int x = tid; x < kTQ * (K / 4); x += kDenseThreads) {
     int q = x / (K / 4), wd = x - q * (K / 4);
     int a = 0, m = 0;
@@ -256,13 +265,6 @@ __global__ void __launch_bounds__(kDenseThreads, (N * kImg <= 64 ? 4 : 2) * 256 
       m = reinterpret_cast<const int *>(nmask + (q0 + q) * K)[wd];
     }
     am[q][wd] = make_int2(a, m);
-  }
-  if (tid < kTQ) {
-    const int64_t q = q0 + tid;
-    bool act = q < Q && nflags[q] == 0 && !nwide[q];
-    int64_t t = act ? dtrue[q] : -1;
-    thr_s[tid] = t > 0x7fffffffll ? 0x7fffffff : (int)t;
-    act_s[tid] = act;
   }
   __syncthreads();
   // Rows are visited heaviest first so that distances pass the early-exit threshold sooner;
@@ -736,9 +738,10 @@ __global__ void k_auto_assign(const int *__restrict__ ecount, const int *__restr
   }
 }
 
-// skip_tile[m] = 1 when no needle of tensor-core needle tile m (128 needles) is ranked there.
+// skip_tile[m] = 1 when no needle of tensor-core needle tile m (128 needles) is ranked there;
+// *any_tile (zeroed before) becomes 1 when some tile is left.
 __global__ void k_auto_tiles(const int *__restrict__ excl_dense, int64_t Q, int64_t tiles_m,
-                             int *__restrict__ skip_tile) {
+                             int *__restrict__ skip_tile, int *__restrict__ any_tile) {
   const int lane = threadIdx.x & 31;
   for (int64_t m = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; m < tiles_m;
        m += ((int64_t)gridDim.x * blockDim.x) >> 5) {
@@ -748,7 +751,10 @@ __global__ void k_auto_tiles(const int *__restrict__ excl_dense, int64_t Q, int6
       any |= i < Q && !excl_dense[i];
     }
     any = __any_sync(0xffffffffu, any);
-    if (lane == 0) skip_tile[m] = !any;
+    if (lane == 0) {
+      skip_tile[m] = !any;
+      if (any) atomicOr(any_tile, 1);
+    }
   }
 }
 
@@ -1049,13 +1055,13 @@ cudaError_t launch_search_batch(const SearchScene *scenes, const SearchBatch &b,
       k_auto_assign<<<blocks_for(Q / 32 + 1), 256, 0, st>>>(scount, mid_nflag, Q, (int)(K / 4),
                                                             sparse_of, excl_dense, excl_sparse);
       k_auto_tiles<<<blocks_for(Q / 128 + 1), 256, 0, st>>>(excl_dense, Q, (Q + 127) / 128,
-                                                            skip_tile);
+                                                            skip_tile, counts + 5);
       count_launches(3);
     }
     if ((e = launch_tc_encode_and_rank(tab, b.num_scenes, qscene, hscene, Q, H, b.tiles_total, N,
                                        tc_ws, nwide, hwide, wn_list, wh_list, counts, nflags, dt,
                                        rank, best, b.status, withhold, st, sparse_of,
-                                       autom ? skip_tile : nullptr)) != cudaSuccess)
+                                       autom ? skip_tile : nullptr, counts + 5)) != cudaSuccess)
       return e;
     wide(0);  // needles outside the fp16 class against the whole haystack (int64)
     if (mid) {

@@ -181,8 +181,12 @@ __global__ void k_tc_encode(const SearchScene *__restrict__ tab, const int *__re
                             int64_t n, int N, int needle_side, __half *__restrict__ op,
                             int *__restrict__ wide_flag, int *__restrict__ wide_list,
                             int *__restrict__ wide_count, int *__restrict__ asum,
-                            uint32_t *__restrict__ valid_mask) {
+                            uint32_t *__restrict__ valid_mask, const int *__restrict__ skip_tile,
+                            const int *__restrict__ any_tile) {
   const int lane = threadIdx.x & 31;
+  // operand rows no tile will load are not written (the classes are still computed): needle
+  // rows of skipped needle tiles, and every haystack row when no needle tile is left
+  const bool hay_written = needle_side || !any_tile || *any_tile != 0;
   const int64_t w = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int K0 = N * N;
@@ -193,6 +197,7 @@ __global__ void k_tc_encode(const SearchScene *__restrict__ tab, const int *__re
     __half *row = op + i * (int64_t)(2 * K0);
     const int lim = needle_side ? kNarrowA : kNarrowB;
     int wide = 0, a2 = 0, s1 = 0;  // needles: a2 = sum a^2; haystack: a2 = S2_j, s1 = S1_j
+    const bool write = needle_side ? !(skip_tile && skip_tile[i / kBM]) : hay_written;
     for (int k0 = lane * 8; k0 < K0; k0 += 32 * 8) {
       __align__(16) __half lo[8], hi[8];
 #pragma unroll
@@ -213,8 +218,10 @@ __global__ void k_tc_encode(const SearchScene *__restrict__ tab, const int *__re
           hi[e] = __int2half_rn(-2 * dc);
         }
       }
-      *reinterpret_cast<int4 *>(row + k0) = *reinterpret_cast<int4 *>(lo);
-      *reinterpret_cast<int4 *>(row + K0 + k0) = *reinterpret_cast<int4 *>(hi);
+      if (write) {
+        *reinterpret_cast<int4 *>(row + k0) = *reinterpret_cast<int4 *>(lo);
+        *reinterpret_cast<int4 *>(row + K0 + k0) = *reinterpret_cast<int4 *>(hi);
+      }
     }
     wide = __any_sync(0xffffffffu, wide);
 #pragma unroll
@@ -485,7 +492,7 @@ cudaError_t launch_tc_encode_and_rank(const SearchScene *tab, int num_scenes, co
                                       const int *nflags, const int64_t *dtrue, int *rank,
                                       unsigned long long *best, int *status, int test_withhold,
                                       cudaStream_t st, const int *skip_needle,
-                                      const int *skip_tile) {
+                                      const int *skip_tile, const int *any_tile) {
   const int64_t KT = 2ll * N * N;
   Carver c(ws);
   __half *opa = c.take<__half>(Q * KT);
@@ -500,9 +507,9 @@ cudaError_t launch_tc_encode_and_rank(const SearchScene *tab, int num_scenes, co
     return (int)(b < 152 * 64 ? (b > 0 ? b : 1) : 152 * 64);
   };
   k_tc_encode<<<blocks_for(Q), 256, 0, st>>>(tab, qscene, Q, N, 1, opa, nwide, wn_list, counts + 0,
-                                             asum, nullptr);
+                                             asum, nullptr, skip_tile, nullptr);
   k_tc_encode<<<blocks_for(H), 256, 0, st>>>(tab, hscene, H, N, 0, opb, hwide, wh_list, counts + 1,
-                                             nullptr, hvalid);
+                                             nullptr, hvalid, nullptr, skip_tile ? any_tile : nullptr);
   count_launches(2);
   if (tiles_total == 0) return cudaGetLastError();
   CUtensorMap ma, mb;
