@@ -78,9 +78,12 @@ __global__ void k_encode(const uint16_t *__restrict__ imgs, int64_t n, int N,
   const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
   const int K = N * N;
   if (list) n = *list_count < n ? *list_count : n;
+  // rows of a multiple of 32 positions: every pass of the warp lies in one row, so the row sums
+  // of squared (clamped) deltas come from one warp reduction per pass
+  const bool rows_by_pass = N % 32 == 0;
   for (int64_t i = w; i < n; i += nw) {
     const uint16_t *img = imgs + (list ? (int64_t)list[i] : i) * K;
-    int wide = 0;
+    int wide = 0, row_acc = 0;
     for (int k = lane; k < K; k += 32) {
       int r = k / N, c = k - r * N;
       int d = delta_at(img, N, r, c);
@@ -91,8 +94,15 @@ __global__ void k_encode(const uint16_t *__restrict__ imgs, int64_t n, int N,
                                             : i * K + k;
       delta[off] = (int8_t)dc;
       if (mask) mask[i * K + k] = (int8_t)(d != 0 ? -1 : 0);
+      if (row_sq && rows_by_pass) {
+        row_acc += (int)__reduce_add_sync(0xffffffffu, (unsigned)(dc * dc));
+        if (c - lane + 32 == N) {  // the row's last pass (uniform over the warp)
+          if (lane == 0) row_sq[i * N + r] = row_acc;
+          row_acc = 0;
+        }
+      }
     }
-    if (row_sq) {
+    if (row_sq && !rows_by_pass) {
       for (int r = lane; r < N; r += 32) {
         int sq = 0;
         for (int c = 1; c < N; ++c) {
@@ -220,9 +230,11 @@ __global__ void __launch_bounds__(kDenseThreads, (N * kImg <= 64 ? 4 : 2) * 256 
     const int *__restrict__ hwide, int64_t H, const int64_t *__restrict__ dtrue,
     const int *__restrict__ nflags, int *__restrict__ rank, unsigned long long *__restrict__ best,
     unsigned long long *__restrict__ counters, int64_t tile0, int64_t tiles_q, int64_t tiles_h,
-    int64_t band_h, const int *__restrict__ hcount, const int *__restrict__ hmap) {
+    int64_t band_h, const int *__restrict__ hcount, const int *__restrict__ hmap,
+    const int *__restrict__ gate) {
   // hcount (optional): the haystack holds *hcount images (H is then an upper bound); hmap
-  // (optional): haystack image j is image hmap[j] of the caller's haystack (a compacted subset)
+  // (optional): haystack image j is image hmap[j] of the caller's haystack (a compacted subset);
+  // gate (optional): *gate == 0 means no needle is ranked here, and every block returns at once
   constexpr int WPR = N / 4;  // 32-bit words per row
   constexpr int K = N * N;
   extern __shared__ int2 am_raw[];  // [kTQ][K/4] (needle delta word, mask word)
@@ -243,6 +255,7 @@ __global__ void __launch_bounds__(kDenseThreads, (N * kImg <= 64 ? 4 : 2) * 256 
   const int64_t h0 = band * band_h;
   const int64_t h1 = tiles_h - h0 < band_h ? tiles_h : h0 + band_h;
   const int64_t q0 = qt * kTQ;
+  if (gate && *gate == 0) return;  // uniform over the grid
   if (hcount) {
     H = *hcount < H ? *hcount : H;
     if (h0 * (int64_t)(kDenseThreads * kImg) >= H) return;  // uniform over the block
@@ -836,7 +849,8 @@ cudaError_t launch_dense(const int8_t *nd, const int8_t *nm, const int *nrs, con
                          const int8_t *hd, const int *hw, int64_t H, const int64_t *dt,
                          const int *nf, int *rank, unsigned long long *best,
                          unsigned long long *counters, cudaStream_t st,
-                         const int *hcount = nullptr, const int *hmap = nullptr) {
+                         const int *hcount = nullptr, const int *hmap = nullptr,
+                         const int *gate = nullptr) {
   // 4 needles x 4 haystack images per thread (N <= 64; 120 registers, two blocks of 256 threads
   // per SM) is the fastest measured shape: each broadcast needle word serves four images, and
   // the per-row bookkeeping is shared by 16 (needle, image) pairs
@@ -860,7 +874,7 @@ cudaError_t launch_dense(const int8_t *nd, const int8_t *nm, const int *nrs, con
     const int64_t n = total - t0 < kMaxGrid ? total - t0 : kMaxGrid;
     kern<<<(unsigned)n, kDenseThreads, smem, st>>>(nd, nm, nrs, nw, Q, hd, hw, H, dt, nf, rank,
                                                    best, counters, t0, tq, th, band_h, hcount,
-                                                   hmap);
+                                                   hmap, gate);
     count_launches(1);
   }
   return cudaGetLastError();
@@ -1032,13 +1046,14 @@ cudaError_t launch_search_batch(const SearchScene *scenes, const SearchBatch &b,
                                                    sub_list, sub_count);
     count_launches(1);
   };
-  auto run_dense = [&](const int *nexcl, const int *hexcl, const int *hcount, const int *hmap) {
+  auto run_dense = [&](const int *nexcl, const int *hexcl, const int *hcount, const int *hmap,
+                       const int *gate = nullptr) {
     switch (N) {
-      case 8: return launch_dense<8>(nd, nm, nrs, nexcl, Q, hd, hexcl, H, dt, nflags, rank, best, cnt, st, hcount, hmap);
-      case 16: return launch_dense<16>(nd, nm, nrs, nexcl, Q, hd, hexcl, H, dt, nflags, rank, best, cnt, st, hcount, hmap);
-      case 32: return launch_dense<32>(nd, nm, nrs, nexcl, Q, hd, hexcl, H, dt, nflags, rank, best, cnt, st, hcount, hmap);
-      case 64: return launch_dense<64>(nd, nm, nrs, nexcl, Q, hd, hexcl, H, dt, nflags, rank, best, cnt, st, hcount, hmap);
-      default: return launch_dense<128>(nd, nm, nrs, nexcl, Q, hd, hexcl, H, dt, nflags, rank, best, cnt, st, hcount, hmap);
+      case 8: return launch_dense<8>(nd, nm, nrs, nexcl, Q, hd, hexcl, H, dt, nflags, rank, best, cnt, st, hcount, hmap, gate);
+      case 16: return launch_dense<16>(nd, nm, nrs, nexcl, Q, hd, hexcl, H, dt, nflags, rank, best, cnt, st, hcount, hmap, gate);
+      case 32: return launch_dense<32>(nd, nm, nrs, nexcl, Q, hd, hexcl, H, dt, nflags, rank, best, cnt, st, hcount, hmap, gate);
+      case 64: return launch_dense<64>(nd, nm, nrs, nexcl, Q, hd, hexcl, H, dt, nflags, rank, best, cnt, st, hcount, hmap, gate);
+      default: return launch_dense<128>(nd, nm, nrs, nexcl, Q, hd, hexcl, H, dt, nflags, rank, best, cnt, st, hcount, hmap, gate);
     }
   };
   if (tensor) {
@@ -1072,8 +1087,9 @@ cudaError_t launch_search_batch(const SearchScene *scenes, const SearchBatch &b,
                                                    mid_list + Q, counts + 3, 1, nullptr, wh_list,
                                                    counts + 1);
       count_launches(1);
-      if ((e = run_dense(autom ? excl_dense : nwide, mid_hflag, counts + 1, wh_list)) !=
-          cudaSuccess)
+      // (AUTO: counts[5] = 0 when no needle is left for the tensor-core side)
+      if ((e = run_dense(autom ? excl_dense : nwide, mid_hflag, counts + 1, wh_list,
+                         autom ? counts + 5 : nullptr)) != cudaSuccess)
         return e;
       // the compacted encode listed its images outside the int8 class (compact indices)
       wide(1, mid_list + Q, counts + 3);

@@ -258,6 +258,7 @@ struct TcArgs {
   int group_m;              // needle tiles per group of the tile order
   const int *skip_needle;   // optional: 1 = this needle is ranked by another form
   const int *skip_tile;     // optional (single scene): 1 = needle tile m has no needle here
+  const int *any_tile;      // with skip_tile: 0 = every tile is skipped (the grid returns at once)
 };
 
 // Tiles and their order: search_tile_of (common.cuh).
@@ -282,6 +283,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drain + 1);
   int *abort_flag = reinterpret_cast<int *>(tmem_slot + 1);
 
+  // nothing to rank: return before any barrier, TMEM or TMA work (uniform over the grid)
+  if (a.any_tile && *a.any_tile == 0) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t tiles = a.tiles;
   const int kblocks = a.KT / kBK;
@@ -532,6 +535,7 @@ cudaError_t launch_tc_encode_and_rank(const SearchScene *tab, int num_scenes, co
   a.group_m = current_tuning().tc_group_m;
   a.skip_needle = skip_needle;
   a.skip_tile = skip_tile;
+  a.any_tile = skip_tile ? any_tile : nullptr;
   const size_t smem = 1024 + kStages * (kStageA + kStageB) + 256;
   if ((e = cudaFuncSetAttribute(k_tc_rank, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)smem)) != cudaSuccess)

@@ -110,7 +110,7 @@ def test_batch_equals_per_scene_calls_and_oracle(rici, oracle_mod, batch):
             assert np.array_equal(res[i][k].cpu().numpy(), ro[k]), (i, k)
 
 
-@pytest.mark.parametrize("mode", [1, 4, 5])
+@pytest.mark.parametrize("mode", [1, 4, 5, 6])
 def test_batch_search_forms_agree(rici, batch, mode):
     """Every exact form of the multi-scene search gives the tensor-core form's ranks, true
     distances and top-1 on the batch's images (each needle against its own scene only)."""
