@@ -74,8 +74,8 @@ DP4A_PER_SM_CLK = 64
 # profiles/); None where the kernel changed since it was captured
 # (k_generate at R = 0.6: 647.4 GB read + 73.7 GB written on 131,072 origins, scaled to the
 # full launch by 2,509,797 / 131,072 origins)
-TRAFFIC = {"k_generate_R0.6": (647.44e9 + 73.67e9) * 2509797 / 131072, "k_tc_rank": None,
-           "k_dense_clutter": 1.895e9 + 5.57e6}
+TRAFFIC = {"k_generate_R0.6": (647.44e9 + 73.67e9) * 2509797 / 131072,
+           "k_tc_rank_clutter": 21.483e9 + 3.71e5, "k_dense_clutter": 1.895e9 + 5.57e6}
 
 
 def parse():
@@ -377,8 +377,10 @@ def clutter_scene_comparison(p, torch, dev, stream, flush, steps=3):
     cnt = torch.zeros(4, dtype=torch.int64, device=dev)
     p.crss_search(nd, hy, m, mode=p.SEARCH_CUDA_CORE, counters=cnt)
     cnt = [int(x) for x in cnt.cpu()]
+    torch.cuda.nvtx.range_push("clutter_tc")  # selects these launches for ncu
     tc_ms, rt = timed_ms(torch, stream, lambda: p.crss_search(nd, hy, m, mode=p.SEARCH_TENSOR),
                          reps=steps, flush=flush)
+    torch.cuda.nvtx.range_pop()
     same = all(bool(torch.equal(rt[k], r[k])) for k in ("rank", "true_distance", "top1"))
     pairs = V * Vt
     res = {"recipe": "synth.clutter_scene(seed=2): 10 meshes, 229,756 triangles, N = 64, R = 0.3",
@@ -902,7 +904,7 @@ def main():
             "peak": pk.get("bf16_tflops", 1900.0),
             "work": f"{c['comparisons']} pairs x 2 x {kt} fp16 multiply-adds (dense, K = 2 N^2; "
                     "every image of the clutter scene is in the fp16 class)",
-            "traffic": None,
+            "traffic": TRAFFIC["k_tc_rank_clutter"],
             "peak_kind": f"{pk_kind} bf16 dense burst (fp16 runs at the bf16 rate)"}
         rooflines["search_cuda_core_clutter_scene"] = {
             "bound": "alu", "unit": "G int8-MAC/s",
