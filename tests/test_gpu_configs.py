@@ -5,7 +5,7 @@
   GPU images equal to the oracle's search of the oracle's images for 64 sampled needles.
 * Precision form: 2^20 RICI images (N = 64, R = 0.3) of 6,473 seeded subdivision-2 icospheres
   with the stated heavy-tailed plateaus, 65,536 needles taken before clutter plateaus: every
-  base image equal to the oracle's, all four search forms identical on every needle, and the
+  base image equal to the oracle's, all five fast search forms identical on every needle, and the
   oracle's ranks of 128 sampled needles against all 2^20 of its own images.
 * Large scene (5,019,510 triangles): the 100,000 x 2,509,797 search on the scene's own RICI
   images (R = 0.3) with the int8 tensor-core form.  The oracle cannot image 2.5M points, so
