@@ -365,15 +365,19 @@ RICI_API int64_t rici_kernel_launches(void);
  * process-wide (every device and stream) and is read when a call launches its kernels.  The
  * paper has no counterpart (it fixes one kernel configuration for its GPU). */
 struct RiciTuning {
-  int32_t gen_cells_per_reach; /* 2, 3 or 4: generation grid cells per triangle reach (the
-                                  support sphere's radius plus the largest binned triangle's);
-                                  each oriented point scans (2 x this + 1)^3 cells (the clutter
-                                  measure and spin images use at most 3). Default 2. */
-  float gen_big_radius;        /* in [1/16, 1]: triangles whose bounding radius exceeds this
-                                  fraction of the support sphere's radius are checked by every
-                                  oriented point of their scene instead of being binned.
+  int32_t gen_cells_per_reach; /* 2, 3 or 4: grid cells per triangle reach (the support
+                                  sphere's radius plus the largest binned triangle's) of the
+                                  clutter measure and spin images, which scan up to 7^3 cells
+                                  around each oriented point (at most 3 per reach). Image
+                                  generation sorts its triangles along a space-filling curve
+                                  and culls them by bounding spheres of runs of 32 and 1024
+                                  instead, and ignores this field. Default 2. */
+  float gen_big_radius;        /* in [1/16, 1]: in the clutter measure and spin images,
+                                  triangles whose bounding radius exceeds this fraction of the
+                                  support sphere's radius are checked by every oriented point
+                                  instead of being binned (image generation ignores it).
                                   Default 0.25. */
-  int32_t gen_warps;           /* 4 or 8 warps per oriented point. Default 4. */
+  int32_t gen_warps;           /* 4 or 8 warps per oriented point (image generation). Default 4. */
   int32_t tc_group_m;          /* 1..64: needle tiles of 128 that the tensor-core search sweeps
                                   together over the haystack (L2 reuse). Default 8. */
 };
@@ -386,8 +390,8 @@ RICI_API int rici_set_tuning(const RiciTuning *tuning);
 RICI_API int rici_get_tuning(RiciTuning *tuning);
 
 /* Autotuner of the batched run.  Runs rici_generate_batch on the given scenes under each candidate
- * generation setting (gen_cells_per_reach in {2,3,4} x gen_big_radius in {1/8, 1/4, 1/2, 1} x
- * gen_warps in {4,8}; the other fields as in force), one untimed warm-up and `repeats` (1..100)
+ * generation setting (gen_warps in {4,8}; the other fields as in force, since image generation
+ * reads no other field), one untimed warm-up and `repeats` (1..100)
  * runs timed with CUDA events on `stream`, and writes the fastest setting to *best and its mean
  * time in milliseconds to *best_ms (may be NULL).  The scenes' output images are written by every
  * run (with identical results).  Synchronises the stream; the tuning in force is restored, not

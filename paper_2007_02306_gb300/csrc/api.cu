@@ -815,12 +815,9 @@ int rici_autotune_generate_batch(const RiciGenerateScene *scenes, int32_t num_sc
   t_last_error.clear();
   std::vector<Tuning> cands;
   const Tuning base = current_tuning();
-  const int cells[] = {2, 3, 4};
-  const float big[] = {0.125f, 0.25f, 0.5f, 1.0f};
-  const int warps[] = {4, 8};
-  for (int c : cells)
-    for (float b : big)
-      for (int w : warps) cands.push_back(Tuning{c, b, w, base.tc_group_m});
+  // image generation reads gen_warps only (its culling has no grid)
+  for (int w : {4, 8})
+    cands.push_back(Tuning{base.gen_cells_per_reach, base.gen_big_radius, w, base.tc_group_m});
   return autotune(
       cands, repeats, stream,
       [&]() {

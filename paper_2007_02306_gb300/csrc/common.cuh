@@ -252,6 +252,9 @@ constexpr int64_t generate_batch_workspace_bytes(int num_scenes, int64_t total_t
   c.take<uint32_t>(total_tris);                    // bucket of each triangle
   c.take<int>(total_tris);                         // slot within its bucket
   c.take<float4>(4 * total_tris);                  // records
+  c.take<int>(8 * (int64_t)num_scenes);            // per-scene box of triangle centres
+  c.take<float4>((total_tris + 31) / 32);          // bounding spheres of 32-record chunks
+  c.take<float4>((total_tris + 1023) / 1024);      // bounding spheres of 1024-record groups
   return c.off + 256;
 }
 

@@ -1,20 +1,26 @@
 // RICI generation on sm_103a (Section 3.1 of the paper).
 //
 // Pipeline per rici_generate call (all on the caller's stream, no host synchronisation):
-//   1. k_tri_bin      bounding sphere of every triangle; bin it into a hashed uniform grid
-//                     (cell edge = reach / 2 or / 3, reach = support sphere + largest binned
-//                     triangle radius) or, for wide triangles, into its scene's "big" list.
-//   2. scan           bucket counts -> bucket starts.
-//   3. k_tri_scatter  64-byte triangle records (sphere, FP32 vertices, global indices) in
-//                     bucket order, so candidates of one cell are contiguous.
-//   4. k_generate     one CTA per oriented point.  Its warps stream the triangles of the
-//                     5^3 or 7^3 neighbouring cells that lie within reach of the spin vertex
-//                     and of the support cylinder (plus the big list), cull them against the
-//                     cylinder, project the survivors (Eqs. relativeLocation..secondRotation)
-//                     and split the (triangle, layer) work evenly over the 32 lanes.  Each
-//                     layer's single/double crossing radii (Section 3.1.2) become column
-//                     intervals added to a shared-memory difference image, which is prefix
-//                     summed, saturated and stored as packed uint16 (32- or 64-bit stores).
+//   1. k_tri_bbox     box of the triangles' bounding-sphere centres, per scene.
+//   2. k_tri_bin      bounding sphere of every triangle; bin it by the Morton code of its centre
+//                     on a 2^L grid over that box (8^L bins, L <= 7).
+//   3. scan           bin counts -> bin starts.
+//   4. k_tri_scatter  64-byte triangle records (sphere, FP32 vertices, global indices) in bin
+//                     order: the records follow a space-filling curve, so runs of consecutive
+//                     records are compact in space.
+//   5. k_chunk_spheres  a bounding sphere of every run of 32 records (chunk) and of 1024
+//                     records (group).
+//   6. k_generate     one CTA per oriented point.  Its warps test the groups of the point's
+//                     scene against the support cylinder, then the chunks of passing groups,
+//                     then the records of passing chunks (a sphere fails only if every record
+//                     in it fails), project the surviving triangles (Eqs.
+//                     relativeLocation..secondRotation) and split the (triangle, layer) work
+//                     evenly over the 32 lanes.  Each layer's single/double crossing radii
+//                     (Section 3.1.2) become column intervals added to a shared-memory
+//                     difference image, which is prefix summed, saturated and stored as packed
+//                     uint16 (32- or 64-bit stores).
+// The clutter measure and spin images (bottom of this file) bin triangles into a hashed uniform
+// grid instead and scan the grid cells around each oriented point.
 //
 // Exactness: the FP32 path carries a forward error bound for every predicate (vertex side
 // of a layer, |E|^2 against alpha^2, the signs of E0.D and E1.D, alpha^2 |D|^2 against
@@ -53,6 +59,24 @@ __device__ __forceinline__ int cell_coord(float x, float inv_cell) {
 __device__ __forceinline__ uint32_t cell_hash(int ix, int iy, int iz, uint32_t mask) {
   return (((uint32_t)ix * 73856093u) ^ ((uint32_t)iy * 19349663u) ^ ((uint32_t)iz * 83492791u)) &
          mask;
+}
+
+// Order-preserving map of finite floats to int32 (a min / max of the ints is a min / max of the
+// floats); the map is its own inverse.
+__device__ __forceinline__ int float_order(float f) {
+  const int i = __float_as_int(f);
+  return i >= 0 ? i : i ^ 0x7fffffff;
+}
+__device__ __forceinline__ float order_float(int i) { return __int_as_float(i >= 0 ? i : i ^ 0x7fffffff); }
+
+// Bits of x (< 2^10) spread to every third position.
+__device__ __forceinline__ uint32_t spread3(uint32_t x) {
+  x &= 0x3ffu;
+  x = (x | (x << 16)) & 0x030000FFu;
+  x = (x | (x << 8)) & 0x0300F00Fu;
+  x = (x | (x << 4)) & 0x030C30C3u;
+  x = (x | (x << 2)) & 0x09249249u;
+  return x;
 }
 
 struct TriSphere {
@@ -100,9 +124,69 @@ __device__ __forceinline__ int scene_of_origin(const GenScene *tab, int ns, int6
   return lo;
 }
 
+// Box of the bounding-sphere centres of each scene's valid triangles (ints of float_order; the
+// table fill sets every box empty).  Triangles with a bad index or a non-finite vertex are left
+// to k_tri_bin, which reports them.  Warps whose triangles all belong to one scene reduce first.
+__global__ void k_tri_bbox(const GenScene *__restrict__ tab, int ns, int64_t nt_total,
+                           int *__restrict__ bbox) {
+  const int lane = threadIdx.x & 31;
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;  // a multiple of 32
+  for (int64_t t0 = blockIdx.x * (int64_t)blockDim.x + (threadIdx.x & ~31); t0 < nt_total;
+       t0 += stride) {
+    const int64_t t = t0 + lane < nt_total ? t0 + lane : nt_total - 1;
+    const int sidx = scene_of_tri(tab, ns, t);
+    const GenScene &sc = tab[sidx];
+    const int64_t tl = t - sc.tri_off;
+    const int64_t nv = sc.nv;
+    bool ok = t0 + lane < nt_total;
+    float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+    if (ok) {
+      int id[3] = {sc.tris[3 * tl], sc.tris[3 * tl + 1], sc.tris[3 * tl + 2]};
+      ok = id[0] >= 0 && id[0] < nv && id[1] >= 0 && id[1] < nv && id[2] >= 0 && id[2] < nv;
+      if (ok) {
+        float v[9];
+        for (int k = 0; k < 3; ++k)
+          for (int d = 0; d < 3; ++d) {
+            v[3 * k + d] = sc.V[3 * (int64_t)id[k] + d];
+            ok = ok && isfinite(v[3 * k + d]);
+          }
+        if (ok) {
+          const TriSphere ts_ = tri_sphere(v);
+          lo[0] = hi[0] = ts_.cx;
+          lo[1] = hi[1] = ts_.cy;
+          lo[2] = hi[2] = ts_.cz;
+        }
+      }
+    }
+    const int s0 = __shfl_sync(0xffffffffu, sidx, 0);
+    if (__all_sync(0xffffffffu, sidx == s0)) {
+#pragma unroll
+      for (int d = 16; d > 0; d >>= 1)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          lo[k] = fminf(lo[k], __shfl_xor_sync(0xffffffffu, lo[k], d));
+          hi[k] = fmaxf(hi[k], __shfl_xor_sync(0xffffffffu, hi[k], d));
+        }
+      ok = lane == 0 && lo[0] <= hi[0];
+    }
+    if (ok) {
+      int *bb = bbox + 8 * (int64_t)sidx;
+      for (int k = 0; k < 3; ++k) {
+        atomicMin(bb + k, float_order(lo[k]));
+        atomicMax(bb + 3 + k, float_order(hi[k]));
+      }
+    }
+  }
+}
+
+// Bins every triangle by its bounding sphere.  With bbox == nullptr (clutter measure, spin
+// images): a hashed uniform grid of cell edge 1 / inv_cell, wide triangles in the scene's big
+// list.  Otherwise (generation): every triangle by the Morton code of its centre on a 2^L grid
+// over its scene's box of centres (8^L <= the scene's bucket count), so that records sorted by
+// bucket follow a space-filling curve and runs of consecutive records are compact.
 __global__ void k_tri_bin(const GenScene *__restrict__ tab, int ns, int64_t nt_total, GridParams g,
-                          int *__restrict__ counts, uint32_t *__restrict__ tb,
-                          int *__restrict__ ts, int *status) {
+                          const int *__restrict__ bbox, int *__restrict__ counts,
+                          uint32_t *__restrict__ tb, int *__restrict__ ts, int *status) {
   for (int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; t < nt_total;
        t += (int64_t)gridDim.x * blockDim.x) {
     const GenScene &sc = tab[scene_of_tri(tab, ns, t)];
@@ -127,13 +211,30 @@ __global__ void k_tri_bin(const GenScene *__restrict__ tab, int ns, int64_t nt_t
       continue;
     }
     TriSphere s = tri_sphere(v);
-    const float lim = kCellClamp - 4.0f;
-    bool big = s.r > g.r_big || !(fabsf(s.cx * g.inv_cell) < lim) ||
-               !(fabsf(s.cy * g.inv_cell) < lim) || !(fabsf(s.cz * g.inv_cell) < lim);
     uint32_t b = sc.nbuckets;  // the scene's big list
-    if (!big)
-      b = cell_hash(cell_coord(s.cx, g.inv_cell), cell_coord(s.cy, g.inv_cell),
-                    cell_coord(s.cz, g.inv_cell), sc.nbuckets - 1);
+    if (bbox) {
+      const int *bb = bbox + 8 * (int64_t)scene_of_tri(tab, ns, t);
+      const float lo[3] = {order_float(bb[0]), order_float(bb[1]), order_float(bb[2])};
+      const float ext = fmaxf(fmaxf(order_float(bb[3]) - lo[0], order_float(bb[4]) - lo[1]),
+                              order_float(bb[5]) - lo[2]);
+      const int L = (31 - __clz(sc.nbuckets)) / 3;
+      const float top = (float)((1 << L) - 1);
+      const float scale = (ext > 0.0f && ext < 1e30f) ? (float)(1 << L) / ext : 0.0f;
+      const float c[3] = {s.cx, s.cy, s.cz};
+      uint32_t q[3];
+      for (int k = 0; k < 3; ++k) {
+        const float f = scale > 0.0f ? floorf((c[k] - lo[k]) * scale) : 0.0f;
+        q[k] = (uint32_t)fminf(fmaxf(f, 0.0f), top);
+      }
+      b = spread3(q[0]) | (spread3(q[1]) << 1) | (spread3(q[2]) << 2);
+    } else {
+      const float lim = kCellClamp - 4.0f;
+      bool big = s.r > g.r_big || !(fabsf(s.cx * g.inv_cell) < lim) ||
+                 !(fabsf(s.cy * g.inv_cell) < lim) || !(fabsf(s.cz * g.inv_cell) < lim);
+      if (!big)
+        b = cell_hash(cell_coord(s.cx, g.inv_cell), cell_coord(s.cy, g.inv_cell),
+                      cell_coord(s.cz, g.inv_cell), sc.nbuckets - 1);
+    }
     const uint32_t gb = (uint32_t)(sc.bucket_off + b);
     tb[t] = gb;
     ts[t] = atomicAdd(&counts[gb], 1);
@@ -165,14 +266,80 @@ __global__ void k_tri_scatter(const GenScene *__restrict__ tab, int ns, int64_t 
   }
 }
 
-// Writes up to kFillChunk scene-table entries passed by value (no host memory is read later).
+// Warp collective: a sphere containing every lane's sphere c (c.w < 0: none).  Returns w < 0 when
+// no lane has one and an infinite radius when the result is not finite.  The centre is that of
+// the box of the spheres; the radius is the largest |c - C| + c.w, raised to cover its rounding.
+__device__ __forceinline__ float4 sphere_of_spheres(float4 c) {
+  const bool v = c.w >= 0.0f;
+  float lo[3] = {v ? c.x - c.w : INFINITY, v ? c.y - c.w : INFINITY, v ? c.z - c.w : INFINITY};
+  float hi[3] = {v ? c.x + c.w : -INFINITY, v ? c.y + c.w : -INFINITY, v ? c.z + c.w : -INFINITY};
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1)
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      lo[k] = fminf(lo[k], __shfl_xor_sync(0xffffffffu, lo[k], d));
+      hi[k] = fmaxf(hi[k], __shfl_xor_sync(0xffffffffu, hi[k], d));
+    }
+  if (!__any_sync(0xffffffffu, v)) return make_float4(0.0f, 0.0f, 0.0f, -1.0f);
+  const float Cx = 0.5f * (lo[0] + hi[0]), Cy = 0.5f * (lo[1] + hi[1]), Cz = 0.5f * (lo[2] + hi[2]);
+  float e = 0.0f;
+  if (v) {
+    const float dx = c.x - Cx, dy = c.y - Cy, dz = c.z - Cz;
+    e = sqrtf(dx * dx + dy * dy + dz * dz) + c.w;
+  }
+#pragma unroll
+  for (int d = 16; d > 0; d >>= 1) e = fmaxf(e, __shfl_xor_sync(0xffffffffu, e, d));
+  const float rho = e * (1.0f + 1e-5f) + 1e-6f * (fabsf(Cx) + fabsf(Cy) + fabsf(Cz)) + 1e-30f;
+  if (!(isfinite(Cx) && isfinite(Cy) && isfinite(Cz) && rho < 1e30f))
+    return make_float4(0.0f, 0.0f, 0.0f, INFINITY);
+  return make_float4(Cx, Cy, Cz, rho);
+}
+
+constexpr int kChunkShift = 5;   // 32 records per chunk
+constexpr int kGroupShift = 10;  // 32 chunks (1024 records) per group
+
+// Bounding spheres of every 32-record chunk and every 1024-record group of the sorted records
+// (*nrec of them), each containing the bounding spheres of its records; a chunk or group at a
+// scene boundary covers the records of both scenes.  One block of 32 warps per group.
+__global__ void __launch_bounds__(1024) k_chunk_spheres(const float4 *__restrict__ rec,
+                                                        const int *__restrict__ nrec,
+                                                        float4 *__restrict__ chk,
+                                                        float4 *__restrict__ grp) {
+  __shared__ float4 cs[32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int64_t n = *nrec;
+  const int64_t g = blockIdx.x;
+  const int64_t ci = (g << (kGroupShift - kChunkShift)) + w;
+  const int64_t t = (ci << kChunkShift) + lane;
+  float4 c = make_float4(0.0f, 0.0f, 0.0f, -1.0f);
+  if (t < n) c = rec[t];
+  const float4 sc = sphere_of_spheres(c);
+  if (lane == 0) {
+    cs[w] = sc;
+    if (sc.w >= 0.0f) chk[ci] = sc;
+  }
+  __syncthreads();
+  if (w == 0) {
+    const float4 gs = sphere_of_spheres(cs[lane]);
+    if (lane == 0 && gs.w >= 0.0f) grp[g] = gs;
+  }
+}
+
+// Writes up to kFillChunk scene-table entries passed by value (no host memory is read later) and
+// sets their boxes of triangle centres empty.
 constexpr int kFillChunk = 200;
 struct GenFill {
   GenScene e[kFillChunk];
   int n;
 };
-__global__ void k_fill_gen_table(GenScene *dst, GenFill f) {
-  for (int i = threadIdx.x; i < f.n; i += blockDim.x) dst[i] = f.e[i];
+__global__ void k_fill_gen_table(GenScene *dst, GenFill f, int *bbox) {
+  for (int i = threadIdx.x; i < f.n; i += blockDim.x) {
+    dst[i] = f.e[i];
+    for (int k = 0; k < 3; ++k) {
+      bbox[8 * i + k] = 0x7fffffff;
+      bbox[8 * i + 3 + k] = (int)0x80000000;
+    }
+  }
 }
 
 // ------------------------------------------------------------------ exclusive scan (int32)
@@ -274,6 +441,8 @@ struct KArgs {
   int mode;
   int nhalf;        // neighbourhood half-width in cells (cell edge > reach / nhalf)
   float r_big;      // largest bounding radius of a binned triangle
+  const float4 *chk;  // generation: bounding spheres of 32-record chunks of rec
+  const float4 *grp;  // generation: bounding spheres of 1024-record groups of rec
   unsigned long long *counters;
   int *status;
 };
@@ -688,9 +857,7 @@ __global__ void __launch_bounds__(NW * 32, NW == 4 ? 7 : 3) k_generate(KArgs a) 
     s.fr[2] = Sz;
     frame_fp64(nxf, nyf, nzf, s.fr + 3);
   }
-  const int nneigh = (2 * a.nhalf + 1) * (2 * a.nhalf + 1) * (2 * a.nhalf + 1);
-  neighbour_ranges(a, bucket_off, nbuckets, Sx, Sy, Sz, nxf, nyf, nzf, s.buckets, s.bdup, tid,
-                   NW * 32);
+  __syncthreads();
 
   const float fax = __double2float_rn(s.fr[3]), fay = __double2float_rn(s.fr[4]);
   const float fbx = __double2float_rn(s.fr[5]), fbz = __double2float_rn(s.fr[6]);
@@ -858,39 +1025,80 @@ __global__ void __launch_bounds__(NW * 32, NW == 4 ? 7 : 3) k_generate(KArgs a) 
     __syncwarp();
   };
 
-  // ---- stream candidates of the listed neighbouring cells and the scene's big list
-  for (int nb = 0; nb <= nneigh; ++nb) {
-    const int64_t beg = s.buckets[nb], end = s.bdup[nb];
-    // the warp's next 32 bounding spheres of the cell are loaded before the current ones are
-    // tested and queued, so the load's latency overlaps that work (and any batch it triggers)
-    float4 cn = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-    if (beg + warp * 32 + lane < end) cn = a.rec[beg + warp * 32 + lane];
-    for (int64_t base = beg + warp * 32; base < end; base += NW * 32) {
-      const int64_t t = base + lane;
-      const float4 c = cn;
-      if (t + NW * 32 < end) cn = a.rec[t + NW * 32];
-      bool pass = false;
-      if (t < end) {
-        float dx = c.x - Sx, dy = c.y - Sy, dz = c.z - Sz;
-        float z = fmaf(wx, dx, fmaf(wy, dy, wz * dz));
-        float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-        float m = 1e-3f * R + 1e-5f * (fabsf(dx) + fabsf(dy) + fabsf(dz));
-        float al = a.alpha_cull + c.w + m;
-        pass = fabsf(z) <= a.beta_cull + c.w + m && d2 - z * z <= al * al;
-        ++n_cand;
-      }
-      unsigned bal = __ballot_sync(0xffffffffu, pass);
-      if (pass) s.wq[qn + __popc(bal & ((1u << lane) - 1u))] = (int)t;
-      qn += __popc(bal);
-      __syncwarp();
-      if (qn >= 32) {
-        process_batch(32);
-        int rest = qn - 32;
-        int moved = lane < rest ? s.wq[32 + lane] : 0;
-        __syncwarp();
-        if (lane < rest) s.wq[lane] = moved;
-        qn = rest;
-        __syncwarp();
+  // ---- candidate triangles: the records of this point's scene, culled by the bounding spheres of
+  // their 1024-record groups, then of the 32-record chunks of passing groups, then one by one.  A
+  // sphere containing the bounding spheres of its records fails its test only if every record
+  // fails the record test: the record test widened by the sphere's radius, with a margin that
+  // covers the record test's own and both tests' rounding.
+  const float mpos = 4e-7f * (fabsf(Sx) + fabsf(Sy) + fabsf(Sz));
+  auto sphere_pass = [&](const float4 c) -> bool {
+    if (!(c.w < 1e30f)) return true;
+    const float dx = c.x - Sx, dy = c.y - Sy, dz = c.z - Sz;
+    const float z = fmaf(wx, dx, fmaf(wy, dy, wz * dz));
+    const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+    const float m = 2e-3f * R + 2e-5f * (fabsf(dx) + fabsf(dy) + fabsf(dz) + 2.0f * c.w) + mpos;
+    const float al = a.alpha_cull + c.w + m;
+    return fabsf(z) <= a.beta_cull + c.w + m && d2 - z * z <= al * al;
+  };
+  const int64_t rb = a.starts[bucket_off], re = a.starts[bucket_off + nbuckets + 1];
+  if (re > rb) {
+    const int64_t c_lo = rb >> kChunkShift, c_hi = (re - 1) >> kChunkShift;
+    const int64_t g_lo = rb >> kGroupShift, ng = ((re - 1) >> kGroupShift) - g_lo + 1;
+    // group g_lo + k0 + lane * NW + warp: consecutive groups (neighbours in space) go to
+    // different warps
+    for (int64_t k0 = 0; k0 < ng; k0 += 32 * NW) {
+      const int64_t gi = k0 + (int64_t)lane * NW + warp;
+      const bool gp = gi < ng && sphere_pass(a.grp[g_lo + gi]);
+      unsigned gm = __ballot_sync(0xffffffffu, gp);
+      while (gm) {
+        const int64_t g = g_lo + k0 + (int64_t)(__ffs(gm) - 1) * NW + warp;
+        gm &= gm - 1;
+        const int64_t ci = (g << (kGroupShift - kChunkShift)) + lane;
+        const bool cp = ci >= c_lo && ci <= c_hi && sphere_pass(a.chk[ci]);
+        unsigned cm = __ballot_sync(0xffffffffu, cp);
+        // records of the passing chunks; the next chunk's spheres are loaded before the current
+        // ones are tested and queued, so the load's latency overlaps that work
+        int64_t t = 0;
+        float4 cn = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+        bool more = cm != 0;
+        if (more) {
+          t = (((g << (kGroupShift - kChunkShift)) + __ffs(cm) - 1) << kChunkShift) + lane;
+          cm &= cm - 1;
+          if (t >= rb && t < re) cn = a.rec[t];
+        }
+        while (more) {
+          const int64_t tc = t;
+          const float4 c = cn;
+          more = cm != 0;
+          if (more) {
+            t = (((g << (kGroupShift - kChunkShift)) + __ffs(cm) - 1) << kChunkShift) + lane;
+            cm &= cm - 1;
+            if (t >= rb && t < re) cn = a.rec[t];
+          }
+          bool pass = false;
+          if (tc >= rb && tc < re) {
+            float dx = c.x - Sx, dy = c.y - Sy, dz = c.z - Sz;
+            float z = fmaf(wx, dx, fmaf(wy, dy, wz * dz));
+            float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            float m = 1e-3f * R + 1e-5f * (fabsf(dx) + fabsf(dy) + fabsf(dz));
+            float al = a.alpha_cull + c.w + m;
+            pass = fabsf(z) <= a.beta_cull + c.w + m && d2 - z * z <= al * al;
+            ++n_cand;
+          }
+          const unsigned bal = __ballot_sync(0xffffffffu, pass);
+          if (pass) s.wq[qn + __popc(bal & ((1u << lane) - 1u))] = (int)tc;
+          qn += __popc(bal);
+          __syncwarp();
+          if (qn >= 32) {
+            process_batch(32);
+            int rest = qn - 32;
+            int moved = lane < rest ? s.wq[32 + lane] : 0;
+            __syncwarp();
+            if (lane < rest) s.wq[lane] = moved;
+            qn = rest;
+            __syncwarp();
+          }
+        }
       }
     }
   }
@@ -1481,7 +1689,8 @@ cudaError_t launch_project_fp32(const float *pts, int64_t n, const float *sv, co
 // bucket starts, cell size, reach, pretest limits, neighbourhood width).
 static cudaError_t bin_triangles(const GenScene *scenes, int num_scenes, int64_t nt, int64_t TB,
                                  double R, double amax, double bmax, void *ws, int *status,
-                                 cudaStream_t st, KArgs &k, int max_cells_per_reach) {
+                                 cudaStream_t st, KArgs &k, int max_cells_per_reach,
+                                 bool morton) {
   Carver c(ws);
   GenScene *tab = c.take<GenScene>(num_scenes);
   int *counts = c.take<int>(TB);
@@ -1490,13 +1699,16 @@ static cudaError_t bin_triangles(const GenScene *scenes, int num_scenes, int64_t
   uint32_t *tb = c.take<uint32_t>(nt);
   int *ts = c.take<int>(nt);
   float4 *rec = c.take<float4>(4 * nt);
+  int *bbox = c.take<int>(8 * (int64_t)num_scenes);
+  float4 *chk = c.take<float4>((nt + 31) / 32);
+  float4 *grp = c.take<float4>((nt + 1023) / 1024);
 
   cudaError_t e;
   for (int s0 = 0; s0 < num_scenes; s0 += kFillChunk) {
     GenFill f;
     f.n = num_scenes - s0 < kFillChunk ? num_scenes - s0 : kFillChunk;
     for (int i = 0; i < f.n; ++i) f.e[i] = scenes[s0 + i];
-    k_fill_gen_table<<<1, 256, 0, st>>>(tab + s0, f);
+    k_fill_gen_table<<<1, 256, 0, st>>>(tab + s0, f, bbox + 8 * (int64_t)s0);
     count_launches(1);
   }
 
@@ -1519,7 +1731,12 @@ static cudaError_t bin_triangles(const GenScene *scenes, int num_scenes, int64_t
   const int64_t want = (nt + tpb - 1) / tpb;
   const int grid = (int)(want < 152 * 32 ? (want > 0 ? want : 1) : 152 * 32);
   if (nt > 0) {
-    k_tri_bin<<<grid, tpb, 0, st>>>(tab, num_scenes, nt, gp, counts, tb, ts, status);
+    if (morton) {
+      k_tri_bbox<<<grid, tpb, 0, st>>>(tab, num_scenes, nt, bbox);
+      count_launches(1);
+    }
+    k_tri_bin<<<grid, tpb, 0, st>>>(tab, num_scenes, nt, gp, morton ? bbox : nullptr, counts, tb,
+                                    ts, status);
     count_launches(1);
   }
   const int nb = (int)((TB + kScanItems - 1) / kScanItems);
@@ -1530,7 +1747,13 @@ static cudaError_t bin_triangles(const GenScene *scenes, int num_scenes, int64_t
   if (nt > 0) {
     k_tri_scatter<<<grid, tpb, 0, st>>>(tab, num_scenes, nt, tb, ts, starts, rec);
     count_launches(1);
+    if (morton) {
+      k_chunk_spheres<<<(unsigned)((nt + 1023) / 1024), 1024, 0, st>>>(rec, starts + TB, chk, grp);
+      count_launches(1);
+    }
   }
+  k.chk = chk;
+  k.grp = grp;
 
   k.tab = tab;
   k.num_scenes = num_scenes;
@@ -1559,8 +1782,9 @@ cudaError_t launch_generate_batch(const GenScene *scenes, const GenerateBatch &g
   const double bmax = R * (N - 1.0) / (2.0 * N);
   KArgs k;
   cudaError_t e = bin_triangles(scenes, g.num_scenes, g.total_tris, g.total_buckets, R, amax,
-                                bmax, ws, g.status, st, k, kGenMaxCellsPerReach);
+                                bmax, ws, g.status, st, k, kGenMaxCellsPerReach, true);
   if (e != cudaSuccess) return e;
+  k.nhalf = 0;  // no neighbour-cell list: candidates come from the sphere hierarchy
   k.R = g.R;
   k.N = N;
   k.mode = g.mode;
@@ -1585,7 +1809,7 @@ cudaError_t launch_clutter(const ClutterArgs &a, void *ws, cudaStream_t st) {
   const double R = a.support_radius;
   KArgs k;
   cudaError_t e = bin_triangles(&sc, 1, a.num_triangles, (int64_t)sc.nbuckets + 1, R, R, 0.5 * R,
-                                ws, a.status, st, k, kClutterMaxCellsPerReach);
+                                ws, a.status, st, k, kClutterMaxCellsPerReach, false);
   if (e != cudaSuccess) return e;
   k.N = 0;
   k.mode = 0;
@@ -1616,7 +1840,7 @@ cudaError_t launch_spin(const SpinArgs &a, void *ws, cudaStream_t st) {
   const double R = a.support_radius;
   KArgs k;
   cudaError_t e = bin_triangles(&sc, 1, a.num_triangles, (int64_t)sc.nbuckets + 1, R, R, 0.5 * R,
-                                ws, a.status, st, k, kClutterMaxCellsPerReach);
+                                ws, a.status, st, k, kClutterMaxCellsPerReach, false);
   if (e != cudaSuccess) return e;
   k.N = a.resolution;
   k.mode = 0;
