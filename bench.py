@@ -72,9 +72,10 @@ MACS_PER_TERM = 2
 DP4A_PER_SM_CLK = 64
 # DRAM bytes (read + write) per full-size launch from one-pass ncu captures (commands in
 # profiles/); None where the kernel changed since it was captured
-# (k_generate at R = 0.6: 647.4 GB read + 73.7 GB written on 131,072 origins, scaled to the
-# full launch by 2,509,797 / 131,072 origins)
-TRAFFIC = {"k_generate_R0.6": (647.44e9 + 73.67e9) * 2509797 / 131072,
+# (k_generate at R = 0.6: 235.9 GB read + 32.2 GB written on the first 131,072 origins, in a
+# run whose tuner chose 8 warps per point, scaled to the full launch by 2,509,797 / 131,072
+# origins)
+TRAFFIC = {"k_generate_R0.6": (235.93e9 + 32.17e9) * 2509797 / 131072,
            "k_tc_rank_clutter": 21.483e9 + 3.71e5, "k_dense_clutter": 1.895e9 + 5.57e6}
 
 
