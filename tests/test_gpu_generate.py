@@ -128,6 +128,47 @@ def test_large_and_degenerate_triangles(rici, oracle_mod):
     assert np.array_equal(got, ref)
 
 
+def test_coarse_curve_order_exact(rici, oracle_mod):
+    """One far triangle stretches the scene's box of triangle centres, so every other triangle
+    falls into one Morton bin and the sorted records follow no curve: the bounding spheres of
+    their chunks and groups are then as wide as the mesh, and the images must not change."""
+    m = synth.meshes.displaced_icosphere(np.random.default_rng(8), 4)  # 5,120 triangles
+    far = np.array([[1e4, 1e4, 1e4], [1e4 + 1, 1e4, 1e4], [1e4, 1e4 + 1, 1e4]])
+    v = np.concatenate([m.vertices, far]).astype(np.float32)
+    t = np.concatenate([m.triangles, m.triangles[:700],  # repeated triangles
+                        [[len(m.vertices), len(m.vertices) + 1, len(m.vertices) + 2]]])
+    t = t.astype(np.int32)
+    n = synth.meshes.area_weighted_normals(v.astype(np.float64), t).astype(np.float32)
+    o = np.random.default_rng(9).choice(len(m.vertices), 96, replace=False)
+    for R in (0.3, 1.2):
+        ref = oracle_mod.rici_fp64(v, n, t, o, R, 32)
+        got = gpu_images(rici, v, n, t, o, R, 32)
+        assert np.array_equal(got, ref), R
+
+
+def test_batch_scene_boundaries_inside_chunks_and_groups(rici, oracle_mod):
+    """Scenes of 1,000, 37 and 2,100 triangles share 32-record chunks and 1,024-record groups at
+    their boundaries; each origin must see only its own scene's triangles."""
+    import torch
+
+    rng = np.random.default_rng(12)
+    scenes, want = [], []
+    for nt in (1000, 37, 2100):
+        nv = max(3, nt // 2)
+        v = rng.uniform(-0.5, 0.5, size=(nv, 3)).astype(np.float32)
+        t = rng.integers(0, nv, size=(nt, 3)).astype(np.int32)
+        nrm = rng.normal(size=(nv, 3)).astype(np.float32)
+        o = rng.choice(nv, min(nv, 40), replace=False).astype(np.int32)
+        scenes.append({"vertices": dev(v), "normals": dev(nrm), "triangles": dev(t),
+                       "origins": dev(o)})
+        want.append(oracle_mod.rici_fp64(v, nrm, t, o, 0.3, 32))
+    outs = rici.rici_generate_batch(scenes, 0.3, 32)
+    torch.cuda.synchronize()
+    assert rici.sync_status() == 0
+    for out, ref in zip(outs, want):
+        assert np.array_equal(out.view(torch.int16).cpu().numpy().view(np.uint16), ref)
+
+
 def test_empty_inputs(rici):
     import torch
 
