@@ -119,7 +119,8 @@ RICI_API int rici_generate(const float *vertices, const float *normals, int64_t 
  *   [0] (origin, triangle) pairs fully processed after culling,
  *   [1] (origin, triangle, layer) items processed,
  *   [2] items re-evaluated in FP64 because a predicate fell inside the FP32 error band,
- *   [3] candidate (origin, triangle) pairs tested by the spatial cull. */
+ *   [3] candidate (origin, triangle) pairs tested one by one by the spatial cull (those in
+ *       32-triangle chunks whose bounding spheres passed). */
 RICI_API int rici_generate_ex(const float *vertices, const float *normals, int64_t num_vertices,
                      const int32_t *triangles, int64_t num_triangles, const int32_t *origins,
                      int64_t num_origins, float support_radius, int32_t resolution,
@@ -313,7 +314,7 @@ RICI_API int rici_clutter(const float *vertices, const float *normals, int64_t n
  *              exactly as an integer number of units of 2^-24 (rounding error <= 2^-25 per
  *              weight; the sums do not depend on the order of the samples), so each bin differs
  *              from the FP64 definition by at most the rounding of those FP32 steps.
- * Workspace: rici_clutter_workspace_size bytes (the same grid), or NULL.
+ * Workspace: rici_clutter_workspace_size bytes (the clutter measure's grid), or NULL.
  * Errors: as rici_generate (a zero image for an oriented point with a bad index or a
  * non-finite coordinate).
  */

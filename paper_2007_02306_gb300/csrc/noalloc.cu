@@ -9,9 +9,9 @@
 //
 // The array lives in device memory of every GPU that loads the library until the process
 // exits.  All calls share it: calls that overlap on the GPU (for example on two streams
-// without ordering between them) race on it and give wrong images.  Each call clears the
-// parts that must start at zero (the grid bucket counts and the big-list length) before
-// its kernels use them; the rest is overwritten before it is read.
+// without ordering between them) race on it and give wrong images.  Each call resets the
+// parts that must start from a fixed value (the bin counts, and the box of triangle centres,
+// which starts empty) before its kernels use them; the rest is overwritten before it is read.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
