@@ -1,8 +1,9 @@
 """Launch tunings change speed, never results; the autotuners measure and pick valid tunings.
 
-Every candidate generation tuning (grid cells per reach x big-triangle radius x warps per
-oriented point) must give images bit-identical to the default tuning on a small batch of uneven
-clutter scenes (and to the oracle on sampled origins under the most different tuning); every
+Every generation tuning (warps per oriented point, and the grid cells per reach and
+big-triangle radius that only the clutter measure and spin images read) must give images
+bit-identical to the default tuning on a small batch of uneven clutter scenes (and to the oracle
+on sampled origins under the most different tuning); every
 tensor-core tile grouping must give the default's ranks, distances and top-1.  The autotuners
 must return one of their candidates and leave the tuning in force unchanged, and the cached
 tuner must store and apply its choice.
