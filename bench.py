@@ -257,6 +257,24 @@ def release(p, torch):
     torch.cuda.empty_cache()
 
 
+def run_comparisons(todo, t_start: float, budget_s: float, after=None, clock=time.time) -> dict:
+    """Runs the enabled workloads of todo = [(name, enabled, run)] in order; one whose start would
+    come more than budget_s seconds after t_start is reported as skipped instead.  after() runs
+    after each workload that ran."""
+    out = {}
+    for name, enabled, run in todo:
+        if not enabled:
+            continue
+        if clock() - t_start > budget_s:
+            out[name] = {"skipped": f"the run's wall-time budget ({budget_s:.0f} s) was spent "
+                                    "before it started"}
+            continue
+        out[name] = run()
+        if after:
+            after()
+    return out
+
+
 def build_workload():
     import synth
 
@@ -845,15 +863,7 @@ def main():
                  lambda: clutterbox_experiment(p, torch, dev, stream)),
                 ("spin_images", args.spin_compare,
                  lambda: spin_comparison(p, torch, dev, stream, flush))]
-        for name, on_, run in todo:
-            if not on_:
-                continue
-            if time.time() - t_start > args.budget_s:
-                cmp[name] = {"skipped": f"the run's wall-time budget ({args.budget_s:.0f} s) "
-                                        f"was spent before it started"}
-                continue
-            cmp[name] = run()
-            release(p, torch)
+        cmp = run_comparisons(todo, t_start, args.budget_s, after=lambda: release(p, torch))
 
     # oracle on the host cores: the CPU baseline, and the definition's work counts per radius
     cpu, work = None, None

@@ -70,3 +70,28 @@ def test_input_digest_is_deterministic():
     assert a == bench.input_digest(synth.tiny_scene(seed=1))
     assert a != bench.input_digest(synth.tiny_scene(seed=2))
     assert len(a) == 16
+
+
+def test_comparisons_stop_starting_once_the_budget_is_spent():
+    sys.path.insert(0, ROOT)
+    import bench
+
+    now = [0.0]
+    ran = []
+
+    def work(name, seconds):
+        def run():
+            ran.append(name)
+            now[0] += seconds
+            return {"ms": seconds * 1e3}
+        return run
+
+    todo = [("a", 1, work("a", 50)), ("off", 0, work("off", 1)), ("b", 1, work("b", 80)),
+            ("c", 1, work("c", 5)), ("d", 1, work("d", 5))]
+    after = []
+    out = bench.run_comparisons(todo, 0.0, 100.0, after=lambda: after.append(1),
+                                clock=lambda: now[0])
+    # a starts at 0 and b at 50 (inside the budget); c would start at 130 and d as well
+    assert ran == ["a", "b"] and len(after) == 2
+    assert out["a"] == {"ms": 50e3} and out["b"] == {"ms": 80e3}
+    assert "skipped" in out["c"] and "skipped" in out["d"] and "off" not in out
